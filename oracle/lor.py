@@ -1,0 +1,355 @@
+"""Low-order-refined additive-Schwarz preconditioner (oracle; FP64).
+
+Follows Section 3 step by step, with dense/sparse library primitives only:
+
+* Section 3.1: T_h subdivides every element at its GLL points; K_h is the
+  assembled multilinear (p=1) stiffness on T_h.  Reading: 2-point Gauss per
+  direction on each sub-element, coefficient of the parent element.
+* Section 3.3: element-structured hierarchy.  Each level keeps every other
+  point of the previous level's 1D subgrid (positions 0, 2, 4, ... plus the
+  last endpoint) until only the element vertices remain.  Prolongation is
+  1D linear interpolation in the element's reference coordinate (tensor
+  product in d dimensions); coarse operators are Galerkin P^T A P (reading).
+  V(1,1): one pre- and one post-smoothing per level, exact solve on the
+  coarsest (vertex) level.
+* Section 3.4: smoothing by ILU(0) of the patch matrix on its structural
+  (3^d-point) pattern, rows in patch-lexicographic order (x fastest).
+* Section 3.2, Eq. (as) and Eq. (patch): B = sum_j R_j Q_j with one patch per
+  coarse vertex, Omega_j = union of the elements touching the vertex, homogeneous
+  Dirichlet on its boundary, plus the coarse space V_0 = Q1 on T_p.
+  Reading (R_0): the paper uses one BoomerAMG V-cycle, a third-party system;
+  here R_0 is one V-cycle on the coarse vertex grid: keep-even-plus-last 2x
+  coarsening, index-space linear interpolation, Galerkin operators, two sweeps of
+  l1-scaled Jacobi before and after (the relaxation BoomerAMG offers, Section 5.4),
+  and an exact dense solve once at most 343 unknowns remain.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .basis import gll
+from .cg import boundary_mask, node_coordinates, node_shape
+from .mesh import Mesh, multilinear
+
+COARSE_DIRECT_MAX = 343
+COARSE_SWEEPS = 2
+
+
+# --------------------------------------------------------------------------- K_h
+def q1_stiffness_batch(corners, kappa):
+    """Q1 element stiffness for a batch of cells: corners (C, 2^d, d) -> (C, 2^d, 2^d)."""
+    C, nc, d = corners.shape
+    g = 0.5 - 0.5 / np.sqrt(3.0)
+    g1 = np.array([g, 1.0 - g])
+    K = np.zeros((C, nc, nc))
+    for gp in itertools.product(range(2), repeat=d):
+        xi = np.array([g1[gp[a]] for a in range(d)])
+        w = 0.5 ** d
+        # reference gradients of the 2^d corner functions at xi
+        dN = np.zeros((nc, d))
+        for c in range(nc):
+            bits = [(c >> a) & 1 for a in range(d)]
+            for b in range(d):
+                v = 1.0
+                for a in range(d):
+                    f = xi[a] if bits[a] else 1.0 - xi[a]
+                    df = 1.0 if bits[a] else -1.0
+                    v *= df if a == b else f
+                dN[c, b] = v
+        J = np.einsum("Cca,cb->Cab", corners, dN)          # dX_a/dxi_b
+        detJ = np.linalg.det(J)
+        Jinv = np.linalg.inv(J)
+        gphys = np.einsum("Cba,cb->Cca", Jinv, dN)         # J^{-T} dN
+        K += (w * np.abs(detJ) * kappa)[:, None, None] * np.einsum("Cia,Cja->Cij", gphys, gphys)
+    return K
+
+
+def assemble_lor(mesh: Mesh, p: int):
+    """K_h over all nodes of the GLL-refined grid (no Dirichlet elimination), CSR."""
+    d = mesh.dim
+    N = node_shape(mesh.n, p)
+    X = node_coordinates(mesh, p)
+    cells = np.array(list(itertools.product(*[range(v - 1) for v in reversed(N)])))
+    cells = cells[:, ::-1]                          # (C, d) as (I, J, K)
+    strides = np.cumprod([1] + list(N[:-1]))
+    corner_ids = np.zeros((len(cells), 2 ** d), dtype=np.int64)
+    for c in range(2 ** d):
+        off = np.array([(c >> a) & 1 for a in range(d)])
+        corner_ids[:, c] = ((cells + off) * strides).sum(axis=1)
+    elem = cells // p
+    kap = mesh.kappa[tuple(elem[:, a] for a in reversed(range(d)))]
+    Kc = q1_stiffness_batch(X[corner_ids], kap)
+    rows = np.repeat(corner_ids, 2 ** d, axis=1).ravel()
+    cols = np.tile(corner_ids, (1, 2 ** d)).ravel()
+    ntot = int(np.prod(N))
+    K = sp.coo_matrix((Kc.ravel(), (rows, cols)), shape=(ntot, ntot)).tocsr()
+    K.sum_duplicates()
+    return K
+
+
+# --------------------------------------------------------------- hierarchy (3.3)
+def level_selections(p: int, mg_levels: int = 0):
+    """GLL-index subsets per level, finest first, ending with [0, p].
+
+    mg_levels = 0 takes the full hierarchy; mg_levels = L >= 2 keeps its first
+    L-1 levels and then jumps to the vertex level.
+    """
+    sels = [list(range(p + 1))]
+    while len(sels[-1]) > 2:
+        s = sels[-1]
+        t = s[0::2]
+        if t[-1] != s[-1]:
+            t = t + [s[-1]]
+        sels.append(t)
+    if mg_levels and mg_levels < len(sels):
+        sels = sels[: mg_levels - 1] + [sels[-1]]
+    return sels
+
+
+def prolong_1d(nel: int, p: int, sel_f, sel_c):
+    """Global 1D prolongation (N_f x N_c): linear interpolation in reference coordinates."""
+    xg = gll(p)[0]
+    mf, mc = len(sel_f) - 1, len(sel_c) - 1
+    P = np.zeros((nel * mf + 1, nel * mc + 1))
+    for e in range(nel):
+        for t, g in enumerate(sel_f):
+            a = max(i for i in range(mc + 1) if sel_c[i] <= g)
+            if sel_c[a] == g:
+                P[e * mf + t, e * mc + a] = 1.0
+                continue
+            b = a + 1
+            w = (xg[g] - xg[sel_c[a]]) / (xg[sel_c[b]] - xg[sel_c[a]])
+            P[e * mf + t, e * mc + a] = 1.0 - w
+            P[e * mf + t, e * mc + b] = w
+    return P
+
+
+def kron_nd(mats_xyz):
+    """kron over axes given in x, y, z order with x fastest in the result."""
+    out = sp.csr_matrix(mats_xyz[-1])
+    for m in reversed(mats_xyz[:-1]):
+        out = sp.kron(out, sp.csr_matrix(m), format="csr")
+    return out
+
+
+# ----------------------------------------------------------------- ILU(0) (3.4)
+def ilu0(A, pattern):
+    """IKJ ILU(0) on the structural ``pattern``; returns dense unit-L and U.
+
+    A pivot that is not positive is a breakdown (raises FloatingPointError).
+    """
+    a = np.array(A, dtype=np.float64, copy=True)
+    m = a.shape[0]
+    if m and a[0, 0] <= 0:
+        raise FloatingPointError("ILU(0) breakdown: non-positive pivot at row 0")
+    for i in range(1, m):
+        ks = np.nonzero(pattern[i, :i])[0]
+        for k in ks:
+            a[i, k] /= a[k, k]
+            cols = np.nonzero(pattern[i, k + 1:])[0] + k + 1
+            a[i, cols] -= a[i, k] * a[k, cols]
+        if a[i, i] <= 0:
+            raise FloatingPointError(f"ILU(0) breakdown: non-positive pivot at row {i}")
+    L = np.tril(a, -1) + np.eye(m)
+    U = np.triu(a)
+    return L, U
+
+
+def ilu_solve(L, U, r):
+    w = sla.solve_triangular(L, r, lower=True, unit_diagonal=True)
+    return sla.solve_triangular(U, w, lower=False)
+
+
+# ------------------------------------------------------------- patches (3.2)
+def patch_range_1d(v: int, nel: int, m: int):
+    """Global level indices of the open interior of the patch of vertex v (one axis)."""
+    lo = max(v - 1, 0) * m
+    hi = min(v + 1, nel) * m
+    return np.arange(lo + 1, hi)
+
+
+def box_indices(ranges, N):
+    """Flattened global indices of the tensor box of 1D index ranges (x fastest)."""
+    grids = np.meshgrid(*reversed(ranges), indexing="ij")
+    idx = np.zeros(grids[0].shape, dtype=np.int64)
+    stride = 1
+    for a in range(len(ranges)):
+        idx = idx + grids[len(ranges) - 1 - a] * stride
+        stride *= N[a]
+    return idx.ravel()
+
+
+def box_pattern(ranges):
+    """Structural 3^d-point pattern of a tensor box: |di|,|dj|,|dk| <= 1."""
+    grids = np.meshgrid(*reversed(ranges), indexing="ij")
+    coords = np.stack([g.ravel() for g in reversed(grids)], axis=1)
+    diff = np.abs(coords[:, None, :] - coords[None, :, :])
+    return np.all(diff <= 1, axis=2)
+
+
+class LORPreconditioner:
+    """B = P_0 R_0 P_0^T + sum_j R_j^T V_j R_j (Eq. (as)), with options for exact solves."""
+
+    def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0,
+                 exact_local: bool = False, exact_coarse: bool = False, K_h=None):
+        self.mesh, self.p, self.dim = mesh, p, mesh.dim
+        self.exact_local, self.exact_coarse = exact_local, exact_coarse
+        n = mesh.n
+        self.sels = level_selections(p, mg_levels)
+        self.ms = [len(s) - 1 for s in self.sels]
+        self.Ns = [tuple(v * m + 1 for v in n) for m in self.ms]
+        self.K_h = assemble_lor(mesh, p) if K_h is None else K_h
+        # global level operators A_l (Galerkin) and 1D/ND prolongations l+1 -> l
+        self.P1 = []      # per level: list over axes of 1D matrices
+        self.A = [self.K_h]
+        for l in range(len(self.sels) - 1):
+            mats = [prolong_1d(n[a], p, self.sels[l], self.sels[l + 1]) for a in range(self.dim)]
+            self.P1.append(mats)
+            P = kron_nd(mats)
+            self.A.append((P.T @ self.A[l] @ P).tocsr())
+        self._build_patches()
+        self._build_coarse()
+
+    # ---------------------------------------------------------------- patches
+    def vertices(self):
+        return [tuple(reversed(t)) for t in
+                itertools.product(*[range(v + 1) for v in reversed(self.mesh.n)])]
+
+    def _build_patches(self):
+        self.patches = []
+        L = len(self.sels)
+        for v in self.vertices():
+            levels = []
+            for l in range(L):
+                ranges = [patch_range_1d(v[a], self.mesh.n[a], self.ms[l]) for a in range(self.dim)]
+                idx = box_indices(ranges, self.Ns[l])
+                Aj = self.A[l][idx][:, idx].toarray() if len(idx) else np.zeros((0, 0))
+                lev = {"ranges": ranges, "idx": idx, "A": Aj}
+                if len(idx) and l < L - 1 and not self.exact_local:
+                    lev["LU"] = ilu0(Aj, box_pattern(ranges))
+                if l < L - 1:
+                    rc = [patch_range_1d(v[a], self.mesh.n[a], self.ms[l + 1]) for a in range(self.dim)]
+                    mats = [self.P1[l][a][np.ix_(ranges[a], rc[a])] for a in range(self.dim)]
+                    lev["P"] = kron_nd(mats).toarray() if all(len(r) for r in ranges + rc) \
+                        else np.zeros((len(idx), int(np.prod([len(r) for r in rc]))))
+                levels.append(lev)
+            self.patches.append({"v": v, "levels": levels})
+
+    def vcycle(self, levels, l, r):
+        """One V(1,1) cycle on patch level l for right-hand side r (x0 = 0)."""
+        lev = levels[l]
+        if len(r) == 0:
+            return np.zeros(0)
+        if l == len(levels) - 1:
+            return np.linalg.solve(lev["A"], r)
+        A = lev["A"]
+        L_, U_ = lev["LU"]
+        x = ilu_solve(L_, U_, r)
+        t = r - A @ x
+        P = lev["P"]
+        if P.shape[1] > 0:
+            x = x + P @ self.vcycle(levels, l + 1, P.T @ t)
+        t = r - A @ x
+        return x + ilu_solve(L_, U_, t)
+
+    def local_solve(self, j, r):
+        levels = self.patches[j]["levels"]
+        if self.exact_local:
+            A0 = levels[0]["A"]
+            return np.linalg.solve(A0, r) if len(r) else r
+        return self.vcycle(levels, 0, r)
+
+    # ----------------------------------------------------------------- coarse
+    def _build_coarse(self):
+        n, d = self.mesh.n, self.dim
+        mats = [prolong_1d(n[a], self.p, list(range(self.p + 1)), [0, self.p]) for a in range(d)]
+        self.P0 = kron_nd(mats)                                  # fine nodes x vertices
+        A0 = (self.P0.T @ self.K_h @ self.P0).tocsr()
+        Nv = tuple(v + 1 for v in n)
+        self.vmask = ~boundary_mask(Nv)
+        # coarse hierarchy on the vertex grid (1D point lists in vertex indices)
+        pts = [list(range(v + 1)) for v in n]
+        self.cA, self.cP, self.cmask = [], [], []
+        Acur, mask, pcur = A0, self.vmask, pts
+        while True:
+            Ai = Acur[mask][:, mask].tocsr()
+            self.cA.append(Ai)
+            self.cmask.append(mask)
+            if self.exact_coarse or Ai.shape[0] <= COARSE_DIRECT_MAX:
+                break
+            pnext = []
+            mats = []
+            for a in range(d):
+                s = pcur[a]
+                t = s[0::2]
+                if t[-1] != s[-1]:
+                    t = t + [s[-1]]
+                Pa = np.zeros((len(s), len(t)))
+                for i, g in enumerate(s):
+                    b = next(k for k in range(len(t)) if t[k] >= g)
+                    if t[b] == g:
+                        Pa[i, b] = 1.0
+                    else:
+                        w = (g - t[b - 1]) / (t[b] - t[b - 1])
+                        Pa[i, b - 1] = 1.0 - w
+                        Pa[i, b] = w
+                mats.append(Pa)
+                pnext.append(t)
+            P = kron_nd(mats)
+            Acur = (P.T @ Acur @ P).tocsr()
+            shape_next = tuple(len(t) for t in pnext)
+            mnext = ~boundary_mask(shape_next)
+            self.cP.append(P[mask][:, mnext].tocsr())
+            mask, pcur = mnext, pnext
+        self.cDl1 = [np.asarray(abs(Ai).sum(axis=1)).ravel() for Ai in self.cA]
+        self.cInv = np.linalg.inv(self.cA[-1].toarray()) if self.cA[-1].shape[0] else None
+
+    def coarse_vcycle(self, l, r):
+        A = self.cA[l]
+        if l == len(self.cA) - 1:
+            return self.cInv @ r
+        D = self.cDl1[l]
+        x = np.zeros_like(r)
+        for _ in range(COARSE_SWEEPS):
+            x = x + (r - A @ x) / D
+        P = self.cP[l]
+        x = x + P @ self.coarse_vcycle(l + 1, P.T @ (r - A @ x))
+        for _ in range(COARSE_SWEEPS):
+            x = x + (r - A @ x) / D
+        return x
+
+    def coarse_solve(self, rc):
+        """R_0 applied to interior-vertex vector rc."""
+        if len(rc) == 0:
+            return rc
+        return self.coarse_vcycle(0, rc)
+
+    # ------------------------------------------------------------------ apply
+    def apply(self, r, parts=("patches", "coarse")):
+        r = np.asarray(r, dtype=np.float64)
+        z = np.zeros_like(r)
+        N0 = self.Ns[0]
+        rr = np.where(boundary_mask(N0), 0.0, r)
+        if "patches" in parts:
+            for j in range(len(self.patches)):
+                idx = self.patches[j]["levels"][0]["idx"]
+                if len(idx):
+                    z[idx] += self.local_solve(j, rr[idx])
+        if "coarse" in parts:
+            rc = (self.P0.T @ rr)[self.vmask]
+            ec = np.zeros(self.P0.shape[1])
+            ec[self.vmask] = self.coarse_solve(rc)
+            z += self.P0 @ ec
+        return z
+
+    def patch_contribution(self, j, r):
+        """R_j^T V_j(R_j r) scattered onto the full level-0 grid (for sampled checks)."""
+        z = np.zeros(len(r))
+        idx = self.patches[j]["levels"][0]["idx"]
+        if len(idx):
+            z[idx] = self.local_solve(j, np.where(boundary_mask(self.Ns[0]), 0.0, r)[idx])
+        return z

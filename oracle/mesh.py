@@ -1,0 +1,69 @@
+"""Tensor-product mesh geometry (oracle; FP64).
+
+Section 2: every element D of T_p is the image of the unit cube [0,1]^d.  Here
+the map is the multilinear (bilinear/trilinear) interpolation of the element's
+2^d vertices (the reading used for all perturbed meshes).  Corner c of an
+element has offsets (c & 1, (c >> 1) & 1, (c >> 2) & 1) along (x, y, z).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+
+class Mesh:
+    """Structured-topology mesh with n = (nx, ny[, nz]) elements."""
+
+    def __init__(self, vertices, kappa):
+        self.vertices = np.asarray(vertices, dtype=np.float64)
+        self.kappa = np.asarray(kappa, dtype=np.float64)
+        self.dim = self.vertices.shape[0]
+        self.n = tuple(reversed(self.kappa.shape))          # (nx, ny[, nz])
+        assert len(self.n) == self.dim
+
+    @property
+    def nel(self):
+        return int(np.prod(self.n))
+
+    def elements(self):
+        """Element multi-indices (ex, ey[, ez]) in lexicographic order (x fastest)."""
+        for t in itertools.product(*[range(v) for v in reversed(self.n)]):
+            yield tuple(reversed(t))
+
+    def corners(self, e):
+        """(2^d, d) vertex coordinates of element e, corner order c = cx + 2cy + 4cz."""
+        d = self.dim
+        out = np.empty((2 ** d, d))
+        for c in range(2 ** d):
+            off = [(c >> a) & 1 for a in range(d)]
+            idx = tuple(reversed([e[a] + off[a] for a in range(d)]))
+            out[c] = self.vertices[(slice(None),) + idx]
+        return out
+
+    def kappa_of(self, e):
+        return float(self.kappa[tuple(reversed(e))])
+
+
+def multilinear(corners, xi):
+    """Map reference points xi (Q, d) through the multilinear map of ``corners``.
+
+    Returns X (Q, d) and the Jacobian J (Q, d, d) with J[q, a, b] = dX_a/dxi_b.
+    """
+    corners = np.asarray(corners)
+    xi = np.atleast_2d(xi)
+    Q, d = xi.shape
+    X = np.zeros((Q, d))
+    J = np.zeros((Q, d, d))
+    for c in range(2 ** d):
+        bits = [(c >> a) & 1 for a in range(d)]
+        f = [xi[:, a] if bits[a] else 1.0 - xi[:, a] for a in range(d)]
+        df = [np.ones(Q) if bits[a] else -np.ones(Q) for a in range(d)]
+        shape = np.prod(f, axis=0)
+        X += shape[:, None] * corners[c][None, :]
+        for b in range(d):
+            g = np.ones(Q)
+            for a in range(d):
+                g = g * (df[a] if a == b else f[a])
+            J[:, :, b] += g[:, None] * corners[c][None, :]
+    return X, J

@@ -1,0 +1,130 @@
+"""Seeded synthetic inputs: perturbed tensor-product meshes and element coefficients.
+
+This module is the only code shared by the CUDA path's tests/bench and the CPU
+oracle.  It holds none of the method's arithmetic: it only draws random numbers
+and lays out the mesh vertices and the per-element coefficient, which are the
+*inputs* of the solver (the model problem of Section 2, Eq. (poisson), on a
+tensor-product mesh of [0,1]^d whose elements are images of the unit cube).
+
+Random numbers come from one counter-based generator, SplitMix64 (Steele, Lea &
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014): the i-th
+draw of stream ``key`` is ``mix64(key + (i+1)*GAMMA)``.  Uniforms in [0,1) take
+the top 53 bits; standard normals use the Box-Muller transform on consecutive
+pairs of uniforms.
+
+Layouts (all float64, C order):
+  * vertices: shape (d, nz+1, ny+1, nx+1) for d=3, (d, ny+1, nx+1) for d=2;
+    component c of vertex (i,j,k) sits at vertices[c, k, j, i] (x fastest).
+  * kappa: shape (nz, ny, nx) (or (ny, nx)); element (ex,ey,ez) at [ez, ey, ex].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def mix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 output finaliser applied elementwise to uint64 values."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def splitmix64(key: int, count: int, start: int = 0) -> np.ndarray:
+    """Draws start..start+count-1 of the SplitMix64 sequence seeded with ``key``."""
+    i = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        state = np.uint64(key & 0xFFFFFFFFFFFFFFFF) + i * GAMMA
+    return mix64(state)
+
+
+def stream_key(seed: int, tag: int) -> int:
+    """Independent stream per (seed, purpose tag)."""
+    z = mix64(np.array([(seed * 0x100000001B3 + tag * 0x9E3779B1) & 0xFFFFFFFFFFFFFFFF],
+                       dtype=np.uint64))
+    return int(z[0])
+
+
+def uniform01(key: int, count: int) -> np.ndarray:
+    """Uniform doubles in [0,1) from the top 53 bits of each draw."""
+    return (splitmix64(key, count) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(key: int, count: int) -> np.ndarray:
+    """Standard normals by Box-Muller on pairs of uniforms (u1 mapped to (0,1])."""
+    m = (count + 1) // 2
+    u = uniform01(key, 2 * m)
+    u1 = 1.0 - u[0::2]
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.empty(2 * m)
+    z[0::2] = r * np.cos(2.0 * np.pi * u2)
+    z[1::2] = r * np.sin(2.0 * np.pi * u2)
+    return z[:count]
+
+
+TAG_VERTS = 1
+TAG_KAPPA = 2
+
+
+def make_mesh(dim: int, n, seed: int = 0, perturb: float = 0.15,
+              kappa_sigma: float = 1.0, kappa_const: float | None = None):
+    """Unit-cube tensor mesh with n=(nx,ny[,nz]) elements.
+
+    Interior vertices move by U(-perturb*h, perturb*h) per coordinate (h = 1/n
+    along that axis); boundary vertices stay on the boundary, sliding only
+    tangentially is not allowed (they stay fixed), so the domain is exactly
+    [0,1]^d.  kappa_e = exp(kappa_sigma * Z_e), Z_e ~ N(0,1), unless
+    ``kappa_const`` is given.
+    Returns (vertices, kappa) in the layouts of the module docstring.
+    """
+    if np.isscalar(n):
+        n = (int(n),) * dim
+    n = tuple(int(v) for v in n)
+    assert len(n) == dim and dim in (2, 3)
+    shape_v = tuple(v + 1 for v in reversed(n))         # (nz+1, ny+1, nx+1)
+    nv = int(np.prod(shape_v))
+    axes = [np.linspace(0.0, 1.0, v + 1) for v in n]     # x, y, z
+    grids = np.meshgrid(*reversed(axes), indexing="ij")  # each (nz+1, ny+1, nx+1)
+    verts = np.empty((dim,) + shape_v)
+    for c in range(dim):
+        verts[c] = grids[dim - 1 - c]
+    if perturb != 0.0:
+        u = uniform01(stream_key(seed, TAG_VERTS), dim * nv).reshape((dim,) + shape_v)
+        interior = np.ones(shape_v, dtype=bool)
+        for ax in range(dim):
+            sl = [slice(None)] * dim
+            sl[ax] = 0
+            interior[tuple(sl)] = False
+            sl[ax] = -1
+            interior[tuple(sl)] = False
+        for c in range(dim):
+            h = 1.0 / n[c]
+            verts[c] += np.where(interior, (2.0 * u[c] - 1.0) * perturb * h, 0.0)
+    shape_e = tuple(reversed(n))
+    ne = int(np.prod(shape_e))
+    if kappa_const is not None:
+        kappa = np.full(shape_e, float(kappa_const))
+    else:
+        kappa = np.exp(kappa_sigma * normal(stream_key(seed, TAG_KAPPA), ne)).reshape(shape_e)
+    return np.ascontiguousarray(verts), np.ascontiguousarray(kappa)
+
+
+def random_vector(shape, seed: int, tag: int = 7) -> np.ndarray:
+    """Seeded N(0,1) test vector (e.g. an input x for operator parity tests)."""
+    cnt = int(np.prod(shape))
+    return normal(stream_key(seed, tag), cnt).reshape(shape)
+
+
+def batch_plan(nsolves: int, seed: int = 0, nmin: int = 4, nmax: int = 16,
+               pmin: int = 2, pmax: int = 7):
+    """Per-solve (n, p) of a batched workload: n ~ U{nmin..nmax}, p ~ U{pmin..pmax}."""
+    u = uniform01(stream_key(seed, 11), 2 * nsolves).reshape(nsolves, 2)
+    ns = nmin + np.minimum((u[:, 0] * (nmax - nmin + 1)).astype(int), nmax - nmin)
+    ps = pmin + np.minimum((u[:, 1] * (pmax - pmin + 1)).astype(int), pmax - pmin)
+    return [(int(a), int(b)) for a, b in zip(ns, ps)]
