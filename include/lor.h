@@ -1,0 +1,141 @@
+/*
+ * lor.h -- C ABI of the GB300 LOR-preconditioned matrix-free Poisson solver.
+ *
+ * Method: Pazner, "Efficient low-order refined preconditioners for high-order
+ * matrix-free continuous and discontinuous Galerkin methods" (arXiv:1908.07071).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns lor_status; on failure lor_last_error(ctx) returns a
+ *    message owned by the context, valid until the next call on that context.
+ *  - Mesh: a structured-topology tensor mesh of nx*ny(*nz) elements, each the
+ *    multilinear image of [0,1]^d of its 2^d vertices (Section 2).  Vertex
+ *    coordinates are SoA float64: component c of vertex (i,j,k) at
+ *    vertices[c*NV + (k*(ny+1)+j)*(nx+1)+i], NV = (nx+1)(ny+1)(nz+1).
+ *    kappa[(ez*ny+ey)*nx+ex] > 0 is the piecewise-constant coefficient b of
+ *    Eq. (poisson).  Both are HOST pointers, copied by lor_create.
+ *  - CG vectors ("L-vectors"): float64 (or float32 where a call says so) on
+ *    the full Q_p node grid Nx*Ny(*Nz), N = p*n+1 per direction, x fastest:
+ *    node (I,J,K) at (K*Ny+J)*Nx+I.  Boundary (Dirichlet) entries of inputs are
+ *    ignored; those of outputs are written as 0.  Vector pointers are DEVICE
+ *    pointers owned by the caller, unless the name ends in _host.
+ *  - DG vectors: element-major blocks of (p+1)^d GLL-nodal values, element e
+ *    at offset e*(p+1)^d, node (i,j,k) of the block at (k*(p+1)+j)*(p+1)+i.
+ *  - Work runs on the stream given to lor_create (NULL = legacy default
+ *    stream).  Calls after lor_setup allocate no memory.
+ */
+#ifndef LOR_H
+#define LOR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LOR_OK = 0,
+  LOR_EINVAL = 1,      /* bad argument, inverted element, unsupported size   */
+  LOR_ENOMEM = 2,      /* device allocation failed                           */
+  LOR_ECUDA = 3,       /* a CUDA runtime call or launch failed               */
+  LOR_EBREAKDOWN = 4,  /* ILU(0) met a non-positive pivot (no shifting)      */
+  LOR_ENAN = 5,        /* NaN/Inf or p.Ap <= 0 in the Krylov recurrences     */
+  LOR_ENOCONV = 6,     /* max_it reached before rtol                        */
+  LOR_ETIMEOUT = 7,    /* a bounded device wait ran out                     */
+  LOR_ESTATE = 8       /* call out of order (e.g. apply before setup)       */
+} lor_status;
+
+typedef enum { LOR_CG = 0, LOR_DG_IP = 1, LOR_DG_BR2 = 2 } lor_disc;
+typedef enum { LOR_FP64 = 0, LOR_FP32 = 1, LOR_MIXED = 2 } lor_prec;
+
+typedef struct lor_ctx lor_ctx;
+
+typedef struct {
+  int dim;          /* 2 or 3                                                  */
+  int p;            /* polynomial degree, 1..8                                 */
+  int nx, ny, nz;   /* elements per direction (nz ignored for dim 2)           */
+  int disc;         /* lor_disc                                                */
+  double eta;       /* DG penalty parameter (IP: sigma = eta p^2 kappa / h)    */
+  int mg_levels;    /* patch V-cycle levels: 0 = full element-structured
+                       hierarchy (Section 3.3), L >= 2 = first L-1 levels then
+                       the vertex level                                        */
+  int prec;         /* lor_prec used by lor_pcg_solve                          */
+  double rtol;      /* stop when ||r||_2 <= rtol ||b||_2                       */
+  int max_it;       /* Krylov iteration cap                                    */
+  double inner_rtol;/* LOR_MIXED: relative tolerance of each FP32 inner solve  */
+  int factor_bf16;  /* LOR_MIXED/FP32: store ILU factors in bf16 (1) or fp32 */
+} lor_options;
+
+/* Fills *opt with defaults: dim 3, p 4, 8^3 elements, CG, eta 1, full
+ * hierarchy, FP64, rtol 1e-8, max_it 1000, inner_rtol 1e-3, fp32 factors. */
+void lor_default_options(lor_options* opt);
+
+/* Creates a context for the mesh (Section 2).  Validates sizes, copies the host
+ * mesh arrays to the device, checks every element for det J > 0 at its
+ * quadrature points (LOR_EINVAL otherwise).  stream: a cudaStream_t or NULL. */
+lor_status lor_create(lor_ctx** ctx, const lor_options* opt,
+                      const double* vertices, const double* kappa, void* stream);
+
+/* Builds everything the iteration needs (Sections 3.1-3.4, Table 1): geometric
+ * factors of the sum-factorized operator, the LOR matrix K_h as a 3^d-point
+ * stencil, Galerkin level stencils of the element-structured hierarchy, the
+ * lexicographic ILU(0) factors of every vertex patch at every level, and the
+ * coarse-space hierarchy.  Allocates all device memory of the context.
+ * LOR_EBREAKDOWN if any ILU(0) pivot is not positive. */
+lor_status lor_setup(lor_ctx* ctx);
+
+typedef struct {
+  long long nvec;      /* length of an L-vector (all grid nodes)               */
+  long long ndof;      /* unknowns: interior nodes (CG) or all DG nodes        */
+  long long npatch;    /* vertex patches J                                     */
+  long long ncoarse;   /* interior coarse-space unknowns                       */
+  int levels;          /* patch hierarchy levels                               */
+  int coarse_levels;   /* coarse-space V-cycle levels                          */
+  long long factor_rows; /* sum of patch rows over all patches and levels     */
+  size_t device_bytes; /* device memory held by the context                    */
+} lor_info;
+
+lor_status lor_get_info(const lor_ctx* ctx, lor_info* info);
+
+/* b = M f for the Galerkin right-hand side of Eq. (system), integrated with
+ * (p+1)^d Gauss-Legendre points: kind 0: f = 1; kind 1: f = d pi^2 prod_a
+ * sin(pi x_a) (manufactured solution u = prod_a sin(pi x_a)).  d_b: device
+ * float64 L-vector (or DG vector for DG contexts). */
+lor_status lor_rhs(lor_ctx* ctx, int kind, double* d_b);
+
+/* y = A x, the matrix-free sum-factorized operator (Section 2; Eq. (ip)/(br2)
+ * for DG contexts).  prec LOR_FP64: x, y float64; LOR_FP32: x, y float32. */
+lor_status lor_apply_A(lor_ctx* ctx, const void* d_x, void* d_y, int prec);
+
+/* z = B r, the additive-Schwarz LOR preconditioner of Eq. (as): coarse-space
+ * correction plus one V(1,1) cycle with ordered ILU(0) smoothing on every
+ * vertex patch (Sections 3.2-3.4); for DG contexts B_DG of Eq. (dg-as).
+ * prec LOR_FP64: float64 vectors and factors; LOR_FP32: float32 vectors,
+ * float32 stencils and float32/bf16 factors. */
+lor_status lor_apply_P(lor_ctx* ctx, const void* d_r, void* d_z, int prec);
+
+/* Solves A x = b by preconditioned CG from x0 = 0 to ||r|| <= rtol ||b||
+ * (Section 5).  LOR_FP64: plain FP64 PCG.  LOR_MIXED: iterative refinement
+ * with FP64 residuals b - A x and FP64 corrections; each correction is a PCG
+ * solve with FP32 operator and preconditioner and FP64 inner products.
+ * d_b, d_x: device float64 L-vectors.  iters: total (inner) iterations;
+ * rel_res: final ||b - A x|| / ||b|| computed in FP64.  Either may be NULL. */
+lor_status lor_pcg_solve(lor_ctx* ctx, const double* d_b, double* d_x,
+                         int* iters, double* rel_res);
+
+/* Same as lor_pcg_solve with HOST buffers (pageable or pinned): copies b to
+ * the device, solves, copies x back, all on the context stream. */
+lor_status lor_pcg_solve_host(lor_ctx* ctx, const double* h_b, double* h_x,
+                              int* iters, double* rel_res);
+
+/* Per-iteration residual norms ||r_k||_2 of the last solve (k = 0..count-1,
+ * FP64 outer residuals and inner FP64-accumulated norms for LOR_MIXED). */
+lor_status lor_residual_history(const lor_ctx* ctx, double* out, int cap, int* count);
+
+const char* lor_last_error(const lor_ctx* ctx);
+void lor_destroy(lor_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOR_H */

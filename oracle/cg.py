@@ -168,11 +168,11 @@ def apply_A_rows(mesh: Mesh, p: int, x, rows):
     return out
 
 
-def load_vector(mesh: Mesh, p: int, f):
-    """b_a = sum_e sum_q w_q |det J| f(X_q) phi_a(X_q) with (p+2)-point GL; boundary zeroed."""
+def load_vector(mesh: Mesh, p: int, f, q=None):
+    """b_a = sum_e sum_q w_q |det J| f(X_q) phi_a(X_q) with q-point GL (default p+2); boundary zeroed."""
     N = node_shape(mesh.n, p)
     ntot = int(np.prod(N))
-    x1, w1 = gauss_legendre(p + 2)
+    x1, w1 = gauss_legendre(p + 2 if q is None else q)
     pts, w = tensor_points(mesh.dim, x1, w1)
     phi, _ = tensor_basis(mesh.dim, p, x1)
     b = np.zeros(ntot)

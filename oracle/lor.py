@@ -195,7 +195,12 @@ class LORPreconditioner:
     """B = P_0 R_0 P_0^T + sum_j R_j^T V_j R_j (Eq. (as)), with options for exact solves."""
 
     def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0,
-                 exact_local: bool = False, exact_coarse: bool = False, K_h=None):
+                 exact_local: bool = False, exact_coarse: bool = False, K_h=None,
+                 patch_subset=None, coarse=True):
+        """patch_subset: vertex multi-indices whose patches are built (default all);
+        coarse=False skips the coarse space (for checks of the patch part alone)."""
+        self.patch_subset = None if patch_subset is None else set(map(tuple, patch_subset))
+        self.with_coarse = coarse
         self.mesh, self.p, self.dim = mesh, p, mesh.dim
         self.exact_local, self.exact_coarse = exact_local, exact_coarse
         n = mesh.n
@@ -212,7 +217,8 @@ class LORPreconditioner:
             P = kron_nd(mats)
             self.A.append((P.T @ self.A[l] @ P).tocsr())
         self._build_patches()
-        self._build_coarse()
+        if coarse:
+            self._build_coarse()
 
     # ---------------------------------------------------------------- patches
     def vertices(self):
@@ -223,6 +229,8 @@ class LORPreconditioner:
         self.patches = []
         L = len(self.sels)
         for v in self.vertices():
+            if self.patch_subset is not None and tuple(v) not in self.patch_subset:
+                continue
             levels = []
             for l in range(L):
                 ranges = [patch_range_1d(v[a], self.mesh.n[a], self.ms[l]) for a in range(self.dim)]
@@ -339,7 +347,7 @@ class LORPreconditioner:
                 idx = self.patches[j]["levels"][0]["idx"]
                 if len(idx):
                     z[idx] += self.local_solve(j, rr[idx])
-        if "coarse" in parts:
+        if "coarse" in parts and self.with_coarse:
             rc = (self.P0.T @ rr)[self.vmask]
             ec = np.zeros(self.P0.shape[1])
             ec[self.vmask] = self.coarse_solve(rc)

@@ -1,0 +1,217 @@
+// C ABI of the LOR solver (declared in include/lor.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lor_internal.h"
+
+lor_status lor_fail(lor_ctx* c, lor_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+lor_status lor_cuda_check(lor_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LOR_OK;
+  return lor_fail(c, e == cudaErrorMemoryAllocation ? LOR_ENOMEM : LOR_ECUDA,
+                  std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* lor_alloc(lor_ctx* c, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (cudaMemsetAsync(p, 0, bytes, c->stream) != cudaSuccess) {
+    cudaFree(p);
+    return nullptr;
+  }
+  c->allocs.push_back(p);
+  c->bytes += bytes;
+  return p;
+}
+
+extern "C" {
+
+void lor_default_options(lor_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->dim = 3;
+  o->p = 4;
+  o->nx = o->ny = o->nz = 8;
+  o->disc = LOR_CG;
+  o->eta = 1.0;
+  o->mg_levels = 0;
+  o->prec = LOR_FP64;
+  o->rtol = 1e-8;
+  o->max_it = 1000;
+  o->inner_rtol = 1e-3;
+  o->factor_bf16 = 0;
+}
+
+lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* vertices, const double* kappa,
+                      void* stream) {
+  if (!out || !opt || !vertices || !kappa) return LOR_EINVAL;
+  *out = nullptr;
+  if (opt->dim != 2 && opt->dim != 3) return LOR_EINVAL;
+  if (opt->p < 1 || opt->p > LOR_MAXP) return LOR_EINVAL;
+  if (opt->nx < 1 || opt->ny < 1 || (opt->dim == 3 && opt->nz < 1)) return LOR_EINVAL;
+  if (opt->disc != LOR_CG) return LOR_EINVAL;   // DG contexts: see lor_dg.h
+  if (!(opt->rtol > 0) || opt->max_it < 1) return LOR_EINVAL;
+  lor_ctx* c = new (std::nothrow) lor_ctx();
+  if (!c) return LOR_ENOMEM;
+  c->opt = *opt;
+  c->dim = opt->dim;
+  c->p = opt->p;
+  c->n[0] = opt->nx;
+  c->n[1] = opt->ny;
+  c->n[2] = opt->dim == 3 ? opt->nz : 1;
+  c->nel = c->n[0] * c->n[1] * c->n[2];
+  c->stream = (cudaStream_t)stream;
+  const long long NV = (long long)(c->n[0] + 1) * (c->n[1] + 1) * (c->dim == 3 ? c->n[2] + 1 : 1);
+  c->h_vert.assign(vertices, vertices + NV * c->dim);
+  c->h_kappa.assign(kappa, kappa + c->nel);
+  for (double k : c->h_kappa)
+    if (!(k > 0) || !std::isfinite(k)) {
+      delete c;
+      return LOR_EINVAL;
+    }
+  for (double v : c->h_vert)
+    if (!std::isfinite(v)) {
+      delete c;
+      return LOR_EINVAL;
+    }
+  *out = c;
+  return LOR_OK;
+}
+
+static size_t patch_smem(const lor_ctx* c, size_t elem) {
+  size_t tot = 0;
+  for (int l = 0; l < c->L; ++l) {
+    const BoxShape& bs = c->shapes[l * 8 + 0];   // interior shape is the largest
+    const size_t padn = (size_t)(bs.dims[0] + 2) * (bs.dims[1] + 2) * (c->dim == 3 ? bs.dims[2] + 2 : 1);
+    tot += 2 * padn + (l > 0 ? (size_t)bs.rows : 0);
+  }
+  return tot * elem;
+}
+
+lor_status lor_setup(lor_ctx* c) {
+  if (!c) return LOR_EINVAL;
+  if (c->setup_done) return lor_fail(c, LOR_ESTATE, "lor_setup called twice");
+  lor_status s;
+  if ((s = lor_setup_geometry(c))) return s;
+  if ((s = lor_setup_stencils(c))) return s;
+  if ((s = lor_setup_patches(c))) return s;
+  if ((s = lor_setup_coarse(c))) return s;
+  if ((s = lor_setup_krylov(c))) return s;
+  c->smem_patch64 = (int)patch_smem(c, 8);
+  c->smem_patch32 = (int)patch_smem(c, 4);
+  int dev = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (c->smem_patch64 > maxsm) return lor_fail(c, LOR_EINVAL, "patch does not fit in shared memory");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return lor_cuda_check(c, e, "setup");
+  c->setup_done = true;
+  return LOR_OK;
+}
+
+lor_status lor_get_info(const lor_ctx* c, lor_info* info) {
+  if (!c || !info) return LOR_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  long long nvec = 1, ndof = 1;
+  for (int a = 0; a < c->dim; ++a) {
+    nvec *= (long long)c->n[a] * c->p + 1;
+    ndof *= (long long)c->n[a] * c->p - 1;
+  }
+  info->nvec = nvec;
+  info->ndof = ndof;
+  long long J = 1, nc = 1;
+  for (int a = 0; a < c->dim; ++a) { J *= c->n[a] + 1; nc *= c->n[a] - 1; }
+  info->npatch = J;
+  info->ncoarse = nc;
+  info->levels = c->L;
+  info->coarse_levels = c->CL;
+  info->factor_rows = c->fac_rows;
+  info->device_bytes = c->bytes;
+  return LOR_OK;
+}
+
+static lor_status ready(lor_ctx* c) {
+  if (!c) return LOR_EINVAL;
+  if (!c->setup_done) return lor_fail(c, LOR_ESTATE, "lor_setup has not completed");
+  return LOR_OK;
+}
+
+lor_status lor_rhs(lor_ctx* c, int kind, double* d_b) {
+  lor_status s = ready(c);
+  if (s) return s;
+  if (!d_b || kind < 0 || kind > 1) return lor_fail(c, LOR_EINVAL, "lor_rhs: bad argument");
+  return lor_launch_rhs(c, kind, d_b);
+}
+
+lor_status lor_apply_A(lor_ctx* c, const void* x, void* y, int prec) {
+  lor_status s = ready(c);
+  if (s) return s;
+  if (!x || !y) return lor_fail(c, LOR_EINVAL, "lor_apply_A: null vector");
+  if (prec == LOR_FP64) return lor_launch_apply_A64(c, (const double*)x, (double*)y);
+  if (prec == LOR_FP32) return lor_launch_apply_A32(c, (const float*)x, (float*)y);
+  return lor_fail(c, LOR_EINVAL, "lor_apply_A: prec must be LOR_FP64 or LOR_FP32");
+}
+
+lor_status lor_apply_P(lor_ctx* c, const void* r, void* z, int prec) {
+  lor_status s = ready(c);
+  if (s) return s;
+  if (!r || !z) return lor_fail(c, LOR_EINVAL, "lor_apply_P: null vector");
+  if (prec == LOR_FP64) return lor_launch_apply_P64(c, (const double*)r, (double*)z);
+  if (prec == LOR_FP32) return lor_launch_apply_P32(c, (const float*)r, (float*)z);
+  return lor_fail(c, LOR_EINVAL, "lor_apply_P: prec must be LOR_FP64 or LOR_FP32");
+}
+
+lor_status lor_pcg_solve(lor_ctx* c, const double* b, double* x, int* iters, double* rel_res) {
+  lor_status s = ready(c);
+  if (s) return s;
+  if (!b || !x) return lor_fail(c, LOR_EINVAL, "lor_pcg_solve: null vector");
+  if (c->opt.prec == LOR_MIXED) return lor_pcg_mixed(c, b, x, iters, rel_res);
+  return lor_pcg64(c, b, x, iters, rel_res);
+}
+
+lor_status lor_pcg_solve_host(lor_ctx* c, const double* hb, double* hx, int* iters, double* rel_res) {
+  lor_status s = ready(c);
+  if (s) return s;
+  if (!hb || !hx) return lor_fail(c, LOR_EINVAL, "lor_pcg_solve_host: null vector");
+  const long long n = c->lev[0].ntot;
+  double* db = c->d_v64[5];
+  double* dx = c->d_v64[6];
+  cudaError_t e = cudaMemcpyAsync(db, hb, n * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return lor_cuda_check(c, e, "copy b");
+  s = lor_pcg_solve(c, db, dx, iters, rel_res);
+  if (s != LOR_OK && s != LOR_ENOCONV) return s;
+  e = cudaMemcpyAsync(hx, dx, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return lor_cuda_check(c, e, "copy x");
+  return s;
+}
+
+lor_status lor_residual_history(const lor_ctx* c, double* out, int cap, int* count) {
+  if (!c || !count) return LOR_EINVAL;
+  *count = (int)c->hist.size();
+  if (out)
+    for (int i = 0; i < cap && i < (int)c->hist.size(); ++i) out[i] = c->hist[i];
+  return LOR_OK;
+}
+
+const char* lor_last_error(const lor_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void lor_destroy(lor_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  delete c;
+}
+
+}  // extern "C"

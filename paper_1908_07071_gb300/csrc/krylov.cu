@@ -1,0 +1,324 @@
+// Preconditioned conjugate gradients (Section 3.2 uses B inside CG; Section 5
+// stops on a residual reduction).  All inner products accumulate in FP64 with a
+// deterministic two-stage reduction (fixed grid, per-block partials, the last
+// block sums the partials in order), so repeated solves are bit-identical.
+// Scalars (alpha, beta, r.z, p.Ap, r.r) stay on the device; the host reads r.r
+// once per iteration for the stopping test.
+//
+// LOR_MIXED: iterative refinement.  The outer loop keeps x and r = b - A x in
+// FP64 (FP64 sum-factorized apply); each correction solves A d = r/||r|| with
+// PCG on FP32 vectors, FP32 operator and FP32 preconditioner, FP64 dots, to a
+// relative tolerance inner_rtol; x += ||r|| d in FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "lor_internal.h"
+
+namespace {
+
+enum { S_RZ = 0, S_PAP = 1, S_RR = 2, S_RZNEW = 3, S_ALPHA = 4, S_BETA = 5, S_BB = 6, S_FLAG = 7, S_TMP = 8 };
+enum { OP_STORE = 0, OP_ALPHA = 1, OP_BETA = 2 };
+
+const int kRedBlocks = 1024;
+const int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0;
+  if (w == 0) {
+    s = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;   // valid in thread 0
+}
+
+// Finish a reduction: the last block to arrive sums the partials in block order.
+__device__ void finish(double mine, double* part, unsigned* count, double* scal, int slot, int op) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const double s = block_sum(mine, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s;
+    __threadfence();
+    const unsigned t = atomicInc(count, gridDim.x - 1);   // wraps to 0 for the next use
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    double v = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += ((volatile double*)part)[b];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+      if (op == OP_STORE) {
+        scal[slot] = v;
+      } else if (op == OP_ALPHA) {
+        scal[S_PAP] = v;
+        if (!(v > 0.0) || !isfinite(v)) scal[S_FLAG] = 1.0;
+        scal[S_ALPHA] = scal[S_RZ] / v;
+      } else {   // OP_BETA: v = r.z_new
+        scal[S_RZNEW] = v;
+        if (!isfinite(v)) scal[S_FLAG] = 1.0;
+        scal[S_BETA] = v / scal[S_RZ];
+        scal[S_RZ] = v;
+      }
+    }
+  }
+}
+
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256) k_dot(const TA* __restrict__ a, const TB* __restrict__ b, long long n,
+                                             double* part, unsigned* count, double* scal, int slot, int op) {
+  double s = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += (double)a[i] * (double)b[i];
+  finish(s, part, count, scal, slot, op);
+}
+
+// x += alpha p ; r -= alpha Ap ; then r.r
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                                const T* __restrict__ Ap, long long n, double* part,
+                                                unsigned* count, double* scal) {
+  const double alpha = scal[S_ALPHA];
+  const T a = (T)alpha;
+  double s = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] += a * p[i];
+    const T ri = r[i] - a * Ap[i];
+    r[i] = ri;
+    s += (double)ri * (double)ri;
+  }
+  finish(s, part, count, scal, S_RR, OP_STORE);
+}
+
+// p = z + beta p
+template <typename T>
+__global__ void k_xpay(T* __restrict__ p, const T* __restrict__ z, long long n, const double* scal) {
+  const T beta = (T)scal[S_BETA];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+template <typename T>
+__global__ void k_copy(T* __restrict__ d, const T* __restrict__ s, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+
+// r32 = (float)(r64 * scale)
+__global__ void k_down(float* __restrict__ d, const double* __restrict__ s, double scale, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    d[i] = (float)(s[i] * scale);
+}
+
+// x64 += scale * d32
+__global__ void k_up_add(double* __restrict__ x, const float* __restrict__ d, double scale, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] += scale * (double)d[i];
+}
+
+// r = b - Ax (boundary entries of b are ignored: A x has zero boundary rows, and
+// r is masked to zero there by the caller-independent rule that b's boundary
+// entries do not count)
+__global__ void __launch_bounds__(256) k_resid(double* __restrict__ r, const double* __restrict__ b,
+                                               const double* __restrict__ Ax, const unsigned char* __restrict__ bmask,
+                                               long long n, double* part, unsigned* count, double* scal) {
+  double s = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = bmask[i] ? 0.0 : b[i] - Ax[i];
+    r[i] = v;
+    s += v * v;
+  }
+  finish(s, part, count, scal, S_RR, OP_STORE);
+}
+
+__global__ void k_mask_copy(double* __restrict__ d, const double* __restrict__ s, const unsigned char* __restrict__ bmask,
+                            long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    d[i] = bmask[i] ? 0.0 : s[i];
+}
+
+__global__ void k_bmask(int dim, int Nx, int Ny, int Nz, unsigned char* m) {
+  const long long n = (long long)Nx * Ny * Nz;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(g % Nx), J = (int)((g / Nx) % Ny), K = (int)(g / ((long long)Nx * Ny));
+    m[g] = (I == 0 || I == Nx - 1 || J == 0 || J == Ny - 1 || (dim == 3 && (K == 0 || K == Nz - 1))) ? 1 : 0;
+  }
+}
+
+}  // namespace
+
+// Krylov work buffers: 8 FP64 vectors (nvec; vector 7 also serves as rhs scratch
+// of nel*(p+1)^d), 6 FP32 vectors, scalars, partials, boundary mask.
+static unsigned char* bmask_of(lor_ctx* c) { return (unsigned char*)c->d_v32[7]; }
+
+lor_status lor_setup_krylov(lor_ctx* c) {
+  const long long n = c->lev[0].ntot;
+  const int Q = c->p + 1;
+  const long long qd = (long long)c->nel * (c->dim == 3 ? Q * Q * Q : Q * Q);
+  for (int k = 0; k < 8; ++k) {
+    const long long len = k == 7 ? std::max(n, qd) : n;
+    c->d_v64[k] = (double*)lor_alloc(c, len * 8);
+    if (!c->d_v64[k]) return lor_fail(c, LOR_ENOMEM, "alloc krylov vectors");
+  }
+  for (int k = 0; k < 7; ++k) {
+    c->d_v32[k] = (float*)lor_alloc(c, n * 4);
+    if (!c->d_v32[k]) return lor_fail(c, LOR_ENOMEM, "alloc krylov vectors");
+  }
+  c->d_v32[7] = (float*)lor_alloc(c, n);   // boundary mask (bytes)
+  c->d_scal = (double*)lor_alloc(c, 64 * 8);
+  c->d_part = (double*)lor_alloc(c, kRedBlocks * 8);
+  c->d_count = (unsigned*)lor_alloc(c, 64);
+  if (!c->d_v32[7] || !c->d_scal || !c->d_part || !c->d_count) return lor_fail(c, LOR_ENOMEM, "alloc krylov scalars");
+  if (!c->h_scal && cudaMallocHost(&c->h_scal, 64 * 8) != cudaSuccess) return lor_fail(c, LOR_ENOMEM, "pinned");
+  k_bmask<<<1024, 256, 0, c->stream>>>(c->dim, c->lev[0].N[0], c->lev[0].N[1], c->lev[0].N[2], bmask_of(c));
+  return lor_cuda_check(c, cudaGetLastError(), "krylov setup");
+}
+
+static unsigned red_blocks(long long n) {
+  return (unsigned)std::max<long long>(1, std::min<long long>(kRedBlocks, lor_ceil_div(n, kRedThreads * 4)));
+}
+
+template <typename TA, typename TB>
+static void dot(lor_ctx* c, const TA* a, const TB* b, long long n, int slot, int op) {
+  k_dot<TA, TB><<<red_blocks(n), kRedThreads, 0, c->stream>>>(a, b, n, c->d_part, c->d_count, c->d_scal, slot, op);
+}
+
+static lor_status read_scalars(lor_ctx* c) {
+  cudaError_t e = cudaMemcpyAsync(c->h_scal, c->d_scal, 16 * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return lor_cuda_check(c, e, "read scalars");
+}
+
+// PCG on vectors of type T with operator/preconditioner callbacks.
+// x starts at 0, r = rhs.  Stops at ||r|| <= tol_abs.  Returns iterations via *it.
+template <typename T, typename FA, typename FP>
+static lor_status pcg_core(lor_ctx* c, T* x, T* r, T* z, T* p, T* Ap, long long n, double tol_abs, int max_it,
+                           FA applyA, FP applyP, int* it_out, double* rr_out, bool record) {
+  const unsigned gb = red_blocks(n);
+  cudaMemsetAsync(x, 0, sizeof(T) * n, c->stream);
+  cudaMemsetAsync(c->d_scal, 0, 16 * 8, c->stream);
+  dot(c, r, r, n, S_RR, OP_STORE);
+  if (applyP(r, z)) return LOR_ECUDA;
+  dot(c, r, z, n, S_RZ, OP_STORE);
+  k_copy<T><<<gb, kRedThreads, 0, c->stream>>>(p, z, n);
+  if (read_scalars(c)) return LOR_ECUDA;
+  double rr = c->h_scal[S_RR];
+  if (record) c->hist.push_back(sqrt(rr));
+  int it = 0;
+  lor_status st = LOR_OK;
+  while (it < max_it && sqrt(rr) > tol_abs) {
+    if (applyA(p, Ap)) return LOR_ECUDA;
+    dot(c, p, Ap, n, 0, OP_ALPHA);
+    k_update<T><<<gb, kRedThreads, 0, c->stream>>>(x, r, p, Ap, n, c->d_part, c->d_count, c->d_scal);
+    if (read_scalars(c)) return LOR_ECUDA;
+    ++it;
+    rr = c->h_scal[S_RR];
+    if (record) c->hist.push_back(sqrt(rr));
+    if (c->h_scal[S_FLAG] != 0.0 || !std::isfinite(rr)) { st = LOR_ENAN; break; }
+    if (sqrt(rr) <= tol_abs) break;
+    if (applyP(r, z)) return LOR_ECUDA;
+    dot(c, r, z, n, 0, OP_BETA);
+    k_xpay<T><<<gb, kRedThreads, 0, c->stream>>>(p, z, n, c->d_scal);
+  }
+  *it_out = it;
+  *rr_out = rr;
+  if (st == LOR_ENAN) return lor_fail(c, LOR_ENAN, "CG breakdown: p.Ap <= 0 or non-finite value");
+  return lor_cuda_check(c, cudaGetLastError(), "pcg");
+}
+
+static lor_status true_residual(lor_ctx* c, const double* b, const double* x, double* r, double* Ax, double* rn) {
+  const long long n = c->lev[0].ntot;
+  if (lor_launch_apply_A64(c, x, Ax)) return LOR_ECUDA;
+  k_resid<<<red_blocks(n), kRedThreads, 0, c->stream>>>(r, b, Ax, bmask_of(c), n, c->d_part, c->d_count, c->d_scal);
+  if (read_scalars(c)) return LOR_ECUDA;
+  *rn = sqrt(c->h_scal[S_RR]);
+  return LOR_OK;
+}
+
+static double norm_b(lor_ctx* c, const double* b, double* tmp) {
+  const long long n = c->lev[0].ntot;
+  k_mask_copy<<<red_blocks(n), kRedThreads, 0, c->stream>>>(tmp, b, bmask_of(c), n);
+  dot(c, tmp, tmp, n, S_BB, OP_STORE);
+  if (read_scalars(c)) return -1.0;
+  return sqrt(c->h_scal[S_BB]);
+}
+
+lor_status lor_pcg64(lor_ctx* c, const double* b, double* x, int* iters, double* relres) {
+  const long long n = c->lev[0].ntot;
+  double* r = c->d_v64[0];
+  double* z = c->d_v64[1];
+  double* p = c->d_v64[2];
+  double* Ap = c->d_v64[3];
+  c->hist.clear();
+  const double bn = norm_b(c, b, r);   // r = masked b
+  if (bn < 0) return LOR_ECUDA;
+  if (bn == 0.0) {
+    cudaMemsetAsync(x, 0, 8 * n, c->stream);
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return LOR_OK;
+  }
+  auto A = [&](const double* in, double* out) { return lor_launch_apply_A64(c, in, out); };
+  auto P = [&](const double* in, double* out) { return lor_launch_apply_P64(c, in, out); };
+  int it = 0;
+  double rr = 0;
+  lor_status st = pcg_core<double>(c, x, r, z, p, Ap, n, c->opt.rtol * bn, c->opt.max_it, A, P, &it, &rr, true);
+  if (st) return st;
+  double rn = 0;
+  if (true_residual(c, b, x, r, Ap, &rn)) return LOR_ECUDA;
+  if (iters) *iters = it;
+  if (relres) *relres = rn / bn;
+  if (it >= c->opt.max_it && sqrt(rr) > c->opt.rtol * bn) return lor_fail(c, LOR_ENOCONV, "max_it reached");
+  return LOR_OK;
+}
+
+lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, double* relres) {
+  const long long n = c->lev[0].ntot;
+  double* r = c->d_v64[0];
+  double* Ax = c->d_v64[3];
+  float* d = c->d_v32[0];
+  float* r32 = c->d_v32[1];
+  float* z32 = c->d_v32[2];
+  float* p32 = c->d_v32[3];
+  float* Ap32 = c->d_v32[4];
+  c->hist.clear();
+  const double bn = norm_b(c, b, r);    // r = masked b = b - A*0
+  if (bn < 0) return LOR_ECUDA;
+  cudaMemsetAsync(x, 0, 8 * n, c->stream);
+  if (bn == 0.0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return LOR_OK;
+  }
+  double rn = bn;
+  c->hist.push_back(rn);
+  auto A = [&](const float* in, float* out) { return lor_launch_apply_A32(c, in, out); };
+  auto P = [&](const float* in, float* out) { return lor_launch_apply_P32(c, in, out); };
+  int total = 0, outer = 0;
+  while (rn > c->opt.rtol * bn && total < c->opt.max_it && outer < 100) {
+    k_down<<<red_blocks(n), kRedThreads, 0, c->stream>>>(r32, r, 1.0 / rn, n);
+    // inner tolerance: inner_rtol, but never tighter than needed to reach rtol
+    const double need = c->opt.rtol * bn / rn;
+    const double tol = std::max(c->opt.inner_rtol, 0.5 * need);
+    int it = 0;
+    double rr = 0;
+    lor_status st = pcg_core<float>(c, d, r32, z32, p32, Ap32, n, tol, c->opt.max_it - total, A, P, &it, &rr, false);
+    if (st) return st;
+    total += it;
+    k_up_add<<<red_blocks(n), kRedThreads, 0, c->stream>>>(x, d, rn, n);
+    if (true_residual(c, b, x, r, Ax, &rn)) return LOR_ECUDA;
+    c->hist.push_back(rn);
+    ++outer;
+    if (!std::isfinite(rn)) return lor_fail(c, LOR_ENAN, "mixed precision: non-finite residual");
+  }
+  if (iters) *iters = total;
+  if (relres) *relres = rn / bn;
+  if (rn > c->opt.rtol * bn) return lor_fail(c, LOR_ENOCONV, "mixed precision: max_it reached");
+  return LOR_OK;
+}

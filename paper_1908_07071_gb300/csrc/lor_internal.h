@@ -1,0 +1,172 @@
+// Internal declarations of the LOR solver library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lor.h"
+
+#define LOR_MAXP 8
+#define LOR_MAXLEV 5      // p <= 8: at most 4 patch levels (8,4,2,1) + slack
+#define LOR_MAXCLEV 8     // coarse-space V-cycle levels
+
+// ------------------------------------------------------------------ host basis
+namespace lorh {
+// GLL points/weights of degree p on [0,1]; Gauss-Legendre with q points on [0,1].
+void gll(int p, double* x, double* w);
+void gauss(int q, double* x, double* w);
+// Lagrange basis on `nodes` (m of them) at points t (nt): B[t*m+i], D[t*m+i].
+void lagrange(int m, const double* nodes, int nt, const double* t, double* B, double* D);
+// Element-structured hierarchy (Section 3.3): GLL-index subsets per level.
+std::vector<std::vector<int>> level_selections(int p, int mg_levels);
+}  // namespace lorh
+
+// ---------------------------------------------------------- device-side tables
+// 1D prolongation entry of a fine point: value = w0*coarse[c0] + w1*coarse[c1].
+struct Prolong1D { int c0, c1; double w0, w1; };
+
+// Patch 1D structure of one level and one axis type (0 interior, 1 boundary).
+struct RestrictEntry { int f[3]; double w[3]; };
+
+struct PatchAxis {
+  int len;        // unknowns along the axis at this level
+  int clen;       // unknowns at the next coarser level
+};
+
+struct LevelGrid {
+  int m;                  // intervals per element
+  int N[3];               // nodes per direction (1 for unused dims)
+  long long ntot;
+};
+
+// Shape of a patch box at one level: wavefront schedule for lexicographic ILU(0).
+struct BoxShape {
+  int dims[3];            // box extents (x, y, z); 1 for unused dims
+  int rows;
+  int nfront;
+  int front_off;          // offset into ctx->d_front (nfront+1 entries)
+  int row_off;            // offset into ctx->d_rowpad (rows entries)
+};
+
+struct lor_ctx {
+  lor_options opt;
+  int dim, p;
+  int n[3];
+  int nel;
+  cudaStream_t stream;
+  std::string err;
+  bool setup_done = false;
+
+  // mesh
+  double* d_vert = nullptr;   // SoA dim x NV
+  double* d_kappa = nullptr;
+  std::vector<double> h_vert, h_kappa;
+
+  // 1D basis (host copies, device constant tables are uploaded per launch)
+  double gll_x[LOR_MAXP + 1], gll_w[LOR_MAXP + 1];
+  double gl_x[LOR_MAXP + 2], gl_w[LOR_MAXP + 2];
+  double B[(LOR_MAXP + 1) * (LOR_MAXP + 1)];   // B[q*(p+1)+i] = l_i(gl_q)
+  double Dq[(LOR_MAXP + 1) * (LOR_MAXP + 1)];  // collocated derivative at GL points
+
+  // operator data
+  double* d_G64 = nullptr;    // [nel][ncomp][Q] geometric factors (kappa w detJ J^-1 J^-T)
+  float* d_G32 = nullptr;
+  double* d_X = nullptr;      // level-0 node coordinates SoA dim x ntot
+
+  // level hierarchy
+  int L = 0;
+  std::vector<std::vector<int>> sel;
+  LevelGrid lev[LOR_MAXLEV];
+  double* d_S64[LOR_MAXLEV] = {};   // [NS][ntot_l] stencils
+  float* d_S32[LOR_MAXLEV] = {};
+  Prolong1D* d_P1[LOR_MAXLEV][3] = {};    // global 1D prolongation level l+1 -> l (per axis)
+  int* d_R1ptr[LOR_MAXLEV][3] = {};       // restriction CSR: coarse -> fine list
+  int* d_R1idx[LOR_MAXLEV][3] = {};
+  double* d_R1w[LOR_MAXLEV][3] = {};
+
+  // patches
+  int J = 0;                  // number of vertex patches
+  int NS = 27;                // stencil size 3^dim
+  std::vector<BoxShape> shapes;           // [level][8 shapes]
+  BoxShape* d_shapes = nullptr;           // device copy of `shapes`
+  int* d_poslex = nullptr;                // lexicographic index -> wavefront position
+  int* d_front = nullptr;
+  int* d_rowpad = nullptr;    // padded-box index of row at wavefront position
+  int* d_rowlex = nullptr;    // unpadded lexicographic index of row
+  // per-level per-axis-type patch-local 1D prolongation (fine -> coarse, local idx)
+  Prolong1D* d_pp[LOR_MAXLEV][2] = {};
+  // per-level per-axis-type patch-local restriction: coarse local c -> 3 (fine local f, w), f = -1 unused
+  struct RestrictEntry* d_rr[LOR_MAXLEV][2] = {};
+  long long* d_facoff = nullptr;          // [level][J] offsets into factor arrays
+  long long fac_rows = 0;
+  double* d_F64 = nullptr;
+  float* d_F32 = nullptr;
+  __nv_bfloat16* d_F16 = nullptr;
+  int smem_patch64 = 0, smem_patch32 = 0;
+  int* d_status = nullptr;    // device error word
+
+  // coarse space (vertex grid hierarchy)
+  int CL = 0;
+  int cN[LOR_MAXCLEV][3];
+  long long cntot[LOR_MAXCLEV];
+  double* d_cS64[LOR_MAXCLEV] = {};
+  float* d_cS32[LOR_MAXCLEV] = {};
+  double* d_cDinv64[LOR_MAXCLEV] = {};   // 1 / l1 row sums
+  float* d_cDinv32[LOR_MAXCLEV] = {};
+  Prolong1D* d_cP1[LOR_MAXCLEV][3] = {};
+  int* d_cR1ptr[LOR_MAXCLEV][3] = {};
+  int* d_cR1idx[LOR_MAXCLEV][3] = {};
+  double* d_cR1w[LOR_MAXCLEV][3] = {};
+  int ncoarse_direct = 0;
+  int* d_cdirect_idx = nullptr;           // interior node index of each direct unknown
+  double* d_cInv64 = nullptr;             // dense inverse at the coarsest level
+  float* d_cInv32 = nullptr;
+  // coarse work vectors per level: r, x, t (double and float)
+  double* d_cw64[LOR_MAXCLEV][4] = {};
+  float* d_cw32[LOR_MAXCLEV][4] = {};
+
+  // Krylov work (double) and mixed inner (float)
+  double* d_v64[8] = {};
+  float* d_v32[8] = {};
+  double* d_scal = nullptr;   // device scalars
+  double* d_part = nullptr;   // reduction partials
+  unsigned int* d_count = nullptr;
+  double* h_scal = nullptr;   // pinned mirror
+  std::vector<double> hist;
+
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+};
+
+// ---------------------------------------------------------------- error helpers
+lor_status lor_fail(lor_ctx* c, lor_status s, const std::string& msg);
+lor_status lor_cuda_check(lor_ctx* c, cudaError_t e, const char* what);
+void* lor_alloc(lor_ctx* c, size_t bytes);   // tracked device allocation (nullptr on failure)
+
+// -------------------------------------------------------------- kernel launchers
+// setup.cu
+lor_status lor_setup_geometry(lor_ctx* c);
+lor_status lor_setup_stencils(lor_ctx* c);
+lor_status lor_setup_patches(lor_ctx* c);
+lor_status lor_setup_coarse(lor_ctx* c);
+// apply_a.cu
+lor_status lor_launch_apply_A64(lor_ctx* c, const double* x, double* y);
+lor_status lor_launch_apply_A32(lor_ctx* c, const float* x, float* y);
+lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b);
+// apply_p.cu
+lor_status lor_launch_apply_P64(lor_ctx* c, const double* r, double* z);
+lor_status lor_launch_apply_P32(lor_ctx* c, const float* r, float* z);
+// krylov.cu
+lor_status lor_pcg64(lor_ctx* c, const double* b, double* x, int* iters, double* relres);
+lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, double* relres);
+lor_status lor_setup_krylov(lor_ctx* c);
+BoxShape* lor_dev_shapes(lor_ctx* c);
+double* lor_basis64(lor_ctx* c, int which);
+float* lor_basis32(lor_ctx* c, int which);
+
+// small device utilities shared by the .cu files
+__host__ __device__ inline long long lor_ceil_div(long long a, long long b) { return (a + b - 1) / b; }

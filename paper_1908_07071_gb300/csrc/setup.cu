@@ -1,0 +1,831 @@
+// Setup of the LOR preconditioner and the operator data (Section 3, Table 1).
+//  * geometric factors of the sum-factorized operator (Section 2)
+//  * K_h: multilinear stiffness on the GLL-refined mesh T_h as a 3^d-point stencil
+//    per node (Section 3.1), 2-point Gauss per direction on every sub-element
+//  * Galerkin level stencils A_{l+1} = P^T A_l P of the element-structured
+//    hierarchy (Section 3.3), P = tensor 1D linear interpolation in reference
+//    coordinates
+//  * lexicographic ILU(0) of every vertex patch at every level (Section 3.4),
+//    one CTA per patch, rows level-scheduled by wavefront i + 2j + 4k
+//  * coarse-space hierarchy on the vertex grid (Section 3.2, R_0)
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lor_internal.h"
+
+// ------------------------------------------------------------------ basis block
+// Device layout of the small basis block: for precision 64: [B | Dq | glx | glw |
+// gllx], each (LOR_MAXP+2)^2 doubles; for 32: [B | Dq] floats.
+static const int kBlk = (LOR_MAXP + 2) * (LOR_MAXP + 2);
+
+// The two blocks are the first two allocations of the context (lor_setup_geometry).
+double* lor_basis64(lor_ctx* c, int which) { return (double*)c->allocs[0] + which * kBlk; }
+float* lor_basis32(lor_ctx* c, int which) { return (float*)c->allocs[1] + which * kBlk; }
+BoxShape* lor_dev_shapes(lor_ctx* c) { return c->d_shapes; }
+
+namespace {
+
+__device__ inline double det3(const double J[3][3]) {
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+// inverse of a dim x dim matrix (dim 2 or 3) by the adjugate
+__device__ inline void inv_dd(int dim, const double J[3][3], double det, double Ji[3][3]) {
+  if (dim == 3) {
+    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  } else {
+    Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
+    Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+  }
+}
+
+// Multilinear map of the 2^dim points P[c][a] (corner c = cx + 2cy + 4cz) at xi:
+// X and J[a][b] = dX_a/dxi_b.
+__device__ inline void multilinear(int dim, const double (*Pc)[3], const double* xi, double* X, double J[3][3]) {
+  for (int a = 0; a < 3; ++a) { X[a] = 0; for (int b = 0; b < 3; ++b) J[a][b] = 0; }
+  const int nc = 1 << dim;
+  for (int cc = 0; cc < nc; ++cc) {
+    double f[3], df[3];
+    for (int a = 0; a < 3; ++a) {
+      const int bit = (cc >> a) & 1;
+      f[a] = bit ? xi[a] : 1.0 - xi[a];
+      df[a] = bit ? 1.0 : -1.0;
+    }
+    double N = 1.0;
+    for (int t = 0; t < dim; ++t) N *= f[t];
+    for (int bb = 0; bb < dim; ++bb) {
+      double g = 1.0;
+      for (int t = 0; t < dim; ++t) g *= (t == bb) ? df[t] : f[t];
+      for (int a = 0; a < dim; ++a) J[a][bb] += g * Pc[cc][a];
+    }
+    for (int a = 0; a < dim; ++a) X[a] += N * Pc[cc][a];
+  }
+}
+
+__device__ inline void element_corners(int dim, int nx, int ny, int ex, int ey, int ez, const double* vert,
+                                       long long NV, double (*Pc)[3]) {
+  const int nc = 1 << dim;
+  for (int cc = 0; cc < nc; ++cc) {
+    const int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
+    const long long vid = ((long long)(ez + bz) * (ny + 1) + (ey + by)) * (nx + 1) + (ex + bx);
+    for (int a = 0; a < 3; ++a) Pc[cc][a] = a < dim ? vert[a * NV + vid] : 0.0;
+  }
+}
+
+// G[e][comp][q] = kappa_e w_q det J (J^{-1} J^{-T})_{ab}, comps (00,01,02,11,12,22) / (00,01,11)
+__global__ void k_geom(int dim, int p, int nx, int ny, int nz, const double* __restrict__ vert,
+                       const double* __restrict__ kappa, const double* __restrict__ glx,
+                       const double* __restrict__ glw, double* __restrict__ G64, float* __restrict__ G32,
+                       int* status) {
+  const int Q = p + 1;
+  const int Qd = dim == 3 ? Q * Q * Q : Q * Q;
+  const long long nel = (long long)nx * ny * (dim == 3 ? nz : 1);
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nel * Qd) return;
+  const long long e = gid / Qd;
+  const int q = (int)(gid - e * Qd);
+  const int qx = q % Q, qy = (q / Q) % Q, qz = dim == 3 ? q / (Q * Q) : 0;
+  const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = dim == 3 ? (int)(e / ((long long)nx * ny)) : 0;
+  const long long NV = (long long)(nx + 1) * (ny + 1) * (dim == 3 ? (nz + 1) : 1);
+  double Pc[8][3];
+  element_corners(dim, nx, ny, ex, ey, ez, vert, NV, Pc);
+  const double xi[3] = {glx[qx], glx[qy], dim == 3 ? glx[qz] : 0.0};
+  double X[3], J[3][3];
+  multilinear(dim, Pc, xi, X, J);
+  const double det = dim == 3 ? det3(J) : (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+  if (!(det > 0)) { atomicOr(status, 1); return; }
+  double Ji[3][3];
+  inv_dd(dim, J, det, Ji);
+  const double w = glw[qx] * glw[qy] * (dim == 3 ? glw[qz] : 1.0);
+  const double s = kappa[e] * w * det;
+  const int ncomp = dim == 3 ? 6 : 3;
+  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+  const int ja[3] = {0, 0, 1}, jb[3] = {0, 1, 1};
+  for (int cpt = 0; cpt < ncomp; ++cpt) {
+    const int a = dim == 3 ? ia[cpt] : ja[cpt], b = dim == 3 ? ib[cpt] : jb[cpt];
+    double g = 0;
+    for (int t = 0; t < dim; ++t) g += Ji[a][t] * Ji[b][t];
+    const long long o = e * ncomp * Qd + (long long)cpt * Qd + q;
+    G64[o] = s * g;
+    G32[o] = (float)(s * g);
+  }
+}
+
+// physical coordinates of every level-0 node: element map at the GLL point
+__global__ void k_nodes(int dim, int p, int nx, int ny, int nz, const double* __restrict__ vert,
+                        const double* __restrict__ gllx, double* __restrict__ X) {
+  const int Nx = nx * p + 1, Ny = ny * p + 1, Nz = dim == 3 ? nz * p + 1 : 1;
+  const long long ntot = (long long)Nx * Ny * Nz;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ntot) return;
+  const int I = (int)(gid % Nx), Jn = (int)((gid / Nx) % Ny), K = (int)(gid / ((long long)Nx * Ny));
+  const int ex = min(I / p, nx - 1), ey = min(Jn / p, ny - 1), ez = dim == 3 ? min(K / p, nz - 1) : 0;
+  const double xi[3] = {gllx[I - ex * p], gllx[Jn - ey * p], dim == 3 ? gllx[K - ez * p] : 0.0};
+  const long long NV = (long long)(nx + 1) * (ny + 1) * (dim == 3 ? (nz + 1) : 1);
+  double Pc[8][3];
+  element_corners(dim, nx, ny, ex, ey, ez, vert, NV, Pc);
+  double Xp[3], J[3][3];
+  multilinear(dim, Pc, xi, Xp, J);
+  for (int a = 0; a < dim; ++a) X[a * ntot + gid] = Xp[a];
+}
+
+// K_h stencil row of every level-0 node (all 2^d sub-cells around it).
+__global__ void k_lor_stencil(int dim, int p, int nx, int ny, int nz, const double* __restrict__ X,
+                              const double* __restrict__ kappa, double* __restrict__ S) {
+  const int Nx = nx * p + 1, Ny = ny * p + 1, Nz = dim == 3 ? nz * p + 1 : 1;
+  const long long ntot = (long long)Nx * Ny * Nz;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ntot) return;
+  const int NS = dim == 3 ? 27 : 9;
+  const int I = (int)(gid % Nx), Jn = (int)((gid / Nx) % Ny), K = (int)(gid / ((long long)Nx * Ny));
+  double acc[27];
+  for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+  const double gq = 0.5 - 0.5 / sqrt(3.0);
+  const double g1[2] = {gq, 1.0 - gq};
+  const int ncz = dim == 3 ? 2 : 1;
+  for (int cz = 0; cz < ncz; ++cz)
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cx = 0; cx < 2; ++cx) {
+        // cell with origin (I-1+cx, Jn-1+cy, K-1+cz); this node is its corner (1-cx, 1-cy, 1-cz)
+        const int ox = I - 1 + cx, oy = Jn - 1 + cy, oz = dim == 3 ? K - 1 + cz : 0;
+        if (ox < 0 || ox > Nx - 2 || oy < 0 || oy > Ny - 2) continue;
+        if (dim == 3 && (oz < 0 || oz > Nz - 2)) continue;
+        const int me = (1 - cx) + 2 * (1 - cy) + (dim == 3 ? 4 * (1 - cz) : 0);
+        double Pc[8][3];
+        const int nc = 1 << dim;
+        for (int t = 0; t < nc; ++t) {
+          const long long nid = ((long long)(oz + ((t >> 2) & 1)) * Ny + (oy + ((t >> 1) & 1))) * Nx + (ox + (t & 1));
+          for (int a = 0; a < 3; ++a) Pc[t][a] = a < dim ? X[a * ntot + nid] : 0.0;
+        }
+        const long long e = dim == 3 ? ((long long)(oz / p) * ny + oy / p) * nx + ox / p : (long long)(oy / p) * nx + ox / p;
+        const double kap = kappa[e];
+        const int ngz = dim == 3 ? 2 : 1;
+        for (int gz = 0; gz < ngz; ++gz)
+          for (int gy = 0; gy < 2; ++gy)
+            for (int gx = 0; gx < 2; ++gx) {
+              const double xi[3] = {g1[gx], g1[gy], dim == 3 ? g1[gz] : 0.0};
+              double Xq[3], J[3][3];
+              multilinear(dim, Pc, xi, Xq, J);
+              const double det = dim == 3 ? det3(J) : (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+              double Ji[3][3];
+              inv_dd(dim, J, det, Ji);
+              const double wq = (dim == 3 ? 0.125 : 0.25) * fabs(det) * kap;
+              // reference gradients of the corner functions
+              double gme[3];
+              double gref[8][3];
+              for (int t = 0; t < nc; ++t) {
+                double f[3], df[3];
+                for (int a = 0; a < 3; ++a) {
+                  const int bit = (t >> a) & 1;
+                  f[a] = bit ? xi[a] : 1.0 - xi[a];
+                  df[a] = bit ? 1.0 : -1.0;
+                }
+                for (int bb = 0; bb < dim; ++bb) {
+                  double g = 1.0;
+                  for (int a = 0; a < dim; ++a) g *= (a == bb) ? df[a] : f[a];
+                  gref[t][bb] = g;
+                }
+              }
+              // physical gradient J^{-T} gref
+              double gph[8][3];
+              for (int t = 0; t < nc; ++t)
+                for (int a = 0; a < dim; ++a) {
+                  double s = 0;
+                  for (int bb = 0; bb < dim; ++bb) s += Ji[bb][a] * gref[t][bb];
+                  gph[t][a] = s;
+                }
+              for (int a = 0; a < dim; ++a) gme[a] = gph[me][a];
+              for (int t = 0; t < nc; ++t) {
+                double d = 0;
+                for (int a = 0; a < dim; ++a) d += gme[a] * gph[t][a];
+                const int dx = ox + (t & 1) - I, dy = oy + ((t >> 1) & 1) - Jn, dz = dim == 3 ? oz + ((t >> 2) & 1) - K : 0;
+                const int o = dim == 3 ? (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1) : (dy + 1) * 3 + (dx + 1);
+                acc[o] += wq * d;
+              }
+            }
+      }
+  for (int o = 0; o < NS; ++o) S[(long long)o * ntot + gid] = acc[o];
+}
+
+// Galerkin coarse stencil A_c = P^T A_f P on structured grids with tensor 1D P.
+// Pf: per axis, per fine index: coarse (c0,w0,c1,w1); R: per axis CSR coarse -> fine.
+struct GalerkinArgs {
+  int dim;
+  int Nf[3], Nc[3];
+  const Prolong1D* Pf[3];
+  const int* Rptr[3];
+  const int* Ridx[3];
+  const double* Rw[3];
+};
+
+__global__ void k_galerkin(GalerkinArgs g, const double* __restrict__ Sf, double* __restrict__ Sc) {
+  const long long ntc = (long long)g.Nc[0] * g.Nc[1] * g.Nc[2];
+  const long long ntf = (long long)g.Nf[0] * g.Nf[1] * g.Nf[2];
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ntc) return;
+  const int dim = g.dim;
+  const int NS = dim == 3 ? 27 : 9;
+  const int C[3] = {(int)(gid % g.Nc[0]), (int)((gid / g.Nc[0]) % g.Nc[1]), (int)(gid / ((long long)g.Nc[0] * g.Nc[1]))};
+  double acc[27];
+  for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+  const int zlo = dim == 3 ? g.Rptr[2][C[2]] : 0, zhi = dim == 3 ? g.Rptr[2][C[2] + 1] : 1;
+  for (int iz = zlo; iz < zhi; ++iz) {
+    const int fz = dim == 3 ? g.Ridx[2][iz] : 0;
+    const double wz = dim == 3 ? g.Rw[2][iz] : 1.0;
+    for (int iy = g.Rptr[1][C[1]]; iy < g.Rptr[1][C[1] + 1]; ++iy) {
+      const int fy = g.Ridx[1][iy];
+      const double wy = g.Rw[1][iy];
+      for (int ix = g.Rptr[0][C[0]]; ix < g.Rptr[0][C[0] + 1]; ++ix) {
+        const int fx = g.Ridx[0][ix];
+        const double wi = g.Rw[0][ix] * wy * wz;
+        const long long fi = ((long long)fz * g.Nf[1] + fy) * g.Nf[0] + fx;
+        for (int o = 0; o < NS; ++o) {
+          const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = dim == 3 ? o / 9 - 1 : 0;
+          const int jx = fx + dx, jy = fy + dy, jz = fz + dz;
+          if (jx < 0 || jx >= g.Nf[0] || jy < 0 || jy >= g.Nf[1]) continue;
+          if (dim == 3 && (jz < 0 || jz >= g.Nf[2])) continue;
+          const double a = Sf[(long long)o * ntf + fi];
+          if (a == 0.0) continue;
+          const Prolong1D px = g.Pf[0][jx], py = g.Pf[1][jy];
+          Prolong1D pz;
+          if (dim == 3) pz = g.Pf[2][jz]; else { pz.c0 = 0; pz.w0 = 1.0; pz.c1 = -1; pz.w1 = 0.0; }
+          for (int sz = 0; sz < 2; ++sz) {
+            const int cz = sz ? pz.c1 : pz.c0;
+            const double vz = sz ? pz.w1 : pz.w0;
+            if (cz < 0) continue;
+            for (int sy = 0; sy < 2; ++sy) {
+              const int cy = sy ? py.c1 : py.c0;
+              const double vy = sy ? py.w1 : py.w0;
+              if (cy < 0) continue;
+              for (int sx = 0; sx < 2; ++sx) {
+                const int cx = sx ? px.c1 : px.c0;
+                const double vx = sx ? px.w1 : px.w0;
+                if (cx < 0) continue;
+                const int ox = cx - C[0], oy = cy - C[1], oz = dim == 3 ? cz - C[2] : 0;
+                const int oc = dim == 3 ? (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1) : (oy + 1) * 3 + (ox + 1);
+                acc[oc] += wi * a * vx * vy * vz;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  for (int o = 0; o < NS; ++o) Sc[(long long)o * ntc + gid] = acc[o];
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __double2bfloat16(a[i]);
+}
+
+// ILU(0) of every patch at one level.  One CTA per patch; rows in wavefront order.
+struct IluArgs {
+  int dim, NS;
+  int n[3];            // elements per direction
+  int m;               // intervals per element at this level
+  int N[3];            // level grid
+  const BoxShape* shapes;   // 8 shapes of this level
+  const int* rowlex;
+  const int* front;
+  const int* poslex;   // lex -> pos, per shape (offset = shape.row_off)
+  const long long* facoff;  // this level's offsets [J]
+  const double* S;
+  double* F;
+  int* status;
+};
+
+__device__ inline void patch_vertex(int j, const int* n, int dim, int* v) {
+  v[0] = j % (n[0] + 1);
+  v[1] = (j / (n[0] + 1)) % (n[1] + 1);
+  v[2] = dim == 3 ? j / ((n[0] + 1) * (n[1] + 1)) : 0;
+}
+
+__global__ void k_ilu0(IluArgs a) {
+  const int j = blockIdx.x;
+  int v[3];
+  patch_vertex(j, a.n, a.dim, v);
+  int sh = 0;
+  for (int t = 0; t < a.dim; ++t) sh |= ((v[t] == 0 || v[t] == a.n[t]) ? 1 : 0) << t;
+  const BoxShape bs = a.shapes[sh];
+  if (bs.rows == 0) return;
+  const int dx0 = bs.dims[0], dy0 = bs.dims[1], dz0 = bs.dims[2];
+  int org[3];
+  for (int t = 0; t < 3; ++t) org[t] = (t < a.dim) ? (v[t] > 0 ? v[t] - 1 : 0) * a.m + 1 : 0;
+  const long long ntot = (long long)a.N[0] * a.N[1] * a.N[2];
+  double* F = a.F + a.facoff[j];
+  const int rows = bs.rows;
+  const int* rowlex = a.rowlex + bs.row_off;
+  const int* poslex = a.poslex + bs.row_off;
+  const int* front = a.front + bs.front_off;
+  const int NS = a.NS, C = NS / 2;
+  for (int f = 0; f < bs.nfront; ++f) {
+    for (int pos = front[f] + threadIdx.x; pos < front[f + 1]; pos += blockDim.x) {
+      const int lex = rowlex[pos];
+      const int i = lex % dx0, jj = (lex / dx0) % dy0, k = lex / (dx0 * dy0);
+      const long long G = ((long long)(org[2] + k) * a.N[1] + (org[1] + jj)) * a.N[0] + (org[0] + i);
+      double r[27];
+      for (int o = 0; o < NS; ++o) {
+        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = a.dim == 3 ? o / 9 - 1 : 0;
+        const int ni = i + ox, nj = jj + oy, nk = k + oz;
+        const bool in = ni >= 0 && ni < dx0 && nj >= 0 && nj < dy0 && nk >= 0 && nk < dz0;
+        r[o] = in ? a.S[(long long)o * ntot + G] : 0.0;
+      }
+      for (int o = 0; o < C; ++o) {            // lower neighbours, ascending column order
+        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = a.dim == 3 ? o / 9 - 1 : 0;
+        const int ni = i + ox, nj = jj + oy, nk = k + oz;
+        if (!(ni >= 0 && ni < dx0 && nj >= 0 && nj < dy0 && nk >= 0 && nk < dz0)) continue;
+        const int kp = poslex[(nk * dy0 + nj) * dx0 + ni];
+        const double l = r[o] * F[(long long)C * rows + kp];   // a_ik / u_kk
+        r[o] = l;
+        for (int o2 = C + 1; o2 < NS; ++o2) {   // upper part of row k
+          const int px = ox + (o2 % 3 - 1), py = oy + ((o2 / 3) % 3 - 1), pz = oz + (a.dim == 3 ? o2 / 9 - 1 : 0);
+          if (px < -1 || px > 1 || py < -1 || py > 1 || pz < -1 || pz > 1) continue;
+          const int ot = a.dim == 3 ? (pz + 1) * 9 + (py + 1) * 3 + (px + 1) : (py + 1) * 3 + (px + 1);
+          if (ot <= o) continue;                // only entries to the right of column k
+          r[ot] -= l * F[(long long)o2 * rows + kp];
+        }
+      }
+      const int pos_me = pos;
+      if (!(r[C] > 0.0)) atomicOr(a.status, 2);
+      for (int o = 0; o < NS; ++o) F[(long long)o * rows + pos_me] = (o == C) ? 1.0 / r[C] : r[o];
+    }
+    __syncthreads();
+  }
+}
+
+// l1 row sums over interior neighbours, inverted; boundary rows get 0.
+__global__ void k_l1_dinv(int dim, int Nx, int Ny, int Nz, const double* __restrict__ S, double* __restrict__ D64,
+                          float* __restrict__ D32) {
+  const long long ntot = (long long)Nx * Ny * Nz;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ntot) return;
+  const int I = (int)(gid % Nx), Jn = (int)((gid / Nx) % Ny), K = (int)(gid / ((long long)Nx * Ny));
+  const bool bnd = I == 0 || I == Nx - 1 || Jn == 0 || Jn == Ny - 1 || (dim == 3 && (K == 0 || K == Nz - 1));
+  double s = 0;
+  const int NS = dim == 3 ? 27 : 9;
+  if (!bnd) {
+    for (int o = 0; o < NS; ++o) {
+      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = dim == 3 ? o / 9 - 1 : 0;
+      const int a = I + dx, b = Jn + dy, c = K + dz;
+      const bool nb = a == 0 || a == Nx - 1 || b == 0 || b == Ny - 1 || (dim == 3 && (c == 0 || c == Nz - 1));
+      if (!nb) s += fabs(S[(long long)o * ntot + gid]);
+    }
+  }
+  const double di = bnd ? 0.0 : 1.0 / s;
+  D64[gid] = di;
+  D32[gid] = (float)di;
+}
+
+}  // namespace
+
+// ============================================================== host-side setup
+static lor_status upload(lor_ctx* c, void** dst, const void* src, size_t bytes) {
+  *dst = lor_alloc(c, bytes);
+  if (!*dst) return lor_fail(c, LOR_ENOMEM, "device allocation failed");
+  return lor_cuda_check(c, cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, c->stream), "upload");
+}
+
+static lor_status check_status(lor_ctx* c, const char* what) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return lor_cuda_check(c, e, what);
+  if (st & 1) return lor_fail(c, LOR_EINVAL, "inverted element: det J <= 0 at a quadrature point");
+  if (st & 2) return lor_fail(c, LOR_EBREAKDOWN, "ILU(0) breakdown: non-positive pivot");
+  return LOR_OK;
+}
+
+lor_status lor_setup_geometry(lor_ctx* c) {
+  const int p = c->p, Q = p + 1;
+  // basis block (allocation 0: doubles, allocation 1: floats)
+  std::vector<double> h64(5 * kBlk, 0.0);
+  std::vector<float> h32(2 * kBlk, 0.0f);
+  lorh::gll(p, c->gll_x, c->gll_w);
+  lorh::gauss(Q, c->gl_x, c->gl_w);
+  double Dn[(LOR_MAXP + 2) * (LOR_MAXP + 2)];
+  lorh::lagrange(Q, c->gll_x, Q, c->gl_x, c->B, Dn);          // B[q][i] at Gauss points
+  double Bg[(LOR_MAXP + 2) * (LOR_MAXP + 2)];
+  lorh::lagrange(Q, c->gl_x, Q, c->gl_x, Bg, c->Dq);          // Gauss-nodal differentiation
+  for (int i = 0; i < Q * Q; ++i) {
+    h64[0 * kBlk + i] = c->B[i];
+    h64[1 * kBlk + i] = c->Dq[i];
+    h32[0 * kBlk + i] = (float)c->B[i];
+    h32[1 * kBlk + i] = (float)c->Dq[i];
+  }
+  for (int i = 0; i < Q; ++i) {
+    h64[2 * kBlk + i] = c->gl_x[i];
+    h64[3 * kBlk + i] = c->gl_w[i];
+    h64[4 * kBlk + i] = c->gll_x[i];
+  }
+  void* d;
+  if (upload(c, &d, h64.data(), h64.size() * 8)) return LOR_ENOMEM;
+  if (upload(c, &d, h32.data(), h32.size() * 4)) return LOR_ENOMEM;
+  c->d_status = (int*)lor_alloc(c, 64);
+  if (!c->d_status) return lor_fail(c, LOR_ENOMEM, "alloc status");
+  cudaMemsetAsync(c->d_status, 0, 64, c->stream);
+  // mesh
+  if (upload(c, (void**)&c->d_vert, c->h_vert.data(), c->h_vert.size() * 8)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_kappa, c->h_kappa.data(), c->h_kappa.size() * 8)) return LOR_ENOMEM;
+  // geometric factors
+  const int Qd = c->dim == 3 ? Q * Q * Q : Q * Q;
+  const int ncomp = c->dim == 3 ? 6 : 3;
+  const long long ng = (long long)c->nel * ncomp * Qd;
+  c->d_G64 = (double*)lor_alloc(c, ng * 8);
+  c->d_G32 = (float*)lor_alloc(c, ng * 4);
+  if (!c->d_G64 || !c->d_G32) return lor_fail(c, LOR_ENOMEM, "alloc geometric factors");
+  const long long tot = (long long)c->nel * Qd;
+  k_geom<<<(unsigned)lor_ceil_div(tot, 128), 128, 0, c->stream>>>(
+      c->dim, p, c->n[0], c->n[1], c->n[2], c->d_vert, c->d_kappa, lor_basis64(c, 2), lor_basis64(c, 3),
+      c->d_G64, c->d_G32, c->d_status);
+  if (lor_cuda_check(c, cudaGetLastError(), "geometry")) return LOR_ECUDA;
+  return check_status(c, "geometry");
+}
+
+// 1D global prolongation (level l+1 -> l) of one axis with nel elements:
+// linear interpolation in the element reference coordinate (GLL positions).
+static std::vector<Prolong1D> prolong_axis(int nel, const double* gllx, const std::vector<int>& sf,
+                                           const std::vector<int>& sc) {
+  const int mf = (int)sf.size() - 1, mc = (int)sc.size() - 1;
+  std::vector<Prolong1D> P(nel * mf + 1);
+  for (int e = 0; e < nel; ++e)
+    for (int t = 0; t <= mf; ++t) {
+      const int g = sf[t];
+      int a = 0;
+      while (a + 1 <= mc && sc[a + 1] <= g) ++a;
+      Prolong1D pr;
+      if (sc[a] == g) { pr.c0 = e * mc + a; pr.w0 = 1.0; pr.c1 = -1; pr.w1 = 0.0; }
+      else {
+        const double w = (gllx[g] - gllx[sc[a]]) / (gllx[sc[a + 1]] - gllx[sc[a]]);
+        pr.c0 = e * mc + a; pr.w0 = 1.0 - w; pr.c1 = e * mc + a + 1; pr.w1 = w;
+      }
+      P[e * mf + t] = pr;
+    }
+  return P;
+}
+
+// coarse-vertex-grid 1D coarsening (keep even positions + last), index-space weights
+static std::vector<Prolong1D> prolong_index(int nf, int* nc_out) {
+  std::vector<int> keep;
+  for (int i = 0; i < nf; i += 2) keep.push_back(i);
+  if (keep.back() != nf - 1) keep.push_back(nf - 1);
+  *nc_out = (int)keep.size();
+  std::vector<Prolong1D> P(nf);
+  for (int i = 0; i < nf; ++i) {
+    int b = 0;
+    while (keep[b] < i) ++b;
+    Prolong1D pr;
+    if (keep[b] == i) { pr.c0 = b; pr.w0 = 1.0; pr.c1 = -1; pr.w1 = 0.0; }
+    else {
+      const double w = double(i - keep[b - 1]) / double(keep[b] - keep[b - 1]);
+      pr.c0 = b - 1; pr.w0 = 1.0 - w; pr.c1 = b; pr.w1 = w;
+    }
+    P[i] = pr;
+  }
+  return P;
+}
+
+// transpose of a 1D prolongation as CSR (coarse -> list of fine with weights)
+static void restrict_csr(const std::vector<Prolong1D>& P, int nc, std::vector<int>& ptr, std::vector<int>& idx,
+                         std::vector<double>& w) {
+  std::vector<std::vector<std::pair<int, double>>> rows(nc);
+  for (int f = 0; f < (int)P.size(); ++f) {
+    if (P[f].c0 >= 0 && P[f].w0 != 0.0) rows[P[f].c0].push_back({f, P[f].w0});
+    if (P[f].c1 >= 0 && P[f].w1 != 0.0) rows[P[f].c1].push_back({f, P[f].w1});
+  }
+  ptr.assign(nc + 1, 0);
+  idx.clear();
+  w.clear();
+  for (int cidx = 0; cidx < nc; ++cidx) {
+    for (auto& pr : rows[cidx]) { idx.push_back(pr.first); w.push_back(pr.second); }
+    ptr[cidx + 1] = (int)idx.size();
+  }
+}
+
+static lor_status upload_prolong(lor_ctx* c, const std::vector<Prolong1D>& P, int nc, Prolong1D** dP, int** dptr,
+                                 int** didx, double** dw) {
+  std::vector<int> ptr, idx;
+  std::vector<double> w;
+  restrict_csr(P, nc, ptr, idx, w);
+  if (upload(c, (void**)dP, P.data(), P.size() * sizeof(Prolong1D))) return LOR_ENOMEM;
+  if (upload(c, (void**)dptr, ptr.data(), ptr.size() * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)didx, idx.data(), std::max<size_t>(1, idx.size()) * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)dw, w.data(), std::max<size_t>(1, w.size()) * 8)) return LOR_ENOMEM;
+  return LOR_OK;
+}
+
+static lor_status galerkin(lor_ctx* c, int dim, const int* Nf, const int* Nc, Prolong1D* const* P,
+                           int* const* Rptr, int* const* Ridx, double* const* Rw, const double* Sf, double* Sc) {
+  GalerkinArgs g;
+  g.dim = dim;
+  for (int a = 0; a < 3; ++a) {
+    g.Nf[a] = Nf[a]; g.Nc[a] = Nc[a];
+    g.Pf[a] = P[a]; g.Rptr[a] = Rptr[a]; g.Ridx[a] = Ridx[a]; g.Rw[a] = Rw[a];
+  }
+  const long long ntc = (long long)Nc[0] * Nc[1] * Nc[2];
+  k_galerkin<<<(unsigned)lor_ceil_div(ntc, 128), 128, 0, c->stream>>>(g, Sf, Sc);
+  return lor_cuda_check(c, cudaGetLastError(), "galerkin");
+}
+
+lor_status lor_setup_stencils(lor_ctx* c) {
+  const int dim = c->dim, p = c->p;
+  c->NS = dim == 3 ? 27 : 9;
+  c->sel = lorh::level_selections(p, c->opt.mg_levels);
+  c->L = (int)c->sel.size();
+  if (c->L > LOR_MAXLEV) return lor_fail(c, LOR_EINVAL, "too many levels");
+  for (int l = 0; l < c->L; ++l) {
+    LevelGrid& g = c->lev[l];
+    g.m = (int)c->sel[l].size() - 1;
+    for (int a = 0; a < 3; ++a) g.N[a] = a < dim ? c->n[a] * g.m + 1 : 1;
+    g.ntot = (long long)g.N[0] * g.N[1] * g.N[2];
+  }
+  const long long nt0 = c->lev[0].ntot;
+  c->d_X = (double*)lor_alloc(c, nt0 * dim * 8);
+  if (!c->d_X) return lor_fail(c, LOR_ENOMEM, "alloc coordinates");
+  k_nodes<<<(unsigned)lor_ceil_div(nt0, 128), 128, 0, c->stream>>>(dim, p, c->n[0], c->n[1], c->n[2], c->d_vert,
+                                                                     lor_basis64(c, 4), c->d_X);
+  for (int l = 0; l < c->L; ++l) {
+    const long long nt = c->lev[l].ntot;
+    c->d_S64[l] = (double*)lor_alloc(c, nt * c->NS * 8);
+    c->d_S32[l] = (float*)lor_alloc(c, nt * c->NS * 4);
+    if (!c->d_S64[l] || !c->d_S32[l]) return lor_fail(c, LOR_ENOMEM, "alloc stencils");
+  }
+  k_lor_stencil<<<(unsigned)lor_ceil_div(nt0, 128), 128, 0, c->stream>>>(dim, p, c->n[0], c->n[1], c->n[2], c->d_X,
+                                                                           c->d_kappa, c->d_S64[0]);
+  if (lor_cuda_check(c, cudaGetLastError(), "lor stencil")) return LOR_ECUDA;
+  for (int l = 0; l + 1 < c->L; ++l) {
+    for (int a = 0; a < dim; ++a) {
+      std::vector<Prolong1D> P = prolong_axis(c->n[a], c->gll_x, c->sel[l], c->sel[l + 1]);
+      if (upload_prolong(c, P, c->lev[l + 1].N[a], &c->d_P1[l][a], &c->d_R1ptr[l][a], &c->d_R1idx[l][a],
+                         &c->d_R1w[l][a]))
+        return LOR_ENOMEM;
+    }
+    if (galerkin(c, dim, c->lev[l].N, c->lev[l + 1].N, c->d_P1[l], c->d_R1ptr[l], c->d_R1idx[l], c->d_R1w[l],
+                 c->d_S64[l], c->d_S64[l + 1]))
+      return LOR_ECUDA;
+  }
+  for (int l = 0; l < c->L; ++l) {
+    const long long n = c->lev[l].ntot * c->NS;
+    k_to_float<<<(unsigned)lor_ceil_div(n, 256), 256, 0, c->stream>>>(c->d_S64[l], c->d_S32[l], n);
+  }
+  return lor_cuda_check(c, cudaGetLastError(), "stencil conversion");
+}
+
+// ------------------------------------------------------------ patch structures
+static int axis_len(int type, int m) { return type == 0 ? 2 * m - 1 : m - 1; }
+
+lor_status lor_setup_patches(lor_ctx* c) {
+  const int dim = c->dim;
+  c->J = 1;
+  for (int a = 0; a < dim; ++a) c->J *= (c->n[a] + 1);
+  const int nshape = 1 << dim;
+  std::vector<int> front, rowpad, rowlex, poslex;
+  c->shapes.assign(c->L * 8, BoxShape());
+  for (int l = 0; l < c->L; ++l) {
+    const int m = c->lev[l].m;
+    for (int s = 0; s < nshape; ++s) {
+      BoxShape bs;
+      for (int a = 0; a < 3; ++a) bs.dims[a] = a < dim ? axis_len((s >> a) & 1, m) : 1;
+      // an axis with a single element has both ends on the boundary: its patches
+      // only ever use the boundary shape, so nothing special is needed here.
+      bs.rows = bs.dims[0] * bs.dims[1] * bs.dims[2];
+      const int A = bs.dims[0], Bd = bs.dims[1], Cd = bs.dims[2];
+      const int nfront = bs.rows ? (A - 1) + 2 * (Bd - 1) + (dim == 3 ? 4 * (Cd - 1) : 0) + 1 : 0;
+      bs.nfront = nfront;
+      bs.front_off = (int)front.size();
+      bs.row_off = (int)rowlex.size();
+      std::vector<std::vector<int>> byf(std::max(nfront, 0));
+      for (int k = 0; k < Cd; ++k)
+        for (int j = 0; j < Bd; ++j)
+          for (int i = 0; i < A; ++i) byf[i + 2 * j + 4 * k].push_back((k * Bd + j) * A + i);
+      std::vector<int> pl(bs.rows);
+      front.push_back(0);
+      int pos = 0;
+      for (int f = 0; f < nfront; ++f) {
+        for (int lex : byf[f]) {
+          const int i = lex % A, j = (lex / A) % Bd, k = lex / (A * Bd);
+          rowlex.push_back(lex);
+          const int pz = dim == 3 ? (k + 1) : 0;
+          rowpad.push_back((pz * (Bd + 2) + (j + 1)) * (A + 2) + (i + 1));
+          pl[lex] = pos++;
+        }
+        front.push_back(pos);
+      }
+      for (int t = 0; t < bs.rows; ++t) poslex.push_back(pl[t]);
+      c->shapes[l * 8 + s] = bs;
+    }
+  }
+  if (upload(c, (void**)&c->d_front, front.data(), front.size() * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_rowpad, rowpad.data(), std::max<size_t>(1, rowpad.size()) * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_rowlex, rowlex.data(), std::max<size_t>(1, rowlex.size()) * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_poslex, poslex.data(), std::max<size_t>(1, poslex.size()) * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_shapes, c->shapes.data(), c->shapes.size() * sizeof(BoxShape))) return LOR_ENOMEM;
+  int* d_poslex = c->d_poslex;
+  BoxShape* d_shapes = c->d_shapes;
+
+  // patch-local 1D prolongation per level and axis type (fine local -> coarse local)
+  for (int l = 0; l + 1 < c->L; ++l) {
+    const int m = c->lev[l].m, mc = c->lev[l + 1].m;
+    for (int type = 0; type < 2; ++type) {
+      // model axis: interior type = vertex 1 of 2 elements; boundary type = vertex 0
+      const int v = type == 0 ? 1 : 0, nel = type == 0 ? 2 : 1;
+      std::vector<Prolong1D> P = prolong_axis(nel, c->gll_x, c->sel[l], c->sel[l + 1]);
+      const int len = axis_len(type, m);
+      const int of = (v > 0 ? v - 1 : 0) * m + 1, oc = (v > 0 ? v - 1 : 0) * mc + 1;
+      std::vector<Prolong1D> loc(std::max(len, 1));
+      for (int f = 0; f < len; ++f) {
+        Prolong1D pr = P[of + f];
+        pr.c0 = pr.c0 >= 0 ? pr.c0 - oc : -2;
+        pr.c1 = pr.c1 >= 0 ? pr.c1 - oc : -2;
+        loc[f] = pr;   // local coarse index in [-1, clen]; -1 / clen are the patch boundary
+      }
+      if (upload(c, (void**)&c->d_pp[l][type], loc.data(), loc.size() * sizeof(Prolong1D))) return LOR_ENOMEM;
+      // transpose: for every coarse local index the (<= 3) fine local indices feeding it
+      const int clen = axis_len(type, mc);
+      std::vector<RestrictEntry> rr(std::max(clen, 1));
+      for (auto& e : rr) for (int t = 0; t < 3; ++t) { e.f[t] = -1; e.w[t] = 0.0; }
+      for (int f = 0; f < len; ++f) {
+        const int cs[2] = {loc[f].c0, loc[f].c1};
+        const double ws[2] = {loc[f].w0, loc[f].w1};
+        for (int s2 = 0; s2 < 2; ++s2) {
+          if (cs[s2] < 0 || cs[s2] >= clen || ws[s2] == 0.0) continue;
+          RestrictEntry& e = rr[cs[s2]];
+          int t = 0;
+          while (t < 3 && e.f[t] >= 0) ++t;
+          if (t == 3) return lor_fail(c, LOR_EINVAL, "restriction stencil wider than 3");
+          e.f[t] = f; e.w[t] = ws[s2];
+        }
+      }
+      if (upload(c, (void**)&c->d_rr[l][type], rr.data(), rr.size() * sizeof(RestrictEntry))) return LOR_ENOMEM;
+    }
+  }
+
+  // factor storage offsets
+  std::vector<long long> off((size_t)c->L * c->J);
+  long long tot = 0;
+  for (int l = 0; l < c->L; ++l)
+    for (int j = 0; j < c->J; ++j) {
+      int v[3] = {j % (c->n[0] + 1), (j / (c->n[0] + 1)) % (c->n[1] + 1), dim == 3 ? j / ((c->n[0] + 1) * (c->n[1] + 1)) : 0};
+      int sh = 0;
+      for (int a = 0; a < dim; ++a) sh |= ((v[a] == 0 || v[a] == c->n[a]) ? 1 : 0) << a;
+      off[(size_t)l * c->J + j] = tot;
+      tot += (long long)c->shapes[l * 8 + sh].rows * c->NS;
+    }
+  c->fac_rows = tot / c->NS;
+  if (upload(c, (void**)&c->d_facoff, off.data(), off.size() * 8)) return LOR_ENOMEM;
+  c->d_F64 = (double*)lor_alloc(c, std::max<long long>(tot, 1) * 8);
+  c->d_F32 = (float*)lor_alloc(c, std::max<long long>(tot, 1) * 4);
+  if (c->opt.factor_bf16) c->d_F16 = (__nv_bfloat16*)lor_alloc(c, std::max<long long>(tot, 1) * 2);
+  if (!c->d_F64 || !c->d_F32 || (c->opt.factor_bf16 && !c->d_F16)) return lor_fail(c, LOR_ENOMEM, "alloc factors");
+  // ILU(0) per level (the last level is solved exactly and needs no factors)
+  for (int l = 0; l + 1 < c->L; ++l) {
+    IluArgs a;
+    a.dim = dim; a.NS = c->NS;
+    for (int t = 0; t < 3; ++t) { a.n[t] = c->n[t]; a.N[t] = c->lev[l].N[t]; }
+    a.m = c->lev[l].m;
+    a.shapes = d_shapes + l * 8;
+    a.rowlex = c->d_rowlex; a.front = c->d_front; a.poslex = d_poslex;
+    a.facoff = c->d_facoff + (size_t)l * c->J;
+    a.S = c->d_S64[l];
+    a.F = c->d_F64;
+    a.status = c->d_status;
+    k_ilu0<<<c->J, 128, 0, c->stream>>>(a);
+    if (lor_cuda_check(c, cudaGetLastError(), "ilu0")) return LOR_ECUDA;
+  }
+  k_to_float<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F32, tot);
+  if (c->d_F16) k_to_bf16<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F16, tot);
+  if (lor_cuda_check(c, cudaGetLastError(), "factor conversion")) return LOR_ECUDA;
+  return check_status(c, "ilu0");
+}
+
+// ------------------------------------------------------------------ coarse space
+lor_status lor_setup_coarse(lor_ctx* c) {
+  const int dim = c->dim;
+  // level 0 of the coarse hierarchy = the vertex level of the patch hierarchy
+  const LevelGrid& lv = c->lev[c->L - 1];
+  for (int a = 0; a < 3; ++a) c->cN[0][a] = lv.N[a];
+  c->cntot[0] = lv.ntot;
+  c->d_cS64[0] = c->d_S64[c->L - 1];
+  c->d_cS32[0] = c->d_S32[c->L - 1];
+  auto interior = [&](int l) {
+    long long s = 1;
+    for (int a = 0; a < dim; ++a) s *= std::max(c->cN[l][a] - 2, 0);
+    return s;
+  };
+  int l = 0;
+  while (interior(l) > 343 && l + 1 < LOR_MAXCLEV) {
+    int Nc[3] = {1, 1, 1};
+    for (int a = 0; a < dim; ++a) {
+      int ncn;
+      std::vector<Prolong1D> P = prolong_index(c->cN[l][a], &ncn);
+      Nc[a] = ncn;
+      if (upload_prolong(c, P, ncn, &c->d_cP1[l][a], &c->d_cR1ptr[l][a], &c->d_cR1idx[l][a], &c->d_cR1w[l][a]))
+        return LOR_ENOMEM;
+    }
+    for (int a = 0; a < 3; ++a) c->cN[l + 1][a] = Nc[a];
+    c->cntot[l + 1] = (long long)Nc[0] * Nc[1] * Nc[2];
+    c->d_cS64[l + 1] = (double*)lor_alloc(c, c->cntot[l + 1] * c->NS * 8);
+    c->d_cS32[l + 1] = (float*)lor_alloc(c, c->cntot[l + 1] * c->NS * 4);
+    if (!c->d_cS64[l + 1] || !c->d_cS32[l + 1]) return lor_fail(c, LOR_ENOMEM, "alloc coarse stencils");
+    if (galerkin(c, dim, c->cN[l], c->cN[l + 1], c->d_cP1[l], c->d_cR1ptr[l], c->d_cR1idx[l], c->d_cR1w[l],
+                 c->d_cS64[l], c->d_cS64[l + 1]))
+      return LOR_ECUDA;
+    const long long n = c->cntot[l + 1] * c->NS;
+    k_to_float<<<(unsigned)lor_ceil_div(n, 256), 256, 0, c->stream>>>(c->d_cS64[l + 1], c->d_cS32[l + 1], n);
+    ++l;
+  }
+  c->CL = l + 1;
+  for (int t = 0; t < c->CL; ++t) {
+    const long long nt = c->cntot[t];
+    c->d_cDinv64[t] = (double*)lor_alloc(c, nt * 8);
+    c->d_cDinv32[t] = (float*)lor_alloc(c, nt * 4);
+    for (int k = 0; k < 4; ++k) {
+      c->d_cw64[t][k] = (double*)lor_alloc(c, nt * 8);
+      c->d_cw32[t][k] = (float*)lor_alloc(c, nt * 4);
+      if (!c->d_cw64[t][k] || !c->d_cw32[t][k]) return lor_fail(c, LOR_ENOMEM, "alloc coarse vectors");
+    }
+    if (!c->d_cDinv64[t] || !c->d_cDinv32[t]) return lor_fail(c, LOR_ENOMEM, "alloc coarse diag");
+    k_l1_dinv<<<(unsigned)lor_ceil_div(nt, 128), 128, 0, c->stream>>>(dim, c->cN[t][0], c->cN[t][1], c->cN[t][2],
+                                                                        c->d_cS64[t], c->d_cDinv64[t], c->d_cDinv32[t]);
+  }
+  if (lor_cuda_check(c, cudaGetLastError(), "coarse setup")) return LOR_ECUDA;
+  // dense inverse of the coarsest operator (interior unknowns) on the host
+  const int t = c->CL - 1;
+  const long long nt = c->cntot[t];
+  std::vector<double> S(nt * c->NS);
+  cudaError_t e = cudaMemcpyAsync(S.data(), c->d_cS64[t], S.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return lor_cuda_check(c, e, "coarse copy");
+  const int* N = c->cN[t];
+  std::vector<int> idx;
+  std::vector<long long> where(nt, -1);
+  for (long long g = 0; g < nt; ++g) {
+    const int I = (int)(g % N[0]), Jn = (int)((g / N[0]) % N[1]), K = (int)(g / ((long long)N[0] * N[1]));
+    const bool bnd = I == 0 || I == N[0] - 1 || Jn == 0 || Jn == N[1] - 1 || (dim == 3 && (K == 0 || K == N[2] - 1));
+    if (!bnd) { where[g] = (long long)idx.size(); idx.push_back((int)g); }
+  }
+  const int nd = (int)idx.size();
+  c->ncoarse_direct = nd;
+  std::vector<double> A((size_t)nd * nd, 0.0), Inv((size_t)nd * nd, 0.0);
+  for (int r = 0; r < nd; ++r) {
+    const long long g = idx[r];
+    const int I = (int)(g % N[0]), Jn = (int)((g / N[0]) % N[1]), K = (int)(g / ((long long)N[0] * N[1]));
+    for (int o = 0; o < c->NS; ++o) {
+      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = dim == 3 ? o / 9 - 1 : 0;
+      const long long h = ((long long)(K + dz) * N[1] + (Jn + dy)) * N[0] + (I + dx);
+      if (h < 0 || h >= nt || where[h] < 0) continue;
+      A[(size_t)r * nd + where[h]] = S[(size_t)o * nt + g];
+    }
+  }
+  // Cholesky A = L L^T, then columns of A^{-1}
+  std::vector<double> Lc((size_t)nd * nd, 0.0);
+  for (int j = 0; j < nd; ++j) {
+    double s = A[(size_t)j * nd + j];
+    for (int k = 0; k < j; ++k) s -= Lc[(size_t)j * nd + k] * Lc[(size_t)j * nd + k];
+    if (!(s > 0)) return lor_fail(c, LOR_EBREAKDOWN, "coarse Cholesky: matrix not positive definite");
+    const double d = sqrt(s);
+    Lc[(size_t)j * nd + j] = d;
+    for (int i = j + 1; i < nd; ++i) {
+      double t2 = A[(size_t)i * nd + j];
+      for (int k = 0; k < j; ++k) t2 -= Lc[(size_t)i * nd + k] * Lc[(size_t)j * nd + k];
+      Lc[(size_t)i * nd + j] = t2 / d;
+    }
+  }
+  std::vector<double> y(nd);
+  for (int col = 0; col < nd; ++col) {
+    for (int i = 0; i < nd; ++i) {
+      double s = (i == col) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= Lc[(size_t)i * nd + k] * y[k];
+      y[i] = s / Lc[(size_t)i * nd + i];
+    }
+    for (int i = nd - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int k = i + 1; k < nd; ++k) s -= Lc[(size_t)k * nd + i] * Inv[(size_t)k * nd + col];
+      Inv[(size_t)i * nd + col] = s / Lc[(size_t)i * nd + i];
+    }
+  }
+  std::vector<float> Inv32(Inv.begin(), Inv.end());
+  if (nd > 0) {
+    if (upload(c, (void**)&c->d_cdirect_idx, idx.data(), idx.size() * 4)) return LOR_ENOMEM;
+    if (upload(c, (void**)&c->d_cInv64, Inv.data(), Inv.size() * 8)) return LOR_ENOMEM;
+    if (upload(c, (void**)&c->d_cInv32, Inv32.data(), Inv32.size() * 4)) return LOR_ENOMEM;
+  }
+  e = cudaStreamSynchronize(c->stream);
+  return lor_cuda_check(c, e, "coarse setup");
+}

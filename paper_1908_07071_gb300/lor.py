@@ -1,0 +1,191 @@
+"""ctypes binding of the C ABI in include/lor.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library ``liblor.so``; this module only
+checks tensor dtypes/sizes and passes raw device pointers and the current CUDA
+stream.  Importing it raises if the library has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblor.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "lor.h")
+
+LOR_OK, LOR_EINVAL, LOR_ENOMEM, LOR_ECUDA, LOR_EBREAKDOWN, LOR_ENAN, LOR_ENOCONV, LOR_ETIMEOUT, LOR_ESTATE = range(9)
+LOR_CG, LOR_DG_IP, LOR_DG_BR2 = 0, 1, 2
+LOR_FP64, LOR_FP32, LOR_MIXED = 0, 1, 2
+STATUS_NAMES = {0: "LOR_OK", 1: "LOR_EINVAL", 2: "LOR_ENOMEM", 3: "LOR_ECUDA", 4: "LOR_EBREAKDOWN",
+                5: "LOR_ENAN", 6: "LOR_ENOCONV", 7: "LOR_ETIMEOUT", 8: "LOR_ESTATE"}
+
+
+class LorError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("p", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("disc", ctypes.c_int), ("eta", ctypes.c_double),
+                ("mg_levels", ctypes.c_int), ("prec", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("max_it", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("factor_bf16", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nvec", ctypes.c_longlong), ("ndof", ctypes.c_longlong), ("npatch", ctypes.c_longlong),
+                ("ncoarse", ctypes.c_longlong), ("levels", ctypes.c_int), ("coarse_levels", ctypes.c_int),
+                ("factor_rows", ctypes.c_longlong), ("device_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load():
+    """Loads liblor.so (raises FileNotFoundError if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FileNotFoundError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    pi, pd = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    lib.lor_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.lor_default_options.restype = None
+    lib.lor_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Options), vp, vp, vp]
+    lib.lor_setup.argtypes = [vp]
+    lib.lor_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.lor_rhs.argtypes = [vp, i, vp]
+    lib.lor_apply_A.argtypes = [vp, vp, vp, i]
+    lib.lor_apply_P.argtypes = [vp, vp, vp, i]
+    lib.lor_pcg_solve.argtypes = [vp, vp, vp, pi, pd]
+    lib.lor_pcg_solve_host.argtypes = [vp, vp, vp, pi, pd]
+    lib.lor_residual_history.argtypes = [vp, pd, i, pi]
+    lib.lor_last_error.argtypes = [vp]
+    lib.lor_last_error.restype = ctypes.c_char_p
+    lib.lor_destroy.argtypes = [vp]
+    lib.lor_destroy.restype = None
+    for name in ("lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
+                 "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def header_functions():
+    """Names of the functions declared in include/lor.h."""
+    txt = open(HEADER).read()
+    decl = r"^\s*(?:lor_status|void|const\s+char\s*\*)\s*(lor_\w+)\s*\("
+    return sorted(set(re.findall(decl, txt, re.M)))
+
+
+def _ptr(t, dtype, n, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One LOR-preconditioned problem on the current CUDA device and stream."""
+
+    def __init__(self, vertices, kappa, p, *, mg_levels=0, prec=LOR_FP64, rtol=1e-8, max_it=1000,
+                 inner_rtol=1e-3, factor_bf16=False, stream=None):
+        import torch
+        self.lib = load()
+        vertices = np.ascontiguousarray(vertices, dtype=np.float64)
+        kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+        dim = vertices.shape[0]
+        n = list(reversed(kappa.shape))
+        opt = Options()
+        self.lib.lor_default_options(ctypes.byref(opt))
+        opt.dim, opt.p = dim, p
+        opt.nx, opt.ny = n[0], n[1]
+        opt.nz = n[2] if dim == 3 else 1
+        opt.mg_levels, opt.prec, opt.rtol, opt.max_it = mg_levels, prec, rtol, max_it
+        opt.inner_rtol, opt.factor_bf16 = inner_rtol, int(bool(factor_bf16))
+        self.opt = opt
+        self.dim, self.p, self.n = dim, p, tuple(n)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        ctx = ctypes.c_void_p()
+        st = self.lib.lor_create(ctypes.byref(ctx), ctypes.byref(opt), vertices.ctypes.data_as(ctypes.c_void_p),
+                                 kappa.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(stream))
+        if st != LOR_OK:
+            raise LorError(st, "lor_create rejected the input")
+        self.ctx = ctx
+        self._check(self.lib.lor_setup(ctx))
+        self.info = Info()
+        self._check(self.lib.lor_get_info(ctx, ctypes.byref(self.info)))
+        self.nvec = self.info.nvec
+        self.shape = tuple(reversed([v * p + 1 for v in n]))
+
+    def _check(self, st):
+        if st != LOR_OK:
+            raise LorError(st, self.lib.lor_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lor_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dt(self, prec):
+        import torch
+        return torch.float64 if prec == LOR_FP64 else torch.float32
+
+    def rhs(self, b, kind=0):
+        import torch
+        self._check(self.lib.lor_rhs(self.ctx, kind, _ptr(b, torch.float64, self.nvec, "b")))
+
+    def apply_A(self, x, y, prec=LOR_FP64):
+        dt = self._dt(prec)
+        self._check(self.lib.lor_apply_A(self.ctx, _ptr(x, dt, self.nvec, "x"), _ptr(y, dt, self.nvec, "y"), prec))
+
+    def apply_P(self, r, z, prec=LOR_FP64):
+        dt = self._dt(prec)
+        self._check(self.lib.lor_apply_P(self.ctx, _ptr(r, dt, self.nvec, "r"), _ptr(z, dt, self.nvec, "z"), prec))
+
+    def solve(self, b, x):
+        import torch
+        it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(self.lib.lor_pcg_solve(self.ctx, _ptr(b, torch.float64, self.nvec, "b"),
+                                           _ptr(x, torch.float64, self.nvec, "x"), ctypes.byref(it),
+                                           ctypes.byref(rr)))
+        return it.value, rr.value
+
+    def solve_host(self, b: np.ndarray, x: np.ndarray):
+        if b.dtype != np.float64 or x.dtype != np.float64 or b.size != self.nvec or x.size != self.nvec:
+            raise ValueError("host vectors must be float64 of length nvec")
+        if not (b.flags.c_contiguous and x.flags.c_contiguous):
+            raise ValueError("host vectors must be contiguous")
+        it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(self.lib.lor_pcg_solve_host(self.ctx, b.ctypes.data_as(ctypes.c_void_p),
+                                                x.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it),
+                                                ctypes.byref(rr)))
+        return it.value, rr.value
+
+    def history(self):
+        cnt = ctypes.c_int(0)
+        self.lib.lor_residual_history(self.ctx, None, 0, ctypes.byref(cnt))
+        out = (ctypes.c_double * max(cnt.value, 1))()
+        self.lib.lor_residual_history(self.ctx, out, cnt.value, ctypes.byref(cnt))
+        return np.array(out[:cnt.value])

@@ -1,0 +1,64 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+function declared in include/lor.h, and rejects invalid input on the host."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1908_07071_gb300 import lor
+from paper_1908_07071_gb300.build import build_library
+from paper_1908_07071_gb300.synthetic import make_mesh
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_library()
+    return lor.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = lor.header_functions()
+    assert len(names) >= 12, names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in lor.h but not exported"
+
+
+def _create(lib, opt, verts, kappa):
+    ctx = ctypes.c_void_p()
+    st = lib.lor_create(ctypes.byref(ctx), ctypes.byref(opt), verts.ctypes.data_as(ctypes.c_void_p),
+                        kappa.ctypes.data_as(ctypes.c_void_p), None)
+    return st, ctx
+
+
+def test_create_validates_on_host(lib):
+    verts, kappa = make_mesh(3, 2, seed=0)
+    opt = lor.Options()
+    lib.lor_default_options(ctypes.byref(opt))
+    opt.nx = opt.ny = opt.nz = 2
+    st, ctx = _create(lib, opt, verts, kappa)
+    assert st == lor.LOR_OK and ctx.value
+    lib.lor_destroy(ctx)
+    for field, bad in (("p", 0), ("p", 9), ("dim", 4), ("nx", 0), ("rtol", 0.0), ("max_it", 0)):
+        o = lor.Options()
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(opt), ctypes.sizeof(o))
+        setattr(o, field, bad)
+        assert _create(lib, o, verts, kappa)[0] == lor.LOR_EINVAL, field
+    bad_kappa = kappa.copy()
+    bad_kappa.flat[3] = -1.0
+    assert _create(lib, opt, verts, bad_kappa)[0] == lor.LOR_EINVAL
+    nan_verts = verts.copy()
+    nan_verts.flat[5] = np.nan
+    assert _create(lib, opt, nan_verts, kappa)[0] == lor.LOR_EINVAL
+
+
+def test_calls_before_setup_are_rejected(lib):
+    verts, kappa = make_mesh(2, 2, seed=0)
+    opt = lor.Options()
+    lib.lor_default_options(ctypes.byref(opt))
+    opt.dim, opt.nx, opt.ny = 2, 2, 2
+    st, ctx = _create(lib, opt, verts, kappa)
+    assert st == lor.LOR_OK
+    assert lib.lor_apply_A(ctx, None, None, 0) == lor.LOR_ESTATE
+    assert lib.lor_pcg_solve(ctx, None, None, None, None) == lor.LOR_ESTATE
+    assert b"setup" in lib.lor_last_error(ctx)
+    lib.lor_destroy(ctx)
