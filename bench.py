@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the LOR-preconditioned matrix-free Q_p Poisson solver on GB300.
+
+Workload: 3D variable-coefficient Poisson, continuous Q_8 on a 32^3 hex mesh of
+the unit cube, interior vertices perturbed by U(-0.15h, 0.15h), kappa = exp(Z),
+Z ~ N(0,1) per element, f = 1, homogeneous Dirichlet (16,581,375 unknowns).
+One step = one solve to ||r|| <= 1e-8 ||b|| with the chosen form (mixed
+precision: FP32 operator/preconditioner with bf16 ILU factors inside FP64
+iterative refinement), inputs resident in HBM.  The JSON line also carries the
+plain FP64 solve time, per-apply MDOF/s of apply_A and apply_P in FP64 and FP32,
+the roofline of the dominant kernel, the end-to-end number through the host-
+buffer C-ABI call, and the CPU oracle timed on a bounded sample.
+
+N > 1 GPUs (torchrun): independent replicas, one problem per rank (seed = rank);
+no data-path collective.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D Q_p PCG time-to-1e-8 and MDOF/s per apply: plain FP64 vs chosen form"
+WORKLOAD = "3D CG Q8, 32^3 perturbed hex mesh (+-0.15h), log-normal kappa (sigma 1), f=1, rtol 1e-8"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--form", default="mixed-bf16", choices=["mixed-bf16", "mixed-fp32", "fp64"])
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64 solve, per-apply and CPU legs")
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- CPU leg
+def cpu_sample_worker(p: int, n: int, seed: int, budget_s: float, iters: int) -> dict:
+    """Times the CPU oracle as it stands on a bounded sample of the workload and
+    extrapolates one solve: per iteration nel element applies (dense element
+    matrix times element vector, the oracle's assembled-operator cost) and J
+    patch V-cycles (ILU(0) V(1,1) on a 2x2x2-element patch), times `iters`."""
+    import numpy as np
+    from oracle import cg as ocg
+    from oracle import lor as olor
+    from oracle.mesh import Mesh
+    from paper_1908_07071_gb300.synthetic import make_mesh
+
+    verts, kappa = make_mesh(3, n, seed=seed, perturb=0.15)
+    m = Mesh(verts, kappa)
+    rng = np.random.default_rng(0)
+    t_el, n_el = 0.0, 0
+    t_pa, n_pa = 0.0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < 0.4 * budget_s or n_el < 2:
+        e = tuple(int(v) for v in rng.integers(0, n, 3))
+        Ke = ocg.element_stiffness(m.corners(e), m.kappa_of(e), p)
+        xe = rng.standard_normal(Ke.shape[0])
+        ts = time.perf_counter()
+        for _ in range(5):
+            Ke @ xe
+        t_el += (time.perf_counter() - ts) / 5
+        n_el += 1
+    t1 = time.perf_counter()
+    while time.perf_counter() - t1 < 0.6 * budget_s or n_pa < 1:
+        v = [int(x) for x in rng.integers(1, n, 3)]
+        sub_v = verts[:, v[2] - 1:v[2] + 2, v[1] - 1:v[1] + 2, v[0] - 1:v[0] + 2].copy()
+        sub_k = kappa[v[2] - 1:v[2] + 1, v[1] - 1:v[1] + 1, v[0] - 1:v[0] + 1].copy()
+        B = olor.LORPreconditioner(Mesh(sub_v, sub_k), p, patch_subset=[(1, 1, 1)], coarse=False)
+        pt = B.patches[0]
+        r = rng.standard_normal(len(pt["levels"][0]["idx"]))
+        ts = time.perf_counter()
+        B.vcycle(pt["levels"], 0, r)
+        t_pa += time.perf_counter() - ts
+        n_pa += 1
+    nel = n ** 3
+    J = (n + 1) ** 3
+    per_it = nel * t_el / n_el + J * t_pa / n_pa
+    solve_s = iters * per_it
+    return {"solve_s": solve_s, "sample": f"{n_el} element applies (Q{p}, dense element matrix) and {n_pa} "
+            f"interior patch V-cycles timed, extrapolated to {nel} elements + {J} patches per iteration "
+            f"x {iters} iterations", "cores": 1}
+
+
+def run_cpu_leg(p, n, seed, budget_s, iters):
+    """Runs the oracle sample in a single-threaded subprocess (BLAS pinned to 1 thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import json,sys; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench.cpu_sample_worker({p},{n},{seed},{budget_s},{iters})))")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, dev_index=0):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or not f[0].isdigit() or int(f[0]) != dev_index:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- reference arm
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    steps = []
+    res = None
+    for k in range(args.warmup + args.steps):
+        res = run_cpu_leg(args.p, args.n, 0, args.cpu_sample_s, 60)
+        if k >= args.warmup:
+            steps.append(res["solve_s"])
+    solve_s = statistics.mean(steps)
+    value = 1.0 / solve_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "p": args.p, "n": args.n},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": res["cores"], "kind": "oracle",
+                             "sample": res["sample"] + " (60 iterations assumed per solve)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1908_07071_gb300 import lor
+    from paper_1908_07071_gb300.build import build_library
+    from paper_1908_07071_gb300.synthetic import make_mesh
+    if rank == 0:
+        build_library()
+    if world > 1:
+        dist.barrier()
+
+    p, n = args.p, args.n
+    verts, kappa = make_mesh(3, n, seed=rank, perturb=0.15)
+    bf16 = args.form == "mixed-bf16"
+    form = lor.LOR_FP64 if args.form == "fp64" else lor.LOR_MIXED
+    t_setup = time.perf_counter()
+    s = lor.Solver(verts, kappa, p, prec=form, rtol=1e-8, factor_bf16=bf16)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    ndof = s.info.ndof
+    b = torch.empty(s.nvec, dtype=torch.float64, device="cuda")
+    s.rhs(b, 0)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        s.solve(b, x)
+    barrier()
+    clocks = Clocks()
+    clocks.start()
+    l0 = s.launches()
+    s.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its, rels = [], []
+    e0.record(stream)
+    for _ in range(args.steps):
+        it, rel = s.solve(b, x)
+        its.append(it)
+        rels.append(rel)
+    e1.record(stream)
+    barrier()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    s.profile(False)
+    launches = s.launches() - l0
+    prof = {k: s.profile_read(k) for k in range(6)}
+    clk = clocks.stop(local)
+    t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    ms_per_step = elapsed / args.steps * 1e3
+    value = world * args.steps / elapsed
+
+    extras = {}
+    if not args.no_extras:
+        # end to end through the host-buffer call (copies inside the timed region)
+        hb = torch.empty(s.nvec, dtype=torch.float64).pin_memory()
+        hb.copy_(b)
+        hx = torch.empty_like(hb).pin_memory()
+        hbn, hxn = hb.numpy(), hx.numpy()
+        s.solve_host(hbn, hxn)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.solve_host(hbn, hxn)
+        barrier()
+        e2e = world * args.steps / (time.perf_counter() - t0)
+        extras["e2e"] = {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": int(s.nvec * 8),
+                         "d2h_bytes_per_step": int(s.nvec * 8)}
+        # per-apply throughput
+        xa = torch.randn(s.nvec, dtype=torch.float64, device="cuda")
+        ya = torch.empty_like(xa)
+        xf, yf = xa.float(), torch.empty(s.nvec, dtype=torch.float32, device="cuda")
+        mdofs = {}
+        for name, fn in (("apply_A_fp64", lambda: s.apply_A(xa, ya)),
+                         ("apply_A_fp32", lambda: s.apply_A(xf, yf, lor.LOR_FP32)),
+                         ("apply_P_fp64", lambda: s.apply_P(xa, ya)),
+                         ("apply_P_fp32", lambda: s.apply_P(xf, yf, lor.LOR_FP32))):
+            for _ in range(2):
+                fn()
+            reps = 10
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(reps):
+                fn()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms = a0.elapsed_time(a1) / reps
+            mdofs[name] = {"ms": ms, "MDOF/s": ndof / (ms * 1e-3) / 1e6}
+        extras["per_apply"] = mdofs
+        # plain FP64 solve for comparison
+        if form != lor.LOR_FP64:
+            s.set_prec(lor.LOR_FP64)
+            x64 = torch.zeros_like(b)
+            s.solve(b, x64)
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            it64, rel64 = s.solve(b, x64)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            s.set_prec(form)
+            dx = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+            extras["fp64_plain"] = {"time_to_tol_ms": f0.elapsed_time(f1), "iterations": it64,
+                                    "rel_res": rel64, "chosen_vs_fp64_x_rel_diff": dx,
+                                    "speedup_chosen_vs_fp64": f0.elapsed_time(f1) / ms_per_step}
+
+    # roofline of the dominant kernel class inside the timed region
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    names = {0: "patch_vcycle_fp64", 1: "patch_vcycle_fp32", 2: "apply_A_fp64", 3: "apply_A_fp32",
+             4: "coarse_fp64", 5: "coarse_fp32"}
+    dom = max(prof, key=lambda k: prof[k][0])
+    tot_ms, nl = prof[dom]
+    per_launch_s = tot_ms / max(nl, 1) / 1e3
+    Q = p + 1
+    nel = n ** 3
+    info = s.info
+    rows = info.factor_rows
+    if dom in (0, 1):
+        fb = 8 if dom == 0 else (2 if bf16 else 4)
+        vb = 8 if dom == 0 else 4
+        lev_nodes = sum(((n * m + 1) ** 3) for m in level_intervals(p))
+        alg = rows * 27 * fb + lev_nodes * 27 * vb + 3 * s.nvec * vb
+        roof = {"bound": "hbm", "achieved": alg / per_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_kind": "measured" if "hbm_gbs" in pk else "fallback"}
+    elif dom == 2:
+        flops = nel * (24 * Q ** 4 + 18 * Q ** 3)
+        fp64_peak = 1.26   # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+        roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                "peak_kind": "derived"}
+    else:
+        bts = nel * 6 * Q ** 3 * (8 if dom == 4 else 4) + 3 * s.nvec * 4
+        roof = {"bound": "hbm", "achieved": bts / per_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_kind": "measured" if "hbm_gbs" in pk else "fallback"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = names[dom]
+    roof["launch_ms"] = per_launch_s * 1e3
+    roof["launches_in_timed_region"] = nl
+    roof["kernel_time_share"] = {names[k]: round(prof[k][0] / max(elapsed * 1e3, 1e-9), 4) for k in prof if prof[k][1]}
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+bf16/f64" if bf16 else ("f32/f64" if form != lor.LOR_FP64 else "f64"),
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "p": p, "n": n, "ndof": ndof, "form": args.form,
+                       "l2": "working set (ILU factors, stencils) >> 129 MB L2; no flush needed",
+                       "parallelism": f"replicas x{world}"},
+            "iterations": its[-1], "rel_res": rels[-1], "setup_s": t_setup, "gpu_launches": launches,
+            "roofline": roof, "clocks": clk}
+    line.update(extras)
+    if rank == 0 and not args.no_extras:
+        its64 = extras.get("fp64_plain", {}).get("iterations", 60)
+        try:
+            cb = run_cpu_leg(p, n, 0, args.cpu_sample_s, its64)
+            line["cpu_baseline"] = {"value": 1.0 / cb["solve_s"], "unit": "solves/s", "cores": cb["cores"],
+                                    "kind": "oracle", "sample": cb["sample"]}
+        except Exception as exc:   # the CPU leg must not hide the GPU result
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {exc}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def level_intervals(p):
+    sels = [list(range(p + 1))]
+    while len(sels[-1]) > 2:
+        c = sels[-1][0::2]
+        if c[-1] != sels[-1][-1]:
+            c.append(sels[-1][-1])
+        sels.append(c)
+    return [len(s) - 1 for s in sels]
+
+
+if __name__ == "__main__":
+    main()

@@ -128,6 +128,23 @@ lor_status lor_pcg_solve(lor_ctx* ctx, const double* d_b, double* d_x,
 lor_status lor_pcg_solve_host(lor_ctx* ctx, const double* h_b, double* h_x,
                               int* iters, double* rel_res);
 
+/* Selects the precision lor_pcg_solve uses from now on (lor_prec); the context
+ * keeps FP64 and FP32 (and, if requested, bf16) data, so no setup is redone. */
+lor_status lor_set_prec(lor_ctx* ctx, int prec);
+
+/* Number of kernels this context has launched so far (all entry points). */
+lor_status lor_launch_count(const lor_ctx* ctx, long long* count);
+
+/* Kernel timing with CUDA events recorded on the context stream around every
+ * launch of the hot kernels while profiling is on (at most 8192 launches per
+ * kernel are kept).  lor_profile(ctx, 1) clears and starts, 0 stops.
+ * lor_profile_read sums the recorded durations of one kernel class:
+ *   0 patch V-cycle FP64, 1 patch V-cycle FP32, 2 apply_A FP64, 3 apply_A FP32,
+ *   4 coarse-space correction FP64, 5 coarse-space correction FP32.
+ * It synchronises the stream. */
+lor_status lor_profile(lor_ctx* ctx, int on);
+lor_status lor_profile_read(lor_ctx* ctx, int kernel, double* total_ms, long long* launches);
+
 /* Per-iteration residual norms ||r_k||_2 of the last solve (k = 0..count-1,
  * FP64 outer residuals and inner FP64-accumulated norms for LOR_MIXED). */
 lor_status lor_residual_history(const lor_ctx* ctx, double* out, int cap, int* count);

@@ -262,6 +262,8 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
   cudaError_t e = cudaMemsetAsync(y, 0, sizeof(T) * nvec, c->stream);
   if (e != cudaSuccess) return lor_cuda_check(c, e, "apply_A memset");
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
+  const int pk = sizeof(T) == 8 ? 2 : 3;
+  lor_prof_begin(c, pk);
 #define LOR_CASE3(PP)                                                                       \
   case PP: {                                                                                \
     constexpr int NE = ElemsPerBlock<PP>::v2;                                               \
@@ -278,6 +280,8 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
     default: return lor_fail(c, LOR_EINVAL, "unsupported p");
   }
 #undef LOR_CASE3
+  ++c->launches;
+  lor_prof_end(c, pk);
   return lor_cuda_check(c, cudaGetLastError(), "apply_A launch");
 }
 
@@ -381,6 +385,8 @@ lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b) {
   const unsigned blocks = (unsigned)lor_ceil_div(tot, 256);
   k_rhs_weights<<<blocks, 256, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1], c->n[2], c->d_vert,
                                                lor_basis64(c, 2), lor_basis64(c, 3), kind, W);
+  ++c->launches;
   k_rhs_scatter<<<blocks, 256, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1], c->n[2], lor_basis64(c, 0), W, b);
+  ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "rhs launch");
 }

@@ -193,23 +193,18 @@ __global__ void __launch_bounds__(128) k_patch_vcycle(PatchArgs a) {
     const Box& bc = bx[l + 1];
     for (int lex = threadIdx.x; lex < bc.rows; lex += blockDim.x) {
       const int ci = lex % bc.A, cj = (lex / bc.A) % bc.B, ck = lex / (bc.A * bc.B);
-      const RestrictEntry ex = lv.rr[b.type[0]][ci];
-      const RestrictEntry ey = lv.rr[b.type[1]][cj];
-      RestrictEntry ez;
-      if (DIM == 3) ez = lv.rr[b.type[2]][ck];
+      const RestrictEntry& ex = lv.rr[b.type[0]][ci];
+      const RestrictEntry& ey = lv.rr[b.type[1]][cj];
+      const RestrictEntry* ez = DIM == 3 ? &lv.rr[b.type[2]][ck] : nullptr;
       T s = 0;
-      const int nz = DIM == 3 ? 3 : 1;
+      const int nz = DIM == 3 ? ez->cnt : 1;
       for (int tz = 0; tz < nz; ++tz) {
-        const int fz = DIM == 3 ? ez.f[tz] : 0;
-        if (fz < 0) continue;
-        const T wz = DIM == 3 ? (T)ez.w[tz] : T(1);
-        for (int ty = 0; ty < 3; ++ty) {
-          if (ey.f[ty] < 0) continue;
+        const int fz = DIM == 3 ? ez->f[tz] : 0;
+        const T wz = DIM == 3 ? (T)ez->w[tz] : T(1);
+        for (int ty = 0; ty < ey.cnt; ++ty) {
           const T wy = (T)ey.w[ty] * wz;
-          for (int tx = 0; tx < 3; ++tx) {
-            if (ex.f[tx] < 0) continue;
-            s += (T)ex.w[tx] * wy * ts[l][pad_of(b, ex.f[tx], ey.f[ty], fz)];
-          }
+          const int fy = ey.f[ty];
+          for (int tx = 0; tx < ex.cnt; ++tx) s += (T)ex.w[tx] * wy * ts[l][pad_of(b, ex.f[tx], fy, fz)];
         }
       }
       rs[l + 1][lex] = s;
@@ -526,6 +521,7 @@ T* coarse_vcycle(lor_ctx* c, int l) {
       const int nd = c->ncoarse_direct;
       k_cdense<T><<<(unsigned)lor_ceil_div((long long)nd * 32, 128), 128, 0, c->stream>>>(
           nd, c->d_cdirect_idx, Sel<T>::inv(c), r, xa);
+      ++c->launches;
     }
     return xa;
   }
@@ -534,11 +530,14 @@ T* coarse_vcycle(lor_ctx* c, int l) {
   T* cur = xa;
   T* oth = xb;
   k_cjacobi<T><<<nb, 128, 0, c->stream>>>(g, S, D, r, (const T*)nullptr, cur);
+  ++c->launches;
   for (int s = 1; s < kCoarseSweeps; ++s) {
     k_cjacobi<T><<<nb, 128, 0, c->stream>>>(g, S, D, r, cur, oth);
+    ++c->launches;
     T* tmp = cur; cur = oth; oth = tmp;
   }
   k_cresid<T><<<nb, 128, 0, c->stream>>>(g, S, r, cur, t);
+  ++c->launches;
   CTransfer tr;
   tr.dim = c->dim;
   for (int a = 0; a < 3; ++a) {
@@ -547,10 +546,13 @@ T* coarse_vcycle(lor_ctx* c, int l) {
   }
   const long long ntc = c->cntot[l + 1];
   k_crestrict<T><<<(unsigned)lor_ceil_div(ntc, 128), 128, 0, c->stream>>>(tr, t, Sel<T>::cw(c, l + 1, 0));
+  ++c->launches;
   T* xc = coarse_vcycle<T>(c, l + 1);
   k_cprolong_add<T><<<nb, 128, 0, c->stream>>>(tr, xc, cur);
+  ++c->launches;
   for (int s = 0; s < kCoarseSweeps; ++s) {
     k_cjacobi<T><<<nb, 128, 0, c->stream>>>(g, S, D, r, cur, oth);
+    ++c->launches;
     T* tmp = cur; cur = oth; oth = tmp;
   }
   return cur;
@@ -576,24 +578,33 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F, size_t smem
   a.front = c->d_front; a.rowpad = c->d_rowpad; a.rowlex = c->d_rowlex;
   a.facoff = c->d_facoff;
   a.F = F; a.r = r; a.z = z;
+  const int pk = sizeof(T) == 8 ? 0 : 1;
+  lor_prof_begin(c, pk);
   if (c->dim == 3) {
     auto kern = k_patch_vcycle<3, T, FT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<c->J, 128, smem, c->stream>>>(a);
+    ++c->launches;
   } else {
     auto kern = k_patch_vcycle<2, T, FT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<c->J, 128, smem, c->stream>>>(a);
+    ++c->launches;
   }
+  lor_prof_end(c, pk);
   if (lor_cuda_check(c, cudaGetLastError(), "patch vcycle")) return LOR_ECUDA;
+  lor_prof_begin(c, pk + 4);
   // coarse space
   const double* gllx = lor_basis64(c, 4);
   const long long nv = c->cntot[0];
   k_coarse_restrict0<T><<<(unsigned)lor_ceil_div(nv, 128), 128, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1],
                                                                                    c->n[2], gllx, r, Sel<T>::cw(c, 0, 0));
+  ++c->launches;
   T* ec = coarse_vcycle<T>(c, 0);
   k_coarse_prolong0<T><<<(unsigned)lor_ceil_div(nvec, 128), 128, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1],
                                                                                    c->n[2], gllx, ec, z);
+  ++c->launches;
+  lor_prof_end(c, pk + 4);
   return lor_cuda_check(c, cudaGetLastError(), "coarse space");
 }
 

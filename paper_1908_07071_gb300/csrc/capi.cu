@@ -33,7 +33,52 @@ void* lor_alloc(lor_ctx* c, size_t bytes) {
   return p;
 }
 
+static const int kMaxProf = 8192;
+
+void lor_prof_begin(lor_ctx* c, int k) {
+  if (!c->prof || c->nev[k] >= kMaxProf) return;
+  std::vector<cudaEvent_t>& v = c->ev[k];
+  const int i = c->nev[k];
+  while ((int)v.size() < 2 * (i + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    v.push_back(e);
+  }
+  cudaEventRecord(v[2 * i], c->stream);
+}
+
+void lor_prof_end(lor_ctx* c, int k) {
+  if (!c->prof || c->nev[k] >= kMaxProf) return;
+  if ((int)c->ev[k].size() < 2 * (c->nev[k] + 1)) return;
+  cudaEventRecord(c->ev[k][2 * c->nev[k] + 1], c->stream);
+  c->nev[k]++;
+}
+
 extern "C" {
+
+lor_status lor_profile(lor_ctx* c, int on) {
+  if (!c) return LOR_EINVAL;
+  c->prof = on != 0;
+  if (on)
+    for (int k = 0; k < 6; ++k) c->nev[k] = 0;
+  return LOR_OK;
+}
+
+lor_status lor_profile_read(lor_ctx* c, int kernel, double* total_ms, long long* launches) {
+  if (!c || kernel < 0 || kernel >= 6 || !total_ms || !launches) return LOR_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return lor_cuda_check(c, e, "profile read");
+  double tot = 0;
+  for (int i = 0; i < c->nev[kernel]; ++i) {
+    float ms = 0;
+    e = cudaEventElapsedTime(&ms, c->ev[kernel][2 * i], c->ev[kernel][2 * i + 1]);
+    if (e != cudaSuccess) return lor_cuda_check(c, e, "event elapsed");
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = c->nev[kernel];
+  return LOR_OK;
+}
 
 void lor_default_options(lor_options* o) {
   if (!o) return;
@@ -195,6 +240,19 @@ lor_status lor_pcg_solve_host(lor_ctx* c, const double* hb, double* hx, int* ite
   return s;
 }
 
+lor_status lor_set_prec(lor_ctx* c, int prec) {
+  if (!c) return LOR_EINVAL;
+  if (prec != LOR_FP64 && prec != LOR_MIXED) return lor_fail(c, LOR_EINVAL, "lor_set_prec: LOR_FP64 or LOR_MIXED");
+  c->opt.prec = prec;
+  return LOR_OK;
+}
+
+lor_status lor_launch_count(const lor_ctx* c, long long* count) {
+  if (!c || !count) return LOR_EINVAL;
+  *count = c->launches;
+  return LOR_OK;
+}
+
 lor_status lor_residual_history(const lor_ctx* c, double* out, int cap, int* count) {
   if (!c || !count) return LOR_EINVAL;
   *count = (int)c->hist.size();
@@ -210,6 +268,8 @@ void lor_destroy(lor_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
+  for (int k = 0; k < 6; ++k)
+    for (cudaEvent_t e : c->ev[k]) cudaEventDestroy(e);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;
 }

@@ -177,6 +177,7 @@ lor_status lor_setup_krylov(lor_ctx* c) {
   if (!c->d_v32[7] || !c->d_scal || !c->d_part || !c->d_count) return lor_fail(c, LOR_ENOMEM, "alloc krylov scalars");
   if (!c->h_scal && cudaMallocHost(&c->h_scal, 64 * 8) != cudaSuccess) return lor_fail(c, LOR_ENOMEM, "pinned");
   k_bmask<<<1024, 256, 0, c->stream>>>(c->dim, c->lev[0].N[0], c->lev[0].N[1], c->lev[0].N[2], bmask_of(c));
+  ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "krylov setup");
 }
 
@@ -187,6 +188,7 @@ static unsigned red_blocks(long long n) {
 template <typename TA, typename TB>
 static void dot(lor_ctx* c, const TA* a, const TB* b, long long n, int slot, int op) {
   k_dot<TA, TB><<<red_blocks(n), kRedThreads, 0, c->stream>>>(a, b, n, c->d_part, c->d_count, c->d_scal, slot, op);
+  ++c->launches;
 }
 
 static lor_status read_scalars(lor_ctx* c) {
@@ -207,6 +209,7 @@ static lor_status pcg_core(lor_ctx* c, T* x, T* r, T* z, T* p, T* Ap, long long 
   if (applyP(r, z)) return LOR_ECUDA;
   dot(c, r, z, n, S_RZ, OP_STORE);
   k_copy<T><<<gb, kRedThreads, 0, c->stream>>>(p, z, n);
+  ++c->launches;
   if (read_scalars(c)) return LOR_ECUDA;
   double rr = c->h_scal[S_RR];
   if (record) c->hist.push_back(sqrt(rr));
@@ -216,6 +219,7 @@ static lor_status pcg_core(lor_ctx* c, T* x, T* r, T* z, T* p, T* Ap, long long 
     if (applyA(p, Ap)) return LOR_ECUDA;
     dot(c, p, Ap, n, 0, OP_ALPHA);
     k_update<T><<<gb, kRedThreads, 0, c->stream>>>(x, r, p, Ap, n, c->d_part, c->d_count, c->d_scal);
+    ++c->launches;
     if (read_scalars(c)) return LOR_ECUDA;
     ++it;
     rr = c->h_scal[S_RR];
@@ -225,6 +229,7 @@ static lor_status pcg_core(lor_ctx* c, T* x, T* r, T* z, T* p, T* Ap, long long 
     if (applyP(r, z)) return LOR_ECUDA;
     dot(c, r, z, n, 0, OP_BETA);
     k_xpay<T><<<gb, kRedThreads, 0, c->stream>>>(p, z, n, c->d_scal);
+    ++c->launches;
   }
   *it_out = it;
   *rr_out = rr;
@@ -236,6 +241,7 @@ static lor_status true_residual(lor_ctx* c, const double* b, const double* x, do
   const long long n = c->lev[0].ntot;
   if (lor_launch_apply_A64(c, x, Ax)) return LOR_ECUDA;
   k_resid<<<red_blocks(n), kRedThreads, 0, c->stream>>>(r, b, Ax, bmask_of(c), n, c->d_part, c->d_count, c->d_scal);
+  ++c->launches;
   if (read_scalars(c)) return LOR_ECUDA;
   *rn = sqrt(c->h_scal[S_RR]);
   return LOR_OK;
@@ -244,6 +250,7 @@ static lor_status true_residual(lor_ctx* c, const double* b, const double* x, do
 static double norm_b(lor_ctx* c, const double* b, double* tmp) {
   const long long n = c->lev[0].ntot;
   k_mask_copy<<<red_blocks(n), kRedThreads, 0, c->stream>>>(tmp, b, bmask_of(c), n);
+  ++c->launches;
   dot(c, tmp, tmp, n, S_BB, OP_STORE);
   if (read_scalars(c)) return -1.0;
   return sqrt(c->h_scal[S_BB]);
@@ -303,6 +310,7 @@ lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, dou
   int total = 0, outer = 0;
   while (rn > c->opt.rtol * bn && total < c->opt.max_it && outer < 100) {
     k_down<<<red_blocks(n), kRedThreads, 0, c->stream>>>(r32, r, 1.0 / rn, n);
+    ++c->launches;
     // inner tolerance: inner_rtol, but never tighter than needed to reach rtol
     const double need = c->opt.rtol * bn / rn;
     const double tol = std::max(c->opt.inner_rtol, 0.5 * need);
@@ -312,6 +320,7 @@ lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, dou
     if (st) return st;
     total += it;
     k_up_add<<<red_blocks(n), kRedThreads, 0, c->stream>>>(x, d, rn, n);
+    ++c->launches;
     if (true_residual(c, b, x, r, Ax, &rn)) return LOR_ECUDA;
     c->hist.push_back(rn);
     ++outer;

@@ -30,7 +30,10 @@ std::vector<std::vector<int>> level_selections(int p, int mg_levels);
 struct Prolong1D { int c0, c1; double w0, w1; };
 
 // Patch 1D structure of one level and one axis type (0 interior, 1 boundary).
-struct RestrictEntry { int f[3]; double w[3]; };
+// Restriction entry of one coarse point: the fine points feeding it (a coarsening
+// step may skip up to 2p-1 fine points per axis when the hierarchy is truncated).
+#define LOR_MAXR (2 * LOR_MAXP)
+struct RestrictEntry { int cnt; int f[LOR_MAXR]; double w[LOR_MAXR]; };
 
 struct PatchAxis {
   int len;        // unknowns along the axis at this level
@@ -138,7 +141,12 @@ struct lor_ctx {
   double* h_scal = nullptr;   // pinned mirror
   std::vector<double> hist;
 
+  // event timing of hot kernels (lor_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev[6];   // start/stop pairs per kernel class
+  int nev[6] = {0, 0, 0, 0, 0, 0};
   size_t bytes = 0;
+  long long launches = 0;      // kernels launched by this context
   std::vector<void*> allocs;
 };
 
@@ -167,6 +175,10 @@ lor_status lor_setup_krylov(lor_ctx* c);
 BoxShape* lor_dev_shapes(lor_ctx* c);
 double* lor_basis64(lor_ctx* c, int which);
 float* lor_basis32(lor_ctx* c, int which);
+
+// event pair around a hot kernel launch (no-op unless profiling)
+void lor_prof_begin(lor_ctx* c, int k);
+void lor_prof_end(lor_ctx* c, int k);
 
 // small device utilities shared by the .cu files
 __host__ __device__ inline long long lor_ceil_div(long long a, long long b) { return (a + b - 1) / b; }

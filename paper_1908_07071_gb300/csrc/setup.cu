@@ -454,6 +454,7 @@ lor_status lor_setup_geometry(lor_ctx* c) {
   k_geom<<<(unsigned)lor_ceil_div(tot, 128), 128, 0, c->stream>>>(
       c->dim, p, c->n[0], c->n[1], c->n[2], c->d_vert, c->d_kappa, lor_basis64(c, 2), lor_basis64(c, 3),
       c->d_G64, c->d_G32, c->d_status);
+  ++c->launches;
   if (lor_cuda_check(c, cudaGetLastError(), "geometry")) return LOR_ECUDA;
   return check_status(c, "geometry");
 }
@@ -540,6 +541,7 @@ static lor_status galerkin(lor_ctx* c, int dim, const int* Nf, const int* Nc, Pr
   }
   const long long ntc = (long long)Nc[0] * Nc[1] * Nc[2];
   k_galerkin<<<(unsigned)lor_ceil_div(ntc, 128), 128, 0, c->stream>>>(g, Sf, Sc);
+  ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "galerkin");
 }
 
@@ -560,6 +562,7 @@ lor_status lor_setup_stencils(lor_ctx* c) {
   if (!c->d_X) return lor_fail(c, LOR_ENOMEM, "alloc coordinates");
   k_nodes<<<(unsigned)lor_ceil_div(nt0, 128), 128, 0, c->stream>>>(dim, p, c->n[0], c->n[1], c->n[2], c->d_vert,
                                                                      lor_basis64(c, 4), c->d_X);
+  ++c->launches;
   for (int l = 0; l < c->L; ++l) {
     const long long nt = c->lev[l].ntot;
     c->d_S64[l] = (double*)lor_alloc(c, nt * c->NS * 8);
@@ -568,6 +571,7 @@ lor_status lor_setup_stencils(lor_ctx* c) {
   }
   k_lor_stencil<<<(unsigned)lor_ceil_div(nt0, 128), 128, 0, c->stream>>>(dim, p, c->n[0], c->n[1], c->n[2], c->d_X,
                                                                            c->d_kappa, c->d_S64[0]);
+  ++c->launches;
   if (lor_cuda_check(c, cudaGetLastError(), "lor stencil")) return LOR_ECUDA;
   for (int l = 0; l + 1 < c->L; ++l) {
     for (int a = 0; a < dim; ++a) {
@@ -583,6 +587,7 @@ lor_status lor_setup_stencils(lor_ctx* c) {
   for (int l = 0; l < c->L; ++l) {
     const long long n = c->lev[l].ntot * c->NS;
     k_to_float<<<(unsigned)lor_ceil_div(n, 256), 256, 0, c->stream>>>(c->d_S64[l], c->d_S32[l], n);
+    ++c->launches;
   }
   return lor_cuda_check(c, cudaGetLastError(), "stencil conversion");
 }
@@ -659,17 +664,15 @@ lor_status lor_setup_patches(lor_ctx* c) {
       // transpose: for every coarse local index the (<= 3) fine local indices feeding it
       const int clen = axis_len(type, mc);
       std::vector<RestrictEntry> rr(std::max(clen, 1));
-      for (auto& e : rr) for (int t = 0; t < 3; ++t) { e.f[t] = -1; e.w[t] = 0.0; }
+      for (auto& e : rr) { e.cnt = 0; for (int t = 0; t < LOR_MAXR; ++t) { e.f[t] = 0; e.w[t] = 0.0; } }
       for (int f = 0; f < len; ++f) {
         const int cs[2] = {loc[f].c0, loc[f].c1};
         const double ws[2] = {loc[f].w0, loc[f].w1};
         for (int s2 = 0; s2 < 2; ++s2) {
           if (cs[s2] < 0 || cs[s2] >= clen || ws[s2] == 0.0) continue;
           RestrictEntry& e = rr[cs[s2]];
-          int t = 0;
-          while (t < 3 && e.f[t] >= 0) ++t;
-          if (t == 3) return lor_fail(c, LOR_EINVAL, "restriction stencil wider than 3");
-          e.f[t] = f; e.w[t] = ws[s2];
+          if (e.cnt == LOR_MAXR) return lor_fail(c, LOR_EINVAL, "restriction stencil too wide");
+          e.f[e.cnt] = f; e.w[e.cnt] = ws[s2]; ++e.cnt;
         }
       }
       if (upload(c, (void**)&c->d_rr[l][type], rr.data(), rr.size() * sizeof(RestrictEntry))) return LOR_ENOMEM;
@@ -706,10 +709,13 @@ lor_status lor_setup_patches(lor_ctx* c) {
     a.F = c->d_F64;
     a.status = c->d_status;
     k_ilu0<<<c->J, 128, 0, c->stream>>>(a);
+    ++c->launches;
     if (lor_cuda_check(c, cudaGetLastError(), "ilu0")) return LOR_ECUDA;
   }
   k_to_float<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F32, tot);
+  ++c->launches;
   if (c->d_F16) k_to_bf16<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F16, tot);
+  ++c->launches;
   if (lor_cuda_check(c, cudaGetLastError(), "factor conversion")) return LOR_ECUDA;
   return check_status(c, "ilu0");
 }
@@ -748,6 +754,7 @@ lor_status lor_setup_coarse(lor_ctx* c) {
       return LOR_ECUDA;
     const long long n = c->cntot[l + 1] * c->NS;
     k_to_float<<<(unsigned)lor_ceil_div(n, 256), 256, 0, c->stream>>>(c->d_cS64[l + 1], c->d_cS32[l + 1], n);
+    ++c->launches;
     ++l;
   }
   c->CL = l + 1;
@@ -763,6 +770,7 @@ lor_status lor_setup_coarse(lor_ctx* c) {
     if (!c->d_cDinv64[t] || !c->d_cDinv32[t]) return lor_fail(c, LOR_ENOMEM, "alloc coarse diag");
     k_l1_dinv<<<(unsigned)lor_ceil_div(nt, 128), 128, 0, c->stream>>>(dim, c->cN[t][0], c->cN[t][1], c->cN[t][2],
                                                                         c->d_cS64[t], c->d_cDinv64[t], c->d_cDinv32[t]);
+    ++c->launches;
   }
   if (lor_cuda_check(c, cudaGetLastError(), "coarse setup")) return LOR_ECUDA;
   // dense inverse of the coarsest operator (interior unknowns) on the host

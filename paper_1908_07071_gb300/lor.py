@@ -71,7 +71,11 @@ def load():
     lib.lor_last_error.restype = ctypes.c_char_p
     lib.lor_destroy.argtypes = [vp]
     lib.lor_destroy.restype = None
-    for name in ("lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
+    lib.lor_set_prec.argtypes = [vp, i]
+    lib.lor_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.lor_profile.argtypes = [vp, i]
+    lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
+    for name in ("lor_set_prec", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -182,6 +186,22 @@ class Solver:
                                                 x.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it),
                                                 ctypes.byref(rr)))
         return it.value, rr.value
+
+    def set_prec(self, prec):
+        self._check(self.lib.lor_set_prec(self.ctx, prec))
+
+    def launches(self):
+        n = ctypes.c_longlong(0)
+        self._check(self.lib.lor_launch_count(self.ctx, ctypes.byref(n)))
+        return n.value
+
+    def profile(self, on):
+        self._check(self.lib.lor_profile(self.ctx, int(on)))
+
+    def profile_read(self, kernel):
+        ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
+        self._check(self.lib.lor_profile_read(self.ctx, kernel, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def history(self):
         cnt = ctypes.c_int(0)
