@@ -15,6 +15,8 @@
 // Coarse space: P_0^T r at the interior vertices, one V-cycle on the vertex grid
 // (l1-Jacobi smoothing, Galerkin levels, dense inverse on the coarsest grid),
 // z += P_0 e.
+#include <algorithm>
+
 #include "lor_internal.h"
 
 namespace {
@@ -23,8 +25,8 @@ template <typename FT> __device__ __forceinline__ float tofl(FT v);
 template <> __device__ __forceinline__ float tofl<float>(float v) { return v; }
 template <> __device__ __forceinline__ float tofl<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <typename T, typename FT> __device__ __forceinline__ T fac(const FT* p) { return (T)tofl<FT>(*p); }
-template <> __device__ __forceinline__ double fac<double, double>(const double* p) { return *p; }
+template <typename T, typename FT> __device__ __forceinline__ T fac(FT v) { return (T)tofl<FT>(v); }
+template <> __device__ __forceinline__ double fac<double, double>(double v) { return v; }
 
 struct PLevel {
   const void* S;          // [NS][ntot] stencil of this level (T)
@@ -33,6 +35,18 @@ struct PLevel {
   int m;
   const Prolong1D* pp[2];       // this level -> next coarser, patch-local, per axis type
   const RestrictEntry* rr[2];   // next coarser <- this level, patch-local, per axis type
+  int len[2], clen[2];          // fine / coarse unknowns along an axis of each type
+};
+
+// Shared-memory copy of one 1D patch-local transfer (one level, one axis type):
+// prolongation rows (fine -> <= 2 coarse) and the transposed restriction lists.
+template <typename T>
+struct Xfer1D {
+  int c0[2 * LOR_MAXP], c1[2 * LOR_MAXP];
+  T w0[2 * LOR_MAXP], w1[2 * LOR_MAXP];
+  int rstart[2 * LOR_MAXP + 1];
+  int rf[4 * LOR_MAXP];
+  T rw[4 * LOR_MAXP];
 };
 
 struct PatchArgs {
@@ -41,267 +55,442 @@ struct PatchArgs {
   PLevel lv[LOR_MAXLEV];
   const BoxShape* shapes;       // [L][8]
   const int* front;
-  const int* rowpad;
+  const int* fpad;
+  const int* chunk;
   const int* rowlex;
-  const long long* facoff;      // [L][J]
+  const int* recof;
+  const unsigned* nbmask;
+  const long long* facoff;      // [L][J] record offsets
   const void* F;
   const void* r;
   void* z;
+  int* status;
+  int slot_bytes;               // ring slot size (bytes, multiple of 16)
+  int tab_ints;                 // shared-memory ints reserved for wavefront tables
+  const int* porder;            // patch visiting order (grouped by box shape)
 };
 
 struct Box {
   int A, B, C;       // extents
   int rows;
-  int pa, pb;        // padded extents (A+2, B+2)
-  int pz;            // 1 if the z axis is padded (3D)
   int org[3];        // global level index of local (0,0,0)
   int type[3];       // axis type (0 interior, 1 boundary)
 };
 
-__device__ __forceinline__ int pad_of(const Box& b, int i, int j, int k) {
-  return ((k + b.pz) * b.pb + (j + 1)) * b.pa + (i + 1);
+// ---- TMA bulk-copy ring (one elected producer thread, mbarrier completion) ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
 }
 
-template <int DIM>
-__device__ __forceinline__ void off_table(const Box& b, int* off) {
-  constexpr int NS = DIM == 3 ? 27 : 9;
-#pragma unroll
-  for (int o = 0; o < NS; ++o) {
-    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
-    off[o] = (dz * b.pb + dy) * b.pa + dx;
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  // order earlier generic-proxy reads of this slot before the async-proxy write
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Waits for the phase `parity` of `bar`; gives up after a bounded number of
+// polls (returns false) so that a lost copy cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned addr = smem_u32(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
   }
+  return false;
 }
 
-// in-place (L U)^{-1} on the padded vector t of one level
-template <int DIM, typename T, typename FT>
-__device__ void ilu_solve(const Box& b, const BoxShape& bs, const int* front, const int* rowpad, const FT* F, T* t) {
+template <typename FT, int NBUF>
+struct Ring {
+  FT* slot[NBUF];
+  unsigned long long* bar;
+  unsigned phase;     // bit s: parity expected next on slot s
+  unsigned inflight;  // producer view: bit s set while a copy into slot s is pending
+};
+
+// Shared-memory copies of one level's wavefront tables.
+struct LevelTables {
+  const unsigned short* rowlex;   // lexicographic row index per wavefront position
+  const int* front;               // nfront+1 row positions
+  const int* fpad;                // nfront+1 record offsets
+  const int* chunk;               // nchunk+1 front indices
+};
+
+// One triangular sweep over a level, run by ONE warp.  Factor blocks stream
+// through the ring in chunks of whole fronts: lane 0 issues the bulk copies and
+// observes their completion, __syncwarp publishes them to the other lanes.
+// Inside a chunk, lanes loop over the rows of a front and __syncwarp separates
+// fronts.  t has a zero guard band, so neighbour reads need no clamping
+// (multipliers of out-of-box neighbours are stored as 0).  BACK selects the
+// backward sweep (U part, fronts in reverse, scaled by 1/u_ii).
+template <int DIM, bool BACK, typename T, typename FT, int NBUF>
+__device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __restrict__ fr,
+                                      const int* __restrict__ fp, const int* __restrict__ ch,
+                                      const unsigned short* __restrict__ rl, int nc, int A, int AB, T* t,
+                                      Ring<FT, NBUF>& rg) {
   constexpr int NS = DIM == 3 ? 27 : 9;
   constexpr int C = NS / 2;
-  int off[NS];
-  off_table<DIM>(b, off);
-  const int rows = bs.rows;
-  const int* fr = front + bs.front_off;
-  const int* rp = rowpad + bs.row_off;
-  for (int f = 0; f < bs.nfront; ++f) {
-    const int e = fr[f + 1];
-    for (int pos = fr[f] + threadIdx.x; pos < e; pos += blockDim.x) {
-      const int pi = rp[pos];
-      T s = t[pi];
-#pragma unroll
-      for (int o = 0; o < C; ++o) s -= fac<T, FT>(F + (long long)o * rows + pos) * t[pi + off[o]];
-      t[pi] = s;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    for (int c = 0; c < NBUF - 1 && c < nc; ++c) {
+      const int k = BACK ? nc - 1 - c : c;
+      bulk_load(rg.slot[c % NBUF], part + (long long)fp[ch[k]] * LOR_REC,
+                (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * LOR_REC * sizeof(FT)), rg.bar + (c % NBUF));
+      rg.inflight |= 1u << (c % NBUF);
     }
-    __syncthreads();
   }
-  for (int f = bs.nfront - 1; f >= 0; --f) {
-    const int e = fr[f + 1];
-    for (int pos = fr[f] + threadIdx.x; pos < e; pos += blockDim.x) {
-      const int pi = rp[pos];
-      T s = t[pi];
-#pragma unroll
-      for (int o = C + 1; o < NS; ++o) s -= fac<T, FT>(F + (long long)o * rows + pos) * t[pi + off[o]];
-      t[pi] = s * fac<T, FT>(F + (long long)C * rows + pos);
+  for (int c = 0; c < nc; ++c) {
+    const int sl = c % NBUF;
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(rg.bar + sl, (rg.phase >> sl) & 1u) ? 1 : 0;
+    rg.phase ^= 1u << sl;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return false;
+    if (lane == 0) {
+      rg.inflight &= ~(1u << sl);
+      const int cn = c + NBUF - 1;
+      if (cn < nc) {
+        const int k = BACK ? nc - 1 - cn : cn;
+        bulk_load(rg.slot[cn % NBUF], part + (long long)fp[ch[k]] * LOR_REC,
+                  (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * LOR_REC * sizeof(FT)), rg.bar + (cn % NBUF));
+        rg.inflight |= 1u << (cn % NBUF);
+      }
     }
-    __syncthreads();
+    __syncwarp();
+    const FT* blk = rg.slot[sl];
+    const int k = BACK ? nc - 1 - c : c;
+    const int fa = ch[k], fb = ch[k + 1];
+    const int r0 = fp[fa];
+    for (int q = 0; q < fb - fa; ++q) {
+      const int f = BACK ? fb - 1 - q : fa + q;
+      const int p0 = fr[f], p1 = fr[f + 1];
+      const FT* fbk = blk + (fp[f] - r0) * LOR_REC;
+      for (int pos = p0 + lane; pos < p1; pos += 32) {
+        const int li = rl[pos];
+        const FT* rec = fbk + (pos - p0) * LOR_REC;
+        T s0 = t[li], s1 = T(0);
+#pragma unroll
+        for (int o = 0; o < C; ++o) {
+          const int so = BACK ? C + 1 + o : o;                 // stencil offset index
+          const int dx = so % 3 - 1, dy = (so / 3) % 3 - 1, dz = DIM == 3 ? so / 9 - 1 : 0;
+          const T v = fac<T, FT>(rec[o]) * t[li + dz * AB + dy * A + dx];
+          if (o & 1) s1 -= v; else s0 -= v;
+        }
+        t[li] = BACK ? (s0 + s1) * fac<T, FT>(rec[LOR_REC - 1]) : s0 + s1;
+      }
+      __syncwarp();
+    }
   }
+  return true;
 }
 
-// t = rhs - A x on one level; rhs from global r (level 0) or from rs
+// in-place (L U)^{-1} t on one level: warp 0 runs the forward and backward
+// sweeps, the other warps wait at the closing __syncthreads.  Returns false on
+// all threads if a bulk copy timed out.
+template <typename FT>
+constexpr int elem_class() { return sizeof(FT) == 2 ? 0 : (sizeof(FT) == 4 ? 1 : 2); }
+
+template <int DIM, typename T, typename FT, int NBUF>
+__device__ bool ilu_solve(const BoxShape& bs, const LevelTables& tb, const FT* FL, T* t, Ring<FT, NBUF>& rg,
+                          int* abort) {
+  constexpr int ES = elem_class<FT>();
+  if (threadIdx.x < 32) {
+    const int A = bs.dims[0], AB = bs.dims[0] * bs.dims[1];
+    bool ok = sweep<DIM, false, T, FT, NBUF>(FL, tb.front, tb.fpad, tb.chunk, tb.rowlex, bs.nchunk[ES], A, AB, t, rg);
+    if (ok)
+      ok = sweep<DIM, true, T, FT, NBUF>(FL + (long long)bs.rpad * LOR_REC, tb.front, tb.fpad, tb.chunk, tb.rowlex,
+                                          bs.nchunk[ES], A, AB, t, rg);
+    if (!ok && threadIdx.x == 0) *abort = 1;
+  }
+  __syncthreads();
+  return *abort == 0;
+}
+
+// t = rhs - A x on one level (rhs from global r on level 0, else from rs).
 template <int DIM, typename T>
-__device__ void residual(const Box& b, const PLevel& lv, const T* rglob, const T* rs, const T* x, T* t) {
+__device__ __forceinline__ void residual(int A, int B, int Cz, int ox, int oy, int oz, int Nx, int Ny, long long ntot,
+                                         const T* __restrict__ S, const T* __restrict__ rglob,
+                                         const T* __restrict__ rs, const T* x, T* t) {
   constexpr int NS = DIM == 3 ? 27 : 9;
-  int off[NS];
-  off_table<DIM>(b, off);
-  const T* S = (const T*)lv.S;
-  for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-    const int i = lex % b.A, j = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-    const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + j)) * lv.N[0] + (b.org[0] + i);
-    const int pi = pad_of(b, i, j, k);
+  const int rows = A * B * Cz;
+  for (int lex = threadIdx.x; lex < rows; lex += blockDim.x) {
+    const int i = lex % A, j = (lex / A) % B, k = lex / (A * B);
+    const long long G = ((long long)(oz + k) * Ny + (oy + j)) * Nx + (ox + i);
     T s = rglob ? rglob[G] : rs[lex];
 #pragma unroll
-    for (int o = 0; o < NS; ++o) s -= S[(long long)o * lv.ntot + G] * x[pi + off[o]];
-    t[pi] = s;
+    for (int o = 0; o < NS; ++o) {
+      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+      const T sv = S[(long long)o * ntot + G];   // the row's own coefficient: always in range
+      const bool in = (unsigned)(i + dx) < (unsigned)A && (unsigned)(j + dy) < (unsigned)B &&
+                      (unsigned)(k + dz) < (unsigned)Cz;
+      const T xv = in ? x[lex + (dz * B + dy) * A + dx] : T(0);
+      s -= sv * xv;
+    }
+    t[lex] = s;
   }
 }
 
-template <int DIM, typename T, typename FT>
-__global__ void __launch_bounds__(128) k_patch_vcycle(PatchArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = (T*)smem_raw;
-  const int j = blockIdx.x;
-  int v[3];
-  v[0] = j % (a.n[0] + 1);
-  v[1] = (j / (a.n[0] + 1)) % (a.n[1] + 1);
-  v[2] = DIM == 3 ? j / ((a.n[0] + 1) * (a.n[1] + 1)) : 0;
-  int sh = 0, type[3] = {0, 0, 0};
-  for (int t = 0; t < DIM; ++t) {
-    type[t] = (v[t] == 0 || v[t] == a.n[t]) ? 1 : 0;
-    sh |= type[t] << t;
+#define LOR_RESID(l_, rglob_) \
+  residual<DIM, T>(bx[l_].A, bx[l_].B, bx[l_].C, bx[l_].org[0], bx[l_].org[1], bx[l_].org[2], a.lv[l_].N[0], \
+                   a.lv[l_].N[1], a.lv[l_].ntot, (const T*)a.lv[l_].S, rglob_, rs[l_], xs[l_], ts[l_])
+
+template <int DIM, typename T, typename FT, int NBUF>
+__global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
+  constexpr int ES = elem_class<FT>();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int abort_flag;
+  // shared memory: [NBUF mbarriers | pad][ring][transfer tables][wavefront tables][vectors]
+  Ring<FT, NBUF> rg;
+  rg.bar = (unsigned long long*)smem_raw;
+  unsigned char* ring0 = smem_raw + 128;
+  for (int s = 0; s < NBUF; ++s) rg.slot[s] = (FT*)(ring0 + (size_t)s * a.slot_bytes);
+  rg.phase = 0;
+  rg.inflight = 0;
+  Xfer1D<T>* xf = (Xfer1D<T>*)(ring0 + (size_t)NBUF * a.slot_bytes);   // [level][type]
+  int* ip = (int*)(xf + 2 * (a.L > 1 ? a.L - 1 : 1));
+  int* ip_end = ip + a.tab_ints;
+  T* sm = (T*)ip_end;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < NBUF; ++s) mbar_init(rg.bar + s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  Box bx[LOR_MAXLEV];
-  BoxShape bsh[LOR_MAXLEV];
-  T* xs[LOR_MAXLEV];
-  T* ts[LOR_MAXLEV];
-  T* rs[LOR_MAXLEV];
-  long long offset = 0;
-  for (int l = 0; l < a.L; ++l) {
-    BoxShape bs = a.shapes[l * 8 + sh];
-    bsh[l] = bs;
-    Box& b = bx[l];
-    b.A = bs.dims[0]; b.B = bs.dims[1]; b.C = bs.dims[2];
-    b.rows = bs.rows;
-    b.pa = b.A + 2; b.pb = b.B + 2; b.pz = DIM == 3 ? 1 : 0;
-    const int pc = DIM == 3 ? b.C + 2 : 1;
-    for (int t = 0; t < 3; ++t) {
-      b.type[t] = type[t];
-      b.org[t] = t < DIM ? (v[t] > 0 ? v[t] - 1 : 0) * a.lv[l].m + 1 : 0;
+  // 1D transfer tables of every level (independent of the patch)
+  for (int l = 0; l + 1 < a.L; ++l)
+    for (int ty = 0; ty < 2; ++ty) {
+      Xfer1D<T>& X = xf[l * 2 + ty];
+      const int len = a.lv[l].len[ty], clen = a.lv[l].clen[ty];
+      for (int f = threadIdx.x; f < len; f += blockDim.x) {
+        const Prolong1D pr = a.lv[l].pp[ty][f];
+        X.c0[f] = pr.c0; X.c1[f] = pr.c1; X.w0[f] = (T)pr.w0; X.w1[f] = (T)pr.w1;
+      }
+      if (threadIdx.x == 0) {
+        int q = 0;
+        for (int cc = 0; cc < clen; ++cc) {
+          X.rstart[cc] = q;
+          const RestrictEntry& e = a.lv[l].rr[ty][cc];
+          for (int t = 0; t < e.cnt; ++t) { X.rf[q] = e.f[t]; X.rw[q] = (T)e.w[t]; ++q; }
+        }
+        X.rstart[clen] = q;
+      }
     }
-    const int padn = b.pa * b.pb * pc;
-    xs[l] = sm + offset; offset += padn;
-    ts[l] = sm + offset; offset += padn;
-    rs[l] = sm + offset; offset += (l > 0 ? b.rows : 0);
-  }
-  if (bx[0].rows == 0) return;
-  for (long long i = threadIdx.x; i < offset; i += blockDim.x) sm[i] = T(0);
-  __syncthreads();
-  const T* rg = (const T*)a.r;
-  const FT* F = (const FT*)a.F;
-  // deepest level with unknowns
-  int bottom = 0;
-  while (bottom + 1 < a.L && bx[bottom + 1].rows > 0) ++bottom;
-  // ---- down
-  for (int l = 0; l < bottom; ++l) {
-    const Box& b = bx[l];
-    const PLevel& lv = a.lv[l];
-    const FT* Fl = F + a.facoff[(long long)l * a.J + j];
+  int cur_sh = -1;
+  LevelTables tb[LOR_MAXLEV];
+  BoxShape bsh[LOR_MAXLEV];
+  for (int jo = blockIdx.x; jo < a.J; jo += gridDim.x) {
+    const int j = a.porder[jo];
+    int v[3];
+    v[0] = j % (a.n[0] + 1);
+    v[1] = (j / (a.n[0] + 1)) % (a.n[1] + 1);
+    v[2] = DIM == 3 ? j / ((a.n[0] + 1) * (a.n[1] + 1)) : 0;
+    int sh = 0, type[3] = {0, 0, 0};
+    for (int t = 0; t < DIM; ++t) {
+      type[t] = (v[t] == 0 || v[t] == a.n[t]) ? 1 : 0;
+      sh |= type[t] << t;
+    }
+    __syncthreads();   // previous patch done with shared memory
+    if (sh != cur_sh) {
+      // wavefront tables of every level of this shape
+      int ioff = 0;
+      for (int l = 0; l < a.L; ++l) {
+        bsh[l] = a.shapes[l * 8 + sh];
+        tb[l].front = ip + ioff; ioff += bsh[l].nfront + 1;
+        tb[l].fpad = ip + ioff; ioff += bsh[l].nfront + 1;
+        tb[l].chunk = ip + ioff; ioff += bsh[l].nchunk[ES] + 1;
+      }
+      unsigned short* up = (unsigned short*)(ip + ioff);
+      int uoff = 0;
+      for (int l = 0; l < a.L; ++l) { tb[l].rowlex = up + uoff; uoff += bsh[l].rows; }
+      for (int l = 0; l < a.L; ++l) {
+        const int nf1 = bsh[l].nfront + 1;
+        for (int i = threadIdx.x; i < nf1; i += blockDim.x) {
+          ((int*)tb[l].front)[i] = a.front[bsh[l].front_off + i];
+          ((int*)tb[l].fpad)[i] = a.fpad[bsh[l].front_off + i];
+        }
+        for (int i = threadIdx.x; i <= bsh[l].nchunk[ES]; i += blockDim.x)
+          ((int*)tb[l].chunk)[i] = a.chunk[bsh[l].chunk_off[ES] + i];
+        for (int i = threadIdx.x; i < bsh[l].rows; i += blockDim.x)
+          ((unsigned short*)tb[l].rowlex)[i] = (unsigned short)a.rowlex[bsh[l].row_off + i];
+      }
+      cur_sh = sh;
+    }
+    if (bsh[0].rows == 0) continue;
+    Box bx[LOR_MAXLEV];
+    T* xs[LOR_MAXLEV];
+    T* ts[LOR_MAXLEV];
+    T* rs[LOR_MAXLEV];
+    long long offset = 0;
+    for (int l = 0; l < a.L; ++l) {
+      const BoxShape& bs = bsh[l];
+      Box& b = bx[l];
+      b.A = bs.dims[0]; b.B = bs.dims[1]; b.C = bs.dims[2];
+      b.rows = bs.rows;
+      for (int t = 0; t < 3; ++t) {
+        b.type[t] = type[t];
+        b.org[t] = t < DIM ? (v[t] > 0 ? v[t] - 1 : 0) * a.lv[l].m + 1 : 0;
+      }
+      xs[l] = sm + offset; offset += b.rows;
+      ts[l] = sm + offset + bs.guard; offset += b.rows + 2 * bs.guard;
+      rs[l] = sm + offset; offset += (l > 0 ? b.rows : 0);
+    }
+    for (long long i = threadIdx.x; i < offset; i += blockDim.x) sm[i] = T(0);
+    __syncthreads();
+    const T* rg0 = (const T*)a.r;
+    const FT* F = (const FT*)a.F;
+    int bottom = 0;
+    while (bottom + 1 < a.L && bx[bottom + 1].rows > 0) ++bottom;
+    bool ok = true;
+    // ---- down
+    for (int l = 0; l < bottom && ok; ++l) {
+      const Box& b = bx[l];
+      const PLevel& lv = a.lv[l];
+      const FT* FL = F + a.facoff[(long long)l * a.J + j] * LOR_REC;
+      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
+        const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
+        const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
+        ts[l][lex] = l == 0 ? rg0[G] : rs[l][lex];
+      }
+      __syncthreads();
+      ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], tb[l], FL, ts[l], rg, &abort_flag);
+      if (!ok) break;
+      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) xs[l][lex] = ts[l][lex];
+      __syncthreads();
+      LOR_RESID(l, l == 0 ? rg0 : nullptr);
+      __syncthreads();
+      const Xfer1D<T>& X0 = xf[l * 2 + type[0]];
+      const Xfer1D<T>& X1 = xf[l * 2 + type[1]];
+      const Xfer1D<T>& X2 = xf[l * 2 + type[2]];
+      const int fA = b.A, fB = b.B;
+      const int cA = bx[l + 1].A, cB = bx[l + 1].B, crows = bx[l + 1].rows;
+      const T* tl = ts[l];
+      T* rn = rs[l + 1];
+      for (int lex = threadIdx.x; lex < crows; lex += blockDim.x) {
+        const int ci = lex % cA, cj = (lex / cA) % cB, ck = lex / (cA * cB);
+        T s = 0;
+        const int z0 = DIM == 3 ? X2.rstart[ck] : 0, z1 = DIM == 3 ? X2.rstart[ck + 1] : 1;
+        for (int tz = z0; tz < z1; ++tz) {
+          const int fz = DIM == 3 ? X2.rf[tz] : 0;
+          const T wz = DIM == 3 ? X2.rw[tz] : T(1);
+          for (int ty = X1.rstart[cj]; ty < X1.rstart[cj + 1]; ++ty) {
+            const T wy = X1.rw[ty] * wz;
+            const int rowb = (fz * fB + X1.rf[ty]) * fA;
+            for (int tx = X0.rstart[ci]; tx < X0.rstart[ci + 1]; ++tx) s += X0.rw[tx] * wy * tl[rowb + X0.rf[tx]];
+          }
+        }
+        rn[lex] = s;
+      }
+      __syncthreads();
+    }
+    // ---- bottom level: exact solve on the vertex level (<= 1 unknown); a
+    // truncated box (boundary patch whose vertex level is empty) is smoothed by
+    // ILU(0) twice instead (pre and post, no coarser correction)
+    if (ok) {
+      const int l = bottom;
+      const Box& b = bx[l];
+      const PLevel& lv = a.lv[l];
+      if (l == a.L - 1) {
+        const T* S = (const T*)lv.S;
+        for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
+          const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
+          const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
+          const T rhs = l == 0 ? rg0[G] : rs[l][lex];
+          xs[l][lex] = rhs / S[(long long)(a.NS / 2) * lv.ntot + G];
+        }
+        __syncthreads();
+      } else {
+        const FT* FL = F + a.facoff[(long long)l * a.J + j] * LOR_REC;
+        for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
+          const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
+          const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
+          ts[l][lex] = l == 0 ? rg0[G] : rs[l][lex];
+        }
+        __syncthreads();
+        ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], tb[l], FL, ts[l], rg, &abort_flag);
+        if (ok) {
+          for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) xs[l][lex] = ts[l][lex];
+          __syncthreads();
+          LOR_RESID(l, l == 0 ? rg0 : nullptr);
+          __syncthreads();
+          ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], tb[l], FL, ts[l], rg, &abort_flag);
+        }
+        if (ok) {
+          for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) xs[l][lex] += ts[l][lex];
+          __syncthreads();
+        }
+      }
+    }
+    // ---- up
+    for (int l = bottom - 1; l >= 0 && ok; --l) {
+      const Box& b = bx[l];
+      const Box& bc = bx[l + 1];
+      const PLevel& lv = a.lv[l];
+      const FT* FL = F + a.facoff[(long long)l * a.J + j] * LOR_REC;
+      const Xfer1D<T>& X0 = xf[l * 2 + type[0]];
+      const Xfer1D<T>& X1 = xf[l * 2 + type[1]];
+      const Xfer1D<T>& X2 = xf[l * 2 + type[2]];
+      const int fA = b.A, fB = b.B, frows = b.rows;
+      const int cA = bc.A, cB = bc.B, cC = bc.C;
+      const T* xc = xs[l + 1];
+      T* xl = xs[l];
+      for (int lex = threadIdx.x; lex < frows; lex += blockDim.x) {
+        const int i = lex % fA, jj = (lex / fA) % fB, k = lex / (fA * fB);
+        T s = 0;
+        const int nzz = DIM == 3 ? 2 : 1;
+        for (int sz = 0; sz < nzz; ++sz) {
+          const int cz = DIM == 3 ? (sz ? X2.c1[k] : X2.c0[k]) : 0;
+          if (cz < 0 || cz >= cC) continue;
+          const T wz = DIM == 3 ? (sz ? X2.w1[k] : X2.w0[k]) : T(1);
+          for (int sy = 0; sy < 2; ++sy) {
+            const int cy = sy ? X1.c1[jj] : X1.c0[jj];
+            if (cy < 0 || cy >= cB) continue;
+            const T wy = (sy ? X1.w1[jj] : X1.w0[jj]) * wz;
+            for (int sx = 0; sx < 2; ++sx) {
+              const int cx = sx ? X0.c1[i] : X0.c0[i];
+              if (cx < 0 || cx >= cA) continue;
+              s += (sx ? X0.w1[i] : X0.w0[i]) * wy * xc[(cz * cB + cy) * cA + cx];
+            }
+          }
+        }
+        xl[lex] += s;
+      }
+      __syncthreads();
+      LOR_RESID(l, l == 0 ? rg0 : nullptr);
+      __syncthreads();
+      ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], tb[l], FL, ts[l], rg, &abort_flag);
+      if (!ok) break;
+      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) xs[l][lex] += ts[l][lex];
+      __syncthreads();
+    }
+    if (!ok) {
+      // a bulk copy did not arrive in time: report, drain what is still in flight, leave
+      if (threadIdx.x == 0) {
+        atomicOr(a.status, 4);
+        for (int s = 0; s < NBUF; ++s)
+          if (rg.inflight & (1u << s)) mbar_wait(rg.bar + s, (rg.phase >> s) & 1u);
+      }
+      return;
+    }
+    // ---- scatter-add R_j^T x_j
+    T* z = (T*)a.z;
+    const Box& b = bx[0];
+    const PLevel& lv = a.lv[0];
     for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
       const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
       const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-      ts[l][pad_of(b, i, jj, k)] = l == 0 ? rg[G] : rs[l][lex];
+      atomicAdd(z + G, xs[0][lex]);
     }
-    __syncthreads();
-    ilu_solve<DIM, T, FT>(b, bsh[l], a.front, a.rowpad, Fl, ts[l]);
-    for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-      const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-      const int pi = pad_of(b, i, jj, k);
-      xs[l][pi] = ts[l][pi];
-    }
-    __syncthreads();
-    residual<DIM, T>(b, lv, l == 0 ? rg : nullptr, rs[l], xs[l], ts[l]);
-    __syncthreads();
-    // restriction to level l+1
-    const Box& bc = bx[l + 1];
-    for (int lex = threadIdx.x; lex < bc.rows; lex += blockDim.x) {
-      const int ci = lex % bc.A, cj = (lex / bc.A) % bc.B, ck = lex / (bc.A * bc.B);
-      const RestrictEntry& ex = lv.rr[b.type[0]][ci];
-      const RestrictEntry& ey = lv.rr[b.type[1]][cj];
-      const RestrictEntry* ez = DIM == 3 ? &lv.rr[b.type[2]][ck] : nullptr;
-      T s = 0;
-      const int nz = DIM == 3 ? ez->cnt : 1;
-      for (int tz = 0; tz < nz; ++tz) {
-        const int fz = DIM == 3 ? ez->f[tz] : 0;
-        const T wz = DIM == 3 ? (T)ez->w[tz] : T(1);
-        for (int ty = 0; ty < ey.cnt; ++ty) {
-          const T wy = (T)ey.w[ty] * wz;
-          const int fy = ey.f[ty];
-          for (int tx = 0; tx < ex.cnt; ++tx) s += (T)ex.w[tx] * wy * ts[l][pad_of(b, ex.f[tx], fy, fz)];
-        }
-      }
-      rs[l + 1][lex] = s;
-    }
-    __syncthreads();
-  }
-  // ---- coarsest level with unknowns: exact solve.  The vertex level of a patch
-  // has a single unknown; a truncated hierarchy may stop above it, in which case
-  // the bottom level is smoothed twice by ILU(0) (pre and post, no coarse solve).
-  {
-    const int l = bottom;
-    const Box& b = bx[l];
-    const PLevel& lv = a.lv[l];
-    if (l == a.L - 1) {
-      const T* S = (const T*)lv.S;
-      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-        const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-        const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-        const T rhs = l == 0 ? rg[G] : rs[l][lex];
-        xs[l][pad_of(b, i, jj, k)] = rhs / S[(long long)(a.NS / 2) * lv.ntot + G];   // rows <= 1
-      }
-      __syncthreads();
-    } else {
-      const FT* Fl = F + a.facoff[(long long)l * a.J + j];
-      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-        const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-        const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-        ts[l][pad_of(b, i, jj, k)] = l == 0 ? rg[G] : rs[l][lex];
-      }
-      __syncthreads();
-      ilu_solve<DIM, T, FT>(b, bsh[l], a.front, a.rowpad, Fl, ts[l]);
-      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-        const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-        const int pi = pad_of(b, i, jj, k);
-        xs[l][pi] = ts[l][pi];
-      }
-      __syncthreads();
-      residual<DIM, T>(b, lv, l == 0 ? rg : nullptr, rs[l], xs[l], ts[l]);
-      __syncthreads();
-      ilu_solve<DIM, T, FT>(b, bsh[l], a.front, a.rowpad, Fl, ts[l]);
-      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-        const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-        const int pi = pad_of(b, i, jj, k);
-        xs[l][pi] += ts[l][pi];
-      }
-      __syncthreads();
-    }
-  }
-  // ---- up
-  for (int l = bottom - 1; l >= 0; --l) {
-    const Box& b = bx[l];
-    const Box& bc = bx[l + 1];
-    const PLevel& lv = a.lv[l];
-    const FT* Fl = F + a.facoff[(long long)l * a.J + j];
-    for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-      const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-      const Prolong1D px = lv.pp[b.type[0]][i], py = lv.pp[b.type[1]][jj];
-      Prolong1D pz;
-      if (DIM == 3) pz = lv.pp[b.type[2]][k]; else { pz.c0 = 0; pz.w0 = 1.0; pz.c1 = -2; pz.w1 = 0.0; }
-      T s = 0;
-      const int nzz = DIM == 3 ? 2 : 1;
-      for (int sz = 0; sz < nzz; ++sz) {
-        const int cz = sz ? pz.c1 : pz.c0;
-        if (cz < -1) continue;
-        const T wz = (T)(sz ? pz.w1 : pz.w0);
-        for (int sy = 0; sy < 2; ++sy) {
-          const int cy = sy ? py.c1 : py.c0;
-          if (cy < -1) continue;
-          const T wy = (T)(sy ? py.w1 : py.w0) * wz;
-          for (int sx = 0; sx < 2; ++sx) {
-            const int cx = sx ? px.c1 : px.c0;
-            if (cx < -1) continue;
-            s += (T)(sx ? px.w1 : px.w0) * wy * xs[l + 1][pad_of(bc, cx, cy, DIM == 3 ? cz : 0)];
-          }
-        }
-      }
-      xs[l][pad_of(b, i, jj, k)] += s;
-    }
-    __syncthreads();
-    residual<DIM, T>(b, lv, l == 0 ? rg : nullptr, rs[l], xs[l], ts[l]);
-    __syncthreads();
-    ilu_solve<DIM, T, FT>(b, bsh[l], a.front, a.rowpad, Fl, ts[l]);
-    for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-      const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-      const int pi = pad_of(b, i, jj, k);
-      xs[l][pi] += ts[l][pi];
-    }
-    __syncthreads();
-  }
-  // ---- scatter-add R_j^T x_j
-  T* z = (T*)a.z;
-  const Box& b = bx[0];
-  const PLevel& lv = a.lv[0];
-  for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-    const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-    const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-    atomicAdd(z + G, xs[0][pad_of(b, i, jj, k)]);
   }
 }
 
@@ -558,8 +747,27 @@ T* coarse_vcycle(lor_ctx* c, int l) {
   return cur;
 }
 
+const int kPatchThreads = 256;
+
+template <typename FT>
+constexpr int ring_depth() { return sizeof(FT) == 2 ? 3 : 2; }
+
 template <typename T, typename FT>
-lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F, size_t smem) {
+size_t patch_smem_bytes(const lor_ctx* c, int* tab_ints = nullptr) {
+  size_t vec = 0, tab = 0;
+  for (int l = 0; l < c->L; ++l) {
+    const BoxShape& bs = c->shapes[l * 8 + 0];   // interior shape is the largest
+    vec += (size_t)bs.rows * (l > 0 ? 3 : 2) + 2 * (size_t)bs.guard;
+    tab += 2 * (size_t)(bs.nfront + 1) + (size_t)(bs.nchunk[elem_class<FT>()] + 1) + ((size_t)bs.rows + 1) / 2;
+  }
+  tab = (tab + 3) / 4 * 4;   // ints, keeps the vectors 16-byte aligned
+  if (tab_ints) *tab_ints = (int)tab;
+  const size_t slot = (size_t)c->maxchunk[elem_class<FT>()] * LOR_REC * sizeof(FT);
+  return 128 + ring_depth<FT>() * slot + 2 * (c->L > 1 ? c->L - 1 : 1) * sizeof(Xfer1D<T>) + 4 * tab + vec * sizeof(T);
+}
+
+template <typename T, typename FT>
+lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
   const long long nvec = c->lev[0].ntot;
   cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * nvec, c->stream);
   if (e != cudaSuccess) return lor_cuda_check(c, e, "apply_P memset");
@@ -573,22 +781,41 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F, size_t smem
     for (int t = 0; t < 3; ++t) lv.N[t] = c->lev[l].N[t];
     lv.m = c->lev[l].m;
     for (int t = 0; t < 2; ++t) { lv.pp[t] = c->d_pp[l][t]; lv.rr[t] = c->d_rr[l][t]; }
+    for (int t = 0; t < 2; ++t) {
+      const int m = c->lev[l].m, mc = l + 1 < c->L ? c->lev[l + 1].m : 1;
+      lv.len[t] = t == 0 ? 2 * m - 1 : m - 1;
+      lv.clen[t] = t == 0 ? 2 * mc - 1 : mc - 1;
+    }
   }
   a.shapes = lor_dev_shapes(c);
-  a.front = c->d_front; a.rowpad = c->d_rowpad; a.rowlex = c->d_rowlex;
+  a.front = c->d_front; a.fpad = c->d_fpad; a.chunk = c->d_chunk; a.rowlex = c->d_rowlex; a.recof = c->d_recof;
+  a.nbmask = c->d_nbmask;
   a.facoff = c->d_facoff;
   a.F = F; a.r = r; a.z = z;
+  a.status = c->d_status;
+  a.porder = c->d_porder;
+  a.slot_bytes = c->maxchunk[elem_class<FT>()] * LOR_REC * (int)sizeof(FT);
+  const size_t smem = patch_smem_bytes<T, FT>(c, &a.tab_ints);
+  constexpr int NB = ring_depth<FT>();
   const int pk = sizeof(T) == 8 ? 0 : 1;
   lor_prof_begin(c, pk);
+  // persistent CTAs: as many as fit on the device, each walking patches j, j+grid, ...
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (c->dim == 3) {
-    auto kern = k_patch_vcycle<3, T, FT>;
+    auto kern = k_patch_vcycle<3, T, FT, NB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<c->J, 128, smem, c->stream>>>(a);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPatchThreads, smem);
+    const int grid = (int)std::min<long long>(c->J, (long long)std::max(per_sm, 1) * nsm);
+    kern<<<grid, kPatchThreads, smem, c->stream>>>(a);
     ++c->launches;
   } else {
-    auto kern = k_patch_vcycle<2, T, FT>;
+    auto kern = k_patch_vcycle<2, T, FT, NB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<c->J, 128, smem, c->stream>>>(a);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPatchThreads, smem);
+    const int grid = (int)std::min<long long>(c->J, (long long)std::max(per_sm, 1) * nsm);
+    kern<<<grid, kPatchThreads, smem, c->stream>>>(a);
     ++c->launches;
   }
   lor_prof_end(c, pk);
@@ -611,10 +838,16 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F, size_t smem
 }  // namespace
 
 lor_status lor_launch_apply_P64(lor_ctx* c, const double* r, double* z) {
-  return launch_apply_P<double, double>(c, r, z, c->d_F64, (size_t)c->smem_patch64);
+  return launch_apply_P<double, double>(c, r, z, c->d_F64);
 }
 
 lor_status lor_launch_apply_P32(lor_ctx* c, const float* r, float* z) {
-  if (c->d_F16) return launch_apply_P<float, __nv_bfloat16>(c, r, z, c->d_F16, (size_t)c->smem_patch32);
-  return launch_apply_P<float, float>(c, r, z, c->d_F32, (size_t)c->smem_patch32);
+  if (c->d_F16) return launch_apply_P<float, __nv_bfloat16>(c, r, z, c->d_F16);
+  return launch_apply_P<float, float>(c, r, z, c->d_F32);
+}
+
+size_t lor_patch_smem(const lor_ctx* c, int which) {
+  if (which == 0) return patch_smem_bytes<double, double>(c);
+  if (which == 1) return patch_smem_bytes<float, float>(c);
+  return patch_smem_bytes<float, __nv_bfloat16>(c);
 }

@@ -132,16 +132,6 @@ lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* verti
   return LOR_OK;
 }
 
-static size_t patch_smem(const lor_ctx* c, size_t elem) {
-  size_t tot = 0;
-  for (int l = 0; l < c->L; ++l) {
-    const BoxShape& bs = c->shapes[l * 8 + 0];   // interior shape is the largest
-    const size_t padn = (size_t)(bs.dims[0] + 2) * (bs.dims[1] + 2) * (c->dim == 3 ? bs.dims[2] + 2 : 1);
-    tot += 2 * padn + (l > 0 ? (size_t)bs.rows : 0);
-  }
-  return tot * elem;
-}
-
 lor_status lor_setup(lor_ctx* c) {
   if (!c) return LOR_EINVAL;
   if (c->setup_done) return lor_fail(c, LOR_ESTATE, "lor_setup called twice");
@@ -151,12 +141,13 @@ lor_status lor_setup(lor_ctx* c) {
   if ((s = lor_setup_patches(c))) return s;
   if ((s = lor_setup_coarse(c))) return s;
   if ((s = lor_setup_krylov(c))) return s;
-  c->smem_patch64 = (int)patch_smem(c, 8);
-  c->smem_patch32 = (int)patch_smem(c, 4);
+  c->smem_patch64 = (int)lor_patch_smem(c, 0);
+  c->smem_patch32 = (int)lor_patch_smem(c, c->d_F16 ? 2 : 1);
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (c->smem_patch64 > maxsm) return lor_fail(c, LOR_EINVAL, "patch does not fit in shared memory");
+  if (c->smem_patch64 > maxsm || c->smem_patch32 > maxsm)
+    return lor_fail(c, LOR_EINVAL, "patch does not fit in shared memory");
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return lor_cuda_check(c, e, "setup");
   c->setup_done = true;

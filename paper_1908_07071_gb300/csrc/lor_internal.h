@@ -47,12 +47,25 @@ struct LevelGrid {
 };
 
 // Shape of a patch box at one level: wavefront schedule for lexicographic ILU(0).
+// Factor storage of one patch level: front-major records of LOR_REC values.
+// L record of a row: its 13 (3D) / 4 (2D) strictly-lower ILU(0) multipliers in
+// stencil-offset order, padded; U record: its upper coefficients in
+// stencil-offset order, then 1/u_ii in the last slot.  The records of each
+// wavefront are padded to a multiple of 4 rows so every front block starts on a
+// 16-byte boundary in every precision (bulk-copy alignment).
+#define LOR_REC 14
 struct BoxShape {
   int dims[3];            // box extents (x, y, z); 1 for unused dims
   int rows;
   int nfront;
-  int front_off;          // offset into ctx->d_front (nfront+1 entries)
-  int row_off;            // offset into ctx->d_rowpad (rows entries)
+  int front_off;          // offset into ctx->d_front / d_fpad (nfront+1 entries)
+  int row_off;            // offset into the per-row tables (rows entries)
+  int rpad;               // padded records of one part (L or U)
+  int maxfront;           // largest padded front (records)
+  int nchunk[3];          // groups of consecutive fronts streamed as one bulk copy,
+  int chunk_off[3];       // per factor element size (index 0: 2, 1: 4, 2: 8 bytes);
+  int maxchunk[3];        // offsets into ctx->d_chunk (nchunk+1 front indices); records
+  int guard;              // largest |stencil offset| in the lexicographic box index
 };
 
 struct lor_ctx {
@@ -97,19 +110,25 @@ struct lor_ctx {
   std::vector<BoxShape> shapes;           // [level][8 shapes]
   BoxShape* d_shapes = nullptr;           // device copy of `shapes`
   int* d_poslex = nullptr;                // lexicographic index -> wavefront position
-  int* d_front = nullptr;
-  int* d_rowpad = nullptr;    // padded-box index of row at wavefront position
-  int* d_rowlex = nullptr;    // unpadded lexicographic index of row
+  int* d_front = nullptr;     // row position where each wavefront starts
+  int* d_fpad = nullptr;      // record offset where each wavefront starts
+  int* d_chunk = nullptr;     // first front of each bulk-copy chunk
+  int* d_rowlex = nullptr;    // lexicographic index of the row at a wavefront position
+  int* d_recof = nullptr;     // record index of the row at a wavefront position
+  unsigned* d_nbmask = nullptr;   // per lexicographic row: bit o set if neighbour o is in the box
   // per-level per-axis-type patch-local 1D prolongation (fine -> coarse, local idx)
   Prolong1D* d_pp[LOR_MAXLEV][2] = {};
   // per-level per-axis-type patch-local restriction: coarse local c -> 3 (fine local f, w), f = -1 unused
   struct RestrictEntry* d_rr[LOR_MAXLEV][2] = {};
-  long long* d_facoff = nullptr;          // [level][J] offsets into factor arrays
+  long long* d_facoff = nullptr;          // [level][J] record offsets into factor arrays
+  int* d_porder = nullptr;                // patches grouped by box shape, interior first
   long long fac_rows = 0;
   double* d_F64 = nullptr;
   float* d_F32 = nullptr;
   __nv_bfloat16* d_F16 = nullptr;
   int smem_patch64 = 0, smem_patch32 = 0;
+  int maxfront = 0;           // largest padded front over all levels/shapes (records)
+  int maxchunk[3] = {0, 0, 0};   // largest chunk (records) for 2-, 4-, 8-byte factors
   int* d_status = nullptr;    // device error word
 
   // coarse space (vertex grid hierarchy)
@@ -168,6 +187,7 @@ lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b);
 // apply_p.cu
 lor_status lor_launch_apply_P64(lor_ctx* c, const double* r, double* z);
 lor_status lor_launch_apply_P32(lor_ctx* c, const float* r, float* z);
+size_t lor_patch_smem(const lor_ctx* c, int which);   // 0 fp64, 1 fp32, 2 fp32+bf16 factors
 // krylov.cu
 lor_status lor_pcg64(lor_ctx* c, const double* b, double* x, int* iters, double* relres);
 lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, double* relres);

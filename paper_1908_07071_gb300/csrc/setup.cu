@@ -303,9 +303,10 @@ struct IluArgs {
   int N[3];            // level grid
   const BoxShape* shapes;   // 8 shapes of this level
   const int* rowlex;
+  const int* recof;
   const int* front;
   const int* poslex;   // lex -> pos, per shape (offset = shape.row_off)
-  const long long* facoff;  // this level's offsets [J]
+  const long long* facoff;  // this level's record offsets [J]
   const double* S;
   double* F;
   int* status;
@@ -329,9 +330,10 @@ __global__ void k_ilu0(IluArgs a) {
   int org[3];
   for (int t = 0; t < 3; ++t) org[t] = (t < a.dim) ? (v[t] > 0 ? v[t] - 1 : 0) * a.m + 1 : 0;
   const long long ntot = (long long)a.N[0] * a.N[1] * a.N[2];
-  double* F = a.F + a.facoff[j];
-  const int rows = bs.rows;
+  double* FL = a.F + a.facoff[j] * LOR_REC;           // L records
+  double* FU = FL + (long long)bs.rpad * LOR_REC;      // U records
   const int* rowlex = a.rowlex + bs.row_off;
+  const int* recof = a.recof + bs.row_off;
   const int* poslex = a.poslex + bs.row_off;
   const int* front = a.front + bs.front_off;
   const int NS = a.NS, C = NS / 2;
@@ -351,20 +353,24 @@ __global__ void k_ilu0(IluArgs a) {
         const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = a.dim == 3 ? o / 9 - 1 : 0;
         const int ni = i + ox, nj = jj + oy, nk = k + oz;
         if (!(ni >= 0 && ni < dx0 && nj >= 0 && nj < dy0 && nk >= 0 && nk < dz0)) continue;
-        const int kp = poslex[(nk * dy0 + nj) * dx0 + ni];
-        const double l = r[o] * F[(long long)C * rows + kp];   // a_ik / u_kk
+        const double* Uk = FU + (long long)recof[poslex[(nk * dy0 + nj) * dx0 + ni]] * LOR_REC;
+        const double l = r[o] * Uk[LOR_REC - 1];   // a_ik / u_kk
         r[o] = l;
         for (int o2 = C + 1; o2 < NS; ++o2) {   // upper part of row k
           const int px = ox + (o2 % 3 - 1), py = oy + ((o2 / 3) % 3 - 1), pz = oz + (a.dim == 3 ? o2 / 9 - 1 : 0);
           if (px < -1 || px > 1 || py < -1 || py > 1 || pz < -1 || pz > 1) continue;
           const int ot = a.dim == 3 ? (pz + 1) * 9 + (py + 1) * 3 + (px + 1) : (py + 1) * 3 + (px + 1);
-          if (ot <= o) continue;                // only entries to the right of column k
-          r[ot] -= l * F[(long long)o2 * rows + kp];
+          r[ot] -= l * Uk[o2 - C - 1];
         }
       }
-      const int pos_me = pos;
       if (!(r[C] > 0.0)) atomicOr(a.status, 2);
-      for (int o = 0; o < NS; ++o) F[(long long)o * rows + pos_me] = (o == C) ? 1.0 / r[C] : r[o];
+      double* Li = FL + (long long)recof[pos] * LOR_REC;
+      double* Ui = FU + (long long)recof[pos] * LOR_REC;
+      for (int o = 0; o < LOR_REC; ++o) {
+        Li[o] = o < C ? r[o] : 0.0;
+        Ui[o] = o < C ? r[C + 1 + o] : 0.0;
+      }
+      Ui[LOR_REC - 1] = 1.0 / r[C];
     }
     __syncthreads();
   }
@@ -594,21 +600,22 @@ lor_status lor_setup_stencils(lor_ctx* c) {
 
 // ------------------------------------------------------------ patch structures
 static int axis_len(int type, int m) { return type == 0 ? 2 * m - 1 : m - 1; }
+static const int kChunkBytes = 5632;   // bulk-copy chunk of bf16 factor records
 
 lor_status lor_setup_patches(lor_ctx* c) {
   const int dim = c->dim;
   c->J = 1;
   for (int a = 0; a < dim; ++a) c->J *= (c->n[a] + 1);
   const int nshape = 1 << dim;
-  std::vector<int> front, rowpad, rowlex, poslex;
+  std::vector<int> front, fpad, rowlex, recof, poslex, chunk;
+  std::vector<unsigned> nbmask;
   c->shapes.assign(c->L * 8, BoxShape());
+  c->maxfront = 0;
   for (int l = 0; l < c->L; ++l) {
     const int m = c->lev[l].m;
     for (int s = 0; s < nshape; ++s) {
       BoxShape bs;
       for (int a = 0; a < 3; ++a) bs.dims[a] = a < dim ? axis_len((s >> a) & 1, m) : 1;
-      // an axis with a single element has both ends on the boundary: its patches
-      // only ever use the boundary shape, so nothing special is needed here.
       bs.rows = bs.dims[0] * bs.dims[1] * bs.dims[2];
       const int A = bs.dims[0], Bd = bs.dims[1], Cd = bs.dims[2];
       const int nfront = bs.rows ? (A - 1) + 2 * (Bd - 1) + (dim == 3 ? 4 * (Cd - 1) : 0) + 1 : 0;
@@ -621,24 +628,65 @@ lor_status lor_setup_patches(lor_ctx* c) {
           for (int i = 0; i < A; ++i) byf[i + 2 * j + 4 * k].push_back((k * Bd + j) * A + i);
       std::vector<int> pl(bs.rows);
       front.push_back(0);
-      int pos = 0;
+      fpad.push_back(0);
+      int pos = 0, rec = 0, mf = 0;
       for (int f = 0; f < nfront; ++f) {
+        int q = 0;
         for (int lex : byf[f]) {
-          const int i = lex % A, j = (lex / A) % Bd, k = lex / (A * Bd);
           rowlex.push_back(lex);
-          const int pz = dim == 3 ? (k + 1) : 0;
-          rowpad.push_back((pz * (Bd + 2) + (j + 1)) * (A + 2) + (i + 1));
+          recof.push_back(rec + q++);
           pl[lex] = pos++;
         }
+        const int padlen = (int)((byf[f].size() + 3) / 4 * 4);
+        rec += padlen;
+        mf = std::max(mf, padlen);
         front.push_back(pos);
+        fpad.push_back(rec);
       }
+      bs.rpad = rec;
+      bs.maxfront = mf;
+      c->maxfront = std::max(c->maxfront, mf);
+      // chunks of whole fronts of at most kChunkBytes per factor element size; a
+      // front larger than that is a chunk of its own
+      for (int es = 0; es < 3; ++es) {
+        const int cap = kChunkBytes / (LOR_REC * (2 << es));
+        bs.chunk_off[es] = (int)chunk.size();
+        bs.nchunk[es] = 0;
+        bs.maxchunk[es] = 0;
+        int fa = 0;
+        chunk.push_back(0);
+        const int base = bs.front_off;
+        while (fa < nfront) {
+          int fb = fa + 1;
+          while (fb < nfront && (fpad[base + fb + 1] - fpad[base + fa]) <= cap) ++fb;
+          chunk.push_back(fb);
+          bs.maxchunk[es] = std::max(bs.maxchunk[es], fpad[base + fb] - fpad[base + fa]);
+          ++bs.nchunk[es];
+          fa = fb;
+        }
+      }
+      bs.guard = A * Bd + A + 1;
       for (int t = 0; t < bs.rows; ++t) poslex.push_back(pl[t]);
+      for (int t = 0; t < bs.rows; ++t) {
+        const int i = t % A, j = (t / A) % Bd, k = t / (A * Bd);
+        unsigned msk = 0;
+        for (int o = 0; o < c->NS; ++o) {
+          const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = dim == 3 ? o / 9 - 1 : 0;
+          if (i + dx >= 0 && i + dx < A && j + dy >= 0 && j + dy < Bd && k + dz >= 0 && k + dz < Cd) msk |= 1u << o;
+        }
+        nbmask.push_back(msk);
+      }
       c->shapes[l * 8 + s] = bs;
     }
   }
   if (upload(c, (void**)&c->d_front, front.data(), front.size() * 4)) return LOR_ENOMEM;
-  if (upload(c, (void**)&c->d_rowpad, rowpad.data(), std::max<size_t>(1, rowpad.size()) * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_fpad, fpad.data(), fpad.size() * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_chunk, chunk.data(), chunk.size() * 4)) return LOR_ENOMEM;
+  for (auto& bs : c->shapes)
+    for (int es = 0; es < 3; ++es) c->maxchunk[es] = std::max(c->maxchunk[es], bs.maxchunk[es]);
   if (upload(c, (void**)&c->d_rowlex, rowlex.data(), std::max<size_t>(1, rowlex.size()) * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_recof, recof.data(), std::max<size_t>(1, recof.size()) * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_nbmask, nbmask.data(), std::max<size_t>(1, nbmask.size()) * 4)) return LOR_ENOMEM;
   if (upload(c, (void**)&c->d_poslex, poslex.data(), std::max<size_t>(1, poslex.size()) * 4)) return LOR_ENOMEM;
   if (upload(c, (void**)&c->d_shapes, c->shapes.data(), c->shapes.size() * sizeof(BoxShape))) return LOR_ENOMEM;
   int* d_poslex = c->d_poslex;
@@ -679,7 +727,19 @@ lor_status lor_setup_patches(lor_ctx* c) {
     }
   }
 
-  // factor storage offsets
+  // visiting order of the patch kernel: patches grouped by box shape
+  {
+    std::vector<int> order;
+    for (int want = 0; want < 8; ++want)
+      for (int j = 0; j < c->J; ++j) {
+        int v[3] = {j % (c->n[0] + 1), (j / (c->n[0] + 1)) % (c->n[1] + 1), dim == 3 ? j / ((c->n[0] + 1) * (c->n[1] + 1)) : 0};
+        int sh = 0;
+        for (int a = 0; a < dim; ++a) sh |= ((v[a] == 0 || v[a] == c->n[a]) ? 1 : 0) << a;
+        if (sh == want) order.push_back(j);
+      }
+    if (upload(c, (void**)&c->d_porder, order.data(), order.size() * 4)) return LOR_ENOMEM;
+  }
+  // factor storage offsets (records; a patch level holds 2*rpad records)
   std::vector<long long> off((size_t)c->L * c->J);
   long long tot = 0;
   for (int l = 0; l < c->L; ++l)
@@ -688,9 +748,12 @@ lor_status lor_setup_patches(lor_ctx* c) {
       int sh = 0;
       for (int a = 0; a < dim; ++a) sh |= ((v[a] == 0 || v[a] == c->n[a]) ? 1 : 0) << a;
       off[(size_t)l * c->J + j] = tot;
-      tot += (long long)c->shapes[l * 8 + sh].rows * c->NS;
+      if (l + 1 < c->L) {   // the vertex level is solved exactly and has no factors
+        tot += 2LL * c->shapes[l * 8 + sh].rpad;
+        c->fac_rows += c->shapes[l * 8 + sh].rows;
+      }
     }
-  c->fac_rows = tot / c->NS;
+  tot *= LOR_REC;   // values
   if (upload(c, (void**)&c->d_facoff, off.data(), off.size() * 8)) return LOR_ENOMEM;
   c->d_F64 = (double*)lor_alloc(c, std::max<long long>(tot, 1) * 8);
   c->d_F32 = (float*)lor_alloc(c, std::max<long long>(tot, 1) * 4);
@@ -703,7 +766,7 @@ lor_status lor_setup_patches(lor_ctx* c) {
     for (int t = 0; t < 3; ++t) { a.n[t] = c->n[t]; a.N[t] = c->lev[l].N[t]; }
     a.m = c->lev[l].m;
     a.shapes = d_shapes + l * 8;
-    a.rowlex = c->d_rowlex; a.front = c->d_front; a.poslex = d_poslex;
+    a.rowlex = c->d_rowlex; a.recof = c->d_recof; a.front = c->d_front; a.poslex = d_poslex;
     a.facoff = c->d_facoff + (size_t)l * c->J;
     a.S = c->d_S64[l];
     a.F = c->d_F64;
