@@ -149,6 +149,29 @@ lor_status lor_profile_read(lor_ctx* ctx, int kernel, double* total_ms, long lon
  * FP64 outer residuals and inner FP64-accumulated norms for LOR_MIXED). */
 lor_status lor_residual_history(const lor_ctx* ctx, double* out, int cap, int* count);
 
+/* Allocation-free right-hand side (no counterpart in the paper; a service for
+ * callers that may not call cudaMalloc).  Some callers cannot allocate device
+ * memory: a host framework that hands all device memory to its own caching
+ * pool and forbids raw cudaMalloc, or a process whose device-memory budget is
+ * fixed at start-up.  They cannot build a lor_ctx either, so this entry point
+ * needs none: given DEVICE vertex coordinates (layout as for lor_create), it
+ * computes the same b = M f as lor_rhs (kinds 0 and 1, (p+1)^d Gauss points)
+ * into the caller's DEVICE vector d_b (an L-vector, boundary entries 0), on
+ * `stream` (a cudaStream_t or NULL).
+ * Scratch: the per-point quadrature weights and the 1D basis tables live in
+ * one file-scope static device array of LOR_RHS_STATIC_MAX_DOUBLES doubles
+ * (16 MiB, held by every GPU that loads the library until the process exits);
+ * problems with nel*(p+1)^d > LOR_RHS_STATIC_MAX_DOUBLES - 256 are rejected
+ * with LOR_EINVAL.  The call allocates nothing and frees nothing.
+ * The first call on a device looks up the device address of that array (with
+ * the device current); make that first call before any stream capture.
+ * Every call shares the one array and overwrites it, so calls that may run
+ * concurrently on the GPU (other streams, other threads) race: serialise them.
+ * Returns LOR_EINVAL for bad arguments, LOR_ECUDA if a CUDA call fails. */
+#define LOR_RHS_STATIC_MAX_DOUBLES (1 << 21)
+lor_status lor_rhs_static(int dim, int p, int nx, int ny, int nz, const double* d_vertices, int kind,
+                          double* d_b, void* stream);
+
 const char* lor_last_error(const lor_ctx* ctx);
 void lor_destroy(lor_ctx* ctx);
 

@@ -9,6 +9,8 @@
 // registers, x/y contractions go through shared memory); several elements per
 // CTA for small p.  Element-interior outputs are stored, shared ones added with
 // atomics; global boundary (Dirichlet) nodes read as 0 and are never written.
+#include <mutex>
+
 #include "lor_internal.h"
 
 namespace {
@@ -389,4 +391,63 @@ lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b) {
   k_rhs_scatter<<<blocks, 256, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1], c->n[2], lor_basis64(c, 0), W, b);
   ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "rhs launch");
+}
+
+// ---------------------------------------------------------- allocation-free rhs
+// One file-scope device array serves every call of lor_rhs_static: the first
+// 256 doubles hold the 1D tables (B at Gauss points, Gauss nodes and weights),
+// the rest the per-point weights W.  Host code must not use the symbol itself
+// as an address: the device address is looked up once per device.
+static __device__ __align__(256) double g_rhs_static[LOR_RHS_STATIC_MAX_DOUBLES];
+
+namespace {
+const int kStaticTables = 256;
+std::mutex g_rhs_static_mu;
+double* g_rhs_static_ptr[128] = {};
+
+double* rhs_static_scratch(cudaError_t* err) {
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
+  std::lock_guard<std::mutex> lk(g_rhs_static_mu);
+  if (!g_rhs_static_ptr[dev]) {
+    void* ptr = nullptr;
+    *err = cudaGetSymbolAddress(&ptr, g_rhs_static);
+    if (*err != cudaSuccess) return nullptr;
+    g_rhs_static_ptr[dev] = (double*)ptr;
+  }
+  return g_rhs_static_ptr[dev];
+}
+}  // namespace
+
+extern "C" lor_status lor_rhs_static(int dim, int p, int nx, int ny, int nz, const double* d_vertices, int kind,
+                                     double* d_b, void* stream) {
+  if ((dim != 2 && dim != 3) || p < 1 || p > LOR_MAXP || nx < 1 || ny < 1 || (dim == 3 && nz < 1)) return LOR_EINVAL;
+  if (!d_vertices || !d_b || kind < 0 || kind > 1) return LOR_EINVAL;
+  const int Q = p + 1;
+  const int zz = dim == 3 ? nz : 1;
+  const long long nel = (long long)nx * ny * zz;
+  const long long Qd = dim == 3 ? (long long)Q * Q * Q : (long long)Q * Q;
+  if (nel * Qd > (long long)LOR_RHS_STATIC_MAX_DOUBLES - kStaticTables) return LOR_EINVAL;
+  cudaError_t e;
+  double* base = rhs_static_scratch(&e);
+  if (!base) return LOR_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  // 1D tables on the host, copied into the head of the static array
+  double tab[kStaticTables] = {0};
+  double gll_x[LOR_MAXP + 1], gll_w[LOR_MAXP + 1], Dn[(LOR_MAXP + 1) * (LOR_MAXP + 1)];
+  double* Bm = tab;                        // Q*Q
+  double* glx = tab + 128;                 // Q
+  double* glw = tab + 192;                 // Q
+  lorh::gll(p, gll_x, gll_w);
+  lorh::gauss(Q, glx, glw);
+  lorh::lagrange(Q, gll_x, Q, glx, Bm, Dn);
+  if ((e = cudaMemcpyAsync(base, tab, sizeof(tab), cudaMemcpyHostToDevice, st)) != cudaSuccess) return LOR_ECUDA;
+  const long long nvec = (long long)(nx * p + 1) * (ny * p + 1) * (dim == 3 ? (nz * p + 1) : 1);
+  if ((e = cudaMemsetAsync(d_b, 0, sizeof(double) * nvec, st)) != cudaSuccess) return LOR_ECUDA;
+  double* W = base + kStaticTables;
+  const unsigned blocks = (unsigned)lor_ceil_div(nel * Qd, 256);
+  k_rhs_weights<<<blocks, 256, 0, st>>>(dim, p, nx, ny, zz, d_vertices, base + 128, base + 192, kind, W);
+  k_rhs_scatter<<<blocks, 256, 0, st>>>(dim, p, nx, ny, zz, base, W, d_b);
+  return cudaGetLastError() == cudaSuccess ? LOR_OK : LOR_ECUDA;
 }

@@ -71,6 +71,8 @@ def load():
     lib.lor_last_error.restype = ctypes.c_char_p
     lib.lor_destroy.argtypes = [vp]
     lib.lor_destroy.restype = None
+    lib.lor_rhs_static.argtypes = [i, i, i, i, i, vp, i, vp, vp]
+    lib.lor_rhs_static.restype = ctypes.c_int
     lib.lor_set_prec.argtypes = [vp, i]
     lib.lor_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.lor_profile.argtypes = [vp, i]
