@@ -1,0 +1,133 @@
+"""Pins of the DG part of the oracle (Section 2.1 and Section 3.5; no GPU)."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+from oracle import cg, dg, krylov, lor
+from oracle.basis import gll
+from oracle.mesh import Mesh
+from paper_1908_07071_gb300.synthetic import make_mesh
+
+
+def _mesh(dim, n, pert=0.15, kc=None, seed=0):
+    v, k = make_mesh(dim, n, seed=seed, perturb=pert, kappa_const=kc)
+    return Mesh(v, k)
+
+
+@pytest.mark.parametrize("form", ["ip", "br2"])
+@pytest.mark.parametrize("dim,n,p", [(2, 3, 3), (3, 2, 2)])
+def test_symmetric_and_conforming_restriction(form, dim, n, p):
+    """A_DG is symmetric and E^T A_DG E = K_p on H^1_0 (jumps of conforming functions vanish)."""
+    m = _mesh(dim, n)
+    A = dg.assemble_dg(m, p, eta=10.0, form=form)
+    assert abs(A - A.T).max() < 1e-12 * abs(A).max()
+    E = dg.injection(m, p)
+    K = cg.assemble_stiffness(m, p)
+    N = cg.node_shape(m.n, p)
+    mask = ~cg.boundary_mask(N)
+    lhs = (E.T @ A @ E).toarray()[np.ix_(mask, mask)]
+    np.testing.assert_allclose(lhs, K.toarray()[np.ix_(mask, mask)], atol=1e-11 * abs(K).max())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_br2_lumped_penalty_closed_form(dim):
+    """Cartesian cells of side h, b = 1: the BR2 penalty per face node is
+    eta w_f h^(d-2) / (2 w_end) on interior faces (two sides of eta w_f h^(d-2) / (4 w_end))."""
+    p, n = 3, 2
+    m = _mesh(dim, n, pert=0.0, kc=1.0)
+    h = 1.0 / n
+    A1 = dg.assemble_dg(m, p, eta=1.0, form="br2")
+    A2 = dg.assemble_dg(m, p, eta=2.0, form="br2")
+    D = (A2 - A1).tocoo()                     # = penalty at eta = 1
+    xg, wg = gll(p)
+    Q = p + 1
+    nb = Q ** dim
+    # face between element 0 and element 1 along x: node (p, j[, k]) of e0 and (0, j[, k]) of e1
+    for j in range(Q):
+        wf = wg[j] if dim == 2 else wg[j] * wg[1]
+        loc0 = p + Q * j + (Q * Q * 1 if dim == 3 else 0)
+        loc1 = 0 + Q * j + (Q * Q * 1 if dim == 3 else 0)
+        expect = wf * h ** (dim - 2) / (2 * wg[0])
+        Dd = D.tocsr()
+        # penalty couples u- and u+ at the node with -beta (jump times jump)
+        assert abs(Dd[loc0, nb + loc1] + expect) < 1e-12 * expect
+
+
+def test_ip_manufactured_order():
+    exact = lambda X: np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1])  # noqa: E731
+    f = lambda X: 2 * np.pi ** 2 * exact(X)  # noqa: E731
+    p = 2
+    errs = []
+    for n in (2, 4, 8):
+        m = _mesh(2, n, pert=0.0, kc=1.0)
+        A = dg.assemble_dg(m, p, eta=4.0, form="ip")
+        b = dg.load_vector_dg(m, p, f, q=p + 3)
+        u = spla.spsolve(A.tocsc(), b)
+        # L2 error element by element with the DG field
+        from oracle.cg import tensor_points
+        from oracle.basis import gauss_legendre
+        from oracle.mesh import multilinear
+        x1, w1 = gauss_legendre(p + 3)
+        pts, w = tensor_points(2, x1, w1)
+        phi, _ = dg.basis_at(p, pts)
+        err = 0.0
+        for e in m.elements():
+            X, J = multilinear(m.corners(e), pts)
+            base = dg.elem_index(e, m.n) * (p + 1) ** 2
+            uh = phi @ u[base:base + (p + 1) ** 2]
+            err += np.sum(w * np.abs(np.linalg.det(J)) * (uh - exact(X)) ** 2)
+        errs.append(np.sqrt(err))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] > p + 1 - 0.3, rates
+
+
+def test_large_penalty_approaches_conforming_solution():
+    m = _mesh(2, 3)
+    p = 3
+    f = lambda X: np.ones(len(X))  # noqa: E731
+    K = cg.assemble_stiffness(m, p)
+    N = cg.node_shape(m.n, p)
+    mask = ~cg.boundary_mask(N)
+    bc = cg.load_vector(m, p, f, q=p + 1)
+    uc = np.zeros(K.shape[0])
+    uc[mask] = spla.spsolve(K[mask][:, mask].tocsc(), bc[mask])
+    E = dg.injection(m, p)
+    bd = dg.load_vector_dg(m, p, f)
+    diffs = []
+    for eta in (1e2, 1e4, 1e6):
+        A = dg.assemble_dg(m, p, eta=eta, form="ip")
+        u = spla.spsolve(A.tocsc(), bd)
+        diffs.append(np.linalg.norm(u - E @ uc) / np.linalg.norm(E @ uc))
+    assert diffs[2] < diffs[1] < diffs[0] and diffs[2] < 1e-3, diffs
+
+
+def _eta_min(m, p, form):
+    for k in range(-8, 40):
+        eta = 2.0 ** (k / 4)
+        A = dg.assemble_dg(m, p, eta=eta, form=form).toarray()
+        try:
+            sla.cholesky(A)
+            return eta
+        except sla.LinAlgError:
+            continue
+    raise AssertionError("no stable eta")
+
+
+@pytest.mark.parametrize("form", ["ip", "br2"])
+def test_spd_threshold_and_eta_robust_iterations(form):
+    """Coercive above a minimal eta; B_DG iteration counts stay flat in eta (Section 3.5, Table 8)."""
+    m = _mesh(3, 2)
+    p = 2
+    emin = _eta_min(m, p, form)
+    assert emin < 4.0
+    if form == "br2":          # literature coercivity bound for BR2: eta > number of faces (2d)
+        emin = max(emin, 6.0)
+    Bc = lor.LORPreconditioner(m, p)
+    its = []
+    for mult in (1.0, 10.0, 100.0, 1000.0):
+        A = dg.assemble_dg(m, p, eta=emin * mult, form=form)
+        P = dg.DGPreconditioner(m, p, A, Bc)
+        b = dg.load_vector_dg(m, p, lambda X: np.ones(len(X)))
+        its.append(krylov.pcg(lambda u: A @ u, P.apply, b, rtol=1e-8)[1])
+    assert max(its) <= 1.6 * min(its) + 2, its
