@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblor.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "setup.cu", "apply_a.cu", "apply_p.cu", "krylov.cu", "host_basis.cpp"]
+SOURCES = ["capi.cu", "setup.cu", "apply_a.cu", "apply_p.cu", "krylov.cu", "dg.cu", "host_basis.cpp"]
 
 
 def _nvcc():
@@ -45,7 +45,8 @@ def build_library(force: bool = False, verbose_ptxas: bool = False) -> str:
     """Compiles (if any source is newer than the library) and returns the .so path."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES] + [
-        os.path.join(CSRC, "lor_internal.h"), os.path.join(HERE, "..", "include", "lor.h")]
+        os.path.join(CSRC, "lor_internal.h"), os.path.join(CSRC, "geom.cuh"),
+        os.path.join(HERE, "..", "include", "lor.h")]
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(s) for s in srcs)
         if os.path.getmtime(LIB) >= newest:

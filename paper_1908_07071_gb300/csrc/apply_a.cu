@@ -21,7 +21,10 @@ struct ElemsPerBlock {
   static constexpr int v2 = (256 / (Q * Q)) > 0 ? (256 / (Q * Q)) : 1;
 };
 
-template <int P, typename T>
+// DGM = false: continuous Q_p on the structured node grid (gather/scatter,
+// Dirichlet nodes masked).  DGM = true: element-local DG blocks of (p+1)^3
+// values (element e at e*(p+1)^3), no masking, outputs stored (not added).
+template <int P, typename T, bool DGM>
 __global__ void __launch_bounds__(256) k_apply3d(int nx, int ny, int nz, const T* __restrict__ Bg,
                                                  const T* __restrict__ Dg, const T* __restrict__ G,
                                                  const T* __restrict__ x, T* __restrict__ y) {
@@ -41,13 +44,16 @@ __global__ void __launch_bounds__(256) k_apply3d(int nx, int ny, int nz, const T
   int ex = 0, ey = 0, ez = 0;
   if (live) { ex = (int)(e % nx); ey = (int)((e / nx) % ny); ez = (int)(e / ((long long)nx * ny)); }
   const int I = ex * P + tx, Jn = ey * P + ty;
-  const bool bxy = (I == 0 || I == Nx - 1 || Jn == 0 || Jn == Ny - 1);
+  const bool bxy = !DGM && (I == 0 || I == Nx - 1 || Jn == 0 || Jn == Ny - 1);
   T u[Q], v[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const int K = ez * P + k;
-    const bool bnd = bxy || K == 0 || K == Nz - 1;
-    u[k] = (live && !bnd) ? x[((long long)K * Ny + Jn) * Nx + I] : T(0);
+    const bool bnd = bxy || (!DGM && (K == 0 || K == Nz - 1));
+    if (DGM)
+      u[k] = live ? x[e * Q3 + (k * Q + ty) * Q + tx] : T(0);
+    else
+      u[k] = (live && !bnd) ? x[((long long)K * Ny + Jn) * Nx + I] : T(0);
   }
   __syncthreads();
   T* S1 = s1[el < NE ? el : 0];
@@ -168,6 +174,10 @@ __global__ void __launch_bounds__(256) k_apply3d(int nx, int ny, int nz, const T
     T a = 0;
 #pragma unroll
     for (int qz = 0; qz < Q; ++qz) a += sB[qz * Q + k] * v[qz];
+    if (DGM) {
+      y[e * Q3 + (k * Q + ty) * Q + tx] = a;
+      continue;
+    }
     const int K = ez * P + k;
     if (bxy || K == 0 || K == Nz - 1) continue;
     T* dst = y + ((long long)K * Ny + Jn) * Nx + I;
@@ -272,7 +282,7 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
     const int threads = NE * (PP + 1) * (PP + 1);                                           \
     const long long blocks = lor_ceil_div((long long)c->nel, NE);                           \
     if (c->dim == 3)                                                                        \
-      k_apply3d<PP, T><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, B, D, G, x, y); \
+      k_apply3d<PP, T, false><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, B, D, G, x, y); \
     else                                                                                    \
       k_apply2d<PP, T><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, B, D, G, x, y); \
   } break;
@@ -285,6 +295,26 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
   ++c->launches;
   lor_prof_end(c, pk);
   return lor_cuda_check(c, cudaGetLastError(), "apply_A launch");
+}
+
+template <typename T>
+lor_status launch_apply_dgvol(lor_ctx* c, const T* B, const T* D, const T* G, const T* x, T* y) {
+  const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
+#define LOR_CASEDG(PP)                                                                        \
+  case PP: {                                                                                  \
+    constexpr int NE = ElemsPerBlock<PP>::v2;                                                 \
+    const int threads = NE * (PP + 1) * (PP + 1);                                             \
+    const long long blocks = lor_ceil_div((long long)c->nel, NE);                             \
+    k_apply3d<PP, T, true><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, B, D, G, x, y); \
+  } break;
+  switch (c->p) {
+    LOR_CASEDG(1) LOR_CASEDG(2) LOR_CASEDG(3) LOR_CASEDG(4)
+    LOR_CASEDG(5) LOR_CASEDG(6) LOR_CASEDG(7) LOR_CASEDG(8)
+    default: return lor_fail(c, LOR_EINVAL, "unsupported p");
+  }
+#undef LOR_CASEDG
+  ++c->launches;
+  return lor_cuda_check(c, cudaGetLastError(), "DG volume launch");
 }
 
 // ---------------------------------------------------------------- right-hand side
@@ -377,17 +407,34 @@ lor_status lor_launch_apply_A32(lor_ctx* c, const float* x, float* y) {
   return launch_apply<float>(c, lor_basis32(c, 0), lor_basis32(c, 1), c->d_G32, x, y);
 }
 
+lor_status lor_launch_dgvol64(lor_ctx* c, const double* x, double* y) {
+  return launch_apply_dgvol<double>(c, lor_basis64(c, 0), lor_basis64(c, 1), c->d_G64, x, y);
+}
+
+lor_status lor_launch_dgvol32(lor_ctx* c, const float* x, float* y) {
+  return launch_apply_dgvol<float>(c, lor_basis32(c, 0), lor_basis32(c, 1), c->d_G32, x, y);
+}
+
+lor_status lor_launch_rhs_weights(lor_ctx* c, int kind, double* W) {
+  const int Q = c->p + 1;
+  const long long Qd = c->dim == 3 ? (long long)Q * Q * Q : (long long)Q * Q;
+  const long long tot = (long long)c->nel * Qd;
+  k_rhs_weights<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(
+      c->dim, c->p, c->n[0], c->n[1], c->n[2], c->d_vert, lor_basis64(c, 2), lor_basis64(c, 3), kind, W);
+  ++c->launches;
+  return lor_cuda_check(c, cudaGetLastError(), "rhs weights");
+}
+
 lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b) {
   const int Q = c->p + 1;
   const long long Qd = c->dim == 3 ? (long long)Q * Q * Q : (long long)Q * Q;
   const long long tot = (long long)c->nel * Qd;
-  double* W = (double*)c->d_v64[7];   // scratch: Krylov vector 7 is >= nel*Qd (see lor_setup_krylov)
+  double* W = (double*)c->d_v64[7];   // scratch: Krylov vector 7 holds >= nel*(p+1)^d (lor_setup_krylov)
+  if (c->dg_state) return lor_launch_rhs_dg(c, kind, b, W);
   cudaError_t e = cudaMemsetAsync(b, 0, sizeof(double) * c->lev[0].ntot, c->stream);
   if (e != cudaSuccess) return lor_cuda_check(c, e, "rhs memset");
+  if (lor_launch_rhs_weights(c, kind, W)) return LOR_ECUDA;
   const unsigned blocks = (unsigned)lor_ceil_div(tot, 256);
-  k_rhs_weights<<<blocks, 256, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1], c->n[2], c->d_vert,
-                                               lor_basis64(c, 2), lor_basis64(c, 3), kind, W);
-  ++c->launches;
   k_rhs_scatter<<<blocks, 256, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1], c->n[2], lor_basis64(c, 0), W, b);
   ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "rhs launch");

@@ -54,6 +54,19 @@ void lor_prof_end(lor_ctx* c, int k) {
   c->nev[k]++;
 }
 
+lor_status lor_opA64(lor_ctx* c, const double* x, double* y) {
+  return c->dg_state ? lor_launch_apply_A_dg64(c, x, y) : lor_launch_apply_A64(c, x, y);
+}
+lor_status lor_opA32(lor_ctx* c, const float* x, float* y) {
+  return c->dg_state ? lor_launch_apply_A_dg32(c, x, y) : lor_launch_apply_A32(c, x, y);
+}
+lor_status lor_opP64(lor_ctx* c, const double* r, double* z) {
+  return c->dg_state ? lor_launch_apply_P_dg64(c, r, z) : lor_launch_apply_P64(c, r, z);
+}
+lor_status lor_opP32(lor_ctx* c, const float* r, float* z) {
+  return c->dg_state ? lor_launch_apply_P_dg32(c, r, z) : lor_launch_apply_P32(c, r, z);
+}
+
 extern "C" {
 
 lor_status lor_profile(lor_ctx* c, int on) {
@@ -103,7 +116,8 @@ lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* verti
   if (opt->dim != 2 && opt->dim != 3) return LOR_EINVAL;
   if (opt->p < 1 || opt->p > LOR_MAXP) return LOR_EINVAL;
   if (opt->nx < 1 || opt->ny < 1 || (opt->dim == 3 && opt->nz < 1)) return LOR_EINVAL;
-  if (opt->disc != LOR_CG) return LOR_EINVAL;   // DG contexts: see lor_dg.h
+  if (opt->disc != LOR_CG && opt->disc != LOR_DG_IP && opt->disc != LOR_DG_BR2) return LOR_EINVAL;
+  if (opt->disc != LOR_CG && (opt->dim != 3 || !(opt->eta > 0))) return LOR_EINVAL;
   if (!(opt->rtol > 0) || opt->max_it < 1) return LOR_EINVAL;
   lor_ctx* c = new (std::nothrow) lor_ctx();
   if (!c) return LOR_ENOMEM;
@@ -140,6 +154,11 @@ lor_status lor_setup(lor_ctx* c) {
   if ((s = lor_setup_stencils(c))) return s;
   if ((s = lor_setup_patches(c))) return s;
   if ((s = lor_setup_coarse(c))) return s;
+  c->nv = c->lev[0].ntot;
+  if (c->opt.disc != LOR_CG) {
+    if ((s = lor_setup_dg(c))) return s;
+    c->nv = (long long)c->nel * (c->p + 1) * (c->p + 1) * (c->p + 1);
+  }
   if ((s = lor_setup_krylov(c))) return s;
   c->smem_patch64 = (int)lor_patch_smem(c, 0);
   c->smem_patch32 = (int)lor_patch_smem(c, c->d_F16 ? 2 : 1);
@@ -164,6 +183,11 @@ lor_status lor_get_info(const lor_ctx* c, lor_info* info) {
   }
   info->nvec = nvec;
   info->ndof = ndof;
+  if (c->opt.disc != LOR_CG) {
+    long long q = 1;
+    for (int a = 0; a < c->dim; ++a) q *= c->p + 1;
+    info->nvec = info->ndof = (long long)c->nel * q;
+  }
   long long J = 1, nc = 1;
   for (int a = 0; a < c->dim; ++a) { J *= c->n[a] + 1; nc *= c->n[a] - 1; }
   info->npatch = J;
@@ -192,8 +216,8 @@ lor_status lor_apply_A(lor_ctx* c, const void* x, void* y, int prec) {
   lor_status s = ready(c);
   if (s) return s;
   if (!x || !y) return lor_fail(c, LOR_EINVAL, "lor_apply_A: null vector");
-  if (prec == LOR_FP64) return lor_launch_apply_A64(c, (const double*)x, (double*)y);
-  if (prec == LOR_FP32) return lor_launch_apply_A32(c, (const float*)x, (float*)y);
+  if (prec == LOR_FP64) return lor_opA64(c, (const double*)x, (double*)y);
+  if (prec == LOR_FP32) return lor_opA32(c, (const float*)x, (float*)y);
   return lor_fail(c, LOR_EINVAL, "lor_apply_A: prec must be LOR_FP64 or LOR_FP32");
 }
 
@@ -201,8 +225,8 @@ lor_status lor_apply_P(lor_ctx* c, const void* r, void* z, int prec) {
   lor_status s = ready(c);
   if (s) return s;
   if (!r || !z) return lor_fail(c, LOR_EINVAL, "lor_apply_P: null vector");
-  if (prec == LOR_FP64) return lor_launch_apply_P64(c, (const double*)r, (double*)z);
-  if (prec == LOR_FP32) return lor_launch_apply_P32(c, (const float*)r, (float*)z);
+  if (prec == LOR_FP64) return lor_opP64(c, (const double*)r, (double*)z);
+  if (prec == LOR_FP32) return lor_opP32(c, (const float*)r, (float*)z);
   return lor_fail(c, LOR_EINVAL, "lor_apply_P: prec must be LOR_FP64 or LOR_FP32");
 }
 
@@ -218,7 +242,7 @@ lor_status lor_pcg_solve_host(lor_ctx* c, const double* hb, double* hx, int* ite
   lor_status s = ready(c);
   if (s) return s;
   if (!hb || !hx) return lor_fail(c, LOR_EINVAL, "lor_pcg_solve_host: null vector");
-  const long long n = c->lev[0].ntot;
+  const long long n = c->nv;
   double* db = c->d_v64[5];
   double* dx = c->d_v64[6];
   cudaError_t e = cudaMemcpyAsync(db, hb, n * 8, cudaMemcpyHostToDevice, c->stream);
@@ -258,6 +282,7 @@ void lor_destroy(lor_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  if (c->dg_state) lor_free_dg(c);
   for (void* p : c->allocs) cudaFree(p);
   for (int k = 0; k < 6; ++k)
     for (cudaEvent_t e : c->ev[k]) cudaEventDestroy(e);

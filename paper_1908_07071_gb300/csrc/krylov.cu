@@ -158,7 +158,7 @@ __global__ void k_bmask(int dim, int Nx, int Ny, int Nz, unsigned char* m) {
 static unsigned char* bmask_of(lor_ctx* c) { return (unsigned char*)c->d_v32[7]; }
 
 lor_status lor_setup_krylov(lor_ctx* c) {
-  const long long n = c->lev[0].ntot;
+  const long long n = std::max(c->nv, c->lev[0].ntot);
   const int Q = c->p + 1;
   const long long qd = (long long)c->nel * (c->dim == 3 ? Q * Q * Q : Q * Q);
   for (int k = 0; k < 8; ++k) {
@@ -176,8 +176,10 @@ lor_status lor_setup_krylov(lor_ctx* c) {
   c->d_count = (unsigned*)lor_alloc(c, 64);
   if (!c->d_v32[7] || !c->d_scal || !c->d_part || !c->d_count) return lor_fail(c, LOR_ENOMEM, "alloc krylov scalars");
   if (!c->h_scal && cudaMallocHost(&c->h_scal, 64 * 8) != cudaSuccess) return lor_fail(c, LOR_ENOMEM, "pinned");
-  k_bmask<<<1024, 256, 0, c->stream>>>(c->dim, c->lev[0].N[0], c->lev[0].N[1], c->lev[0].N[2], bmask_of(c));
-  ++c->launches;
+  if (!c->dg_state) {   // DG vectors have no Dirichlet entries: the mask stays 0
+    k_bmask<<<1024, 256, 0, c->stream>>>(c->dim, c->lev[0].N[0], c->lev[0].N[1], c->lev[0].N[2], bmask_of(c));
+    ++c->launches;
+  }
   return lor_cuda_check(c, cudaGetLastError(), "krylov setup");
 }
 
@@ -238,8 +240,8 @@ static lor_status pcg_core(lor_ctx* c, T* x, T* r, T* z, T* p, T* Ap, long long 
 }
 
 static lor_status true_residual(lor_ctx* c, const double* b, const double* x, double* r, double* Ax, double* rn) {
-  const long long n = c->lev[0].ntot;
-  if (lor_launch_apply_A64(c, x, Ax)) return LOR_ECUDA;
+  const long long n = c->nv;
+  if (lor_opA64(c, x, Ax)) return LOR_ECUDA;
   k_resid<<<red_blocks(n), kRedThreads, 0, c->stream>>>(r, b, Ax, bmask_of(c), n, c->d_part, c->d_count, c->d_scal);
   ++c->launches;
   if (read_scalars(c)) return LOR_ECUDA;
@@ -248,7 +250,7 @@ static lor_status true_residual(lor_ctx* c, const double* b, const double* x, do
 }
 
 static double norm_b(lor_ctx* c, const double* b, double* tmp) {
-  const long long n = c->lev[0].ntot;
+  const long long n = c->nv;
   k_mask_copy<<<red_blocks(n), kRedThreads, 0, c->stream>>>(tmp, b, bmask_of(c), n);
   ++c->launches;
   dot(c, tmp, tmp, n, S_BB, OP_STORE);
@@ -257,7 +259,7 @@ static double norm_b(lor_ctx* c, const double* b, double* tmp) {
 }
 
 lor_status lor_pcg64(lor_ctx* c, const double* b, double* x, int* iters, double* relres) {
-  const long long n = c->lev[0].ntot;
+  const long long n = c->nv;
   double* r = c->d_v64[0];
   double* z = c->d_v64[1];
   double* p = c->d_v64[2];
@@ -271,8 +273,8 @@ lor_status lor_pcg64(lor_ctx* c, const double* b, double* x, int* iters, double*
     if (relres) *relres = 0.0;
     return LOR_OK;
   }
-  auto A = [&](const double* in, double* out) { return lor_launch_apply_A64(c, in, out); };
-  auto P = [&](const double* in, double* out) { return lor_launch_apply_P64(c, in, out); };
+  auto A = [&](const double* in, double* out) { return lor_opA64(c, in, out); };
+  auto P = [&](const double* in, double* out) { return lor_opP64(c, in, out); };
   int it = 0;
   double rr = 0;
   lor_status st = pcg_core<double>(c, x, r, z, p, Ap, n, c->opt.rtol * bn, c->opt.max_it, A, P, &it, &rr, true);
@@ -286,7 +288,7 @@ lor_status lor_pcg64(lor_ctx* c, const double* b, double* x, int* iters, double*
 }
 
 lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, double* relres) {
-  const long long n = c->lev[0].ntot;
+  const long long n = c->nv;
   double* r = c->d_v64[0];
   double* Ax = c->d_v64[3];
   float* d = c->d_v32[0];
@@ -305,8 +307,8 @@ lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, dou
   }
   double rn = bn;
   c->hist.push_back(rn);
-  auto A = [&](const float* in, float* out) { return lor_launch_apply_A32(c, in, out); };
-  auto P = [&](const float* in, float* out) { return lor_launch_apply_P32(c, in, out); };
+  auto A = [&](const float* in, float* out) { return lor_opA32(c, in, out); };
+  auto P = [&](const float* in, float* out) { return lor_opP32(c, in, out); };
   int total = 0, outer = 0;
   while (rn > c->opt.rtol * bn && total < c->opt.max_it && outer < 100) {
     k_down<<<red_blocks(n), kRedThreads, 0, c->stream>>>(r32, r, 1.0 / rn, n);

@@ -164,6 +164,9 @@ struct lor_ctx {
   bool prof = false;
   std::vector<cudaEvent_t> ev[6];   // start/stop pairs per kernel class
   int nev[6] = {0, 0, 0, 0, 0, 0};
+  // DG discretization data (dg.cu); nullptr for continuous contexts
+  void* dg_state = nullptr;
+  long long nv = 0;            // length of the solver's vectors (CG grid or DG blocks)
   size_t bytes = 0;
   long long launches = 0;      // kernels launched by this context
   std::vector<void*> allocs;
@@ -184,6 +187,22 @@ lor_status lor_setup_coarse(lor_ctx* c);
 lor_status lor_launch_apply_A64(lor_ctx* c, const double* x, double* y);
 lor_status lor_launch_apply_A32(lor_ctx* c, const float* x, float* y);
 lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b);
+lor_status lor_launch_rhs_weights(lor_ctx* c, int kind, double* W);
+lor_status lor_launch_dgvol64(lor_ctx* c, const double* x, double* y);
+lor_status lor_launch_dgvol32(lor_ctx* c, const float* x, float* y);
+// dg.cu
+lor_status lor_setup_dg(lor_ctx* c);
+lor_status lor_launch_apply_A_dg64(lor_ctx* c, const double* x, double* y);
+lor_status lor_launch_apply_A_dg32(lor_ctx* c, const float* x, float* y);
+lor_status lor_launch_apply_P_dg64(lor_ctx* c, const double* r, double* z);
+lor_status lor_launch_apply_P_dg32(lor_ctx* c, const float* r, float* z);
+lor_status lor_launch_rhs_dg(lor_ctx* c, int kind, double* b, double* W);
+void lor_free_dg(lor_ctx* c);
+// operator / preconditioner of the context's discretization (CG or DG)
+lor_status lor_opA64(lor_ctx* c, const double* x, double* y);
+lor_status lor_opA32(lor_ctx* c, const float* x, float* y);
+lor_status lor_opP64(lor_ctx* c, const double* r, double* z);
+lor_status lor_opP32(lor_ctx* c, const float* r, float* z);
 // apply_p.cu
 lor_status lor_launch_apply_P64(lor_ctx* c, const double* r, double* z);
 lor_status lor_launch_apply_P32(lor_ctx* c, const float* r, float* z);

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "lor_internal.h"
+#include "geom.cuh"
 
 // ------------------------------------------------------------------ basis block
 // Device layout of the small basis block: for precision 64: [B | Dq | glx | glw |
@@ -26,62 +27,6 @@ float* lor_basis32(lor_ctx* c, int which) { return (float*)c->allocs[1] + which 
 BoxShape* lor_dev_shapes(lor_ctx* c) { return c->d_shapes; }
 
 namespace {
-
-__device__ inline double det3(const double J[3][3]) {
-  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-}
-
-// inverse of a dim x dim matrix (dim 2 or 3) by the adjugate
-__device__ inline void inv_dd(int dim, const double J[3][3], double det, double Ji[3][3]) {
-  if (dim == 3) {
-    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
-    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
-    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
-    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
-    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
-    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
-    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
-    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
-    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
-  } else {
-    Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
-    Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
-  }
-}
-
-// Multilinear map of the 2^dim points P[c][a] (corner c = cx + 2cy + 4cz) at xi:
-// X and J[a][b] = dX_a/dxi_b.
-__device__ inline void multilinear(int dim, const double (*Pc)[3], const double* xi, double* X, double J[3][3]) {
-  for (int a = 0; a < 3; ++a) { X[a] = 0; for (int b = 0; b < 3; ++b) J[a][b] = 0; }
-  const int nc = 1 << dim;
-  for (int cc = 0; cc < nc; ++cc) {
-    double f[3], df[3];
-    for (int a = 0; a < 3; ++a) {
-      const int bit = (cc >> a) & 1;
-      f[a] = bit ? xi[a] : 1.0 - xi[a];
-      df[a] = bit ? 1.0 : -1.0;
-    }
-    double N = 1.0;
-    for (int t = 0; t < dim; ++t) N *= f[t];
-    for (int bb = 0; bb < dim; ++bb) {
-      double g = 1.0;
-      for (int t = 0; t < dim; ++t) g *= (t == bb) ? df[t] : f[t];
-      for (int a = 0; a < dim; ++a) J[a][bb] += g * Pc[cc][a];
-    }
-    for (int a = 0; a < dim; ++a) X[a] += N * Pc[cc][a];
-  }
-}
-
-__device__ inline void element_corners(int dim, int nx, int ny, int ex, int ey, int ez, const double* vert,
-                                       long long NV, double (*Pc)[3]) {
-  const int nc = 1 << dim;
-  for (int cc = 0; cc < nc; ++cc) {
-    const int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
-    const long long vid = ((long long)(ez + bz) * (ny + 1) + (ey + by)) * (nx + 1) + (ex + bx);
-    for (int a = 0; a < 3; ++a) Pc[cc][a] = a < dim ? vert[a * NV + vid] : 0.0;
-  }
-}
 
 // G[e][comp][q] = kappa_e w_q det J (J^{-1} J^{-T})_{ab}, comps (00,01,02,11,12,22) / (00,01,11)
 __global__ void k_geom(int dim, int p, int nx, int ny, int nz, const double* __restrict__ vert,
@@ -99,14 +44,14 @@ __global__ void k_geom(int dim, int p, int nx, int ny, int nz, const double* __r
   const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = dim == 3 ? (int)(e / ((long long)nx * ny)) : 0;
   const long long NV = (long long)(nx + 1) * (ny + 1) * (dim == 3 ? (nz + 1) : 1);
   double Pc[8][3];
-  element_corners(dim, nx, ny, ex, ey, ez, vert, NV, Pc);
+  lorg::element_corners(dim, nx, ny, ex, ey, ez, vert, NV, Pc);
   const double xi[3] = {glx[qx], glx[qy], dim == 3 ? glx[qz] : 0.0};
   double X[3], J[3][3];
-  multilinear(dim, Pc, xi, X, J);
-  const double det = dim == 3 ? det3(J) : (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+  lorg::multilinear(dim, Pc, xi, X, J);
+  const double det = dim == 3 ? lorg::det3(J) : (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
   if (!(det > 0)) { atomicOr(status, 1); return; }
   double Ji[3][3];
-  inv_dd(dim, J, det, Ji);
+  lorg::inv_dd(dim, J, det, Ji);
   const double w = glw[qx] * glw[qy] * (dim == 3 ? glw[qz] : 1.0);
   const double s = kappa[e] * w * det;
   const int ncomp = dim == 3 ? 6 : 3;
@@ -134,9 +79,9 @@ __global__ void k_nodes(int dim, int p, int nx, int ny, int nz, const double* __
   const double xi[3] = {gllx[I - ex * p], gllx[Jn - ey * p], dim == 3 ? gllx[K - ez * p] : 0.0};
   const long long NV = (long long)(nx + 1) * (ny + 1) * (dim == 3 ? (nz + 1) : 1);
   double Pc[8][3];
-  element_corners(dim, nx, ny, ex, ey, ez, vert, NV, Pc);
+  lorg::element_corners(dim, nx, ny, ex, ey, ez, vert, NV, Pc);
   double Xp[3], J[3][3];
-  multilinear(dim, Pc, xi, Xp, J);
+  lorg::multilinear(dim, Pc, xi, Xp, J);
   for (int a = 0; a < dim; ++a) X[a * ntot + gid] = Xp[a];
 }
 
@@ -176,10 +121,10 @@ __global__ void k_lor_stencil(int dim, int p, int nx, int ny, int nz, const doub
             for (int gx = 0; gx < 2; ++gx) {
               const double xi[3] = {g1[gx], g1[gy], dim == 3 ? g1[gz] : 0.0};
               double Xq[3], J[3][3];
-              multilinear(dim, Pc, xi, Xq, J);
-              const double det = dim == 3 ? det3(J) : (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+              lorg::multilinear(dim, Pc, xi, Xq, J);
+              const double det = dim == 3 ? lorg::det3(J) : (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
               double Ji[3][3];
-              inv_dd(dim, J, det, Ji);
+              lorg::inv_dd(dim, J, det, Ji);
               const double wq = (dim == 3 ? 0.125 : 0.25) * fabs(det) * kap;
               // reference gradients of the corner functions
               double gme[3];

@@ -108,7 +108,7 @@ class Solver:
     """One LOR-preconditioned problem on the current CUDA device and stream."""
 
     def __init__(self, vertices, kappa, p, *, mg_levels=0, prec=LOR_FP64, rtol=1e-8, max_it=1000,
-                 inner_rtol=1e-3, factor_bf16=False, stream=None):
+                 inner_rtol=1e-3, factor_bf16=False, disc=LOR_CG, eta=1.0, stream=None):
         import torch
         self.lib = load()
         vertices = np.ascontiguousarray(vertices, dtype=np.float64)
@@ -122,6 +122,7 @@ class Solver:
         opt.nz = n[2] if dim == 3 else 1
         opt.mg_levels, opt.prec, opt.rtol, opt.max_it = mg_levels, prec, rtol, max_it
         opt.inner_rtol, opt.factor_bf16 = inner_rtol, int(bool(factor_bf16))
+        opt.disc, opt.eta = disc, eta
         self.opt = opt
         self.dim, self.p, self.n = dim, p, tuple(n)
         if stream is None:
