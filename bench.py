@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--form", default="mixed-bf16", choices=["mixed-bf16", "mixed-fp32", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 solve, per-apply and CPU legs")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-solve batched leg")
+    ap.add_argument("--no-dg", action="store_true", help="skip the DG penalty-sweep leg")
+    ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     return ap.parse_args()
 
@@ -173,6 +176,103 @@ def reference_arm(args, rank):
                              "sample": res["sample"] + " (60 iterations assumed per solve)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ batched leg
+def leg_batch(nsolves, rank):
+    """256 independent CG solves (n ~ U{4..16} per axis, p ~ U{2..7}, perturbed mesh,
+    log-normal kappa, seed = solve index): batched flexible CG, FP32 preconditioner,
+    FP64 residual, one CUDA graph per iteration."""
+    import torch
+    from paper_1908_07071_gb300 import lor
+    from paper_1908_07071_gb300.synthetic import batch_plan, make_mesh
+    plan = batch_plan(nsolves, seed=rank, nmin=4, nmax=16, pmin=2, pmax=7)
+    t0 = time.perf_counter()
+    solvers, bs, xs = [], [], []
+    for i, (n, p) in enumerate(plan):
+        v, k = make_mesh(3, n, seed=1000 * rank + i, perturb=0.15)
+        s = lor.Solver(v, k, p, rtol=1e-8, factor_bf16=True)
+        b = torch.empty(s.nvec, dtype=torch.float64, device="cuda")
+        s.rhs(b, 0)
+        solvers.append(s)
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    batch = lor.Batch(solvers)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    batch.solve(bs, xs)                      # warm-up (captures the graph)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    its, rels = batch.solve(bs, xs)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    ndofs = [s.info.ndof for s in solvers]
+    _, nodes = batch.stats()
+    out = {"workload": f"{nsolves} solves, n~U{{4..16}}^3, p~U{{2..7}}, perturbed, log-normal kappa, rtol 1e-8",
+           "time_s": t, "solves_per_s": nsolves / t,
+           "dof_iterations_per_s": float(sum(d * i for d, i in zip(ndofs, its))) / t,
+           "total_dofs": int(sum(ndofs)), "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
+           "max_rel_res": float(max(rels)), "graph_nodes": nodes, "setup_s": setup_s,
+           "form": "flexible CG, FP64 vectors/dots, FP32 preconditioner with bf16 ILU factors"}
+    batch.close()
+    for s in solvers:
+        s.close()
+    return out
+
+
+# ----------------------------------------------------------------- DG leg
+def leg_dg():
+    """3D SIPG and BR2 on a 24^3 perturbed mesh, p=4, log-normal kappa: iterations of
+    B_DG-preconditioned CG for eta in {1,10,100,1000} x eta_min (FP64), and DG per-apply
+    throughput."""
+    import torch
+    from paper_1908_07071_gb300 import lor
+    from paper_1908_07071_gb300.synthetic import make_mesh
+    v, k = make_mesh(3, 24, seed=0, perturb=0.15)
+    eta_min = {"ip": 2.0 ** 0.25, "br2": 6.0}
+    out = {"workload": "3D DG p=4, 24^3 perturbed hex mesh, log-normal kappa, f=1, rtol 1e-8",
+           "eta_min": eta_min}
+    for form, disc in (("ip", lor.LOR_DG_IP), ("br2", lor.LOR_DG_BR2)):
+        rows = []
+        for mult in (1.0, 10.0, 100.0, 1000.0):
+            s = lor.Solver(v, k, 4, disc=disc, eta=eta_min[form] * mult, rtol=1e-8, factor_bf16=True)
+            b = torch.empty(s.nvec, dtype=torch.float64, device="cuda")
+            s.rhs(b, 0)
+            x = torch.zeros_like(b)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            it, rel = s.solve(b, x)
+            e1.record()
+            torch.cuda.synchronize()
+            row = {"eta_mult": mult, "iterations_fp64": it, "time_ms_fp64": e0.elapsed_time(e1)}
+            s.set_prec(lor.LOR_MIXED)
+            x2 = torch.zeros_like(b)
+            e0.record()
+            it2, rel2 = s.solve(b, x2)
+            e1.record()
+            torch.cuda.synchronize()
+            row.update({"iterations_mixed": it2, "time_ms_mixed": e0.elapsed_time(e1), "rel_res_mixed": rel2})
+            if mult == 10.0:
+                xa = torch.randn(s.nvec, dtype=torch.float64, device="cuda")
+                ya = torch.empty_like(xa)
+                per = {}
+                for name, fn in (("apply_A_fp64", lambda: s.apply_A(xa, ya)),
+                                 ("apply_P_fp64", lambda: s.apply_P(xa, ya))):
+                    fn()
+                    e0.record()
+                    for _ in range(5):
+                        fn()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / 5
+                    per[name] = {"ms": ms, "MDOF/s": s.nvec / (ms * 1e-3) / 1e6}
+                row["per_apply"] = per
+            rows.append(row)
+            s.close()
+        out[form] = rows
+    return out
 
 
 # ----------------------------------------------------------------- our arm
@@ -351,6 +451,10 @@ def main():
             "iterations": its[-1], "rel_res": rels[-1], "setup_s": t_setup, "gpu_launches": launches,
             "roofline": roof, "clocks": clk}
     line.update(extras)
+    if not args.no_batch:
+        line["batch"] = leg_batch(args.batch_n, rank)
+    if not args.no_dg:
+        line["dg"] = leg_dg()
     if rank == 0 and not args.no_extras:
         its64 = extras.get("fp64_plain", {}).get("iterations", 60)
         try:

@@ -149,6 +149,23 @@ lor_status lor_profile_read(lor_ctx* ctx, int kernel, double* total_ms, long lon
  * FP64 outer residuals and inner FP64-accumulated norms for LOR_MIXED). */
 lor_status lor_residual_history(const lor_ctx* ctx, double* out, int cap, int* count);
 
+/* ---- Batched solves (serving-shaped workloads; the paper solves one problem)
+ * Many independent CG contexts (after lor_setup; uneven sizes and degrees) are
+ * advanced together by flexible CG with FP64 vectors and inner products and
+ * the FP32 LOR preconditioner of each context.  One iteration of all solves is
+ * captured once into a CUDA graph with one branch per solve; the host launches
+ * it until every solve has reached its rtol.  lor_batch_create also tunes the
+ * operator's tile shape per polynomial degree by timing.  The batch borrows the
+ * contexts (they must outlive it) and their work vectors; stream: cudaStream_t
+ * or NULL.  d_b[s], d_x[s]: device float64 L-vectors of context s. */
+typedef struct lor_batch lor_batch;
+lor_status lor_batch_create(lor_batch** batch, int n, lor_ctx** ctxs, void* stream);
+lor_status lor_batch_solve(lor_batch* batch, const double* const* d_b, double* const* d_x, int* iters,
+                           double* rel_res);
+/* Wall time of the last solve's iteration loop (ms) and nodes of its graph. */
+lor_status lor_batch_stats(const lor_batch* batch, double* loop_ms, int* graph_nodes);
+void lor_batch_destroy(lor_batch* batch);
+
 /* Allocation-free right-hand side (no counterpart in the paper; a service for
  * callers that may not call cudaMalloc).  Some callers cannot allocate device
  * memory: a host framework that hands all device memory to its own caching

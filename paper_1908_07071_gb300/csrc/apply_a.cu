@@ -21,16 +21,25 @@ struct ElemsPerBlock {
   static constexpr int v2 = (256 / (Q * Q)) > 0 ? (256 / (Q * Q)) : 1;
 };
 
+// Elements per CTA of the 3D kernel for tile variant V (0: ~128, 1: ~256,
+// 2: ~512 threads), capped so that the two shared tiles fit in 48 KB.
+template <int P, typename T, int V>
+struct TileNE {
+  static constexpr int Q = P + 1;
+  static constexpr int want = ((128 << V) / (Q * Q)) > 0 ? ((128 << V) / (Q * Q)) : 1;
+  static constexpr int cap = (48 * 1024) / (2 * Q * Q * Q * (int)sizeof(T) + 1);
+  static constexpr int v = want < cap ? want : (cap > 0 ? cap : 1);
+};
+
 // DGM = false: continuous Q_p on the structured node grid (gather/scatter,
 // Dirichlet nodes masked).  DGM = true: element-local DG blocks of (p+1)^3
 // values (element e at e*(p+1)^3), no masking, outputs stored (not added).
-template <int P, typename T, bool DGM>
-__global__ void __launch_bounds__(256) k_apply3d(int nx, int ny, int nz, const T* __restrict__ Bg,
-                                                 const T* __restrict__ Dg, const T* __restrict__ G,
-                                                 const T* __restrict__ x, T* __restrict__ y) {
+template <int P, typename T, bool DGM, int NE>
+__global__ void __launch_bounds__(1024) k_apply3d(int nx, int ny, int nz, const T* __restrict__ Bg,
+                                                  const T* __restrict__ Dg, const T* __restrict__ G,
+                                                  const T* __restrict__ x, T* __restrict__ y) {
   constexpr int Q = P + 1;
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
-  constexpr int NE = ElemsPerBlock<P>::v2;
   __shared__ T sB[Q2], sD[Q2];
   __shared__ T s1[NE][Q3], s2[NE][Q3];
   const int tid = threadIdx.x;
@@ -276,15 +285,25 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   const int pk = sizeof(T) == 8 ? 2 : 3;
   lor_prof_begin(c, pk);
-#define LOR_CASE3(PP)                                                                       \
-  case PP: {                                                                                \
-    constexpr int NE = ElemsPerBlock<PP>::v2;                                               \
+#define LOR_VAR3(PP, V)                                                                     \
+  {                                                                                         \
+    constexpr int NE = TileNE<PP, T, V>::v;                                                 \
     const int threads = NE * (PP + 1) * (PP + 1);                                           \
     const long long blocks = lor_ceil_div((long long)c->nel, NE);                           \
-    if (c->dim == 3)                                                                        \
-      k_apply3d<PP, T, false><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, B, D, G, x, y); \
-    else                                                                                    \
+    k_apply3d<PP, T, false, NE><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, B, D, G, x, y); \
+  }
+#define LOR_CASE3(PP)                                                                       \
+  case PP: {                                                                                \
+    if (c->dim == 3) {                                                                      \
+      if (c->tune_ne == 0) LOR_VAR3(PP, 0)                                                  \
+      else if (c->tune_ne == 2) LOR_VAR3(PP, 2)                                             \
+      else LOR_VAR3(PP, 1)                                                                  \
+    } else {                                                                                \
+      constexpr int NE = ElemsPerBlock<PP>::v2;                                             \
+      const int threads = NE * (PP + 1) * (PP + 1);                                         \
+      const long long blocks = lor_ceil_div((long long)c->nel, NE);                         \
       k_apply2d<PP, T><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, B, D, G, x, y); \
+    }                                                                                       \
   } break;
   switch (c->p) {
     LOR_CASE3(1) LOR_CASE3(2) LOR_CASE3(3) LOR_CASE3(4)
@@ -292,6 +311,7 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
     default: return lor_fail(c, LOR_EINVAL, "unsupported p");
   }
 #undef LOR_CASE3
+#undef LOR_VAR3
   ++c->launches;
   lor_prof_end(c, pk);
   return lor_cuda_check(c, cudaGetLastError(), "apply_A launch");
@@ -300,12 +320,18 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
 template <typename T>
 lor_status launch_apply_dgvol(lor_ctx* c, const T* B, const T* D, const T* G, const T* x, T* y) {
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
-#define LOR_CASEDG(PP)                                                                        \
-  case PP: {                                                                                  \
-    constexpr int NE = ElemsPerBlock<PP>::v2;                                                 \
+#define LOR_VARDG(PP, V)                                                                      \
+  {                                                                                           \
+    constexpr int NE = TileNE<PP, T, V>::v;                                                   \
     const int threads = NE * (PP + 1) * (PP + 1);                                             \
     const long long blocks = lor_ceil_div((long long)c->nel, NE);                             \
-    k_apply3d<PP, T, true><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, B, D, G, x, y); \
+    k_apply3d<PP, T, true, NE><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, B, D, G, x, y); \
+  }
+#define LOR_CASEDG(PP)                                                                        \
+  case PP: {                                                                                  \
+    if (c->tune_ne == 0) LOR_VARDG(PP, 0)                                                     \
+    else if (c->tune_ne == 2) LOR_VARDG(PP, 2)                                                \
+    else LOR_VARDG(PP, 1)                                                                     \
   } break;
   switch (c->p) {
     LOR_CASEDG(1) LOR_CASEDG(2) LOR_CASEDG(3) LOR_CASEDG(4)
@@ -313,6 +339,7 @@ lor_status launch_apply_dgvol(lor_ctx* c, const T* B, const T* D, const T* G, co
     default: return lor_fail(c, LOR_EINVAL, "unsupported p");
   }
 #undef LOR_CASEDG
+#undef LOR_VARDG
   ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "DG volume launch");
 }

@@ -68,6 +68,7 @@ struct PatchArgs {
   int slot_bytes;               // ring slot size (bytes, multiple of 16)
   int tab_ints;                 // shared-memory ints reserved for wavefront tables
   const int* porder;            // patch visiting order (grouped by box shape)
+  const double* conv;           // optional: skip all work when *conv != 0 (converged batched solve)
 };
 
 struct Box {
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
   constexpr int ES = elem_class<FT>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int abort_flag;
+  if (a.conv && *a.conv != 0.0) return;
   // shared memory: [NBUF mbarriers | pad][ring][transfer tables][wavefront tables][vectors]
   Ring<FT, NBUF> rg;
   rg.bar = (unsigned long long*)smem_raw;
@@ -794,6 +796,7 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
   a.F = F; a.r = r; a.z = z;
   a.status = c->d_status;
   a.porder = c->d_porder;
+  a.conv = c->conv_flag;
   a.slot_bytes = c->maxchunk[elem_class<FT>()] * LOR_REC * (int)sizeof(FT);
   const size_t smem = patch_smem_bytes<T, FT>(c, &a.tab_ints);
   constexpr int NB = ring_depth<FT>();

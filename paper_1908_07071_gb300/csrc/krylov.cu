@@ -172,7 +172,7 @@ lor_status lor_setup_krylov(lor_ctx* c) {
   }
   c->d_v32[7] = (float*)lor_alloc(c, n);   // boundary mask (bytes)
   c->d_scal = (double*)lor_alloc(c, 64 * 8);
-  c->d_part = (double*)lor_alloc(c, kRedBlocks * 8);
+  c->d_part = (double*)lor_alloc(c, 2 * kRedBlocks * 8);   // room for paired reductions
   c->d_count = (unsigned*)lor_alloc(c, 64);
   if (!c->d_v32[7] || !c->d_scal || !c->d_part || !c->d_count) return lor_fail(c, LOR_ENOMEM, "alloc krylov scalars");
   if (!c->h_scal && cudaMallocHost(&c->h_scal, 64 * 8) != cudaSuccess) return lor_fail(c, LOR_ENOMEM, "pinned");

@@ -167,6 +167,8 @@ struct lor_ctx {
   // DG discretization data (dg.cu); nullptr for continuous contexts
   void* dg_state = nullptr;
   long long nv = 0;            // length of the solver's vectors (CG grid or DG blocks)
+  int tune_ne = 1;             // apply_A tile variant (elements per CTA), set by the autotuner
+  const double* conv_flag = nullptr;   // batched solves: patch kernel returns early when *conv_flag != 0
   size_t bytes = 0;
   long long launches = 0;      // kernels launched by this context
   std::vector<void*> allocs;

@@ -71,6 +71,13 @@ def load():
     lib.lor_last_error.restype = ctypes.c_char_p
     lib.lor_destroy.argtypes = [vp]
     lib.lor_destroy.restype = None
+    lib.lor_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), vp]
+    lib.lor_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), pi, pd]
+    lib.lor_batch_stats.argtypes = [vp, pd, pi]
+    lib.lor_batch_destroy.argtypes = [vp]
+    lib.lor_batch_destroy.restype = None
+    for name in ("lor_batch_create", "lor_batch_solve", "lor_batch_stats"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.lor_rhs_static.argtypes = [i, i, i, i, i, vp, i, vp, vp]
     lib.lor_rhs_static.restype = ctypes.c_int
     lib.lor_set_prec.argtypes = [vp, i]
@@ -212,3 +219,48 @@ class Solver:
         out = (ctypes.c_double * max(cnt.value, 1))()
         self.lib.lor_residual_history(self.ctx, out, cnt.value, ctypes.byref(cnt))
         return np.array(out[:cnt.value])
+
+
+class Batch:
+    """Batched flexible-CG solves of several Solver contexts (one CUDA graph per iteration)."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.lib = load()
+        self.solvers = list(solvers)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.ctx for s in self.solvers])
+        b = ctypes.c_void_p()
+        st = self.lib.lor_batch_create(ctypes.byref(b), len(self.solvers), arr, ctypes.c_void_p(stream))
+        if st != LOR_OK:
+            raise LorError(st, "lor_batch_create failed")
+        self.b = b
+
+    def solve(self, bs, xs):
+        import torch
+        n = len(self.solvers)
+        pb = (ctypes.c_void_p * n)(*[_ptr(b, torch.float64, s.nvec, "b").value for b, s in zip(bs, self.solvers)])
+        px = (ctypes.c_void_p * n)(*[_ptr(x, torch.float64, s.nvec, "x").value for x, s in zip(xs, self.solvers)])
+        its = (ctypes.c_int * n)()
+        rel = (ctypes.c_double * n)()
+        st = self.lib.lor_batch_solve(self.b, pb, px, its, rel)
+        if st != LOR_OK:
+            raise LorError(st, "lor_batch_solve failed")
+        return list(its), list(rel)
+
+    def stats(self):
+        ms, nodes = ctypes.c_double(0.0), ctypes.c_int(0)
+        self.lib.lor_batch_stats(self.b, ctypes.byref(ms), ctypes.byref(nodes))
+        return ms.value, nodes.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.lor_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
