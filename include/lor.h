@@ -166,6 +166,34 @@ lor_status lor_batch_solve(lor_batch* batch, const double* const* d_b, double* c
 lor_status lor_batch_stats(const lor_batch* batch, double* loop_ms, int* graph_nodes);
 void lor_batch_destroy(lor_batch* batch);
 
+/* ---- Learned per-patch correction (the learned form of the method)
+ * After the V(1,1) cycle of every interior vertex patch, a 3-layer 3x3x3
+ * convolutional network (2 -> 16 -> 16 -> 1 channels, ReLU, bf16 weights, FP32
+ * accumulation) maps the remaining level-0 residual t to the correction
+ * rho s N([s t / rho, log(diag/mean diag)]), s = diag(A_j)^(-1/2), rho = rms(s t).
+ * It applies to the FP32 preconditioner (LOR_MIXED solves); with it on, the
+ * Krylov iteration is flexible CG.  Parameters: one float array of
+ * LOR_LEARNED_NPARAM values, W1[16][2][27] b1[16] W2[16][16][27] b2[16]
+ * W3[1][16][27] b3[1], taps ordered (dz+1)*9+(dy+1)*3+(dx+1).
+ * lor_learned_params: copy host parameters in (h_in) and/or out (h_out).
+ * lor_learned_enable: switch the correction on (1) or off (0).
+ * lor_learned_train: `steps` Adam steps (learning rate lr) on batches of
+ *   `batch` interior patches of this context; each step draws random errors e,
+ *   runs the plain V-cycle x = V(A e) and minimises
+ *   (delta - c)^T A_j (delta - c) / delta^T A_j delta, delta = e - x; h_loss
+ *   (host, `steps` floats, may be NULL) receives the mean loss per step.
+ * lor_learned_eval: forward (and, with d_delta, loss and gradient) on given
+ *   patch data: d_ids (device, npatch interior patch ids), d_t / d_delta
+ *   (device, npatch x (2p-1)^3 floats, lexicographic box order); outputs the
+ *   correction d_c, per-patch loss d_loss (device) and the summed gradient
+ *   h_grad (host, LOR_LEARNED_NPARAM floats).  Intended for checks. */
+#define LOR_LEARNED_NPARAM 8241
+lor_status lor_learned_params(lor_ctx* ctx, const float* h_in, float* h_out, int count);
+lor_status lor_learned_enable(lor_ctx* ctx, int on);
+lor_status lor_learned_train(lor_ctx* ctx, int steps, int batch, float lr, unsigned long long seed, float* h_loss);
+lor_status lor_learned_eval(lor_ctx* ctx, int npatch, const int* d_ids, const float* d_t, const float* d_delta,
+                            float* d_c, float* d_loss, float* h_grad);
+
 /* Allocation-free right-hand side (no counterpart in the paper; a service for
  * callers that may not call cudaMalloc).  Some callers cannot allocate device
  * memory: a host framework that hands all device memory to its own caching

@@ -69,6 +69,17 @@ struct PatchArgs {
   int tab_ints;                 // shared-memory ints reserved for wavefront tables
   const int* porder;            // patch visiting order (grouped by box shape)
   const double* conv;           // optional: skip all work when *conv != 0 (converged batched solve)
+  // patch-local mode (learned-correction training data): patches plist[0..nlist)
+  // take their level-0 right-hand side from rloc and write x to xloc (lexicographic
+  // box order, stride vstride per listed patch) instead of gathering / scattering
+  const int* plist;
+  int nlist;
+  const void* rloc;
+  void* xloc;
+  int vstride;
+  // residual capture (learned-correction inference): the level-0 residual left by
+  // the cycle on every interior patch is written to tout + visiting position * vstride
+  void* tout;
 };
 
 struct Box {
@@ -291,8 +302,9 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
   int cur_sh = -1;
   LevelTables tb[LOR_MAXLEV];
   BoxShape bsh[LOR_MAXLEV];
-  for (int jo = blockIdx.x; jo < a.J; jo += gridDim.x) {
-    const int j = a.porder[jo];
+  const int nwork = a.plist ? a.nlist : a.J;
+  for (int jo = blockIdx.x; jo < nwork; jo += gridDim.x) {
+    const int j = a.plist ? a.plist[jo] : a.porder[jo];
     int v[3];
     v[0] = j % (a.n[0] + 1);
     v[1] = (j / (a.n[0] + 1)) % (a.n[1] + 1);
@@ -345,11 +357,17 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
       }
       xs[l] = sm + offset; offset += b.rows;
       ts[l] = sm + offset + bs.guard; offset += b.rows + 2 * bs.guard;
-      rs[l] = sm + offset; offset += (l > 0 ? b.rows : 0);
+      rs[l] = sm + offset; offset += (l > 0 || a.plist ? b.rows : 0);
     }
     for (long long i = threadIdx.x; i < offset; i += blockDim.x) sm[i] = T(0);
     __syncthreads();
-    const T* rg0 = (const T*)a.r;
+    // level-0 right-hand side: the global vector, or the listed patch's own data
+    const T* rg0 = a.plist ? nullptr : (const T*)a.r;
+    if (a.plist) {
+      const T* src = (const T*)a.rloc + (long long)jo * a.vstride;
+      for (int lex = threadIdx.x; lex < bx[0].rows; lex += blockDim.x) rs[0][lex] = src[lex];
+      __syncthreads();
+    }
     const FT* F = (const FT*)a.F;
     int bottom = 0;
     while (bottom + 1 < a.L && bx[bottom + 1].rows > 0) ++bottom;
@@ -362,7 +380,7 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
       for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
         const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
         const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-        ts[l][lex] = l == 0 ? rg0[G] : rs[l][lex];
+        ts[l][lex] = (l == 0 && rg0) ? rg0[G] : rs[l][lex];
       }
       __syncthreads();
       ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], tb[l], FL, ts[l], rg, &abort_flag);
@@ -407,7 +425,7 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
         for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
           const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
           const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-          const T rhs = l == 0 ? rg0[G] : rs[l][lex];
+          const T rhs = (l == 0 && rg0) ? rg0[G] : rs[l][lex];
           xs[l][lex] = rhs / S[(long long)(a.NS / 2) * lv.ntot + G];
         }
         __syncthreads();
@@ -416,7 +434,7 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
         for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
           const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
           const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-          ts[l][lex] = l == 0 ? rg0[G] : rs[l][lex];
+          ts[l][lex] = (l == 0 && rg0) ? rg0[G] : rs[l][lex];
         }
         __syncthreads();
         ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], tb[l], FL, ts[l], rg, &abort_flag);
@@ -484,14 +502,25 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
       }
       return;
     }
-    // ---- scatter-add R_j^T x_j
-    T* z = (T*)a.z;
     const Box& b = bx[0];
     const PLevel& lv = a.lv[0];
+    if (a.plist) {     // patch-local output
+      T* dst = (T*)a.xloc + (long long)jo * a.vstride;
+      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) dst[lex] = xs[0][lex];
+      continue;
+    }
+    // ---- scatter-add R_j^T x_j
+    T* z = (T*)a.z;
     for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
       const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
       const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
       atomicAdd(z + G, xs[0][lex]);
+    }
+    if (a.tout && sh == 0) {   // residual left on an interior patch, for the learned correction
+      LOR_RESID(0, rg0);
+      __syncthreads();
+      T* dst = (T*)a.tout + (long long)jo * a.vstride;
+      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) dst[lex] = ts[0][lex];
     }
   }
 }
@@ -755,11 +784,11 @@ template <typename FT>
 constexpr int ring_depth() { return sizeof(FT) == 2 ? 3 : 2; }
 
 template <typename T, typename FT>
-size_t patch_smem_bytes(const lor_ctx* c, int* tab_ints = nullptr) {
+size_t patch_smem_bytes(const lor_ctx* c, int* tab_ints = nullptr, bool local = false) {
   size_t vec = 0, tab = 0;
   for (int l = 0; l < c->L; ++l) {
     const BoxShape& bs = c->shapes[l * 8 + 0];   // interior shape is the largest
-    vec += (size_t)bs.rows * (l > 0 ? 3 : 2) + 2 * (size_t)bs.guard;
+    vec += (size_t)bs.rows * (l > 0 || local ? 3 : 2) + 2 * (size_t)bs.guard;   // x, t (+guards), r
     tab += 2 * (size_t)(bs.nfront + 1) + (size_t)(bs.nchunk[elem_class<FT>()] + 1) + ((size_t)bs.rows + 1) / 2;
   }
   tab = (tab + 3) / 4 * 4;   // ints, keeps the vectors 16-byte aligned
@@ -769,11 +798,7 @@ size_t patch_smem_bytes(const lor_ctx* c, int* tab_ints = nullptr) {
 }
 
 template <typename T, typename FT>
-lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
-  const long long nvec = c->lev[0].ntot;
-  cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * nvec, c->stream);
-  if (e != cudaSuccess) return lor_cuda_check(c, e, "apply_P memset");
-  PatchArgs a;
+void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
   a.dim = c->dim; a.NS = c->NS; a.L = c->L; a.J = c->J;
   for (int t = 0; t < 3; ++t) a.n[t] = c->n[t];
   for (int l = 0; l < c->L; ++l) {
@@ -793,36 +818,60 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
   a.front = c->d_front; a.fpad = c->d_fpad; a.chunk = c->d_chunk; a.rowlex = c->d_rowlex; a.recof = c->d_recof;
   a.nbmask = c->d_nbmask;
   a.facoff = c->d_facoff;
-  a.F = F; a.r = r; a.z = z;
+  a.F = F; a.r = nullptr; a.z = nullptr;
   a.status = c->d_status;
   a.porder = c->d_porder;
   a.conv = c->conv_flag;
+  a.plist = nullptr; a.nlist = 0; a.rloc = nullptr; a.xloc = nullptr; a.vstride = 0; a.tout = nullptr;
   a.slot_bytes = c->maxchunk[elem_class<FT>()] * LOR_REC * (int)sizeof(FT);
-  const size_t smem = patch_smem_bytes<T, FT>(c, &a.tab_ints);
+}
+
+template <typename T, typename FT>
+lor_status launch_patch_kernel(lor_ctx* c, PatchArgs& a, bool local) {
+  const size_t smem = patch_smem_bytes<T, FT>(c, &a.tab_ints, local);
   constexpr int NB = ring_depth<FT>();
-  const int pk = sizeof(T) == 8 ? 0 : 1;
-  lor_prof_begin(c, pk);
   // persistent CTAs: as many as fit on the device, each walking patches j, j+grid, ...
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long work = a.plist ? a.nlist : c->J;
+  if (work <= 0) return LOR_OK;
   if (c->dim == 3) {
     auto kern = k_patch_vcycle<3, T, FT, NB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPatchThreads, smem);
-    const int grid = (int)std::min<long long>(c->J, (long long)std::max(per_sm, 1) * nsm);
+    const int grid = (int)std::min<long long>(work, (long long)std::max(per_sm, 1) * nsm);
     kern<<<grid, kPatchThreads, smem, c->stream>>>(a);
-    ++c->launches;
   } else {
     auto kern = k_patch_vcycle<2, T, FT, NB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPatchThreads, smem);
-    const int grid = (int)std::min<long long>(c->J, (long long)std::max(per_sm, 1) * nsm);
+    const int grid = (int)std::min<long long>(work, (long long)std::max(per_sm, 1) * nsm);
     kern<<<grid, kPatchThreads, smem, c->stream>>>(a);
-    ++c->launches;
   }
+  ++c->launches;
+  return lor_cuda_check(c, cudaGetLastError(), "patch vcycle");
+}
+
+template <typename T, typename FT>
+lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
+  const long long nvec = c->lev[0].ntot;
+  cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * nvec, c->stream);
+  if (e != cudaSuccess) return lor_cuda_check(c, e, "apply_P memset");
+  PatchArgs a;
+  fill_patch_args<T, FT>(c, a, F);
+  a.r = r; a.z = z;
+  if (c->learned_on && sizeof(T) == 4) {
+    a.tout = c->learned_tout;
+    a.vstride = c->shapes[0].rows;
+  }
+  const int pk = sizeof(T) == 8 ? 0 : 1;
+  lor_prof_begin(c, pk);
+  if (launch_patch_kernel<T, FT>(c, a, false)) return LOR_ECUDA;
   lor_prof_end(c, pk);
-  if (lor_cuda_check(c, cudaGetLastError(), "patch vcycle")) return LOR_ECUDA;
+  if (c->learned_on && sizeof(T) == 4) {
+    if (lor_learned_apply(c, (float*)z)) return LOR_ECUDA;
+  }
   lor_prof_begin(c, pk + 4);
   // coarse space
   const double* gllx = lor_basis64(c, 4);
@@ -847,6 +896,19 @@ lor_status lor_launch_apply_P64(lor_ctx* c, const double* r, double* z) {
 lor_status lor_launch_apply_P32(lor_ctx* c, const float* r, float* z) {
   if (c->d_F16) return launch_apply_P<float, __nv_bfloat16>(c, r, z, c->d_F16);
   return launch_apply_P<float, float>(c, r, z, c->d_F32);
+}
+
+// Patch-local V-cycles (FP32 vectors) of the listed patches: rhs rloc -> x xloc.
+lor_status lor_patch_local32(lor_ctx* c, const int* plist, int nlist, const float* rloc, float* xloc, int vstride) {
+  PatchArgs a;
+  if (c->d_F16) {
+    fill_patch_args<float, __nv_bfloat16>(c, a, c->d_F16);
+    a.plist = plist; a.nlist = nlist; a.rloc = rloc; a.xloc = xloc; a.vstride = vstride;
+    return launch_patch_kernel<float, __nv_bfloat16>(c, a, true);
+  }
+  fill_patch_args<float, float>(c, a, c->d_F32);
+  a.plist = plist; a.nlist = nlist; a.rloc = rloc; a.xloc = xloc; a.vstride = vstride;
+  return launch_patch_kernel<float, float>(c, a, true);
 }
 
 size_t lor_patch_smem(const lor_ctx* c, int which) {

@@ -283,6 +283,7 @@ void lor_destroy(lor_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   if (c->dg_state) lor_free_dg(c);
+  if (c->learned) lor_free_learned(c);
   for (void* p : c->allocs) cudaFree(p);
   for (int k = 0; k < 6; ++k)
     for (cudaEvent_t e : c->ev[k]) cudaEventDestroy(e);

@@ -17,7 +17,7 @@
 namespace {
 
 enum { S_RZ = 0, S_PAP = 1, S_RR = 2, S_RZNEW = 3, S_ALPHA = 4, S_BETA = 5, S_BB = 6, S_FLAG = 7, S_TMP = 8 };
-enum { OP_STORE = 0, OP_ALPHA = 1, OP_BETA = 2 };
+enum { OP_STORE = 0, OP_ALPHA = 1, OP_BETA = 2, OP_BETA_FLEX = 3 };
 
 const int kRedBlocks = 1024;
 const int kRedThreads = 256;
@@ -60,10 +60,15 @@ __device__ void finish(double mine, double* part, unsigned* count, double* scal,
         scal[S_PAP] = v;
         if (!(v > 0.0) || !isfinite(v)) scal[S_FLAG] = 1.0;
         scal[S_ALPHA] = scal[S_RZ] / v;
-      } else {   // OP_BETA: v = r.z_new
+      } else if (op == OP_BETA) {   // v = r.z_new
         scal[S_RZNEW] = v;
         if (!isfinite(v)) scal[S_FLAG] = 1.0;
         scal[S_BETA] = v / scal[S_RZ];
+        scal[S_RZ] = v;
+      } else {   // OP_BETA_FLEX (flexible CG, Polak-Ribiere): v = r.z_new, S_TMP = r.z_old
+        scal[S_RZNEW] = v;
+        if (!isfinite(v)) scal[S_FLAG] = 1.0;
+        scal[S_BETA] = (v - scal[S_TMP]) / scal[S_RZ];
         scal[S_RZ] = v;
       }
     }
@@ -228,8 +233,10 @@ static lor_status pcg_core(lor_ctx* c, T* x, T* r, T* z, T* p, T* Ap, long long 
     if (record) c->hist.push_back(sqrt(rr));
     if (c->h_scal[S_FLAG] != 0.0 || !std::isfinite(rr)) { st = LOR_ENAN; break; }
     if (sqrt(rr) <= tol_abs) break;
+    const bool flexible = c->learned_on;   // the learned correction makes B nonlinear
+    if (flexible) dot(c, r, z, n, S_TMP, OP_STORE);
     if (applyP(r, z)) return LOR_ECUDA;
-    dot(c, r, z, n, 0, OP_BETA);
+    dot(c, r, z, n, 0, flexible ? OP_BETA_FLEX : OP_BETA);
     k_xpay<T><<<gb, kRedThreads, 0, c->stream>>>(p, z, n, c->d_scal);
     ++c->launches;
   }

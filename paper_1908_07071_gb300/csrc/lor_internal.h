@@ -169,6 +169,10 @@ struct lor_ctx {
   long long nv = 0;            // length of the solver's vectors (CG grid or DG blocks)
   int tune_ne = 1;             // apply_A tile variant (elements per CTA), set by the autotuner
   const double* conv_flag = nullptr;   // batched solves: patch kernel returns early when *conv_flag != 0
+  // learned correction (learned.cu)
+  void* learned = nullptr;
+  bool learned_on = false;
+  float* learned_tout = nullptr;       // level-0 residuals of interior patches after the cycle
   size_t bytes = 0;
   long long launches = 0;      // kernels launched by this context
   std::vector<void*> allocs;
@@ -200,6 +204,9 @@ lor_status lor_launch_apply_P_dg64(lor_ctx* c, const double* r, double* z);
 lor_status lor_launch_apply_P_dg32(lor_ctx* c, const float* r, float* z);
 lor_status lor_launch_rhs_dg(lor_ctx* c, int kind, double* b, double* W);
 void lor_free_dg(lor_ctx* c);
+void lor_free_learned(lor_ctx* c);
+lor_status lor_learned_apply(lor_ctx* c, float* z);
+lor_status lor_patch_local32(lor_ctx* c, const int* plist, int nlist, const float* rloc, float* xloc, int vstride);
 // operator / preconditioner of the context's discretization (CG or DG)
 lor_status lor_opA64(lor_ctx* c, const double* x, double* y);
 lor_status lor_opA32(lor_ctx* c, const float* x, float* y);

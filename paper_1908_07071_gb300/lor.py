@@ -78,6 +78,12 @@ def load():
     lib.lor_batch_destroy.restype = None
     for name in ("lor_batch_create", "lor_batch_solve", "lor_batch_stats"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.lor_learned_params.argtypes = [vp, vp, vp, i]
+    lib.lor_learned_enable.argtypes = [vp, i]
+    lib.lor_learned_train.argtypes = [vp, i, i, ctypes.c_float, ctypes.c_ulonglong, vp]
+    lib.lor_learned_eval.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
+    for name in ("lor_learned_params", "lor_learned_enable", "lor_learned_train", "lor_learned_eval"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.lor_rhs_static.argtypes = [i, i, i, i, i, vp, i, vp, vp]
     lib.lor_rhs_static.restype = ctypes.c_int
     lib.lor_set_prec.argtypes = [vp, i]
@@ -212,6 +218,44 @@ class Solver:
         ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
         self._check(self.lib.lor_profile_read(self.ctx, kernel, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    # ---- learned per-patch correction
+    NPARAM = 8241
+
+    def learned_params(self, params=None):
+        """Sets (if given) and returns the FP32 parameter vector."""
+        out = np.zeros(self.NPARAM, dtype=np.float32)
+        pin = None
+        if params is not None:
+            pin = np.ascontiguousarray(params, dtype=np.float32)
+            assert pin.size == self.NPARAM
+        self._check(self.lib.lor_learned_params(self.ctx, None if pin is None else pin.ctypes.data_as(ctypes.c_void_p),
+                                                out.ctypes.data_as(ctypes.c_void_p), self.NPARAM))
+        return out
+
+    def learned_enable(self, on=True):
+        self._check(self.lib.lor_learned_enable(self.ctx, int(bool(on))))
+
+    def learned_train(self, steps, batch=64, lr=1e-3, seed=0):
+        hist = np.zeros(max(steps, 1), dtype=np.float32)
+        self._check(self.lib.lor_learned_train(self.ctx, steps, batch, ctypes.c_float(lr), seed,
+                                               hist.ctypes.data_as(ctypes.c_void_p)))
+        return hist[:steps]
+
+    def learned_eval(self, ids, t, delta=None):
+        """ids: int32 CUDA tensor of interior patch ids; t, delta: float32 (npatch, V).
+        Returns (correction, per-patch loss or None, summed gradient or None)."""
+        import torch
+        n = ids.numel()
+        c = torch.empty_like(t)
+        loss = torch.empty(n, dtype=torch.float32, device="cuda") if delta is not None else None
+        grad = np.zeros(self.NPARAM, dtype=np.float32) if delta is not None else None
+        self._check(self.lib.lor_learned_eval(
+            self.ctx, n, ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+            None if delta is None else ctypes.c_void_p(delta.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+            None if loss is None else ctypes.c_void_p(loss.data_ptr()),
+            None if grad is None else grad.ctypes.data_as(ctypes.c_void_p)))
+        return c, loss, grad
 
     def history(self):
         cnt = ctypes.c_int(0)

@@ -1,0 +1,102 @@
+"""Learned per-patch correction on the GPU: forward, loss and gradients against the
+FP64 oracle; training on the GPU; what the trained correction gains in a solve."""
+import numpy as np
+import pytest
+
+from oracle import learned as L
+from oracle import lor as olor
+from oracle.mesh import Mesh
+from paper_1908_07071_gb300.synthetic import make_mesh
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_07071_gb300.build import build_library
+    build_library()
+
+
+def _flat(P):
+    return np.concatenate([P["W1"].ravel(), P["b1"], P["W2"].ravel(), P["b2"], P["W3"].ravel(), P["b3"]])
+
+
+def _unflat(v):
+    o = 0
+    P = {}
+    for name, shape in (("W1", (16, 2, 27)), ("b1", (16,)), ("W2", (16, 16, 27)), ("b2", (16,)),
+                        ("W3", (1, 16, 27)), ("b3", (1,))):
+        k = int(np.prod(shape))
+        P[name] = np.asarray(v[o:o + k], dtype=np.float64).reshape(shape)
+        o += k
+    return P
+
+
+def test_forward_loss_gradient_parity():
+    from paper_1908_07071_gb300 import lor
+    v, k = make_mesh(3, 3, seed=4, perturb=0.15)
+    p = 3
+    s = lor.Solver(v, k, p)
+    P = L.init_params(seed=7, scale=0.3)
+    P["W3"] = np.random.default_rng(8).standard_normal(P["W3"].shape) * 0.2
+    P["b1"] = np.random.default_rng(9).standard_normal(16) * 0.05
+    s.learned_params(_flat(P).astype(np.float32))
+    # oracle with the parameters the GPU applies: bf16 weights, fp32 biases
+    Pq = {kk: (L.bf16_round(vv) if kk.startswith("W") else vv.astype(np.float32).astype(np.float64))
+          for kk, vv in P.items()}
+    m = Mesh(v, k)
+    B = olor.LORPreconditioner(m, p, coarse=False)
+    shape = (2 * p - 1,) * 3
+    V = int(np.prod(shape))
+    ids = [j for j, pt in enumerate(B.patches) if all(0 < pt["v"][a] < 3 for a in range(3))]
+    rng = np.random.default_rng(10)
+    ts, ds, refs = [], [], []
+    for j in ids:
+        A = B.patches[j]["levels"][0]["A"]
+        delta = rng.standard_normal(V)
+        t = A @ delta
+        Lr, G = L.loss_and_grad(Pq, t.reshape(shape), delta.reshape(shape),
+                                lambda x, A=A: (A @ x.ravel()).reshape(shape), np.diag(A).reshape(shape))
+        c, _ = L.forward(Pq, t.reshape(shape), np.diag(A).reshape(shape))
+        ts.append(t)
+        ds.append(delta)
+        refs.append((Lr, G, c.ravel()))
+    dt = torch.tensor(np.array(ts), dtype=torch.float32, device="cuda")
+    dd = torch.tensor(np.array(ds), dtype=torch.float32, device="cuda")
+    di = torch.tensor(ids, dtype=torch.int32, device="cuda")
+    c, loss, grad = s.learned_eval(di, dt, dd)
+    c = c.cpu().numpy()
+    loss = loss.cpu().numpy()
+    Gsum = _unflat(grad)
+    for q, (Lr, G, cr) in enumerate(refs):
+        assert abs(loss[q] - Lr) <= 1e-4 * abs(Lr), (loss[q], Lr)
+        assert np.abs(c[q] - cr).max() <= 1e-4 * np.abs(cr).max()
+    for name in Gsum:
+        ref = sum(r[1][name] for r in refs)
+        assert np.abs(Gsum[name] - ref).max() <= 2e-3 * np.abs(ref).max() + 1e-7, name
+    s.close()
+
+
+def test_training_lowers_loss_and_correction_in_fcg():
+    from paper_1908_07071_gb300 import lor
+    v, k = make_mesh(3, 6, seed=11, perturb=0.15)
+    s = lor.Solver(v, k, 4, prec=lor.LOR_MIXED, rtol=1e-8, factor_bf16=True)
+    b = torch.empty(s.nvec, dtype=torch.float64, device="cuda")
+    s.rhs(b, 0)
+    x = torch.zeros_like(b)
+    it_plain, rel_plain = s.solve(b, x)
+    s.learned_params(_flat(L.init_params(seed=1)).astype(np.float32))
+    hist = s.learned_train(300, batch=64, lr=2e-3, seed=5)
+    assert hist[0] == pytest.approx(1.0, abs=1e-3)        # zero output layer: plain V-cycle
+    assert hist[-20:].mean() < 0.9 * hist[:5].mean(), hist[::30]
+    s.learned_enable(True)
+    x2 = torch.zeros_like(b)
+    it_l, rel_l = s.solve(b, x2)
+    print(f"mixed-precision FCG iterations: plain {it_plain}, learned {it_l}; "
+          f"loss {hist[:5].mean():.3f} -> {hist[-20:].mean():.3f}")
+    assert rel_l <= 1e-8 and rel_plain <= 1e-8
+    assert it_l <= 1.1 * it_plain + 2
+    s.close()
