@@ -126,7 +126,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 
 template <typename FT, int NBUF>
 struct Ring {
-  FT* slot[NBUF];
+  unsigned char* base;   // slot s starts at base + s * bytes
+  int bytes;
+  __device__ __forceinline__ FT* slot(int s) const { return (FT*)(base + (size_t)s * bytes); }
   unsigned long long* bar;
   unsigned phase;     // bit s: parity expected next on slot s
   unsigned inflight;  // producer view: bit s set while a copy into slot s is pending
@@ -158,7 +160,7 @@ __device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __
   if (lane == 0) {
     for (int c = 0; c < NBUF - 1 && c < nc; ++c) {
       const int k = BACK ? nc - 1 - c : c;
-      bulk_load(rg.slot[c % NBUF], part + (long long)fp[ch[k]] * LOR_REC,
+      bulk_load(rg.slot(c % NBUF), part + (long long)fp[ch[k]] * LOR_REC,
                 (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * LOR_REC * sizeof(FT)), rg.bar + (c % NBUF));
       rg.inflight |= 1u << (c % NBUF);
     }
@@ -175,13 +177,13 @@ __device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __
       const int cn = c + NBUF - 1;
       if (cn < nc) {
         const int k = BACK ? nc - 1 - cn : cn;
-        bulk_load(rg.slot[cn % NBUF], part + (long long)fp[ch[k]] * LOR_REC,
+        bulk_load(rg.slot(cn % NBUF), part + (long long)fp[ch[k]] * LOR_REC,
                   (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * LOR_REC * sizeof(FT)), rg.bar + (cn % NBUF));
         rg.inflight |= 1u << (cn % NBUF);
       }
     }
     __syncwarp();
-    const FT* blk = rg.slot[sl];
+    const FT* blk = rg.slot(sl);
     const int k = BACK ? nc - 1 - c : c;
     const int fa = ch[k], fb = ch[k + 1];
     const int r0 = fp[fa];
@@ -268,7 +270,8 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
   Ring<FT, NBUF> rg;
   rg.bar = (unsigned long long*)smem_raw;
   unsigned char* ring0 = smem_raw + 128;
-  for (int s = 0; s < NBUF; ++s) rg.slot[s] = (FT*)(ring0 + (size_t)s * a.slot_bytes);
+  rg.base = ring0;
+  rg.bytes = a.slot_bytes;
   rg.phase = 0;
   rg.inflight = 0;
   Xfer1D<T>* xf = (Xfer1D<T>*)(ring0 + (size_t)NBUF * a.slot_bytes);   // [level][type]
@@ -300,8 +303,14 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
       }
     }
   int cur_sh = -1;
-  LevelTables tb[LOR_MAXLEV];
-  BoxShape bsh[LOR_MAXLEV];
+  // per-level state of the current patch: one shared copy (thread 0 writes it)
+  __shared__ LevelTables tb[LOR_MAXLEV];
+  __shared__ BoxShape bsh[LOR_MAXLEV];
+  __shared__ Box bx[LOR_MAXLEV];
+  __shared__ T* xs[LOR_MAXLEV];
+  __shared__ T* ts[LOR_MAXLEV];
+  __shared__ T* rs[LOR_MAXLEV];
+  __shared__ long long s_offset;
   const int nwork = a.plist ? a.nlist : a.J;
   for (int jo = blockIdx.x; jo < nwork; jo += gridDim.x) {
     const int j = a.plist ? a.plist[jo] : a.porder[jo];
@@ -317,16 +326,19 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
     __syncthreads();   // previous patch done with shared memory
     if (sh != cur_sh) {
       // wavefront tables of every level of this shape
-      int ioff = 0;
-      for (int l = 0; l < a.L; ++l) {
-        bsh[l] = a.shapes[l * 8 + sh];
-        tb[l].front = ip + ioff; ioff += bsh[l].nfront + 1;
-        tb[l].fpad = ip + ioff; ioff += bsh[l].nfront + 1;
-        tb[l].chunk = ip + ioff; ioff += bsh[l].nchunk[ES] + 1;
+      if (threadIdx.x == 0) {
+        int ioff = 0;
+        for (int l = 0; l < a.L; ++l) {
+          bsh[l] = a.shapes[l * 8 + sh];
+          tb[l].front = ip + ioff; ioff += bsh[l].nfront + 1;
+          tb[l].fpad = ip + ioff; ioff += bsh[l].nfront + 1;
+          tb[l].chunk = ip + ioff; ioff += bsh[l].nchunk[ES] + 1;
+        }
+        unsigned short* up = (unsigned short*)(ip + ioff);
+        int uoff = 0;
+        for (int l = 0; l < a.L; ++l) { tb[l].rowlex = up + uoff; uoff += bsh[l].rows; }
       }
-      unsigned short* up = (unsigned short*)(ip + ioff);
-      int uoff = 0;
-      for (int l = 0; l < a.L; ++l) { tb[l].rowlex = up + uoff; uoff += bsh[l].rows; }
+      __syncthreads();
       for (int l = 0; l < a.L; ++l) {
         const int nf1 = bsh[l].nfront + 1;
         for (int i = threadIdx.x; i < nf1; i += blockDim.x) {
@@ -341,25 +353,25 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
       cur_sh = sh;
     }
     if (bsh[0].rows == 0) continue;
-    Box bx[LOR_MAXLEV];
-    T* xs[LOR_MAXLEV];
-    T* ts[LOR_MAXLEV];
-    T* rs[LOR_MAXLEV];
-    long long offset = 0;
-    for (int l = 0; l < a.L; ++l) {
-      const BoxShape& bs = bsh[l];
-      Box& b = bx[l];
-      b.A = bs.dims[0]; b.B = bs.dims[1]; b.C = bs.dims[2];
-      b.rows = bs.rows;
-      for (int t = 0; t < 3; ++t) {
-        b.type[t] = type[t];
-        b.org[t] = t < DIM ? (v[t] > 0 ? v[t] - 1 : 0) * a.lv[l].m + 1 : 0;
+    if (threadIdx.x == 0) {
+      long long offset = 0;
+      for (int l = 0; l < a.L; ++l) {
+        const BoxShape& bs = bsh[l];
+        Box& b = bx[l];
+        b.A = bs.dims[0]; b.B = bs.dims[1]; b.C = bs.dims[2];
+        b.rows = bs.rows;
+        for (int t = 0; t < 3; ++t) {
+          b.type[t] = type[t];
+          b.org[t] = t < DIM ? (v[t] > 0 ? v[t] - 1 : 0) * a.lv[l].m + 1 : 0;
+        }
+        xs[l] = sm + offset; offset += b.rows;
+        ts[l] = sm + offset + bs.guard; offset += b.rows + 2 * bs.guard;
+        rs[l] = sm + offset; offset += (l > 0 || a.plist ? b.rows : 0);
       }
-      xs[l] = sm + offset; offset += b.rows;
-      ts[l] = sm + offset + bs.guard; offset += b.rows + 2 * bs.guard;
-      rs[l] = sm + offset; offset += (l > 0 || a.plist ? b.rows : 0);
+      s_offset = offset;
     }
-    for (long long i = threadIdx.x; i < offset; i += blockDim.x) sm[i] = T(0);
+    __syncthreads();
+    for (long long i = threadIdx.x; i < s_offset; i += blockDim.x) sm[i] = T(0);
     __syncthreads();
     // level-0 right-hand side: the global vector, or the listed patch's own data
     const T* rg0 = a.plist ? nullptr : (const T*)a.r;
