@@ -4,13 +4,18 @@
 // of the element-structured hierarchy (Section 3.3) smoothed by lexicographic
 // ILU(0) (Section 3.4).
 //
-// Patch kernel: one CTA per patch runs the whole V-cycle in shared memory:
+// Patch kernel: each warp runs the whole V-cycle of one patch at a time:
 // gather R_j r, per level ILU(0) pre-smoothing (wavefront-scheduled forward and
-// backward sweeps), 3^d-point residual with the level's Galerkin LOR stencil,
-// tensor restriction, exact solve on the vertex level (<= 1 unknown), then
-// prolongation, residual and post-smoothing on the way up, and a scatter-add of
-// x_j into z.  Vectors live in zero-padded boxes so that stencil and factor
-// reads need no bounds checks (factors of out-of-box couplings are stored as 0).
+// backward sweeps over factor records streamed by bulk copies), 3^d-point
+// residual with the level's Galerkin LOR stencil, tensor restriction, exact
+// solve on the vertex level (<= 1 unknown), then prolongation, residual and
+// post-smoothing on the way up, and a scatter-add of x_j into z.  Many patches
+// are in flight per SM (one per warp), so the latency-bound sweeps of one patch
+// overlap those of the others.  Vectors live in zero-padded boxes so that
+// factor reads need no bounds checks (factors of out-of-box couplings are
+// stored as 0); the level-0 iterate is kept in a per-warp global slot (L2) and
+// the level-0 residual is formed in place, which keeps a patch's shared-memory
+// footprint to the level-0 work vector, the coarse levels and the copy ring.
 //
 // Coarse space: P_0^T r at the interior vertices, one V-cycle on the vertex grid
 // (l1-Jacobi smoothing, Galerkin levels, dense inverse on the coarsest grid),
@@ -30,6 +35,7 @@ template <> __device__ __forceinline__ double fac<double, double>(double v) { re
 
 struct PLevel {
   const void* S;          // [NS][ntot] stencil of this level (T)
+  const void* Sa;         // [ntot][nsp] row-major copy (T)
   long long ntot;
   int N[3];
   int m;
@@ -54,19 +60,21 @@ struct PatchArgs {
   int n[3];
   PLevel lv[LOR_MAXLEV];
   const BoxShape* shapes;       // [L][8]
-  const int* front;
   const int* fpad;
   const int* chunk;
-  const int* rowlex;
-  const int* recof;
-  const unsigned* nbmask;
   const long long* facoff;      // [L][J] record offsets
   const void* F;
   const void* r;
   void* z;
   int* status;
   int slot_bytes;               // ring slot size (bytes, multiple of 16)
-  int tab_ints;                 // shared-memory ints reserved for wavefront tables
+  int tab_ints;                 // per-warp shared-memory ints reserved for wavefront tables
+  int xf_bytes;                 // shared transfer tables at the start of dynamic shared memory
+  int warp_bytes;               // per-warp block size (bytes, multiple of 128)
+  int aux_n;                    // per-warp vector layout: auxiliary buffers (plane buffers / r1)
+  int ovl_n;                    //   then level-0 t with guards, overlaid by the coarse levels
+  void* xs;                     // per-warp level-0 iterate slots (T), x0_stride values each
+  long long x0_stride;
   const int* porder;            // patch visiting order (grouped by box shape)
   const double* conv;           // optional: skip all work when *conv != 0 (converged batched solve)
   // patch-local mode (learned-correction training data): patches plist[0..nlist)
@@ -82,12 +90,6 @@ struct PatchArgs {
   void* tout;
 };
 
-struct Box {
-  int A, B, C;       // extents
-  int rows;
-  int org[3];        // global level index of local (0,0,0)
-  int type[3];       // axis type (0 interior, 1 boundary)
-};
 
 // ---- TMA bulk-copy ring (one elected producer thread, mbarrier completion) ----
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -134,34 +136,106 @@ struct Ring {
   unsigned inflight;  // producer view: bit s set while a copy into slot s is pending
 };
 
-// Shared-memory copies of one level's wavefront tables.
-struct LevelTables {
-  const unsigned short* rowlex;   // lexicographic row index per wavefront position
-  const int* front;               // nfront+1 row positions
-  const int* fpad;                // nfront+1 record offsets
-  const int* chunk;               // nchunk+1 front indices
+
+// One factor record held in registers: R values of type FT as 32-bit words.
+template <int R, typename FT>
+struct RecRegs {
+  static constexpr int NW = R * (int)sizeof(FT) / 4;
+  unsigned w[NW];
+  __device__ __forceinline__ void load(const FT* rec) {
+    const uint4* q = (const uint4*)rec;
+#pragma unroll
+    for (int v = 0; v < NW / 4; ++v) {
+      const uint4 u = q[v];
+      w[4 * v] = u.x; w[4 * v + 1] = u.y; w[4 * v + 2] = u.z; w[4 * v + 3] = u.w;
+    }
+  }
+  // value of slot o (o a compile-time constant after unrolling)
+  template <typename T>
+  __device__ __forceinline__ T val(int o) const {
+    if constexpr (sizeof(FT) == 2) {
+      const unsigned x = w[o >> 1];
+      return (T)__uint_as_float((o & 1) ? (x & 0xffff0000u) : (x << 16));
+    } else if constexpr (sizeof(FT) == 4) {
+      return (T)__uint_as_float(w[o]);
+    } else {
+      return (T)__hiloint2double((int)w[2 * o + 1], (int)w[2 * o]);
+    }
+  }
 };
+
+// Row index (slot R-1, raw integer bits) of the record at rec.
+template <int R, typename FT>
+__device__ __forceinline__ int rec_index(const FT* rec) {
+  if constexpr (sizeof(FT) == 2) return ((const unsigned short*)rec)[R - 1];
+  else if constexpr (sizeof(FT) == 4) return ((const int*)rec)[R - 1];
+  else return ((const int*)rec)[2 * (R - 1)];
+}
+
+// NR rows of one front of a sweep (row u: record rec[u], box index li[u]):
+// t[li] -= sum of the row's strictly lower (forward) or upper (backward, then
+// scaled by 1/u_ii) couplings.  Rows of one front never couple, so every load
+// of the front is issued before its first store; the row indices of the next
+// front (records nrec[u], read only if nxt) are loaded in the same round.
+template <int DIM, bool BACK, typename T, typename FT, int NR>
+__device__ __forceinline__ void sweep_front(const FT* const* rec, int* li, const FT* const* nrec, bool nxt, int A,
+                                            int AB, T* t) {
+  constexpr int NS = DIM == 3 ? 27 : 9;
+  constexpr int C = NS / 2;
+  constexpr int R = lor_rec(DIM);
+  RecRegs<R, FT> rr[NR];
+  T tv[NR][C + 1];
+#pragma unroll
+  for (int u = 0; u < NR; ++u) {
+    rr[u].load(rec[u]);
+    tv[u][C] = t[li[u]];
+#pragma unroll
+    for (int o = 0; o < C; ++o) {
+      const int so = BACK ? C + 1 + o : o;                 // stencil offset index
+      const int dx = so % 3 - 1, dy = (so / 3) % 3 - 1, dz = DIM == 3 ? so / 9 - 1 : 0;
+      tv[u][o] = t[li[u] + dz * AB + dy * A + dx];
+    }
+  }
+  int ln[NR];
+#pragma unroll
+  for (int u = 0; u < NR; ++u) ln[u] = nxt ? rec_index<R, FT>(nrec[u]) : 0;
+#pragma unroll
+  for (int u = 0; u < NR; ++u) {
+    T s0 = tv[u][C], s1 = T(0);
+#pragma unroll
+    for (int o = 0; o < C; ++o) {
+      const T v = rr[u].template val<T>(o) * tv[u][o];
+      if (o & 1) s1 -= v; else s0 -= v;
+    }
+    t[li[u]] = BACK ? (s0 + s1) * rr[u].template val<T>(R - 2) : s0 + s1;
+  }
+#pragma unroll
+  for (int u = 0; u < NR; ++u) li[u] = ln[u];
+}
 
 // One triangular sweep over a level, run by ONE warp.  Factor blocks stream
 // through the ring in chunks of whole fronts: lane 0 issues the bulk copies and
 // observes their completion, __syncwarp publishes them to the other lanes.
-// Inside a chunk, lanes loop over the rows of a front and __syncwarp separates
-// fronts.  t has a zero guard band, so neighbour reads need no clamping
-// (multipliers of out-of-box neighbours are stored as 0).  BACK selects the
-// backward sweep (U part, fronts in reverse, scaled by 1/u_ii).
+// Inside a chunk, lane q takes records q and q+32 of a front (fronts hold at
+// most 64 records; the second row only when the front is wider than 32).  A
+// lane without a row reads the all-zero record zrec, whose row index `dummy`
+// is the first guard cell after the box, and writes 0 there, like a padding
+// record.  The row indices of the next front are read ahead so that a front's
+// critical path is one round of shared-memory loads of t.  __syncwarp
+// separates fronts.  t has a zero guard band, so neighbour reads need no
+// clamping (multipliers of out-of-box neighbours are stored as 0).  BACK
+// selects the backward sweep (U part, fronts in reverse, scaled by 1/u_ii).
 template <int DIM, bool BACK, typename T, typename FT, int NBUF>
-__device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __restrict__ fr,
-                                      const int* __restrict__ fp, const int* __restrict__ ch,
-                                      const unsigned short* __restrict__ rl, int nc, int A, int AB, T* t,
-                                      Ring<FT, NBUF>& rg) {
-  constexpr int NS = DIM == 3 ? 27 : 9;
-  constexpr int C = NS / 2;
+__device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __restrict__ fp,
+                                      const int* __restrict__ ch, int nc, int A, int AB, int dummy,
+                                      const FT* zrec, T* t, Ring<FT, NBUF>& rg) {
+  constexpr int R = lor_rec(DIM);
   const int lane = threadIdx.x & 31;
   if (lane == 0) {
     for (int c = 0; c < NBUF - 1 && c < nc; ++c) {
       const int k = BACK ? nc - 1 - c : c;
-      bulk_load(rg.slot(c % NBUF), part + (long long)fp[ch[k]] * LOR_REC,
-                (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * LOR_REC * sizeof(FT)), rg.bar + (c % NBUF));
+      bulk_load(rg.slot(c % NBUF), part + (long long)fp[ch[k]] * R,
+                (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * R * sizeof(FT)), rg.bar + (c % NBUF));
       rg.inflight |= 1u << (c % NBUF);
     }
   }
@@ -177,113 +251,271 @@ __device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __
       const int cn = c + NBUF - 1;
       if (cn < nc) {
         const int k = BACK ? nc - 1 - cn : cn;
-        bulk_load(rg.slot(cn % NBUF), part + (long long)fp[ch[k]] * LOR_REC,
-                  (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * LOR_REC * sizeof(FT)), rg.bar + (cn % NBUF));
+        bulk_load(rg.slot(cn % NBUF), part + (long long)fp[ch[k]] * R,
+                  (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * R * sizeof(FT)), rg.bar + (cn % NBUF));
         rg.inflight |= 1u << (cn % NBUF);
       }
     }
     __syncwarp();
     const FT* blk = rg.slot(sl);
     const int k = BACK ? nc - 1 - c : c;
-    const int fa = ch[k], fb = ch[k + 1];
+    const int fa = ch[k], fb = ch[k + 1], nf = fb - fa;
     const int r0 = fp[fa];
-    for (int q = 0; q < fb - fa; ++q) {
-      const int f = BACK ? fb - 1 - q : fa + q;
-      const int p0 = fr[f], p1 = fr[f + 1];
-      const FT* fbk = blk + (fp[f] - r0) * LOR_REC;
-      for (int pos = p0 + lane; pos < p1; pos += 32) {
-        const int li = rl[pos];
-        const FT* rec = fbk + (pos - p0) * LOR_REC;
-        T s0 = t[li], s1 = T(0);
-#pragma unroll
-        for (int o = 0; o < C; ++o) {
-          const int so = BACK ? C + 1 + o : o;                 // stencil offset index
-          const int dx = so % 3 - 1, dy = (so / 3) % 3 - 1, dz = DIM == 3 ? so / 9 - 1 : 0;
-          const T v = fac<T, FT>(rec[o]) * t[li + dz * AB + dy * A + dx];
-          if (o & 1) s1 -= v; else s0 -= v;
-        }
-        t[li] = BACK ? (s0 + s1) * fac<T, FT>(rec[LOR_REC - 1]) : s0 + s1;
+    // records [b, e) of the block for the current front, and their row indices
+    int f = BACK ? fb - 1 : fa;
+    int b = fp[f] - r0, e = fp[f + 1] - r0;
+    int li[2];
+    li[0] = lane < e - b ? rec_index<R, FT>(blk + (b + lane) * R) : dummy;
+    li[1] = lane + 32 < e - b ? rec_index<R, FT>(blk + (b + lane + 32) * R) : dummy;
+    for (int q = 0; q < nf; ++q) {
+      const int n = e - b;
+      const bool more = q + 1 < nf;
+      // the next front shares one bound with this one
+      int bn = b, en = e;
+      if (more) {
+        if (BACK) { en = b; bn = fp[f - 1] - r0; }
+        else { bn = e; en = fp[f + 2] - r0; }
       }
+      const FT* rec[2] = {lane < n ? blk + (b + lane) * R : zrec, lane + 32 < n ? blk + (b + lane + 32) * R : zrec};
+      const FT* nrec[2] = {lane < en - bn ? blk + (bn + lane) * R : zrec,
+                           lane + 32 < en - bn ? blk + (bn + lane + 32) * R : zrec};
+      if (n > 32) {   // warp-uniform
+        sweep_front<DIM, BACK, T, FT, 2>(rec, li, nrec, more, A, AB, t);
+      } else {
+        sweep_front<DIM, BACK, T, FT, 1>(rec, li, nrec, more, A, AB, t);
+        li[1] = more ? rec_index<R, FT>(nrec[1]) : dummy;
+      }
+      if (more) {
+        // lanes past the next front's rows take the zero record (index dummy)
+        if (!(lane < en - bn)) li[0] = dummy;
+        if (!(lane + 32 < en - bn)) li[1] = dummy;
+      }
+      f = BACK ? f - 1 : f + 1; b = bn; e = en;
       __syncwarp();
     }
   }
   return true;
 }
 
-// in-place (L U)^{-1} t on one level: warp 0 runs the forward and backward
-// sweeps, the other warps wait at the closing __syncthreads.  Returns false on
-// all threads if a bulk copy timed out.
+// in-place (L U)^{-1} t on one level, run by the calling warp (forward then
+// backward sweep).  Returns false if a bulk copy timed out.
 template <typename FT>
 constexpr int elem_class() { return sizeof(FT) == 2 ? 0 : (sizeof(FT) == 4 ? 1 : 2); }
 
 template <int DIM, typename T, typename FT, int NBUF>
-__device__ bool ilu_solve(const BoxShape& bs, const LevelTables& tb, const FT* FL, T* t, Ring<FT, NBUF>& rg,
-                          int* abort) {
+__device__ __forceinline__ bool ilu_solve(const BoxShape& bs, const int* fp, const int* ch, const FT* FL, T* t,
+                                          Ring<FT, NBUF>& rg, const FT* zrec) {
   constexpr int ES = elem_class<FT>();
-  if (threadIdx.x < 32) {
-    const int A = bs.dims[0], AB = bs.dims[0] * bs.dims[1];
-    bool ok = sweep<DIM, false, T, FT, NBUF>(FL, tb.front, tb.fpad, tb.chunk, tb.rowlex, bs.nchunk[ES], A, AB, t, rg);
-    if (ok)
-      ok = sweep<DIM, true, T, FT, NBUF>(FL + (long long)bs.rpad * LOR_REC, tb.front, tb.fpad, tb.chunk, tb.rowlex,
-                                          bs.nchunk[ES], A, AB, t, rg);
-    if (!ok && threadIdx.x == 0) *abort = 1;
-  }
-  __syncthreads();
-  return *abort == 0;
+  const int A = bs.dims[0], AB = bs.dims[0] * bs.dims[1];
+  bool ok = sweep<DIM, false, T, FT, NBUF>(FL, fp, ch, bs.nchunk[ES], A, AB, bs.rows, zrec, t, rg);
+  if (ok)
+    ok = sweep<DIM, true, T, FT, NBUF>(FL + (long long)bs.rpad * lor_rec(DIM), fp, ch, bs.nchunk[ES], A, AB, bs.rows,
+                                        zrec, t, rg);
+  __syncwarp();
+  return ok;
 }
 
-// t = rhs - A x on one level (rhs from global r on level 0, else from rs).
+// Lane-strided walk over the rows of a box in lexicographic order: the lane
+// starts at row lex0 and advances by 32 rows per step, tracking (i, j, k).
+struct BoxIter {
+  int i, j, k;
+  int si, sj, sk;   // 32 = sk*A*B + sj*A + si
+  int A, B;
+  __device__ __forceinline__ void init(int lex0, int A_, int B_) {
+    A = A_; B = B_;
+    i = lex0 % A; j = (lex0 / A) % B; k = lex0 / (A * B);
+    si = 32 % A; sj = (32 / A) % B; sk = 32 / (A * B);
+  }
+  __device__ __forceinline__ void next() {
+    i += si;
+    int c = i >= A;
+    i -= c ? A : 0;
+    j += sj + c;
+    c = j >= B;
+    j -= c ? B : 0;
+    k += sk + c;
+  }
+};
+
+// One patch level as seen by a warp: box extents, origin in the level grid, and
+// the shared-memory vectors (offsets from the warp's vector base; -1: absent).
+struct WLevel {
+  int A, B, C, rows;
+  int org[3];
+  int xo, to, ro;   // x (with guards), t (with guards), rhs
+};
+
+// Row s of the row-major stencil (nsp values) into registers.
 template <int DIM, typename T>
-__device__ __forceinline__ void residual(int A, int B, int Cz, int ox, int oy, int oz, int Nx, int Ny, long long ntot,
-                                         const T* __restrict__ S, const T* __restrict__ rglob,
-                                         const T* __restrict__ rs, const T* x, T* t) {
-  constexpr int NS = DIM == 3 ? 27 : 9;
-  const int rows = A * B * Cz;
-  for (int lex = threadIdx.x; lex < rows; lex += blockDim.x) {
-    const int i = lex % A, j = (lex / A) % B, k = lex / (A * B);
-    const long long G = ((long long)(oz + k) * Ny + (oy + j)) * Nx + (ox + i);
-    T s = rglob ? rglob[G] : rs[lex];
+__device__ __forceinline__ void load_row(const T* __restrict__ Sa, int G, T* s) {
+  constexpr int NSP = lor_nsp(DIM);
+  const uint4* q = (const uint4*)(Sa + (size_t)G * NSP);
+  constexpr int NV = NSP * (int)sizeof(T) / 16;
 #pragma unroll
-    for (int o = 0; o < NS; ++o) {
-      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
-      const T sv = S[(long long)o * ntot + G];   // the row's own coefficient: always in range
-      const bool in = (unsigned)(i + dx) < (unsigned)A && (unsigned)(j + dy) < (unsigned)B &&
-                      (unsigned)(k + dz) < (unsigned)Cz;
-      const T xv = in ? x[lex + (dz * B + dy) * A + dx] : T(0);
-      s -= sv * xv;
+  for (int v = 0; v < NV; ++v) {
+    const uint4 u = __ldg(q + v);
+    if constexpr (sizeof(T) == 4) {
+      s[4 * v] = __uint_as_float(u.x); s[4 * v + 1] = __uint_as_float(u.y);
+      s[4 * v + 2] = __uint_as_float(u.z); s[4 * v + 3] = __uint_as_float(u.w);
+    } else {
+      s[2 * v] = __hiloint2double((int)u.y, (int)u.x);
+      s[2 * v + 1] = __hiloint2double((int)u.w, (int)u.z);
     }
-    t[lex] = s;
   }
 }
 
-#define LOR_RESID(l_, rglob_) \
-  residual<DIM, T>(bx[l_].A, bx[l_].B, bx[l_].C, bx[l_].org[0], bx[l_].org[1], bx[l_].org[2], a.lv[l_].N[0], \
-                   a.lv[l_].N[1], a.lv[l_].ntot, (const T*)a.lv[l_].S, rglob_, rs[l_], xs[l_], ts[l_])
-
-template <int DIM, typename T, typename FT, int NBUF>
-__global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
-  constexpr int ES = elem_class<FT>();
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ int abort_flag;
-  if (a.conv && *a.conv != 0.0) return;
-  // shared memory: [NBUF mbarriers | pad][ring][transfer tables][wavefront tables][vectors]
-  Ring<FT, NBUF> rg;
-  rg.bar = (unsigned long long*)smem_raw;
-  unsigned char* ring0 = smem_raw + 128;
-  rg.base = ring0;
-  rg.bytes = a.slot_bytes;
-  rg.phase = 0;
-  rg.inflight = 0;
-  Xfer1D<T>* xf = (Xfer1D<T>*)(ring0 + (size_t)NBUF * a.slot_bytes);   // [level][type]
-  int* ip = (int*)(xf + 2 * (a.L > 1 ? a.L - 1 : 1));
-  int* ip_end = ip + a.tab_ints;
-  T* sm = (T*)ip_end;
-  if (threadIdx.x == 0) {
-    abort_flag = 0;
-    for (int s = 0; s < NBUF; ++s) mbar_init(rg.bar + s, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+// rhs - sum_o S_o x(nbr_o) for the row (i, j, k) of a box (A, B, C): out-of-box
+// neighbours contribute nothing (the patch operator R_j A R_j^T keeps only
+// couplings inside the box).  xv(o) returns the neighbour value; its index is
+// always inside a guarded array, so reads are safe before masking.
+template <int DIM, typename T, typename XV>
+__device__ __forceinline__ T row_residual(const T* s, T rhs, int i, int j, int k, int A, int B, int C, XV xv) {
+  constexpr int NS = DIM == 3 ? 27 : 9;
+  T acc0 = rhs, acc1 = T(0);
+#pragma unroll
+  for (int o = 0; o < NS; ++o) {
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+    const bool in = (unsigned)(i + dx) < (unsigned)A && (unsigned)(j + dy) < (unsigned)B &&
+                    (DIM == 2 || (unsigned)(k + dz) < (unsigned)C);
+    const T v = in ? xv(o, dx, dy, dz) : T(0);
+    if (o & 1) acc1 -= s[o] * v;
+    else acc0 -= s[o] * v;
   }
-  // 1D transfer tables of every level (independent of the patch)
+  return acc0 + acc1;
+}
+
+// Level-0 residual in place: t holds x on entry (rows of the box, zero guard
+// bands) and rhs - A x on exit.  Planes are done in order; plane k is computed
+// into tmp from prev (x of plane k-1, guarded) and t (planes k, k+1 still x),
+// then plane k's x moves to prev (and to xout, when given) and tmp into t.
+template <int DIM, typename T>
+__device__ void resid0_inplace(const WLevel& b, const PLevel& lv, const T* __restrict__ rg0,
+                               const T* __restrict__ rloc, T* t, T* prev, T* tmp, T* xout) {
+  constexpr int NSP = lor_nsp(DIM);
+  const int lane = threadIdx.x & 31;
+  const int A = b.A, B = b.B, C = b.C, AB = A * B;
+  const T* Sa = (const T*)lv.Sa;
+  const int N0 = lv.N[0], N1 = lv.N[1];
+  for (int k = 0; k < C; ++k) {
+    BoxIter it;
+    it.init(lane, A, B);   // walks plane-local rows (k component unused)
+    for (int p = lane; p < AB; p += 32, it.next()) {
+      const int i = it.i, j = it.j;
+      const int lex = k * AB + p;
+      const int G = ((b.org[2] + k) * N1 + (b.org[1] + j)) * N0 + (b.org[0] + i);
+      T s[NSP];
+      load_row<DIM, T>(Sa, G, s);
+      const T rhs = rloc ? rloc[lex] : rg0[G];
+      tmp[p] = row_residual<DIM, T>(s, rhs, i, j, k, A, B, C, [&](int o, int dx, int dy, int dz) -> T {
+        return dz < 0 ? prev[p + dy * A + dx] : t[lex + dz * AB + dy * A + dx];
+      });
+    }
+    __syncwarp();
+    for (int p = lane; p < AB; p += 32) {
+      const T xv = t[k * AB + p];
+      prev[p] = xv;
+      if (xout) xout[k * AB + p] = xv;
+      t[k * AB + p] = tmp[p];
+    }
+    __syncwarp();
+  }
+}
+
+// t = r - A x on a level l >= 1 (separate guarded arrays).
+template <int DIM, typename T>
+__device__ void resid_level(const WLevel& b, const PLevel& lv, const T* r, const T* x, T* t) {
+  constexpr int NSP = lor_nsp(DIM);
+  const int lane = threadIdx.x & 31;
+  const int A = b.A, B = b.B, C = b.C, AB = A * B;
+  const T* Sa = (const T*)lv.Sa;
+  const int N0 = lv.N[0], N1 = lv.N[1];
+  BoxIter it;
+  it.init(lane, A, B);
+  for (int lex = lane; lex < b.rows; lex += 32, it.next()) {
+    const int G = ((b.org[2] + it.k) * N1 + (b.org[1] + it.j)) * N0 + (b.org[0] + it.i);
+    T s[NSP];
+    load_row<DIM, T>(Sa, G, s);
+    t[lex] = row_residual<DIM, T>(s, r[lex], it.i, it.j, it.k, A, B, C, [&](int o, int dx, int dy, int dz) -> T {
+      return x[lex + dz * AB + dy * A + dx];
+    });
+  }
+  __syncwarp();
+}
+
+// r_c = R t: tensor restriction of a level-l vector to level l+1 (patch-local).
+template <int DIM, typename T>
+__device__ void restrict_level(const WLevel& bf, const WLevel& bc, const Xfer1D<T>& X0, const Xfer1D<T>& X1,
+                               const Xfer1D<T>& X2, const T* tl, T* rn) {
+  const int lane = threadIdx.x & 31;
+  const int fA = bf.A, fB = bf.B, cA = bc.A, cB = bc.B;
+  BoxIter it;
+  it.init(lane, cA, cB);
+  for (int lex = lane; lex < bc.rows; lex += 32, it.next()) {
+    const int ci = it.i, cj = it.j, ck = it.k;
+    T s = 0;
+    const int z0 = DIM == 3 ? X2.rstart[ck] : 0, z1 = DIM == 3 ? X2.rstart[ck + 1] : 1;
+    for (int tz = z0; tz < z1; ++tz) {
+      const int fz = DIM == 3 ? X2.rf[tz] : 0;
+      const T wz = DIM == 3 ? X2.rw[tz] : T(1);
+      for (int ty = X1.rstart[cj]; ty < X1.rstart[cj + 1]; ++ty) {
+        const T wy = X1.rw[ty] * wz;
+        const int rowb = (fz * fB + X1.rf[ty]) * fA;
+        for (int tx = X0.rstart[ci]; tx < X0.rstart[ci + 1]; ++tx) s += X0.rw[tx] * wy * tl[rowb + X0.rf[tx]];
+      }
+    }
+    rn[lex] = s;
+  }
+  __syncwarp();
+}
+
+// (P x_c)(row) for a fine row (i, j, k) of level l (patch-local tensor prolongation).
+template <int DIM, typename T>
+__device__ __forceinline__ T prolong_row(const WLevel& bc, const Xfer1D<T>& X0, const Xfer1D<T>& X1,
+                                         const Xfer1D<T>& X2, const T* xc, int i, int j, int k) {
+  const int cA = bc.A, cB = bc.B, cC = bc.C;
+  T s = 0;
+  const int nzz = DIM == 3 ? 2 : 1;
+  for (int sz = 0; sz < nzz; ++sz) {
+    const int cz = DIM == 3 ? (sz ? X2.c1[k] : X2.c0[k]) : 0;
+    if (cz < 0 || cz >= cC) continue;
+    const T wz = DIM == 3 ? (sz ? X2.w1[k] : X2.w0[k]) : T(1);
+    for (int sy = 0; sy < 2; ++sy) {
+      const int cy = sy ? X1.c1[j] : X1.c0[j];
+      if (cy < 0 || cy >= cB) continue;
+      const T wy = (sy ? X1.w1[j] : X1.w0[j]) * wz;
+      for (int sx = 0; sx < 2; ++sx) {
+        const int cx = sx ? X0.c1[i] : X0.c0[i];
+        if (cx < 0 || cx >= cA) continue;
+        s += (sx ? X0.w1[i] : X0.w0[i]) * wy * xc[(cz * cB + cy) * cA + cx];
+      }
+    }
+  }
+  return s;
+}
+
+// Per-warp shared-memory block (byte offsets): mbarriers, a zero factor record,
+// level metadata of the current box shape, the bulk-copy ring, the wavefront
+// tables of the shape, and the vectors.
+constexpr int kWarpBars = 0, kWarpZrec = 32, kWarpMeta = 160, kWarpShape = 288, kWarpRing = 768;
+
+// The patch kernel.  Each warp runs whole V-cycles for its own patches (one
+// after another, no block barriers):
+//   t0 <- R_j r; t0 <- ILU(t0) (= x0); x0 -> its global slot, t0 <- r - A x0
+//   (in place); r1 <- R t0; levels 1..bottom as below; x0 += P x1 (global
+//   slot); t0 <- x0; t0 <- r - A x0; t0 <- ILU(t0); z += R_j^T (x0 + t0).
+// Levels l >= 1 live in shared memory over t0's space: down: t <- r,
+// ILU, x <- t, t <- r - A x, r_{l+1} <- R t; the vertex level is solved exactly
+// (<= 1 unknown), a truncated box (boundary patch whose vertex level is empty)
+// is smoothed by ILU twice instead; up: x += P x_{l+1}, t <- r - A x, ILU, x += t.
+template <int DIM, typename T, typename FT, int NBUF>
+__global__ void __launch_bounds__(256, 1) k_patch_warp(PatchArgs a) {
+  constexpr int ES = elem_class<FT>();
+  constexpr int R = lor_rec(DIM);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (a.conv && *a.conv != 0.0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // CTA-wide: 1D transfer tables of every level (independent of the patch)
+  Xfer1D<T>* xf = (Xfer1D<T>*)smem_raw;   // [level][axis type]
   for (int l = 0; l + 1 < a.L; ++l)
     for (int ty = 0; ty < 2; ++ty) {
       Xfer1D<T>& X = xf[l * 2 + ty];
@@ -302,17 +534,33 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
         X.rstart[clen] = q;
       }
     }
-  int cur_sh = -1;
-  // per-level state of the current patch: one shared copy (thread 0 writes it)
-  __shared__ LevelTables tb[LOR_MAXLEV];
-  __shared__ BoxShape bsh[LOR_MAXLEV];
-  __shared__ Box bx[LOR_MAXLEV];
-  __shared__ T* xs[LOR_MAXLEV];
-  __shared__ T* ts[LOR_MAXLEV];
-  __shared__ T* rs[LOR_MAXLEV];
-  __shared__ long long s_offset;
+  __syncthreads();
+  // per-warp block
+  unsigned char* wb = smem_raw + a.xf_bytes + (size_t)warp * a.warp_bytes;
+  Ring<FT, NBUF> rg;
+  rg.bar = (unsigned long long*)(wb + kWarpBars);
+  rg.base = wb + kWarpRing;
+  rg.bytes = a.slot_bytes;
+  rg.phase = 0;
+  rg.inflight = 0;
+  const FT* zrec = (const FT*)(wb + kWarpZrec);
+  int* meta = (int*)(wb + kWarpMeta);   // tbf[LOR_MAXLEV] | tbc[LOR_MAXLEV]
+  BoxShape* bsh = (BoxShape*)(wb + kWarpShape);
+  int* ip = (int*)(wb + kWarpRing + (size_t)NBUF * a.slot_bytes);
+  T* vec = (T*)(ip + a.tab_ints);
+  if (lane < 32) ((unsigned*)(wb + kWarpZrec))[lane] = 0u;
+  if (lane == 0) {
+    for (int s = 0; s < NBUF; ++s) mbar_init(rg.bar + s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const long long gw = (long long)blockIdx.x * nw + warp;
+  T* xslot = (T*)a.xs + gw * a.x0_stride;       // this warp's level-0 iterate
   const int nwork = a.plist ? a.nlist : a.J;
-  for (int jo = blockIdx.x; jo < nwork; jo += gridDim.x) {
+  const long long step = (long long)gridDim.x * nw;
+  int cur_sh = -1;
+  const FT* F = (const FT*)a.F;
+  for (long long jo = gw; jo < nwork; jo += step) {
     const int j = a.plist ? a.plist[jo] : a.porder[jo];
     int v[3];
     v[0] = j % (a.n[0] + 1);
@@ -323,216 +571,205 @@ __global__ void __launch_bounds__(256) k_patch_vcycle(PatchArgs a) {
       type[t] = (v[t] == 0 || v[t] == a.n[t]) ? 1 : 0;
       sh |= type[t] << t;
     }
-    __syncthreads();   // previous patch done with shared memory
     if (sh != cur_sh) {
       // wavefront tables of every level of this shape
-      if (threadIdx.x == 0) {
+      __syncwarp();
+      if (lane == 0) {
         int ioff = 0;
         for (int l = 0; l < a.L; ++l) {
           bsh[l] = a.shapes[l * 8 + sh];
-          tb[l].front = ip + ioff; ioff += bsh[l].nfront + 1;
-          tb[l].fpad = ip + ioff; ioff += bsh[l].nfront + 1;
-          tb[l].chunk = ip + ioff; ioff += bsh[l].nchunk[ES] + 1;
+          meta[l] = ioff; ioff += bsh[l].nfront + 1;
+          meta[LOR_MAXLEV + l] = ioff; ioff += bsh[l].nchunk[ES] + 1;
         }
-        unsigned short* up = (unsigned short*)(ip + ioff);
-        int uoff = 0;
-        for (int l = 0; l < a.L; ++l) { tb[l].rowlex = up + uoff; uoff += bsh[l].rows; }
       }
-      __syncthreads();
+      __syncwarp();
       for (int l = 0; l < a.L; ++l) {
         const int nf1 = bsh[l].nfront + 1;
-        for (int i = threadIdx.x; i < nf1; i += blockDim.x) {
-          ((int*)tb[l].front)[i] = a.front[bsh[l].front_off + i];
-          ((int*)tb[l].fpad)[i] = a.fpad[bsh[l].front_off + i];
-        }
-        for (int i = threadIdx.x; i <= bsh[l].nchunk[ES]; i += blockDim.x)
-          ((int*)tb[l].chunk)[i] = a.chunk[bsh[l].chunk_off[ES] + i];
-        for (int i = threadIdx.x; i < bsh[l].rows; i += blockDim.x)
-          ((unsigned short*)tb[l].rowlex)[i] = (unsigned short)a.rowlex[bsh[l].row_off + i];
+        for (int i = lane; i < nf1; i += 32) ip[meta[l] + i] = a.fpad[bsh[l].front_off + i];
+        for (int i = lane; i <= bsh[l].nchunk[ES]; i += 32) ip[meta[LOR_MAXLEV + l] + i] = a.chunk[bsh[l].chunk_off[ES] + i];
       }
+      __syncwarp();
       cur_sh = sh;
     }
     if (bsh[0].rows == 0) continue;
-    if (threadIdx.x == 0) {
-      long long offset = 0;
+    // level boxes and their vectors: level 0 keeps t0 after the auxiliary
+    // buffers; levels >= 1 overlay t0's space (x, t with guards, r)
+    WLevel bx[LOR_MAXLEV];
+    int bottom = 0;
+    {
+      long long off = a.aux_n;
       for (int l = 0; l < a.L; ++l) {
         const BoxShape& bs = bsh[l];
-        Box& b = bx[l];
+        WLevel& b = bx[l];
         b.A = bs.dims[0]; b.B = bs.dims[1]; b.C = bs.dims[2];
         b.rows = bs.rows;
-        for (int t = 0; t < 3; ++t) {
-          b.type[t] = type[t];
-          b.org[t] = t < DIM ? (v[t] > 0 ? v[t] - 1 : 0) * a.lv[l].m + 1 : 0;
+        for (int t = 0; t < 3; ++t) b.org[t] = t < DIM ? (v[t] > 0 ? v[t] - 1 : 0) * a.lv[l].m + 1 : 0;
+        if (l == 0) {
+          b.xo = -1; b.to = a.aux_n + bs.guard; b.ro = -1;
+        } else {
+          b.xo = (int)off + bs.guard; off += b.rows + 2 * bs.guard + 1;
+          b.to = (int)off + bs.guard; off += b.rows + 2 * bs.guard + 1;
+          if (l == 1) { b.ro = 0; } else { b.ro = (int)off; off += b.rows; }
         }
-        xs[l] = sm + offset; offset += b.rows;
-        ts[l] = sm + offset + bs.guard; offset += b.rows + 2 * bs.guard;
-        rs[l] = sm + offset; offset += (l > 0 || a.plist ? b.rows : 0);
       }
-      s_offset = offset;
+      while (bottom + 1 < a.L && bx[bottom + 1].rows > 0) ++bottom;
     }
-    __syncthreads();
-    for (long long i = threadIdx.x; i < s_offset; i += blockDim.x) sm[i] = T(0);
-    __syncthreads();
-    // level-0 right-hand side: the global vector, or the listed patch's own data
     const T* rg0 = a.plist ? nullptr : (const T*)a.r;
-    if (a.plist) {
-      const T* src = (const T*)a.rloc + (long long)jo * a.vstride;
-      for (int lex = threadIdx.x; lex < bx[0].rows; lex += blockDim.x) rs[0][lex] = src[lex];
-      __syncthreads();
-    }
-    const FT* F = (const FT*)a.F;
-    int bottom = 0;
-    while (bottom + 1 < a.L && bx[bottom + 1].rows > 0) ++bottom;
+    const T* rloc = a.plist ? (const T*)a.rloc + jo * a.vstride : nullptr;
+    const WLevel& b0 = bx[0];
+    const PLevel& lv0 = a.lv[0];
+    T* t0 = vec + b0.to;
+    const int guard0 = bsh[0].guard;
+    const int AB0 = b0.A * b0.B;
     bool ok = true;
-    // ---- down
-    for (int l = 0; l < bottom && ok; ++l) {
-      const Box& b = bx[l];
-      const PLevel& lv = a.lv[l];
-      const FT* FL = F + a.facoff[(long long)l * a.J + j] * LOR_REC;
-      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-        const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-        const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-        ts[l][lex] = (l == 0 && rg0) ? rg0[G] : rs[l][lex];
+    if (a.L == 1) {
+      // the level-0 box is the vertex level: exact solve
+      const T* S = (const T*)lv0.S;
+      BoxIter it;
+      it.init(lane, b0.A, b0.B);
+      for (int lex = lane; lex < b0.rows; lex += 32, it.next()) {
+        const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
+        xslot[lex] = (rloc ? rloc[lex] : rg0[G]) / S[(long long)(a.NS / 2) * lv0.ntot + G];
+        t0[lex] = T(0);
       }
-      __syncthreads();
-      ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], tb[l], FL, ts[l], rg, &abort_flag);
-      if (!ok) break;
-      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) xs[l][lex] = ts[l][lex];
-      __syncthreads();
-      LOR_RESID(l, l == 0 ? rg0 : nullptr);
-      __syncthreads();
-      const Xfer1D<T>& X0 = xf[l * 2 + type[0]];
-      const Xfer1D<T>& X1 = xf[l * 2 + type[1]];
-      const Xfer1D<T>& X2 = xf[l * 2 + type[2]];
-      const int fA = b.A, fB = b.B;
-      const int cA = bx[l + 1].A, cB = bx[l + 1].B, crows = bx[l + 1].rows;
-      const T* tl = ts[l];
-      T* rn = rs[l + 1];
-      for (int lex = threadIdx.x; lex < crows; lex += blockDim.x) {
-        const int ci = lex % cA, cj = (lex / cA) % cB, ck = lex / (cA * cB);
-        T s = 0;
-        const int z0 = DIM == 3 ? X2.rstart[ck] : 0, z1 = DIM == 3 ? X2.rstart[ck + 1] : 1;
-        for (int tz = z0; tz < z1; ++tz) {
-          const int fz = DIM == 3 ? X2.rf[tz] : 0;
-          const T wz = DIM == 3 ? X2.rw[tz] : T(1);
-          for (int ty = X1.rstart[cj]; ty < X1.rstart[cj + 1]; ++ty) {
-            const T wy = X1.rw[ty] * wz;
-            const int rowb = (fz * fB + X1.rf[ty]) * fA;
-            for (int tx = X0.rstart[ci]; tx < X0.rstart[ci + 1]; ++tx) s += X0.rw[tx] * wy * tl[rowb + X0.rf[tx]];
-          }
+      __syncwarp();
+    } else {
+      // ---- level 0 down: t0 <- rhs (zero guards), ILU, residual in place (x0 -> slot)
+      for (int q = lane; q < b0.rows + 2 * guard0 + 1; q += 32) t0[q - guard0] = T(0);
+      __syncwarp();
+      {
+        BoxIter it;
+        it.init(lane, b0.A, b0.B);
+        for (int lex = lane; lex < b0.rows; lex += 32, it.next()) {
+          const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
+          t0[lex] = rloc ? rloc[lex] : rg0[G];
         }
-        rn[lex] = s;
       }
-      __syncthreads();
-    }
-    // ---- bottom level: exact solve on the vertex level (<= 1 unknown); a
-    // truncated box (boundary patch whose vertex level is empty) is smoothed by
-    // ILU(0) twice instead (pre and post, no coarser correction)
-    if (ok) {
-      const int l = bottom;
-      const Box& b = bx[l];
-      const PLevel& lv = a.lv[l];
-      if (l == a.L - 1) {
-        const T* S = (const T*)lv.S;
-        for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-          const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-          const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-          const T rhs = (l == 0 && rg0) ? rg0[G] : rs[l][lex];
-          xs[l][lex] = rhs / S[(long long)(a.NS / 2) * lv.ntot + G];
-        }
-        __syncthreads();
-      } else {
-        const FT* FL = F + a.facoff[(long long)l * a.J + j] * LOR_REC;
-        for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-          const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-          const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-          ts[l][lex] = (l == 0 && rg0) ? rg0[G] : rs[l][lex];
-        }
-        __syncthreads();
-        ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], tb[l], FL, ts[l], rg, &abort_flag);
-        if (ok) {
-          for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) xs[l][lex] = ts[l][lex];
-          __syncthreads();
-          LOR_RESID(l, l == 0 ? rg0 : nullptr);
-          __syncthreads();
-          ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], tb[l], FL, ts[l], rg, &abort_flag);
+      __syncwarp();
+      const FT* FL0 = F + a.facoff[j] * R;
+      ok = ilu_solve<DIM, T, FT, NBUF>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
+      T* prev = vec + (b0.A + 1);                 // guarded plane buffers
+      T* tmp = prev + AB0 + (b0.A + 1);
+      if (ok) resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, xslot);
+      if (ok && bottom > 0) {
+        // ---- coarse levels
+        restrict_level<DIM, T>(bx[0], bx[1], xf[type[0]], xf[type[1]], xf[type[2]], t0, vec + bx[1].ro);
+        for (int q = lane; q < a.ovl_n; q += 32) vec[a.aux_n + q] = T(0);
+        __syncwarp();
+        for (int l = 1; l < bottom && ok; ++l) {
+          const WLevel& b = bx[l];
+          T* x = vec + b.xo; T* t = vec + b.to; T* r = vec + b.ro;
+          const FT* FL = F + a.facoff[(long long)l * a.J + j] * R;
+          for (int q = lane; q < b.rows; q += 32) t[q] = r[q];
+          __syncwarp();
+          ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+          if (!ok) break;
+          for (int q = lane; q < b.rows; q += 32) x[q] = t[q];
+          __syncwarp();
+          resid_level<DIM, T>(b, a.lv[l], r, x, t);
+          restrict_level<DIM, T>(b, bx[l + 1], xf[l * 2 + type[0]], xf[l * 2 + type[1]], xf[l * 2 + type[2]], t,
+                                 vec + bx[l + 1].ro);
         }
         if (ok) {
-          for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) xs[l][lex] += ts[l][lex];
-          __syncthreads();
-        }
-      }
-    }
-    // ---- up
-    for (int l = bottom - 1; l >= 0 && ok; --l) {
-      const Box& b = bx[l];
-      const Box& bc = bx[l + 1];
-      const PLevel& lv = a.lv[l];
-      const FT* FL = F + a.facoff[(long long)l * a.J + j] * LOR_REC;
-      const Xfer1D<T>& X0 = xf[l * 2 + type[0]];
-      const Xfer1D<T>& X1 = xf[l * 2 + type[1]];
-      const Xfer1D<T>& X2 = xf[l * 2 + type[2]];
-      const int fA = b.A, fB = b.B, frows = b.rows;
-      const int cA = bc.A, cB = bc.B, cC = bc.C;
-      const T* xc = xs[l + 1];
-      T* xl = xs[l];
-      for (int lex = threadIdx.x; lex < frows; lex += blockDim.x) {
-        const int i = lex % fA, jj = (lex / fA) % fB, k = lex / (fA * fB);
-        T s = 0;
-        const int nzz = DIM == 3 ? 2 : 1;
-        for (int sz = 0; sz < nzz; ++sz) {
-          const int cz = DIM == 3 ? (sz ? X2.c1[k] : X2.c0[k]) : 0;
-          if (cz < 0 || cz >= cC) continue;
-          const T wz = DIM == 3 ? (sz ? X2.w1[k] : X2.w0[k]) : T(1);
-          for (int sy = 0; sy < 2; ++sy) {
-            const int cy = sy ? X1.c1[jj] : X1.c0[jj];
-            if (cy < 0 || cy >= cB) continue;
-            const T wy = (sy ? X1.w1[jj] : X1.w0[jj]) * wz;
-            for (int sx = 0; sx < 2; ++sx) {
-              const int cx = sx ? X0.c1[i] : X0.c0[i];
-              if (cx < 0 || cx >= cA) continue;
-              s += (sx ? X0.w1[i] : X0.w0[i]) * wy * xc[(cz * cB + cy) * cA + cx];
+          const int l = bottom;
+          const WLevel& b = bx[l];
+          const PLevel& lv = a.lv[l];
+          T* x = vec + b.xo; T* t = vec + b.to; T* r = vec + b.ro;
+          if (l == a.L - 1) {
+            const T* S = (const T*)lv.S;
+            BoxIter it;
+            it.init(lane, b.A, b.B);
+            for (int lex = lane; lex < b.rows; lex += 32, it.next()) {
+              const int G = ((b.org[2] + it.k) * lv.N[1] + (b.org[1] + it.j)) * lv.N[0] + (b.org[0] + it.i);
+              x[lex] = r[lex] / S[(long long)(a.NS / 2) * lv.ntot + G];
+            }
+            __syncwarp();
+          } else {
+            const FT* FL = F + a.facoff[(long long)l * a.J + j] * R;
+            for (int q = lane; q < b.rows; q += 32) t[q] = r[q];
+            __syncwarp();
+            ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+            if (ok) {
+              for (int q = lane; q < b.rows; q += 32) x[q] = t[q];
+              __syncwarp();
+              resid_level<DIM, T>(b, lv, r, x, t);
+              ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+            }
+            if (ok) {
+              for (int q = lane; q < b.rows; q += 32) x[q] += t[q];
+              __syncwarp();
             }
           }
         }
-        xl[lex] += s;
+        for (int l = bottom - 1; l >= 1 && ok; --l) {
+          const WLevel& b = bx[l];
+          T* x = vec + b.xo; T* t = vec + b.to; T* r = vec + b.ro;
+          const T* xc = vec + bx[l + 1].xo;
+          const FT* FL = F + a.facoff[(long long)l * a.J + j] * R;
+          BoxIter it;
+          it.init(lane, b.A, b.B);
+          for (int lex = lane; lex < b.rows; lex += 32, it.next())
+            x[lex] += prolong_row<DIM, T>(bx[l + 1], xf[l * 2 + type[0]], xf[l * 2 + type[1]], xf[l * 2 + type[2]],
+                                          xc, it.i, it.j, it.k);
+          __syncwarp();
+          resid_level<DIM, T>(b, a.lv[l], r, x, t);
+          ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+          if (!ok) break;
+          for (int q = lane; q < b.rows; q += 32) x[q] += t[q];
+          __syncwarp();
+        }
+        if (ok) {
+          // ---- level 0 up: x0 += P x1 in the slot, t0 <- x0, residual in place
+          const T* x1 = vec + bx[1].xo;
+          BoxIter it;
+          it.init(lane, b0.A, b0.B);
+          for (int lex = lane; lex < b0.rows; lex += 32, it.next())
+            xslot[lex] += prolong_row<DIM, T>(bx[1], xf[type[0]], xf[type[1]], xf[type[2]], x1, it.i, it.j, it.k);
+          __syncwarp();
+          for (int q = lane; q < b0.rows + 2 * guard0 + 1; q += 32) {
+            const int lex = q - guard0;
+            t0[lex] = (lex >= 0 && lex < b0.rows) ? xslot[lex] : T(0);
+          }
+          __syncwarp();
+          resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, nullptr);
+        }
       }
-      __syncthreads();
-      LOR_RESID(l, l == 0 ? rg0 : nullptr);
-      __syncthreads();
-      ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], tb[l], FL, ts[l], rg, &abort_flag);
-      if (!ok) break;
-      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) xs[l][lex] += ts[l][lex];
-      __syncthreads();
+      if (ok) ok = ilu_solve<DIM, T, FT, NBUF>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
     }
     if (!ok) {
       // a bulk copy did not arrive in time: report, drain what is still in flight, leave
-      if (threadIdx.x == 0) {
+      if (lane == 0) {
         atomicOr(a.status, 4);
         for (int s = 0; s < NBUF; ++s)
           if (rg.inflight & (1u << s)) mbar_wait(rg.bar + s, (rg.phase >> s) & 1u);
       }
       return;
     }
-    const Box& b = bx[0];
-    const PLevel& lv = a.lv[0];
-    if (a.plist) {     // patch-local output
-      T* dst = (T*)a.xloc + (long long)jo * a.vstride;
-      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) dst[lex] = xs[0][lex];
+    // ---- x_j = x0 + t0: patch-local output, or scatter-add R_j^T x_j
+    if (a.plist) {
+      T* dst = (T*)a.xloc + jo * a.vstride;
+      for (int lex = lane; lex < b0.rows; lex += 32) dst[lex] = xslot[lex] + t0[lex];
       continue;
     }
-    // ---- scatter-add R_j^T x_j
     T* z = (T*)a.z;
-    for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) {
-      const int i = lex % b.A, jj = (lex / b.A) % b.B, k = lex / (b.A * b.B);
-      const long long G = ((long long)(b.org[2] + k) * lv.N[1] + (b.org[1] + jj)) * lv.N[0] + (b.org[0] + i);
-      atomicAdd(z + G, xs[0][lex]);
+    {
+      BoxIter it;
+      it.init(lane, b0.A, b0.B);
+      for (int lex = lane; lex < b0.rows; lex += 32, it.next()) {
+        const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
+        const T xj = xslot[lex] + t0[lex];
+        atomicAdd(z + G, xj);
+        if (a.tout && sh == 0) t0[lex] = xj;
+      }
     }
+    __syncwarp();
     if (a.tout && sh == 0) {   // residual left on an interior patch, for the learned correction
-      LOR_RESID(0, rg0);
-      __syncthreads();
-      T* dst = (T*)a.tout + (long long)jo * a.vstride;
-      for (int lex = threadIdx.x; lex < b.rows; lex += blockDim.x) dst[lex] = ts[0][lex];
+      T* prev = vec + (b0.A + 1);
+      T* tmp = prev + AB0 + (b0.A + 1);
+      resid0_inplace<DIM, T>(b0, lv0, rg0, nullptr, t0, prev, tmp, nullptr);
+      T* dst = (T*)a.tout + jo * a.vstride;
+      for (int lex = lane; lex < b0.rows; lex += 32) dst[lex] = t0[lex];
+      __syncwarp();
     }
   }
 }
@@ -790,23 +1027,47 @@ T* coarse_vcycle(lor_ctx* c, int l) {
   return cur;
 }
 
-const int kPatchThreads = 256;
+const int kMaxPatchWarps = 8;
 
 template <typename FT>
-constexpr int ring_depth() { return sizeof(FT) == 2 ? 3 : 2; }
+constexpr int ring_depth() { return sizeof(FT) == 2 ? 4 : 3; }
+
+// Per-warp shared-memory layout of the patch kernel (sizes for the largest,
+// interior, box shape; other shapes fit inside).
+struct WarpLayout {
+  int slot_bytes, tab_ints, aux_n, ovl_n, warp_bytes, xf_bytes;
+  long long x0_stride;
+};
 
 template <typename T, typename FT>
-size_t patch_smem_bytes(const lor_ctx* c, int* tab_ints = nullptr, bool local = false) {
-  size_t vec = 0, tab = 0;
-  for (int l = 0; l < c->L; ++l) {
-    const BoxShape& bs = c->shapes[l * 8 + 0];   // interior shape is the largest
-    vec += (size_t)bs.rows * (l > 0 || local ? 3 : 2) + 2 * (size_t)bs.guard;   // x, t (+guards), r
-    tab += 2 * (size_t)(bs.nfront + 1) + (size_t)(bs.nchunk[elem_class<FT>()] + 1) + ((size_t)bs.rows + 1) / 2;
+WarpLayout warp_layout(const lor_ctx* c) {
+  WarpLayout w;
+  const int es = elem_class<FT>();
+  w.slot_bytes = c->maxchunk[es] * lor_rec(c->dim) * (int)sizeof(FT);
+  int tab = 0;
+  for (int s = 0; s < 8; ++s) {
+    int t = 0;
+    for (int l = 0; l < c->L; ++l) t += c->shapes[l * 8 + s].nfront + 1 + c->shapes[l * 8 + s].nchunk[es] + 1;
+    tab = std::max(tab, t);
   }
-  tab = (tab + 3) / 4 * 4;   // ints, keeps the vectors 16-byte aligned
-  if (tab_ints) *tab_ints = (int)tab;
-  const size_t slot = (size_t)c->maxchunk[elem_class<FT>()] * LOR_REC * sizeof(FT);
-  return 128 + ring_depth<FT>() * slot + 2 * (c->L > 1 ? c->L - 1 : 1) * sizeof(Xfer1D<T>) + 4 * tab + vec * sizeof(T);
+  w.tab_ints = (tab + 3) / 4 * 4;
+  const BoxShape& b0 = c->shapes[0];
+  const int A = b0.dims[0], B = b0.dims[1];
+  w.aux_n = 2 * A * B + 2 * (A + 1);
+  if (c->L > 1) w.aux_n = std::max(w.aux_n, c->shapes[8].rows);
+  w.aux_n = (w.aux_n + 3) / 4 * 4;
+  long long ovl = 0;
+  for (int l = 1; l < c->L; ++l) {
+    const BoxShape& bs = c->shapes[l * 8];
+    ovl += 2LL * (bs.rows + 2 * bs.guard + 1) + (l >= 2 ? bs.rows : 0);
+  }
+  w.ovl_n = (int)std::max<long long>(b0.rows + 2LL * b0.guard + 1, ovl);
+  const size_t bytes = (size_t)kWarpRing + (size_t)ring_depth<FT>() * w.slot_bytes + 4 * (size_t)w.tab_ints +
+                       (size_t)(w.aux_n + w.ovl_n) * sizeof(T);
+  w.warp_bytes = (int)((bytes + 127) / 128 * 128);
+  w.xf_bytes = (int)((2 * (c->L > 1 ? c->L - 1 : 1) * sizeof(Xfer1D<T>) + 127) / 128 * 128);
+  w.x0_stride = (b0.rows + 31) / 32 * 32;
+  return w;
 }
 
 template <typename T, typename FT>
@@ -816,6 +1077,7 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
   for (int l = 0; l < c->L; ++l) {
     PLevel& lv = a.lv[l];
     lv.S = Sel<T>::S(c, l);
+    lv.Sa = sizeof(T) == 8 ? (const void*)c->d_SA64[l] : (const void*)c->d_SA32[l];
     lv.ntot = c->lev[l].ntot;
     for (int t = 0; t < 3; ++t) lv.N[t] = c->lev[l].N[t];
     lv.m = c->lev[l].m;
@@ -827,40 +1089,66 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
     }
   }
   a.shapes = lor_dev_shapes(c);
-  a.front = c->d_front; a.fpad = c->d_fpad; a.chunk = c->d_chunk; a.rowlex = c->d_rowlex; a.recof = c->d_recof;
-  a.nbmask = c->d_nbmask;
+  a.fpad = c->d_fpad; a.chunk = c->d_chunk;
   a.facoff = c->d_facoff;
   a.F = F; a.r = nullptr; a.z = nullptr;
   a.status = c->d_status;
   a.porder = c->d_porder;
   a.conv = c->conv_flag;
   a.plist = nullptr; a.nlist = 0; a.rloc = nullptr; a.xloc = nullptr; a.vstride = 0; a.tout = nullptr;
-  a.slot_bytes = c->maxchunk[elem_class<FT>()] * LOR_REC * (int)sizeof(FT);
+  const WarpLayout w = warp_layout<T, FT>(c);
+  a.slot_bytes = w.slot_bytes;
+  a.tab_ints = w.tab_ints;
+  a.xf_bytes = w.xf_bytes;
+  a.warp_bytes = w.warp_bytes;
+  a.aux_n = w.aux_n;
+  a.ovl_n = w.ovl_n;
+  a.xs = c->d_xs;
+  a.x0_stride = w.x0_stride;
+}
+
+// Launch shape of the patch kernel: warps per CTA (shared memory) and resident
+// CTAs per SM; returns false if not even one warp fits.
+template <typename T, typename FT>
+bool patch_launch_shape(const lor_ctx* c, int* nw, int* grid, size_t* smem) {
+  const WarpLayout w = warp_layout<T, FT>(c);
+  int dev = 0, nsm = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int fit = (maxsm - w.xf_bytes) / w.warp_bytes;
+  if (fit < 1) return false;
+  *nw = std::min(kMaxPatchWarps, fit);
+  *smem = (size_t)w.xf_bytes + (size_t)*nw * w.warp_bytes;
+  constexpr int NB = ring_depth<FT>();
+  int per_sm = 0;
+  if (c->dim == 3) {
+    auto kern = k_patch_warp<3, T, FT, NB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * *nw, *smem);
+  } else {
+    auto kern = k_patch_warp<2, T, FT, NB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * *nw, *smem);
+  }
+  *grid = std::max(per_sm, 1) * nsm;
+  return true;
 }
 
 template <typename T, typename FT>
-lor_status launch_patch_kernel(lor_ctx* c, PatchArgs& a, bool local) {
-  const size_t smem = patch_smem_bytes<T, FT>(c, &a.tab_ints, local);
-  constexpr int NB = ring_depth<FT>();
-  // persistent CTAs: as many as fit on the device, each walking patches j, j+grid, ...
-  int dev = 0, nsm = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+lor_status launch_patch_kernel(lor_ctx* c, PatchArgs& a) {
   const long long work = a.plist ? a.nlist : c->J;
   if (work <= 0) return LOR_OK;
-  if (c->dim == 3) {
-    auto kern = k_patch_vcycle<3, T, FT, NB>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPatchThreads, smem);
-    const int grid = (int)std::min<long long>(work, (long long)std::max(per_sm, 1) * nsm);
-    kern<<<grid, kPatchThreads, smem, c->stream>>>(a);
-  } else {
-    auto kern = k_patch_vcycle<2, T, FT, NB>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPatchThreads, smem);
-    const int grid = (int)std::min<long long>(work, (long long)std::max(per_sm, 1) * nsm);
-    kern<<<grid, kPatchThreads, smem, c->stream>>>(a);
-  }
+  int nw = 0, grid = 0;
+  size_t smem = 0;
+  if (!patch_launch_shape<T, FT>(c, &nw, &grid, &smem)) return lor_fail(c, LOR_EINVAL, "patch does not fit");
+  // persistent warps: as many as fit, each walking patches w, w + (all warps), ...
+  grid = (int)std::min<long long>(grid, (work + nw - 1) / nw);
+  if ((long long)grid * nw * a.x0_stride * (long long)sizeof(T) > c->xs_bytes)
+    return lor_fail(c, LOR_ESTATE, "patch iterate slots too small");
+  constexpr int NB = ring_depth<FT>();
+  if (c->dim == 3) k_patch_warp<3, T, FT, NB><<<grid, 32 * nw, smem, c->stream>>>(a);
+  else k_patch_warp<2, T, FT, NB><<<grid, 32 * nw, smem, c->stream>>>(a);
   ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "patch vcycle");
 }
@@ -879,7 +1167,7 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
   }
   const int pk = sizeof(T) == 8 ? 0 : 1;
   lor_prof_begin(c, pk);
-  if (launch_patch_kernel<T, FT>(c, a, false)) return LOR_ECUDA;
+  if (launch_patch_kernel<T, FT>(c, a)) return LOR_ECUDA;
   lor_prof_end(c, pk);
   if (c->learned_on && sizeof(T) == 4) {
     if (lor_learned_apply(c, (float*)z)) return LOR_ECUDA;
@@ -916,15 +1204,31 @@ lor_status lor_patch_local32(lor_ctx* c, const int* plist, int nlist, const floa
   if (c->d_F16) {
     fill_patch_args<float, __nv_bfloat16>(c, a, c->d_F16);
     a.plist = plist; a.nlist = nlist; a.rloc = rloc; a.xloc = xloc; a.vstride = vstride;
-    return launch_patch_kernel<float, __nv_bfloat16>(c, a, true);
+    return launch_patch_kernel<float, __nv_bfloat16>(c, a);
   }
   fill_patch_args<float, float>(c, a, c->d_F32);
   a.plist = plist; a.nlist = nlist; a.rloc = rloc; a.xloc = xloc; a.vstride = vstride;
-  return launch_patch_kernel<float, float>(c, a, true);
+  return launch_patch_kernel<float, float>(c, a);
 }
 
-size_t lor_patch_smem(const lor_ctx* c, int which) {
-  if (which == 0) return patch_smem_bytes<double, double>(c);
-  if (which == 1) return patch_smem_bytes<float, float>(c);
-  return patch_smem_bytes<float, __nv_bfloat16>(c);
+// Checks that the patch kernel fits (every precision this context can run) and
+// allocates the per-warp level-0 iterate slots for the largest launch.
+lor_status lor_patch_prepare(lor_ctx* c) {
+  long long need = 0;
+  int nw = 0, grid = 0;
+  size_t smem = 0;
+  if (!patch_launch_shape<double, double>(c, &nw, &grid, &smem))
+    return lor_fail(c, LOR_EINVAL, "patch does not fit in shared memory");
+  need = std::max(need, (long long)grid * nw * warp_layout<double, double>(c).x0_stride * 8);
+  c->smem_patch64 = (int)smem;
+  const bool bf = c->d_F16 != nullptr;
+  const bool ok32 = bf ? patch_launch_shape<float, __nv_bfloat16>(c, &nw, &grid, &smem)
+                       : patch_launch_shape<float, float>(c, &nw, &grid, &smem);
+  if (!ok32) return lor_fail(c, LOR_EINVAL, "patch does not fit in shared memory");
+  need = std::max(need, (long long)grid * nw * warp_layout<float, float>(c).x0_stride * 4);
+  c->smem_patch32 = (int)smem;
+  c->xs_bytes = need;
+  c->d_xs = lor_alloc(c, (size_t)std::max<long long>(need, 8));
+  if (!c->d_xs) return lor_fail(c, LOR_ENOMEM, "alloc patch iterate slots");
+  return LOR_OK;
 }

@@ -160,13 +160,7 @@ lor_status lor_setup(lor_ctx* c) {
     c->nv = (long long)c->nel * (c->p + 1) * (c->p + 1) * (c->p + 1);
   }
   if ((s = lor_setup_krylov(c))) return s;
-  c->smem_patch64 = (int)lor_patch_smem(c, 0);
-  c->smem_patch32 = (int)lor_patch_smem(c, c->d_F16 ? 2 : 1);
-  int dev = 0, maxsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (c->smem_patch64 > maxsm || c->smem_patch32 > maxsm)
-    return lor_fail(c, LOR_EINVAL, "patch does not fit in shared memory");
+  if ((s = lor_patch_prepare(c))) return s;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return lor_cuda_check(c, e, "setup");
   c->setup_done = true;

@@ -47,13 +47,20 @@ struct LevelGrid {
 };
 
 // Shape of a patch box at one level: wavefront schedule for lexicographic ILU(0).
-// Factor storage of one patch level: front-major records of LOR_REC values.
-// L record of a row: its 13 (3D) / 4 (2D) strictly-lower ILU(0) multipliers in
-// stencil-offset order, padded; U record: its upper coefficients in
-// stencil-offset order, then 1/u_ii in the last slot.  The records of each
-// wavefront are padded to a multiple of 4 rows so every front block starts on a
-// 16-byte boundary in every precision (bulk-copy alignment).
-#define LOR_REC 14
+// Factor storage of one patch level: front-major records of lor_rec(dim) values
+// (16 in 3D, 8 in 2D).  L record of a row: its 13 (3D) / 4 (2D) strictly-lower
+// ILU(0) multipliers in stencil-offset order; U record: its upper coefficients
+// in stencil-offset order and 1/u_ii in slot rec-2.  Slot rec-1 of both holds
+// the row's lexicographic index in the patch box as raw integer bits (low 16
+// bits of a bf16 slot, the 32-bit pattern of a float slot, the low word of a
+// double slot), so a sweep reads a row's position together with its factors.
+// The records of each wavefront are padded to a multiple of 4 rows so every
+// front block starts on a 16-byte boundary (bulk-copy alignment); a padding
+// record is all zero except its index, which points at the first guard cell
+// after the box (index = rows), so a sweep may process it like a real row.
+__host__ __device__ constexpr int lor_rec(int dim) { return dim == 3 ? 16 : 8; }
+// row length of the row-major stencil copies: 3^dim padded to a multiple of 4
+__host__ __device__ constexpr int lor_nsp(int dim) { return dim == 3 ? 28 : 12; }
 struct BoxShape {
   int dims[3];            // box extents (x, y, z); 1 for unused dims
   int rows;
@@ -99,6 +106,10 @@ struct lor_ctx {
   LevelGrid lev[LOR_MAXLEV];
   double* d_S64[LOR_MAXLEV] = {};   // [NS][ntot_l] stencils
   float* d_S32[LOR_MAXLEV] = {};
+  // row-major copies [ntot_l][lor_nsp(dim)] of the patch-level stencils (levels
+  // 0..L-2), read by the patch residuals as whole rows
+  double* d_SA64[LOR_MAXLEV] = {};
+  float* d_SA32[LOR_MAXLEV] = {};
   Prolong1D* d_P1[LOR_MAXLEV][3] = {};    // global 1D prolongation level l+1 -> l (per axis)
   int* d_R1ptr[LOR_MAXLEV][3] = {};       // restriction CSR: coarse -> fine list
   int* d_R1idx[LOR_MAXLEV][3] = {};
@@ -115,7 +126,6 @@ struct lor_ctx {
   int* d_chunk = nullptr;     // first front of each bulk-copy chunk
   int* d_rowlex = nullptr;    // lexicographic index of the row at a wavefront position
   int* d_recof = nullptr;     // record index of the row at a wavefront position
-  unsigned* d_nbmask = nullptr;   // per lexicographic row: bit o set if neighbour o is in the box
   // per-level per-axis-type patch-local 1D prolongation (fine -> coarse, local idx)
   Prolong1D* d_pp[LOR_MAXLEV][2] = {};
   // per-level per-axis-type patch-local restriction: coarse local c -> 3 (fine local f, w), f = -1 unused
@@ -127,6 +137,10 @@ struct lor_ctx {
   float* d_F32 = nullptr;
   __nv_bfloat16* d_F16 = nullptr;
   int smem_patch64 = 0, smem_patch32 = 0;
+  // per-warp level-0 iterate of the patch kernel (one slot of x0_stride values per
+  // resident warp; small enough to stay in L2)
+  void* d_xs = nullptr;
+  long long xs_bytes = 0;
   int maxfront = 0;           // largest padded front over all levels/shapes (records)
   int maxchunk[3] = {0, 0, 0};   // largest chunk (records) for 2-, 4-, 8-byte factors
   int* d_status = nullptr;    // device error word
@@ -215,7 +229,7 @@ lor_status lor_opP32(lor_ctx* c, const float* r, float* z);
 // apply_p.cu
 lor_status lor_launch_apply_P64(lor_ctx* c, const double* r, double* z);
 lor_status lor_launch_apply_P32(lor_ctx* c, const float* r, float* z);
-size_t lor_patch_smem(const lor_ctx* c, int which);   // 0 fp64, 1 fp32, 2 fp32+bf16 factors
+lor_status lor_patch_prepare(lor_ctx* c);   // launch shapes, shared-memory fit, iterate slots
 // krylov.cu
 lor_status lor_pcg64(lor_ctx* c, const double* b, double* x, int* iters, double* relres);
 lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, double* relres);

@@ -235,9 +235,32 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
   if (i < n) b[i] = (float)a[i];
 }
 
-__global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, long long n) {
+// Row-major copy of a stencil: Sa[g * nsp + o] = S[o * ntot + g], zero padded.
+template <typename T>
+__global__ void k_stencil_rows(const T* __restrict__ S, T* __restrict__ Sa, long long ntot, int NS, int nsp) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ntot) return;
+  for (int o = 0; o < nsp; ++o) Sa[g * nsp + o] = o < NS ? S[(long long)o * ntot + g] : T(0);
+}
+
+// Factor records to FP32 / bf16: values rounded, the index slot (rec-1) copied
+// as raw integer bits.
+__global__ void k_fac_to32(const double* __restrict__ a, float* __restrict__ b, long long n, int rec) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = __double2bfloat16(a[i]);
+  if (i >= n) return;
+  b[i] = (i % rec == rec - 1) ? __int_as_float((int)__double_as_longlong(a[i])) : (float)a[i];
+}
+
+__global__ void k_fac_to16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, long long n, int rec) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (i % rec == rec - 1) {
+    __nv_bfloat16_raw raw;
+    raw.x = (unsigned short)__double_as_longlong(a[i]);
+    b[i] = __nv_bfloat16(raw);
+  } else {
+    b[i] = __double2bfloat16(a[i]);
+  }
 }
 
 // ILU(0) of every patch at one level.  One CTA per patch; rows in wavefront order.
@@ -275,8 +298,15 @@ __global__ void k_ilu0(IluArgs a) {
   int org[3];
   for (int t = 0; t < 3; ++t) org[t] = (t < a.dim) ? (v[t] > 0 ? v[t] - 1 : 0) * a.m + 1 : 0;
   const long long ntot = (long long)a.N[0] * a.N[1] * a.N[2];
-  double* FL = a.F + a.facoff[j] * LOR_REC;           // L records
-  double* FU = FL + (long long)bs.rpad * LOR_REC;      // U records
+  const int R = lor_rec(a.dim);
+  double* FL = a.F + a.facoff[j] * R;           // L records
+  double* FU = FL + (long long)bs.rpad * R;      // U records
+  // index slot of every record: padding records point at the guard cell after the box
+  for (int q = threadIdx.x; q < bs.rpad; q += blockDim.x) {
+    FL[(long long)q * R + R - 1] = __longlong_as_double((long long)bs.rows);
+    FU[(long long)q * R + R - 1] = __longlong_as_double((long long)bs.rows);
+  }
+  __syncthreads();
   const int* rowlex = a.rowlex + bs.row_off;
   const int* recof = a.recof + bs.row_off;
   const int* poslex = a.poslex + bs.row_off;
@@ -298,8 +328,8 @@ __global__ void k_ilu0(IluArgs a) {
         const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = a.dim == 3 ? o / 9 - 1 : 0;
         const int ni = i + ox, nj = jj + oy, nk = k + oz;
         if (!(ni >= 0 && ni < dx0 && nj >= 0 && nj < dy0 && nk >= 0 && nk < dz0)) continue;
-        const double* Uk = FU + (long long)recof[poslex[(nk * dy0 + nj) * dx0 + ni]] * LOR_REC;
-        const double l = r[o] * Uk[LOR_REC - 1];   // a_ik / u_kk
+        const double* Uk = FU + (long long)recof[poslex[(nk * dy0 + nj) * dx0 + ni]] * R;
+        const double l = r[o] * Uk[R - 2];   // a_ik / u_kk
         r[o] = l;
         for (int o2 = C + 1; o2 < NS; ++o2) {   // upper part of row k
           const int px = ox + (o2 % 3 - 1), py = oy + ((o2 / 3) % 3 - 1), pz = oz + (a.dim == 3 ? o2 / 9 - 1 : 0);
@@ -309,13 +339,15 @@ __global__ void k_ilu0(IluArgs a) {
         }
       }
       if (!(r[C] > 0.0)) atomicOr(a.status, 2);
-      double* Li = FL + (long long)recof[pos] * LOR_REC;
-      double* Ui = FU + (long long)recof[pos] * LOR_REC;
-      for (int o = 0; o < LOR_REC; ++o) {
+      double* Li = FL + (long long)recof[pos] * R;
+      double* Ui = FU + (long long)recof[pos] * R;
+      for (int o = 0; o < R - 1; ++o) {
         Li[o] = o < C ? r[o] : 0.0;
         Ui[o] = o < C ? r[C + 1 + o] : 0.0;
       }
-      Ui[LOR_REC - 1] = 1.0 / r[C];
+      Ui[R - 2] = 1.0 / r[C];
+      Li[R - 1] = __longlong_as_double((long long)lex);
+      Ui[R - 1] = __longlong_as_double((long long)lex);
     }
     __syncthreads();
   }
@@ -540,12 +572,25 @@ lor_status lor_setup_stencils(lor_ctx* c) {
     k_to_float<<<(unsigned)lor_ceil_div(n, 256), 256, 0, c->stream>>>(c->d_S64[l], c->d_S32[l], n);
     ++c->launches;
   }
+  // row-major copies for the patch residuals
+  if (c->lev[0].ntot >= (1LL << 31)) return lor_fail(c, LOR_EINVAL, "level-0 grid too large");
+  for (int l = 0; l < c->L; ++l) {
+    const long long nt = c->lev[l].ntot;
+    c->d_SA64[l] = (double*)lor_alloc(c, nt * lor_nsp(dim) * 8);
+    c->d_SA32[l] = (float*)lor_alloc(c, nt * lor_nsp(dim) * 4);
+    if (!c->d_SA64[l] || !c->d_SA32[l]) return lor_fail(c, LOR_ENOMEM, "alloc row stencils");
+    k_stencil_rows<double><<<(unsigned)lor_ceil_div(nt, 256), 256, 0, c->stream>>>(c->d_S64[l], c->d_SA64[l], nt,
+                                                                                    c->NS, lor_nsp(dim));
+    k_stencil_rows<float><<<(unsigned)lor_ceil_div(nt, 256), 256, 0, c->stream>>>(c->d_S32[l], c->d_SA32[l], nt,
+                                                                                   c->NS, lor_nsp(dim));
+    c->launches += 2;
+  }
   return lor_cuda_check(c, cudaGetLastError(), "stencil conversion");
 }
 
 // ------------------------------------------------------------ patch structures
 static int axis_len(int type, int m) { return type == 0 ? 2 * m - 1 : m - 1; }
-static const int kChunkBytes = 5632;   // bulk-copy chunk of bf16 factor records
+static const int kChunkBytes = 2048;   // bulk-copy chunk of factor records (a wider front is a chunk of its own)
 
 lor_status lor_setup_patches(lor_ctx* c) {
   const int dim = c->dim;
@@ -553,7 +598,6 @@ lor_status lor_setup_patches(lor_ctx* c) {
   for (int a = 0; a < dim; ++a) c->J *= (c->n[a] + 1);
   const int nshape = 1 << dim;
   std::vector<int> front, fpad, rowlex, recof, poslex, chunk;
-  std::vector<unsigned> nbmask;
   c->shapes.assign(c->L * 8, BoxShape());
   c->maxfront = 0;
   for (int l = 0; l < c->L; ++l) {
@@ -590,11 +634,12 @@ lor_status lor_setup_patches(lor_ctx* c) {
       }
       bs.rpad = rec;
       bs.maxfront = mf;
+      if (mf > 64) return lor_fail(c, LOR_EINVAL, "wavefront wider than 64 rows");
       c->maxfront = std::max(c->maxfront, mf);
       // chunks of whole fronts of at most kChunkBytes per factor element size; a
       // front larger than that is a chunk of its own
       for (int es = 0; es < 3; ++es) {
-        const int cap = kChunkBytes / (LOR_REC * (2 << es));
+        const int cap = kChunkBytes / (lor_rec(dim) * (2 << es));
         bs.chunk_off[es] = (int)chunk.size();
         bs.nchunk[es] = 0;
         bs.maxchunk[es] = 0;
@@ -612,15 +657,6 @@ lor_status lor_setup_patches(lor_ctx* c) {
       }
       bs.guard = A * Bd + A + 1;
       for (int t = 0; t < bs.rows; ++t) poslex.push_back(pl[t]);
-      for (int t = 0; t < bs.rows; ++t) {
-        const int i = t % A, j = (t / A) % Bd, k = t / (A * Bd);
-        unsigned msk = 0;
-        for (int o = 0; o < c->NS; ++o) {
-          const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = dim == 3 ? o / 9 - 1 : 0;
-          if (i + dx >= 0 && i + dx < A && j + dy >= 0 && j + dy < Bd && k + dz >= 0 && k + dz < Cd) msk |= 1u << o;
-        }
-        nbmask.push_back(msk);
-      }
       c->shapes[l * 8 + s] = bs;
     }
   }
@@ -631,7 +667,6 @@ lor_status lor_setup_patches(lor_ctx* c) {
     for (int es = 0; es < 3; ++es) c->maxchunk[es] = std::max(c->maxchunk[es], bs.maxchunk[es]);
   if (upload(c, (void**)&c->d_rowlex, rowlex.data(), std::max<size_t>(1, rowlex.size()) * 4)) return LOR_ENOMEM;
   if (upload(c, (void**)&c->d_recof, recof.data(), std::max<size_t>(1, recof.size()) * 4)) return LOR_ENOMEM;
-  if (upload(c, (void**)&c->d_nbmask, nbmask.data(), std::max<size_t>(1, nbmask.size()) * 4)) return LOR_ENOMEM;
   if (upload(c, (void**)&c->d_poslex, poslex.data(), std::max<size_t>(1, poslex.size()) * 4)) return LOR_ENOMEM;
   if (upload(c, (void**)&c->d_shapes, c->shapes.data(), c->shapes.size() * sizeof(BoxShape))) return LOR_ENOMEM;
   int* d_poslex = c->d_poslex;
@@ -698,7 +733,7 @@ lor_status lor_setup_patches(lor_ctx* c) {
         c->fac_rows += c->shapes[l * 8 + sh].rows;
       }
     }
-  tot *= LOR_REC;   // values
+  tot *= lor_rec(dim);   // values
   if (upload(c, (void**)&c->d_facoff, off.data(), off.size() * 8)) return LOR_ENOMEM;
   c->d_F64 = (double*)lor_alloc(c, std::max<long long>(tot, 1) * 8);
   c->d_F32 = (float*)lor_alloc(c, std::max<long long>(tot, 1) * 4);
@@ -720,9 +755,9 @@ lor_status lor_setup_patches(lor_ctx* c) {
     ++c->launches;
     if (lor_cuda_check(c, cudaGetLastError(), "ilu0")) return LOR_ECUDA;
   }
-  k_to_float<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F32, tot);
+  k_fac_to32<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F32, tot, lor_rec(dim));
   ++c->launches;
-  if (c->d_F16) k_to_bf16<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F16, tot);
+  if (c->d_F16) k_fac_to16<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F16, tot, lor_rec(dim));
   ++c->launches;
   if (lor_cuda_check(c, cudaGetLastError(), "factor conversion")) return LOR_ECUDA;
   return check_status(c, "ilu0");
