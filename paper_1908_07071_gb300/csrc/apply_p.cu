@@ -508,7 +508,7 @@ constexpr int kWarpBars = 0, kWarpZrec = 32, kWarpMeta = 160, kWarpShape = 288, 
 // (<= 1 unknown), a truncated box (boundary patch whose vertex level is empty)
 // is smoothed by ILU twice instead; up: x += P x_{l+1}, t <- r - A x, ILU, x += t.
 template <int DIM, typename T, typename FT, int NBUF>
-__global__ void __launch_bounds__(256, 1) k_patch_warp(PatchArgs a) {
+__global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
   constexpr int ES = elem_class<FT>();
   constexpr int R = lor_rec(DIM);
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1027,10 +1027,10 @@ T* coarse_vcycle(lor_ctx* c, int l) {
   return cur;
 }
 
-const int kMaxPatchWarps = 8;
+const int kMaxPatchWarps = 12;   // warps per CTA (one CTA per SM when shared memory allows)
 
 template <typename FT>
-constexpr int ring_depth() { return sizeof(FT) == 2 ? 4 : 3; }
+constexpr int ring_depth() { return 3; }
 
 // Per-warp shared-memory layout of the patch kernel (sizes for the largest,
 // interior, box shape; other shapes fit inside).

@@ -707,16 +707,37 @@ lor_status lor_setup_patches(lor_ctx* c) {
     }
   }
 
-  // visiting order of the patch kernel: patches grouped by box shape
+  // visiting order of the patch kernel: patches grouped by box shape, interior
+  // patches first and in blocks of kOrderBlock^dim vertices (blocks and the
+  // vertices inside them in lexicographic order), so that the patches in flight
+  // at one time cover a compact set of elements and share stencil rows in L2
   {
+    const int kOrderBlock = 8;
     std::vector<int> order;
-    for (int want = 0; want < 8; ++want)
-      for (int j = 0; j < c->J; ++j) {
-        int v[3] = {j % (c->n[0] + 1), (j / (c->n[0] + 1)) % (c->n[1] + 1), dim == 3 ? j / ((c->n[0] + 1) * (c->n[1] + 1)) : 0};
-        int sh = 0;
-        for (int a = 0; a < dim; ++a) sh |= ((v[a] == 0 || v[a] == c->n[a]) ? 1 : 0) << a;
-        if (sh == want) order.push_back(j);
-      }
+    const int n0 = c->n[0] + 1, n1 = c->n[1] + 1;
+    auto shape_of = [&](int j) {
+      int v[3] = {j % n0, (j / n0) % n1, dim == 3 ? j / (n0 * n1) : 0};
+      int sh = 0;
+      for (int a = 0; a < dim; ++a) sh |= ((v[a] == 0 || v[a] == c->n[a]) ? 1 : 0) << a;
+      return sh;
+    };
+    const int nb[3] = {(c->n[0] + kOrderBlock - 1) / kOrderBlock, (c->n[1] + kOrderBlock - 1) / kOrderBlock,
+                       dim == 3 ? (c->n[2] + kOrderBlock - 1) / kOrderBlock : 1};
+    for (int bz = 0; bz < nb[2]; ++bz)
+      for (int by = 0; by < nb[1]; ++by)
+        for (int bxi = 0; bxi < nb[0]; ++bxi)
+          for (int z = 0; z < (dim == 3 ? kOrderBlock : 1); ++z)
+            for (int y = 0; y < kOrderBlock; ++y)
+              for (int x = 0; x < kOrderBlock; ++x) {
+                const int v0 = 1 + bxi * kOrderBlock + x, v1 = 1 + by * kOrderBlock + y;
+                const int v2 = dim == 3 ? 1 + bz * kOrderBlock + z : 0;
+                if (v0 >= c->n[0] || v1 >= c->n[1] || (dim == 3 && v2 >= c->n[2])) continue;
+                order.push_back((v2 * n1 + v1) * n0 + v0);
+              }
+    for (int want = 1; want < 8; ++want)
+      for (int j = 0; j < c->J; ++j)
+        if (shape_of(j) == want) order.push_back(j);
+    if ((long long)order.size() != c->J) return lor_fail(c, LOR_EINVAL, "patch order incomplete");
     if (upload(c, (void**)&c->d_porder, order.data(), order.size() * 4)) return LOR_ENOMEM;
   }
   // factor storage offsets (records; a patch level holds 2*rpad records)
