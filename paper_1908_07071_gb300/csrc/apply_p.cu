@@ -776,46 +776,32 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
 
 // ------------------------------------------------------------------ coarse space
 // rc[V] = sum_F P0[F][V] r[F] for interior vertices V (P0: Q1 interpolation at GLL nodes)
+// One separable pass of P_0^T = (R_z x R_y x R_x) r: contracts axis `ax` of a
+// d0 x d1 x d2 array (x fastest) to the vertex grid along that axis (Vn vertices):
+//   out[.., v, ..] = sum_{a < 2p-1} w[a] in[.., (v-1)p+1+a, ..]  for interior v, 0 on the boundary,
+// where w are the 1D values of the vertex hat function at the GLL-refined nodes of
+// the two elements around the vertex.
 template <typename T>
-__global__ void k_coarse_restrict0(int dim, int p, int nx, int ny, int nz, const double* __restrict__ gllx,
-                                   const T* __restrict__ r, T* __restrict__ rc) {
-  const int Vx = nx + 1, Vy = ny + 1, Vz = dim == 3 ? nz + 1 : 1;
-  const long long nv = (long long)Vx * Vy * Vz;
+__global__ void k_p0t_pass(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int d2, int ax, int p,
+                           int Vn, const T* __restrict__ w) {
+  const int o0 = ax == 0 ? Vn : d0, o1 = ax == 1 ? Vn : d1, o2 = ax == 2 ? Vn : d2;
+  const long long no = (long long)o0 * o1 * o2;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= nv) return;
-  const int V[3] = {(int)(gid % Vx), (int)((gid / Vx) % Vy), (int)(gid / ((long long)Vx * Vy))};
-  const bool bnd = V[0] == 0 || V[0] == nx || V[1] == 0 || V[1] == ny || (dim == 3 && (V[2] == 0 || V[2] == nz));
-  if (bnd) { rc[gid] = T(0); return; }
-  const int Nx = nx * p + 1, Ny = ny * p + 1;
-  // 1D weights of the fine indices (V-1)p+1 .. (V+1)p-1
+  if (gid >= no) return;
+  const int i = (int)(gid % o0), j = (int)((gid / o0) % o1), k = (int)(gid / ((long long)o0 * o1));
+  const int v = ax == 0 ? i : (ax == 1 ? j : k);
+  if (v == 0 || v == Vn - 1) { out[gid] = T(0); return; }
+  const long long st = ax == 0 ? 1 : (ax == 1 ? (long long)d0 : (long long)d0 * d1);
+  const long long base = ((long long)(ax == 2 ? (v - 1) * p + 1 : k) * d1 + (ax == 1 ? (v - 1) * p + 1 : j)) * d0 +
+                         (ax == 0 ? (v - 1) * p + 1 : i);
   T s = 0;
-  const int len = 2 * p - 1;
-  const int kz = dim == 3 ? len : 1;
-  for (int c = 0; c < kz; ++c) {
-    T wz = 1;
-    int Kf = 0;
-    if (dim == 3) {
-      Kf = (V[2] - 1) * p + 1 + c;
-      const int t = c + 1;   // position within [ (V-1)p, (V+1)p ]
-      wz = (T)(t <= p ? gllx[t] : 1.0 - gllx[t - p]);
-    }
-    for (int b = 0; b < len; ++b) {
-      const int Jf = (V[1] - 1) * p + 1 + b;
-      const int tb = b + 1;
-      const T wy = (T)(tb <= p ? gllx[tb] : 1.0 - gllx[tb - p]) * wz;
-      const T* row = r + ((long long)Kf * Ny + Jf) * Nx + (V[0] - 1) * p + 1;
-      for (int a = 0; a < len; ++a) {
-        const int ta = a + 1;
-        s += (T)(ta <= p ? gllx[ta] : 1.0 - gllx[ta - p]) * wy * row[a];
-      }
-    }
-  }
-  rc[gid] = s;
+  for (int a = 0; a < 2 * p - 1; ++a) s += w[a] * in[base + a * st];
+  out[gid] = s;
 }
 
-// z[F] += sum_V P0[F][V] e[V] for interior fine nodes
+// z[F] += sum_V P0[F][V] e[V] for interior fine nodes (weights in the path precision)
 template <typename T>
-__global__ void k_coarse_prolong0(int dim, int p, int nx, int ny, int nz, const double* __restrict__ gllx,
+__global__ void k_coarse_prolong0(int dim, int p, int nx, int ny, int nz, const T* __restrict__ gllx,
                                   const T* __restrict__ e, T* __restrict__ z) {
   const int Nx = nx * p + 1, Ny = ny * p + 1, Nz = dim == 3 ? nz * p + 1 : 1;
   const long long nt = (long long)Nx * Ny * Nz;
@@ -824,15 +810,15 @@ __global__ void k_coarse_prolong0(int dim, int p, int nx, int ny, int nz, const 
   const int I = (int)(gid % Nx), Jn = (int)((gid / Nx) % Ny), K = (int)(gid / ((long long)Nx * Ny));
   if (I == 0 || I == Nx - 1 || Jn == 0 || Jn == Ny - 1 || (dim == 3 && (K == 0 || K == Nz - 1))) return;
   const int ex = min(I / p, nx - 1), ey = min(Jn / p, ny - 1), ez = dim == 3 ? min(K / p, nz - 1) : 0;
-  const double xi[3] = {gllx[I - ex * p], gllx[Jn - ey * p], dim == 3 ? gllx[K - ez * p] : 0.0};
+  const T xi[3] = {gllx[I - ex * p], gllx[Jn - ey * p], dim == 3 ? gllx[K - ez * p] : T(0)};
   const int Vx = nx + 1, Vy = ny + 1;
   T s = 0;
   const int nc = 1 << dim;
   for (int cc = 0; cc < nc; ++cc) {
     const int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
-    double w = (bx ? xi[0] : 1.0 - xi[0]) * (by ? xi[1] : 1.0 - xi[1]);
-    if (dim == 3) w *= bz ? xi[2] : 1.0 - xi[2];
-    s += (T)w * e[((long long)(ez + bz) * Vy + (ey + by)) * Vx + (ex + bx)];
+    T w = (bx ? xi[0] : T(1) - xi[0]) * (by ? xi[1] : T(1) - xi[1]);
+    if (dim == 3) w *= bz ? xi[2] : T(1) - xi[2];
+    s += w * e[((long long)(ez + bz) * Vy + (ey + by)) * Vx + (ex + bx)];
   }
   z[gid] += s;
 }
@@ -962,6 +948,8 @@ template <> struct Sel<double> {
   static const double* cD(lor_ctx* c, int l) { return c->d_cDinv64[l]; }
   static const double* inv(lor_ctx* c) { return c->d_cInv64; }
   static const void* S(lor_ctx* c, int l) { return c->d_S64[l]; }
+  static const double* p0w(lor_ctx* c) { return c->d_p0w64; }
+  static double* p0t(lor_ctx* c, int k) { return c->d_p0t64[k]; }
 };
 template <> struct Sel<float> {
   static float* cw(lor_ctx* c, int l, int k) { return c->d_cw32[l][k]; }
@@ -969,6 +957,8 @@ template <> struct Sel<float> {
   static const float* cD(lor_ctx* c, int l) { return c->d_cDinv32[l]; }
   static const float* inv(lor_ctx* c) { return c->d_cInv32; }
   static const void* S(lor_ctx* c, int l) { return c->d_S32[l]; }
+  static const float* p0w(lor_ctx* c) { return c->d_p0w32; }
+  static float* p0t(lor_ctx* c, int k) { return c->d_p0t32[k]; }
 };
 
 static const int kCoarseSweeps = 2;
@@ -1173,15 +1163,29 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
     if (lor_learned_apply(c, (float*)z)) return LOR_ECUDA;
   }
   lor_prof_begin(c, pk + 4);
-  // coarse space
-  const double* gllx = lor_basis64(c, 4);
-  const long long nv = c->cntot[0];
-  k_coarse_restrict0<T><<<(unsigned)lor_ceil_div(nv, 128), 128, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1],
-                                                                                   c->n[2], gllx, r, Sel<T>::cw(c, 0, 0));
-  ++c->launches;
+  // coarse space: rc = P_0^T r by separable passes (x, y[, z])
+  {
+    const LevelGrid& g0 = c->lev[0];
+    const int p = c->p, V0 = c->n[0] + 1, V1 = c->n[1] + 1, V2 = c->dim == 3 ? c->n[2] + 1 : 1;
+    const T* w = Sel<T>::p0w(c) + p + 1;
+    T* t1 = Sel<T>::p0t(c, 0);
+    T* t2 = Sel<T>::p0t(c, 1);
+    T* rc = Sel<T>::cw(c, 0, 0);
+    long long m = (long long)g0.N[2] * g0.N[1] * V0;
+    k_p0t_pass<T><<<(unsigned)lor_ceil_div(m, 256), 256, 0, c->stream>>>(r, t1, g0.N[0], g0.N[1], g0.N[2], 0, p, V0, w);
+    m = (long long)g0.N[2] * V1 * V0;
+    k_p0t_pass<T><<<(unsigned)lor_ceil_div(m, 256), 256, 0, c->stream>>>(t1, c->dim == 3 ? t2 : rc, V0, g0.N[1], g0.N[2], 1,
+                                                                          p, V1, w);
+    c->launches += 2;
+    if (c->dim == 3) {
+      m = (long long)V2 * V1 * V0;
+      k_p0t_pass<T><<<(unsigned)lor_ceil_div(m, 256), 256, 0, c->stream>>>(t2, rc, V0, V1, g0.N[2], 2, p, V2, w);
+      ++c->launches;
+    }
+  }
   T* ec = coarse_vcycle<T>(c, 0);
-  k_coarse_prolong0<T><<<(unsigned)lor_ceil_div(nvec, 128), 128, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1],
-                                                                                   c->n[2], gllx, ec, z);
+  k_coarse_prolong0<T><<<(unsigned)lor_ceil_div(nvec, 256), 256, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1],
+                                                                                   c->n[2], Sel<T>::p0w(c), ec, z);
   ++c->launches;
   lor_prof_end(c, pk + 4);
   return lor_cuda_check(c, cudaGetLastError(), "coarse space");

@@ -159,6 +159,13 @@ struct lor_ctx {
   double* d_cR1w[LOR_MAXCLEV][3] = {};
   int ncoarse_direct = 0;
   int* d_cdirect_idx = nullptr;           // interior node index of each direct unknown
+  // P_0 (vertex-grid multilinear basis at the level-0 nodes) in the path precisions:
+  // [gllx (p+1) | 1D restriction weights by offset (2p-1)], and scratch for the
+  // separable passes of P_0^T (x, then y, then z)
+  double* d_p0w64 = nullptr;
+  float* d_p0w32 = nullptr;
+  double* d_p0t64[2] = {};
+  float* d_p0t32[2] = {};
   double* d_cInv64 = nullptr;             // dense inverse at the coarsest level
   float* d_cInv32 = nullptr;
   // coarse work vectors per level: r, x, t (double and float)

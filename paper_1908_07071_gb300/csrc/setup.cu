@@ -837,6 +837,28 @@ lor_status lor_setup_coarse(lor_ctx* c) {
     ++c->launches;
   }
   if (lor_cuda_check(c, cudaGetLastError(), "coarse setup")) return LOR_ECUDA;
+  // P_0 tables and P_0^T scratch (x-pass: Nz*Ny*Vx, y-pass: Nz*Vy*Vx)
+  {
+    const int p = c->p;
+    std::vector<double> w64(3 * p, 0.0);
+    for (int i = 0; i <= p; ++i) w64[i] = c->gll_x[i];
+    for (int a = 0; a < 2 * p - 1; ++a) {
+      const int t = a + 1;   // position in [(V-1)p, (V+1)p]
+      w64[p + 1 + a] = t <= p ? c->gll_x[t] : 1.0 - c->gll_x[t - p];
+    }
+    std::vector<float> w32(w64.begin(), w64.end());
+    if (upload(c, (void**)&c->d_p0w64, w64.data(), w64.size() * 8)) return LOR_ENOMEM;
+    if (upload(c, (void**)&c->d_p0w32, w32.data(), w32.size() * 4)) return LOR_ENOMEM;
+    const LevelGrid& g0 = c->lev[0];
+    const long long V0 = c->n[0] + 1, V1 = c->n[1] + 1;
+    const long long n1 = (long long)g0.N[2] * g0.N[1] * V0, n2 = (long long)g0.N[2] * V1 * V0;
+    for (int k = 0; k < 2; ++k) {
+      const long long nn = k == 0 ? n1 : n2;
+      c->d_p0t64[k] = (double*)lor_alloc(c, nn * 8);
+      c->d_p0t32[k] = (float*)lor_alloc(c, nn * 4);
+      if (!c->d_p0t64[k] || !c->d_p0t32[k]) return lor_fail(c, LOR_ENOMEM, "alloc P0 scratch");
+    }
+  }
   // dense inverse of the coarsest operator (interior unknowns) on the host
   const int t = c->CL - 1;
   const long long nt = c->cntot[t];
