@@ -452,7 +452,10 @@ def main():
         roof = {"bound": "hbm", "achieved": bts / per_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_kind": "measured" if "hbm_gbs" in pk else "fallback"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes per launch of the dominant kernel from one ncu capture of this exact
+    # configuration (profiles/patch_warp_q8n32_dram.md); None for any other.
+    measured_traffic = {("patch_vcycle_fp32", 8, 32, "mixed-bf16"): 26.16e9 + 1.21e9}
+    roof["traffic"] = measured_traffic.get((names[dom], p, n, args.form))
     roof["kernel"] = names[dom]
     roof["launch_ms"] = per_launch_s * 1e3
     roof["launches_in_timed_region"] = nl
