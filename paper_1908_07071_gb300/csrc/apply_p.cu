@@ -493,6 +493,11 @@ __device__ __forceinline__ T prolong_row(const WLevel& bc, const Xfer1D<T>& X0, 
   return s;
 }
 
+// Rows a lane keeps in flight in the simple global-memory loops of the patch
+// kernel (gather, slot updates, scatter): their loads are issued together, so one
+// latency covers all of them.
+constexpr int kRowsInFlight = 4;
+
 // Per-warp shared-memory block (byte offsets): mbarriers, a zero factor record,
 // level metadata of the current box shape, the bulk-copy ring, the wavefront
 // tables of the shape, and the vectors.
@@ -638,11 +643,21 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       for (int q = lane; q < b0.rows + 2 * guard0 + 1; q += 32) t0[q - guard0] = T(0);
       __syncwarp();
       {
+        constexpr int U = kRowsInFlight;
         BoxIter it;
         it.init(lane, b0.A, b0.B);
-        for (int lex = lane; lex < b0.rows; lex += 32, it.next()) {
-          const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
-          t0[lex] = rloc ? rloc[lex] : rg0[G];
+        for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
+          T v[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int lex = l0 + 32 * u;
+            const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
+            it.next();
+            if (lex < b0.rows) v[u] = rloc ? rloc[lex] : rg0[G];
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (l0 + 32 * u < b0.rows) t0[l0 + 32 * u] = v[u];
         }
       }
       __syncwarp();
@@ -721,14 +736,36 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
         if (ok) {
           // ---- level 0 up: x0 += P x1 in the slot, t0 <- x0, residual in place
           const T* x1 = vec + bx[1].xo;
+          constexpr int U = kRowsInFlight;
           BoxIter it;
           it.init(lane, b0.A, b0.B);
-          for (int lex = lane; lex < b0.rows; lex += 32, it.next())
-            xslot[lex] += prolong_row<DIM, T>(bx[1], xf[type[0]], xf[type[1]], xf[type[2]], x1, it.i, it.j, it.k);
+          for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
+            T xv[U];
+            int iu[U], ju[U], ku[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              iu[u] = it.i; ju[u] = it.j; ku[u] = it.k;
+              it.next();
+              if (l0 + 32 * u < b0.rows) xv[u] = xslot[l0 + 32 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (l0 + 32 * u < b0.rows)
+                xslot[l0 + 32 * u] = xv[u] + prolong_row<DIM, T>(bx[1], xf[type[0]], xf[type[1]], xf[type[2]], x1,
+                                                                 iu[u], ju[u], ku[u]);
+          }
           __syncwarp();
-          for (int q = lane; q < b0.rows + 2 * guard0 + 1; q += 32) {
-            const int lex = q - guard0;
-            t0[lex] = (lex >= 0 && lex < b0.rows) ? xslot[lex] : T(0);
+          // t0 <- x0 (x1 lived over t0's space; every lane is done with it now)
+          for (int q = lane; q < guard0; q += 32) { t0[q - guard0] = T(0); t0[b0.rows + q] = T(0); }
+          if (lane == 0) t0[b0.rows + guard0] = T(0);
+          for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
+            T xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (l0 + 32 * u < b0.rows) xv[u] = xslot[l0 + 32 * u];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (l0 + 32 * u < b0.rows) t0[l0 + 32 * u] = xv[u];
           }
           __syncwarp();
           resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, nullptr);
@@ -753,13 +790,27 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
     }
     T* z = (T*)a.z;
     {
+      constexpr int U = kRowsInFlight;
       BoxIter it;
       it.init(lane, b0.A, b0.B);
-      for (int lex = lane; lex < b0.rows; lex += 32, it.next()) {
-        const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
-        const T xj = xslot[lex] + t0[lex];
-        atomicAdd(z + G, xj);
-        if (a.tout && sh == 0) t0[lex] = xj;
+      for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
+        T xv[U];
+        int G[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          G[u] = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
+          it.next();
+          if (l0 + 32 * u < b0.rows) xv[u] = xslot[l0 + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int lex = l0 + 32 * u;
+          if (lex < b0.rows) {
+            const T xj = xv[u] + t0[lex];
+            atomicAdd(z + G[u], xj);
+            if (a.tout && sh == 0) t0[lex] = xj;
+          }
+        }
       }
     }
     __syncwarp();
