@@ -26,13 +26,6 @@
 
 namespace {
 
-template <typename FT> __device__ __forceinline__ float tofl(FT v);
-template <> __device__ __forceinline__ float tofl<float>(float v) { return v; }
-template <> __device__ __forceinline__ float tofl<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-template <typename T, typename FT> __device__ __forceinline__ T fac(FT v) { return (T)tofl<FT>(v); }
-template <> __device__ __forceinline__ double fac<double, double>(double v) { return v; }
-
 struct PLevel {
   const void* S;          // [NS][ntot] stencil of this level (T)
   const void* Sa;         // [ntot][nsp] row-major copy (T)
@@ -104,9 +97,14 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
   // order earlier generic-proxy reads of this slot before the async-proxy write
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  // factor records are read once per smoothing: evict them from L2 first, so that
+  // the stencil rows shared by neighbouring patches stay resident
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
       : "memory");
 }
 
