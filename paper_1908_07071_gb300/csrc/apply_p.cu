@@ -1069,7 +1069,7 @@ T* coarse_vcycle(lor_ctx* c, int l) {
 const int kMaxPatchWarps = 12;   // warps per CTA (one CTA per SM when shared memory allows)
 
 template <typename FT>
-constexpr int ring_depth() { return 3; }
+constexpr int ring_depth() { return 2; }
 
 // Per-warp shared-memory layout of the patch kernel (sizes for the largest,
 // interior, box shape; other shapes fit inside).

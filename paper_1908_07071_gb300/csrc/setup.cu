@@ -590,7 +590,9 @@ lor_status lor_setup_stencils(lor_ctx* c) {
 
 // ------------------------------------------------------------ patch structures
 static int axis_len(int type, int m) { return type == 0 ? 2 * m - 1 : m - 1; }
-static const int kChunkBytes = 2048;   // bulk-copy chunk of factor records (a wider front is a chunk of its own)
+// bulk-copy chunk of factor records per element size (2, 4, 8 bytes); a wider
+// front is a chunk of its own
+static const int kChunkBytes[3] = {4096, 4096, 8192};
 
 lor_status lor_setup_patches(lor_ctx* c) {
   const int dim = c->dim;
@@ -639,7 +641,7 @@ lor_status lor_setup_patches(lor_ctx* c) {
       // chunks of whole fronts of at most kChunkBytes per factor element size; a
       // front larger than that is a chunk of its own
       for (int es = 0; es < 3; ++es) {
-        const int cap = kChunkBytes / (lor_rec(dim) * (2 << es));
+        const int cap = kChunkBytes[es] / (lor_rec(dim) * (2 << es));
         bs.chunk_off[es] = (int)chunk.size();
         bs.nchunk[es] = 0;
         bs.maxchunk[es] = 0;
