@@ -438,7 +438,8 @@ def main():
         fb = 8 if dom == 0 else (2 if bf16 else 4)
         vb = 8 if dom == 0 else 4
         lev_nodes = sum(((n * m + 1) ** 3) for m in level_intervals(p))
-        # per factor row: L and U records of 14 values; level stencils 27 values per node; r read, z RMW
+        # per factor row: L and U parts of 14 values each (13 couplings + diagonal; the stored records
+        # carry 16 slots); level stencils 27 values per node; r read, z RMW
         alg = rows * 2 * 14 * fb + lev_nodes * 27 * vb + 3 * s.nvec * vb
         roof = {"bound": "hbm", "achieved": alg / per_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_kind": "measured" if "hbm_gbs" in pk else "fallback"}
