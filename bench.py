@@ -33,6 +33,23 @@ REF_ITERS = 152   # FP64 PCG iterations to 1e-8 on the Q8 32^3 workload (measure
 WORKLOAD = "3D CG Q8, 32^3 perturbed hex mesh (+-0.15h), log-normal kappa (sigma 1), f=1, rtol 1e-8"
 
 
+def max_over_ranks(seconds: float, world: int, device=None) -> float:
+    """The slowest rank's time: every rank calls this; identity for one rank."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(seconds_max: float, steps: int, world: int) -> float:
+    """Whole-job solves/s: each of `world` replicas solved `steps` problems, and the
+    job took as long as its slowest rank."""
+    return world * steps / seconds_max
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,12 +379,9 @@ def main():
     launches = s.launches() - l0
     prof = {k: s.profile_read(k) for k in range(6)}
     clk = clocks.stop(local)
-    t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, world, device="cuda")
     ms_per_step = elapsed / args.steps * 1e3
-    value = world * args.steps / elapsed
+    value = replica_throughput(elapsed, args.steps, world)
 
     extras = {}
     if not args.no_extras:
@@ -382,7 +396,7 @@ def main():
         for _ in range(args.steps):
             s.solve_host(hbn, hxn)
         barrier()
-        e2e = world * args.steps / (time.perf_counter() - t0)
+        e2e = replica_throughput(max_over_ranks(time.perf_counter() - t0, world, device="cuda"), args.steps, world)
         extras["e2e"] = {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": int(s.nvec * 8),
                          "d2h_bytes_per_step": int(s.nvec * 8)}
         # per-apply throughput
