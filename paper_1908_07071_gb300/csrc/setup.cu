@@ -778,11 +778,15 @@ lor_status lor_setup_patches(lor_ctx* c) {
     ++c->launches;
     if (lor_cuda_check(c, cudaGetLastError(), "ilu0")) return LOR_ECUDA;
   }
-  k_fac_to32<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F32, tot, lor_rec(dim));
-  ++c->launches;
-  if (c->d_F16) k_fac_to16<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F16, tot, lor_rec(dim));
-  ++c->launches;
-  if (lor_cuda_check(c, cudaGetLastError(), "factor conversion")) return LOR_ECUDA;
+  if (tot > 0) {   // p = 1: the patch box is the vertex level, solved exactly, no factors
+    k_fac_to32<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F32, tot, lor_rec(dim));
+    ++c->launches;
+    if (c->d_F16) {
+      k_fac_to16<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F16, tot, lor_rec(dim));
+      ++c->launches;
+    }
+    if (lor_cuda_check(c, cudaGetLastError(), "factor conversion")) return LOR_ECUDA;
+  }
   return check_status(c, "ilu0");
 }
 

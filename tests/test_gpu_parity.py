@@ -46,6 +46,8 @@ CASES = [  # (dim, n, p, perturb, kappa_const, mg_levels)
     (3, 2, 8, 0.15, None, 0),
     (3, 2, 6, 0.15, None, 2),
     (3, 1, 3, 0.15, None, 0),     # single element: no interior vertex
+    (3, 3, 1, 0.15, None, 0),     # p = 1: the patch box is the vertex level (one unknown)
+    (2, 4, 1, 0.15, None, 0),
 ]
 
 
