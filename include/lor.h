@@ -217,6 +217,23 @@ lor_status lor_learned_eval(lor_ctx* ctx, int npatch, const int* d_ids, const fl
 lor_status lor_rhs_static(int dim, int p, int nx, int ny, int nz, const double* d_vertices, int kind,
                           double* d_b, void* stream);
 
+/* Device-side error check (no paper counterpart).  lor_apply_A/lor_apply_P
+ * only enqueue work; a bounded device wait inside them that ran out (a factor
+ * bulk copy of the patch kernel that did not complete within its poll limit;
+ * the kernel then skips the rest of that warp's work and returns) is recorded
+ * in the context's device status word.  This call synchronizes the context
+ * stream, returns LOR_ETIMEOUT if such a wait ran out since the last check and
+ * clears the record (the context stays usable), else LOR_OK.  lor_pcg_solve
+ * performs the same check before it returns. */
+lor_status lor_device_status(lor_ctx* ctx);
+
+/* Self-test of the bounded device waits (no paper counterpart): launches one
+ * warp that waits on an mbarrier at which nothing ever arrives, giving up after
+ * `polls` polls (1 <= polls <= 2^24; 2^12 takes well under a millisecond).  The
+ * expected result is LOR_ETIMEOUT, reported and cleared as by
+ * lor_device_status; LOR_OK would mean the wait did not time out. */
+lor_status lor_selftest_wait(lor_ctx* ctx, int polls);
+
 const char* lor_last_error(const lor_ctx* ctx);
 void lor_destroy(lor_ctx* ctx);
 

@@ -108,11 +108,11 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
       : "memory");
 }
 
-// Waits for the phase `parity` of `bar`; gives up after a bounded number of
-// polls (returns false) so that a lost copy cannot hang the GPU.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// Waits for the phase `parity` of `bar`; gives up after `limit` polls (returns
+// false) so that a lost copy cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int limit = 1 << 22) {
   const unsigned addr = smem_u32(bar);
-  for (int it = 0; it < (1 << 22); ++it) {
+  for (int it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -1240,7 +1240,27 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
   return lor_cuda_check(c, cudaGetLastError(), "coarse space");
 }
 
+// Self-test of the bounded waits: one warp waits on an mbarrier at which nothing
+// arrives; the wait gives up after `polls` polls and the kernel reports it in the
+// context status word (bit 4, the same bit as a bulk-copy timeout of the patch
+// kernel), then invalidates the barrier and returns.
+__global__ void k_wait_selftest(int polls, int* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0u, polls)) atomicOr(status, 4);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  }
+}
+
 }  // namespace
+
+lor_status lor_launch_wait_selftest(lor_ctx* c, int polls) {
+  k_wait_selftest<<<1, 32, 0, c->stream>>>(polls, c->d_status);
+  ++c->launches;
+  return lor_cuda_check(c, cudaGetLastError(), "wait self-test");
+}
 
 lor_status lor_launch_apply_P64(lor_ctx* c, const double* r, double* z) {
   return launch_apply_P<double, double>(c, r, z, c->d_F64);

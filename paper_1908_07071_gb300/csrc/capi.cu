@@ -67,6 +67,20 @@ lor_status lor_opP32(lor_ctx* c, const float* r, float* z) {
   return c->dg_state ? lor_launch_apply_P_dg32(c, r, z) : lor_launch_apply_P32(c, r, z);
 }
 
+lor_status lor_take_device_status(lor_ctx* c) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return lor_cuda_check(c, e, "device status");
+  if (st & 4) {
+    e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return lor_cuda_check(c, e, "device status reset");
+    return lor_fail(c, LOR_ETIMEOUT, "a bounded device wait ran out (factor bulk copy not completed)");
+  }
+  return LOR_OK;
+}
+
 extern "C" {
 
 lor_status lor_profile(lor_ctx* c, int on) {
@@ -224,12 +238,28 @@ lor_status lor_apply_P(lor_ctx* c, const void* r, void* z, int prec) {
   return lor_fail(c, LOR_EINVAL, "lor_apply_P: prec must be LOR_FP64 or LOR_FP32");
 }
 
+lor_status lor_device_status(lor_ctx* c) {
+  lor_status s = ready(c);
+  if (s) return s;
+  return lor_take_device_status(c);
+}
+
+lor_status lor_selftest_wait(lor_ctx* c, int polls) {
+  lor_status s = ready(c);
+  if (s) return s;
+  if (polls < 1 || polls > (1 << 24)) return lor_fail(c, LOR_EINVAL, "lor_selftest_wait: polls in [1, 2^24]");
+  if ((s = lor_launch_wait_selftest(c, polls))) return s;
+  return lor_take_device_status(c);
+}
+
 lor_status lor_pcg_solve(lor_ctx* c, const double* b, double* x, int* iters, double* rel_res) {
   lor_status s = ready(c);
   if (s) return s;
   if (!b || !x) return lor_fail(c, LOR_EINVAL, "lor_pcg_solve: null vector");
-  if (c->opt.prec == LOR_MIXED) return lor_pcg_mixed(c, b, x, iters, rel_res);
-  return lor_pcg64(c, b, x, iters, rel_res);
+  s = c->opt.prec == LOR_MIXED ? lor_pcg_mixed(c, b, x, iters, rel_res) : lor_pcg64(c, b, x, iters, rel_res);
+  if (s != LOR_OK && s != LOR_ENOCONV) return s;
+  const lor_status d = lor_take_device_status(c);   // a timed-out patch V-cycle invalidates the result
+  return d != LOR_OK ? d : s;
 }
 
 lor_status lor_pcg_solve_host(lor_ctx* c, const double* hb, double* hx, int* iters, double* rel_res) {

@@ -237,6 +237,11 @@ lor_status lor_opP32(lor_ctx* c, const float* r, float* z);
 lor_status lor_launch_apply_P64(lor_ctx* c, const double* r, double* z);
 lor_status lor_launch_apply_P32(lor_ctx* c, const float* r, float* z);
 lor_status lor_patch_prepare(lor_ctx* c);   // launch shapes, shared-memory fit, iterate slots
+lor_status lor_launch_wait_selftest(lor_ctx* c, int polls);
+// Synchronizes the context stream and reads the device status word: a bounded
+// device wait that ran out since the last check -> LOR_ETIMEOUT (the word is
+// cleared, so the context stays usable).
+lor_status lor_take_device_status(lor_ctx* c);
 // krylov.cu
 lor_status lor_pcg64(lor_ctx* c, const double* b, double* x, int* iters, double* relres);
 lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, double* relres);

@@ -86,11 +86,13 @@ def load():
         getattr(lib, name).restype = ctypes.c_int
     lib.lor_rhs_static.argtypes = [i, i, i, i, i, vp, i, vp, vp]
     lib.lor_rhs_static.restype = ctypes.c_int
+    lib.lor_device_status.argtypes = [vp]
+    lib.lor_selftest_wait.argtypes = [vp, i]
     lib.lor_set_prec.argtypes = [vp, i]
     lib.lor_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.lor_profile.argtypes = [vp, i]
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
-    for name in ("lor_set_prec", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
+    for name in ("lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -202,6 +204,14 @@ class Solver:
                                                 x.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it),
                                                 ctypes.byref(rr)))
         return it.value, rr.value
+
+    def device_status(self):
+        """Synchronizes and checks for a bounded device wait that ran out (raises LorError LOR_ETIMEOUT)."""
+        self._check(self.lib.lor_device_status(self.ctx))
+
+    def selftest_wait(self, polls=1 << 12):
+        """Runs the bounded-wait self-test; returns the library status (LOR_ETIMEOUT expected)."""
+        return self.lib.lor_selftest_wait(self.ctx, polls)
 
     def set_prec(self, prec):
         self._check(self.lib.lor_set_prec(self.ctx, prec))
