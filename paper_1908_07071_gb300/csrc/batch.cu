@@ -379,11 +379,13 @@ lor_status lor_batch_solve(lor_batch* b, const double* const* d_b, double* const
     double rr = 0;
     cudaMemcpyAsync(&rr, sc + B_RR, 8, cudaMemcpyDeviceToHost, b->main);
     cudaStreamSynchronize(b->main);
+    const lor_status ds = lor_take_device_status(c);   // a timed-out patch V-cycle invalidates this solve
     c->stream = keep;
     if (iters) iters[s] = (int)h[B_ITERS];
     if (rel_res) rel_res[s] = bb > 0 ? sqrt(rr / bb) : 0.0;
     if (h[B_CONV] == 0.0) ret = LOR_ENOCONV;
     if (h[B_FLAG] != 0.0) ret = LOR_ENAN;
+    if (ds != LOR_OK) ret = ds;
   }
   (void)any_flag;
   return ret;
