@@ -31,6 +31,7 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
+from . import ordering
 from .basis import gll
 from .cg import boundary_mask, node_coordinates, node_shape
 from .mesh import Mesh, multilinear
@@ -196,9 +197,12 @@ class LORPreconditioner:
 
     def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0,
                  exact_local: bool = False, exact_coarse: bool = False, K_h=None,
-                 patch_subset=None, coarse=True):
+                 patch_subset=None, coarse=True, ordering: str = "lex"):
         """patch_subset: vertex multi-indices whose patches are built (default all);
-        coarse=False skips the coarse space (for checks of the patch part alone)."""
+        coarse=False skips the coarse space (for checks of the patch part alone);
+        ordering: ILU(0) ordering of every patch level, "lex" (patch-lexicographic),
+        "mdf" or "rcm" (Section 3.4, `oracle.ordering`)."""
+        self.ordering = ordering
         self.patch_subset = None if patch_subset is None else set(map(tuple, patch_subset))
         self.with_coarse = coarse
         self.mesh, self.p, self.dim = mesh, p, mesh.dim
@@ -238,7 +242,13 @@ class LORPreconditioner:
                 Aj = self.A[l][idx][:, idx].toarray() if len(idx) else np.zeros((0, 0))
                 lev = {"ranges": ranges, "idx": idx, "A": Aj}
                 if len(idx) and l < L - 1 and not self.exact_local:
-                    lev["LU"] = ilu0(Aj, box_pattern(ranges))
+                    pat = box_pattern(ranges)
+                    if self.ordering == "lex":
+                        lev["LU"] = ilu0(Aj, pat)
+                    else:
+                        perm = ordering.order_for(self.ordering, Aj, pat)
+                        lev["LU"] = ilu0(Aj[np.ix_(perm, perm)], pat[np.ix_(perm, perm)])
+                        lev["perm"] = perm
                 if l < L - 1:
                     rc = [patch_range_1d(v[a], self.mesh.n[a], self.ms[l + 1]) for a in range(self.dim)]
                     mats = [self.P1[l][a][np.ix_(ranges[a], rc[a])] for a in range(self.dim)]
@@ -255,14 +265,24 @@ class LORPreconditioner:
         if l == len(levels) - 1:
             return np.linalg.solve(lev["A"], r)
         A = lev["A"]
-        L_, U_ = lev["LU"]
-        x = ilu_solve(L_, U_, r)
+        x = self.smooth(lev, r)
         t = r - A @ x
         P = lev["P"]
         if P.shape[1] > 0:
             x = x + P @ self.vcycle(levels, l + 1, P.T @ t)
         t = r - A @ x
-        return x + ilu_solve(L_, U_, t)
+        return x + self.smooth(lev, t)
+
+    @staticmethod
+    def smooth(lev, r):
+        """(L U)^{-1} r with the level's ILU(0) factors, in the level's ordering."""
+        L_, U_ = lev["LU"]
+        perm = lev.get("perm")
+        if perm is None:
+            return ilu_solve(L_, U_, r)
+        y = np.empty_like(r)
+        y[perm] = ilu_solve(L_, U_, r[perm])
+        return y
 
     def local_solve(self, j, r):
         levels = self.patches[j]["levels"]
