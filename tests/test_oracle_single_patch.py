@@ -1,0 +1,97 @@
+"""Pins of the oracle's single-patch preconditioner B(1) (Section 5.1): the whole
+domain as one patch, i.e. one element-structured V(1,1) cycle on K_h with ILU(0)
+smoothing and R_0 at the vertex level."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import cg, krylov, lor as olor
+from oracle.mesh import Mesh
+from oracle.single_patch import SinglePatchPreconditioner, grid_pattern, ilu0_csr
+from paper_1908_07071_gb300.synthetic import make_mesh
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _paper_table2():
+    t = {}
+    for line in open(os.path.join(GOLDEN, "table2_single_patch.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        vals = [int(s) for s in line.split()]
+        for c, nx in enumerate([2, 4, 8, 16, 32]):
+            t[(vals[0], nx)] = vals[c + 1]
+    return t
+
+
+def _cartesian(nx, p):
+    v, k = make_mesh(2, nx, seed=0, perturb=0.0, kappa_const=1.0)
+    m = Mesh(v, k)
+    N = cg.node_shape(m.n, p)
+    K = cg.assemble_stiffness(m, p)
+    f = lambda X: 2 * np.pi ** 2 * np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1])  # noqa: E731
+    return m, N, K, cg.load_vector(m, p, f)
+
+
+@pytest.mark.parametrize("p,nx", [(4, 2), (4, 4), (4, 8), (6, 2), (6, 4), (6, 8), (8, 2), (8, 4), (8, 8)])
+def test_single_patch_counts_match_table2(p, nx):
+    """Table 2 (Section 5.1): within one iteration of the paper's counts, although the
+    ordering (lexicographic vs MDF) and R_0 (own V-cycle vs BoomerAMG) differ."""
+    paper = _paper_table2()[(p, nx)]
+    m, N, K, b = _cartesian(nx, p)
+    B = SinglePatchPreconditioner(m, p)
+    it = krylov.pcg(lambda u: cg.apply_A(K, N, u), B.apply, b, rtol=1e-8)[1]
+    assert abs(it - paper) <= 1, (it, paper)
+
+
+@pytest.mark.parametrize("nx", [2, 4, 8])
+def test_single_patch_p2_magnitude(nx):
+    paper = _paper_table2()[(2, nx)]
+    m, N, K, b = _cartesian(nx, 2)
+    it = krylov.pcg(lambda u: cg.apply_A(K, N, u), SinglePatchPreconditioner(m, 2).apply, b, rtol=1e-8)[1]
+    assert 0.5 * paper <= it <= 2.0 * paper, (it, paper)
+
+
+def test_vertex_patches_need_more_iterations_than_one_patch():
+    """Section 5.1: with vertex patches the counts grow (about twice those of one
+    patch per domain in the paper's tables)."""
+    for p, nx in ((4, 4), (6, 4), (8, 4)):
+        m, N, K, b = _cartesian(nx, p)
+        A = lambda u: cg.apply_A(K, N, u)  # noqa: E731
+        it1 = krylov.pcg(A, SinglePatchPreconditioner(m, p).apply, b, rtol=1e-8)[1]
+        itv = krylov.pcg(A, olor.LORPreconditioner(m, p).apply, b, rtol=1e-8)[1]
+        assert 1.2 * it1 <= itv <= 2.5 * it1, (p, it1, itv)
+
+
+def test_single_patch_is_symmetric_positive_definite():
+    v, k = make_mesh(2, 3, seed=1, perturb=0.15)
+    m = Mesh(v, k)
+    p = 3
+    B = SinglePatchPreconditioner(m, p)
+    N = cg.node_shape(m.n, p)
+    inner = ~cg.boundary_mask(N).ravel()
+    n = inner.sum()
+    E = np.zeros((len(inner), n))
+    E[np.nonzero(inner)[0], np.arange(n)] = 1.0
+    M = np.column_stack([B.apply(E[:, c])[inner] for c in range(n)])
+    assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_sparse_ilu0_matches_the_dense_ilu0_of_a_patch():
+    v, k = make_mesh(3, 2, seed=2, perturb=0.15)
+    m = Mesh(v, k)
+    B = olor.LORPreconditioner(m, 3, coarse=False, patch_subset=[(1, 1, 1)])
+    lev = B.patches[0]["levels"][0]
+    A, pat = lev["A"], olor.box_pattern(lev["ranges"])
+    Ld, Ud = olor.ilu0(A, pat)
+    Ls, Us = ilu0_csr(A, pat)
+    assert np.allclose(Ls.toarray(), Ld, atol=1e-13) and np.allclose(Us.toarray(), Ud, atol=1e-13 * np.abs(A).max())
+
+
+def test_grid_pattern_is_the_3d_point_stencil():
+    P = grid_pattern((4, 3, 5)).toarray()
+    idx = np.array([(i, j, k) for k in range(5) for j in range(3) for i in range(4)])
+    ref = np.all(np.abs(idx[:, None, :] - idx[None, :, :]) <= 1, axis=2)
+    assert np.array_equal(P, ref)
