@@ -374,6 +374,26 @@ class LORPreconditioner:
             z += self.P0 @ ec
         return z
 
+    def apply_hybrid(self, r):
+        """Hybrid Schwarz: the coarse correction applied multiplicatively, the patches
+        additively among themselves (the variant Section 5.1 names as future work after
+        Lottes and Fischer), in the symmetric form
+            B_hyb = B_0 + (I - B_0 K_h) B_loc (I - K_h B_0),
+        B_loc = sum_j R_j^T V_j R_j, B_0 = P_0 R_0 P_0^T, K_h on the interior nodes.
+        B_hyb is B_0 plus a congruence of B_loc, so it is symmetric positive definite
+        without damping (the undamped smoother-coarse-smoother product is not: the
+        overlapping patch sum alone has lambda_max(B_loc K_h) up to 2^d)."""
+        r = np.asarray(r, dtype=np.float64)
+        inner = ~boundary_mask(self.Ns[0])
+        rr = np.where(inner, r, 0.0)
+
+        def K(z):
+            return np.where(inner, self.K_h @ np.where(inner, z, 0.0), 0.0)
+
+        z0 = self.apply(rr, parts=("coarse",))
+        z1 = self.apply(rr - K(z0), parts=("patches",))
+        return z0 + z1 - self.apply(K(z1), parts=("coarse",))
+
     def patch_contribution(self, j, r):
         """R_j^T V_j(R_j r) scattered onto the full level-0 grid (for sampled checks)."""
         z = np.zeros(len(r))

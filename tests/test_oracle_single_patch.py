@@ -95,3 +95,31 @@ def test_grid_pattern_is_the_3d_point_stencil():
     idx = np.array([(i, j, k) for k in range(5) for j in range(3) for i in range(4)])
     ref = np.all(np.abs(idx[:, None, :] - idx[None, :, :]) <= 1, axis=2)
     assert np.array_equal(P, ref)
+
+
+def test_hybrid_schwarz_is_spd_and_close_to_additive():
+    """Coarse correction applied multiplicatively (symmetric hybrid form): symmetric
+    positive definite without damping, and about as effective as the additive form."""
+    v, k = make_mesh(2, 3, seed=1, perturb=0.15)
+    m = Mesh(v, k)
+    p = 3
+    B = olor.LORPreconditioner(m, p)
+    N = cg.node_shape(m.n, p)
+    inner = ~cg.boundary_mask(N)
+    n = inner.sum()
+    E = np.zeros((len(inner), n))
+    E[np.nonzero(inner)[0], np.arange(n)] = 1.0
+    M = np.column_stack([B.apply_hybrid(E[:, c])[inner] for c in range(n)])
+    assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+    for nx, p in ((4, 4), (6, 4)):
+        v, k = make_mesh(2, nx, seed=0, perturb=0.15)
+        m = Mesh(v, k)
+        N = cg.node_shape(m.n, p)
+        K = cg.assemble_stiffness(m, p)
+        b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+        B = olor.LORPreconditioner(m, p)
+        A = lambda u: cg.apply_A(K, N, u)  # noqa: E731
+        ita = krylov.pcg(A, B.apply, b, rtol=1e-8)[1]
+        ith = krylov.pcg(A, B.apply_hybrid, b, rtol=1e-8)[1]
+        assert abs(ith - ita) <= 0.15 * ita, (ita, ith)
