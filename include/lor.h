@@ -64,10 +64,15 @@ typedef struct {
   int max_it;       /* Krylov iteration cap                                    */
   double inner_rtol;/* LOR_MIXED: relative tolerance of each FP32 inner solve  */
   int factor_bf16;  /* LOR_MIXED/FP32: store ILU factors in bf16 (1) or fp32 */
+  int weighting;    /* patch sum of Eq. (as): 0 = unit weights (the paper's
+                       method); 1 = scaled on both sides by D^{-1/2}, D the
+                       number of patches containing each node (the counting
+                       matrix Section 5.1 leaves to future work)            */
 } lor_options;
 
 /* Fills *opt with defaults: dim 3, p 4, 8^3 elements, CG, eta 1, full
- * hierarchy, FP64, rtol 1e-8, max_it 1000, inner_rtol 1e-3, fp32 factors. */
+ * hierarchy, FP64, rtol 1e-8, max_it 1000, inner_rtol 1e-3, fp32 factors,
+ * unit patch weights. */
 void lor_default_options(lor_options* opt);
 
 /* Creates a context for the mesh (Section 2).  Validates sizes, copies the host

@@ -197,12 +197,18 @@ class LORPreconditioner:
 
     def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0,
                  exact_local: bool = False, exact_coarse: bool = False, K_h=None,
-                 patch_subset=None, coarse=True, ordering: str = "lex"):
+                 patch_subset=None, coarse=True, ordering: str = "lex", weighting: str = "none"):
         """patch_subset: vertex multi-indices whose patches are built (default all);
         coarse=False skips the coarse space (for checks of the patch part alone);
         ordering: ILU(0) ordering of every patch level, "lex" (patch-lexicographic),
-        "mdf" or "rcm" (Section 3.4, `oracle.ordering`)."""
+        "mdf" or "rcm" (Section 3.4, `oracle.ordering`);
+        weighting: "none" (unit weights, Eq. (as)) or "count": the patch sum scaled on
+        both sides by D^{-1/2}, D = number of patches containing each node (the counting
+        matrix Section 5.1 names as future work)."""
         self.ordering = ordering
+        if weighting not in ("none", "count"):
+            raise ValueError(f"unknown weighting {weighting!r}")
+        self.weighting = weighting
         self.patch_subset = None if patch_subset is None else set(map(tuple, patch_subset))
         self.with_coarse = coarse
         self.mesh, self.p, self.dim = mesh, p, mesh.dim
@@ -363,16 +369,29 @@ class LORPreconditioner:
         N0 = self.Ns[0]
         rr = np.where(boundary_mask(N0), 0.0, r)
         if "patches" in parts:
+            w = self.count_weights() if self.weighting == "count" else None
+            rp = rr if w is None else w * rr
+            zp = np.zeros_like(r)
             for j in range(len(self.patches)):
                 idx = self.patches[j]["levels"][0]["idx"]
                 if len(idx):
-                    z[idx] += self.local_solve(j, rr[idx])
+                    zp[idx] += self.local_solve(j, rp[idx])
+            z += zp if w is None else w * zp
         if "coarse" in parts and self.with_coarse:
             rc = (self.P0.T @ rr)[self.vmask]
             ec = np.zeros(self.P0.shape[1])
             ec[self.vmask] = self.coarse_solve(rc)
             z += self.P0 @ ec
         return z
+
+    def count_weights(self):
+        """D^{-1/2} on the level-0 grid: D counts the built patches containing each node."""
+        if getattr(self, "_cw", None) is None:
+            cnt = np.zeros(int(np.prod(self.Ns[0])))
+            for P in self.patches:
+                cnt[P["levels"][0]["idx"]] += 1.0
+            self._cw = np.where(cnt > 0, 1.0 / np.sqrt(np.maximum(cnt, 1.0)), 0.0)
+        return self._cw
 
     def apply_hybrid(self, r):
         """Hybrid Schwarz: the coarse correction applied multiplicatively, the patches

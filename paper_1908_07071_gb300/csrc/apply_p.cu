@@ -70,6 +70,7 @@ struct PatchArgs {
   long long x0_stride;
   const int* porder;            // patch visiting order (grouped by box shape)
   const double* conv;           // optional: skip all work when *conv != 0 (converged batched solve)
+  int wp;                       // > 0: patch sum weighted by D^{-1/2} on both sides (wp = p), 0: unit weights
   // patch-local mode (learned-correction training data): patches plist[0..nlist)
   // take their level-0 right-hand side from rloc and write x to xloc (lexicographic
   // box order, stride vstride per listed patch) instead of gathering / scattering
@@ -382,13 +383,24 @@ __device__ __forceinline__ T row_residual(const T* s, T rhs, int i, int j, int k
   return acc0 + acc1;
 }
 
+// Counting-matrix weight D^{-1/2} of a level-0 node (I, J, K): D is the number of
+// vertex patches containing it, 2 per axis along which the node lies strictly
+// inside an element (both vertices of that element edge carry a patch) and 1
+// where it lies on a vertex plane.
+template <int DIM, typename T>
+__device__ __forceinline__ T count_weight(int I, int J, int K, int p) {
+  const int c = (I % p != 0) + (J % p != 0) + (DIM == 3 ? (K % p != 0) : 0);
+  return T(1) / sqrt(T(1 << c));
+}
+
 // Level-0 residual in place: t holds x on entry (rows of the box, zero guard
 // bands) and rhs - A x on exit.  Planes are done in order; plane k is computed
 // into tmp from prev (x of plane k-1, guarded) and t (planes k, k+1 still x),
 // then plane k's x moves to prev (and to xout, when given) and tmp into t.
+// wp > 0: the global right-hand side is weighted by D^{-1/2} (count_weight).
 template <int DIM, typename T>
 __device__ void resid0_inplace(const WLevel& b, const PLevel& lv, const T* __restrict__ rg0,
-                               const T* __restrict__ rloc, T* t, T* prev, T* tmp, T* xout) {
+                               const T* __restrict__ rloc, T* t, T* prev, T* tmp, T* xout, int wp) {
   constexpr int NSP = lor_nsp(DIM);
   const int lane = threadIdx.x & 31;
   const int A = b.A, B = b.B, C = b.C, AB = A * B;
@@ -403,7 +415,8 @@ __device__ void resid0_inplace(const WLevel& b, const PLevel& lv, const T* __res
       const int G = ((b.org[2] + k) * N1 + (b.org[1] + j)) * N0 + (b.org[0] + i);
       T s[NSP];
       load_row<DIM, T>(Sa, G, s);
-      const T rhs = rloc ? rloc[lex] : rg0[G];
+      T rhs = rloc ? rloc[lex] : rg0[G];
+      if (wp) rhs *= count_weight<DIM, T>(b.org[0] + i, b.org[1] + j, b.org[2] + k, wp);
       tmp[p] = row_residual<DIM, T>(s, rhs, i, j, k, A, B, C, [&](int o, int dx, int dy, int dz) -> T {
         return dz < 0 ? prev[p + dy * A + dx] : t[lex + dz * AB + dy * A + dx];
       });
@@ -632,7 +645,9 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       it.init(lane, b0.A, b0.B);
       for (int lex = lane; lex < b0.rows; lex += 32, it.next()) {
         const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
-        xslot[lex] = (rloc ? rloc[lex] : rg0[G]) / S[(long long)(a.NS / 2) * lv0.ntot + G];
+        T rhs = rloc ? rloc[lex] : rg0[G];
+        if (a.wp) rhs *= count_weight<DIM, T>(b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp);
+        xslot[lex] = rhs / S[(long long)(a.NS / 2) * lv0.ntot + G];
         t0[lex] = T(0);
       }
       __syncwarp();
@@ -650,8 +665,9 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           for (int u = 0; u < U; ++u) {
             const int lex = l0 + 32 * u;
             const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
+            const T w = a.wp ? count_weight<DIM, T>(b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp) : T(1);
             it.next();
-            if (lex < b0.rows) v[u] = rloc ? rloc[lex] : rg0[G];
+            if (lex < b0.rows) v[u] = (rloc ? rloc[lex] : rg0[G]) * w;
           }
 #pragma unroll
           for (int u = 0; u < U; ++u)
@@ -663,7 +679,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       ok = ilu_solve<DIM, T, FT, NBUF>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
       T* prev = vec + (b0.A + 1);                 // guarded plane buffers
       T* tmp = prev + AB0 + (b0.A + 1);
-      if (ok) resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, xslot);
+      if (ok) resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, xslot, a.wp);
       if (ok && bottom > 0) {
         // ---- coarse levels
         restrict_level<DIM, T>(bx[0], bx[1], xf[type[0]], xf[type[1]], xf[type[2]], t0, vec + bx[1].ro);
@@ -766,7 +782,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
               if (l0 + 32 * u < b0.rows) t0[l0 + 32 * u] = xv[u];
           }
           __syncwarp();
-          resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, nullptr);
+          resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, nullptr, a.wp);
         }
       }
       if (ok) ok = ilu_solve<DIM, T, FT, NBUF>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
@@ -792,11 +808,12 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       BoxIter it;
       it.init(lane, b0.A, b0.B);
       for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
-        T xv[U];
+        T xv[U], w[U];
         int G[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           G[u] = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
+          w[u] = a.wp ? count_weight<DIM, T>(b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp) : T(1);
           it.next();
           if (l0 + 32 * u < b0.rows) xv[u] = xslot[l0 + 32 * u];
         }
@@ -805,7 +822,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           const int lex = l0 + 32 * u;
           if (lex < b0.rows) {
             const T xj = xv[u] + t0[lex];
-            atomicAdd(z + G[u], xj);
+            atomicAdd(z + G[u], w[u] * xj);
             if (a.tout && sh == 0) t0[lex] = xj;
           }
         }
@@ -815,7 +832,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
     if (a.tout && sh == 0) {   // residual left on an interior patch, for the learned correction
       T* prev = vec + (b0.A + 1);
       T* tmp = prev + AB0 + (b0.A + 1);
-      resid0_inplace<DIM, T>(b0, lv0, rg0, nullptr, t0, prev, tmp, nullptr);
+      resid0_inplace<DIM, T>(b0, lv0, rg0, nullptr, t0, prev, tmp, nullptr, a.wp);
       T* dst = (T*)a.tout + jo * a.vstride;
       for (int lex = lane; lex < b0.rows; lex += 32) dst[lex] = t0[lex];
       __syncwarp();
@@ -1135,6 +1152,7 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
   a.porder = c->d_porder;
   a.conv = c->conv_flag;
   a.plist = nullptr; a.nlist = 0; a.rloc = nullptr; a.xloc = nullptr; a.vstride = 0; a.tout = nullptr;
+  a.wp = c->opt.weighting ? c->p : 0;
   const WarpLayout w = warp_layout<T, FT>(c);
   a.slot_bytes = w.slot_bytes;
   a.tab_ints = w.tab_ints;
@@ -1277,10 +1295,12 @@ lor_status lor_patch_local32(lor_ctx* c, const int* plist, int nlist, const floa
   if (c->d_F16) {
     fill_patch_args<float, __nv_bfloat16>(c, a, c->d_F16);
     a.plist = plist; a.nlist = nlist; a.rloc = rloc; a.xloc = xloc; a.vstride = vstride;
+    a.wp = 0;   // patch-local problems: unit weights
     return launch_patch_kernel<float, __nv_bfloat16>(c, a);
   }
   fill_patch_args<float, float>(c, a, c->d_F32);
   a.plist = plist; a.nlist = nlist; a.rloc = rloc; a.xloc = xloc; a.vstride = vstride;
+  a.wp = 0;   // patch-local problems: unit weights
   return launch_patch_kernel<float, float>(c, a);
 }
 

@@ -121,6 +121,7 @@ void lor_default_options(lor_options* o) {
   o->max_it = 1000;
   o->inner_rtol = 1e-3;
   o->factor_bf16 = 0;
+  o->weighting = 0;
 }
 
 lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* vertices, const double* kappa,
@@ -133,6 +134,7 @@ lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* verti
   if (opt->disc != LOR_CG && opt->disc != LOR_DG_IP && opt->disc != LOR_DG_BR2) return LOR_EINVAL;
   if (opt->disc != LOR_CG && (opt->dim != 3 || !(opt->eta > 0))) return LOR_EINVAL;
   if (!(opt->rtol > 0) || opt->max_it < 1) return LOR_EINVAL;
+  if (opt->weighting != 0 && opt->weighting != 1) return LOR_EINVAL;
   lor_ctx* c = new (std::nothrow) lor_ctx();
   if (!c) return LOR_ENOMEM;
   c->opt = *opt;

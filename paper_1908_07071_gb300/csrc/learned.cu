@@ -409,6 +409,8 @@ lor_status lor_learned_params(lor_ctx* c, const float* h_in, float* h_out, int c
 
 lor_status lor_learned_enable(lor_ctx* c, int on) {
   if (!c || !c->setup_done) return LOR_EINVAL;
+  // the correction is trained on the residuals of the unit-weight patch cycle
+  if (on && c->opt.weighting) return lor_fail(c, LOR_EINVAL, "learned correction needs unit patch weights");
   lor_status st = learned_init(c);
   if (st) return st;
   c->learned_on = on != 0 && LS(c)->nint > 0;

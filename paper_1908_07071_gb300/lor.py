@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("p", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("disc", ctypes.c_int), ("eta", ctypes.c_double),
                 ("mg_levels", ctypes.c_int), ("prec", ctypes.c_int), ("rtol", ctypes.c_double),
-                ("max_it", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("factor_bf16", ctypes.c_int)]
+                ("max_it", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("factor_bf16", ctypes.c_int),
+                ("weighting", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -123,7 +124,7 @@ class Solver:
     """One LOR-preconditioned problem on the current CUDA device and stream."""
 
     def __init__(self, vertices, kappa, p, *, mg_levels=0, prec=LOR_FP64, rtol=1e-8, max_it=1000,
-                 inner_rtol=1e-3, factor_bf16=False, disc=LOR_CG, eta=1.0, stream=None):
+                 inner_rtol=1e-3, factor_bf16=False, disc=LOR_CG, eta=1.0, weighting=0, stream=None):
         import torch
         self.lib = load()
         vertices = np.ascontiguousarray(vertices, dtype=np.float64)
@@ -138,6 +139,7 @@ class Solver:
         opt.mg_levels, opt.prec, opt.rtol, opt.max_it = mg_levels, prec, rtol, max_it
         opt.inner_rtol, opt.factor_bf16 = inner_rtol, int(bool(factor_bf16))
         opt.disc, opt.eta = disc, eta
+        opt.weighting = int(weighting)
         self.opt = opt
         self.dim, self.p, self.n = dim, p, tuple(n)
         if stream is None:

@@ -123,3 +123,45 @@ def test_hybrid_schwarz_is_spd_and_close_to_additive():
         ita = krylov.pcg(A, B.apply, b, rtol=1e-8)[1]
         ith = krylov.pcg(A, B.apply_hybrid, b, rtol=1e-8)[1]
         assert abs(ith - ita) <= 0.15 * ita, (ita, ith)
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, 3, 4), (3, 2, 3), (3, 3, 2)])
+def test_count_weights_closed_form(dim, n, p):
+    """The patch count of a node is 2 per axis along which it lies strictly inside an
+    element and 1 per axis on a vertex plane (the form the GPU kernel evaluates),
+    checked against the oracle's enumeration of the patches."""
+    v, k = make_mesh(dim, n, seed=0, perturb=0.15)
+    B = olor.LORPreconditioner(Mesh(v, k), p, weighting="count", coarse=False)
+    N = cg.node_shape(B.mesh.n, p)
+    idx = np.array(np.unravel_index(np.arange(int(np.prod(N))), tuple(reversed(N)))[::-1]).T
+    c = np.sum(idx % p != 0, axis=1)
+    inner = ~cg.boundary_mask(N)
+    closed = np.where(inner, 1.0 / np.sqrt(2.0 ** c), 0.0)
+    assert np.allclose(B.count_weights(), closed, atol=1e-15)
+
+
+def test_count_weighting_is_spd_and_reduces_iterations():
+    """Counting-matrix weighting (D^{-1/2} on both sides of the patch sum): SPD, and
+    far fewer iterations than unit weights on a perturbed 3D mesh with log-normal b."""
+    v, k = make_mesh(3, 3, seed=0, perturb=0.15)
+    m = Mesh(v, k)
+    p = 3
+    N = cg.node_shape(m.n, p)
+    K = cg.assemble_stiffness(m, p)
+    b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+    A = lambda u: cg.apply_A(K, N, u)  # noqa: E731
+    it1 = krylov.pcg(A, olor.LORPreconditioner(m, p).apply, b, rtol=1e-8)[1]
+    Bw = olor.LORPreconditioner(m, p, weighting="count")
+    itw = krylov.pcg(A, Bw.apply, b, rtol=1e-8)[1]
+    assert itw <= 0.6 * it1, (it1, itw)
+    v2, k2 = make_mesh(2, 3, seed=1, perturb=0.15)
+    m2 = Mesh(v2, k2)
+    B2 = olor.LORPreconditioner(m2, 3, weighting="count")
+    N2 = cg.node_shape(m2.n, 3)
+    inner = ~cg.boundary_mask(N2)
+    n = inner.sum()
+    E = np.zeros((len(inner), n))
+    E[np.nonzero(inner)[0], np.arange(n)] = 1.0
+    M = np.column_stack([B2.apply(E[:, c])[inner] for c in range(n)])
+    assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
