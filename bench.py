@@ -435,6 +435,27 @@ def main():
             extras["fp64_plain"] = {"time_to_tol_ms": f0.elapsed_time(f1), "iterations": it64,
                                     "rel_res": rel64, "chosen_vs_fp64_x_rel_diff": dx,
                                     "speedup_chosen_vs_fp64": f0.elapsed_time(f1) / ms_per_step}
+        # the chosen form with the counting-matrix weighted patch sum (an option beyond
+        # the paper's unit weights; context only, the headline keeps unit weights)
+        try:
+            s.set_weighting(1)
+            xw = torch.zeros_like(b)
+            s.solve(b, xw)
+            w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            xw.zero_()
+            w0.record(stream)
+            itw, relw = s.solve(b, xw)
+            w1.record(stream)
+            torch.cuda.synchronize()
+            extras["count_weighted"] = {"time_to_tol_ms": w0.elapsed_time(w1), "iterations": itw, "rel_res": relw,
+                                        "speedup_vs_unit_weights": ms_per_step / w0.elapsed_time(w1)}
+        except Exception as exc:   # an optional leg must not hide the main result
+            extras["count_weighted"] = {"error": f"{type(exc).__name__}: {exc}"}
+        finally:
+            try:
+                s.set_weighting(0)
+            except Exception:
+                pass
 
     # roofline of the dominant kernel class inside the timed region
     pk = peaks()

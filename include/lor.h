@@ -137,6 +137,12 @@ lor_status lor_pcg_solve_host(lor_ctx* ctx, const double* h_b, double* h_x,
  * keeps FP64 and FP32 (and, if requested, bf16) data, so no setup is redone. */
 lor_status lor_set_prec(lor_ctx* ctx, int prec);
 
+/* Switches the patch-sum weighting of lor_options.weighting (0 unit weights,
+ * 1 counting matrix) for later calls; the weights are evaluated inside the
+ * patch kernel, so no setup is redone.  LOR_EINVAL for other values or if the
+ * learned correction is enabled (it is trained for unit weights). */
+lor_status lor_set_weighting(lor_ctx* ctx, int weighting);
+
 /* Number of kernels this context has launched so far (all entry points). */
 lor_status lor_launch_count(const lor_ctx* ctx, long long* count);
 

@@ -281,6 +281,14 @@ lor_status lor_pcg_solve_host(lor_ctx* c, const double* hb, double* hx, int* ite
   return s;
 }
 
+lor_status lor_set_weighting(lor_ctx* c, int weighting) {
+  if (!c) return LOR_EINVAL;
+  if (weighting != 0 && weighting != 1) return lor_fail(c, LOR_EINVAL, "lor_set_weighting: 0 or 1");
+  if (weighting && c->learned_on) return lor_fail(c, LOR_EINVAL, "learned correction needs unit patch weights");
+  c->opt.weighting = weighting;
+  return LOR_OK;
+}
+
 lor_status lor_set_prec(lor_ctx* c, int prec) {
   if (!c) return LOR_EINVAL;
   if (prec != LOR_FP64 && prec != LOR_MIXED) return lor_fail(c, LOR_EINVAL, "lor_set_prec: LOR_FP64 or LOR_MIXED");

@@ -90,10 +90,11 @@ def load():
     lib.lor_device_status.argtypes = [vp]
     lib.lor_selftest_wait.argtypes = [vp, i]
     lib.lor_set_prec.argtypes = [vp, i]
+    lib.lor_set_weighting.argtypes = [vp, i]
     lib.lor_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.lor_profile.argtypes = [vp, i]
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
-    for name in ("lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
+    for name in ("lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -214,6 +215,10 @@ class Solver:
     def selftest_wait(self, polls=1 << 12):
         """Runs the bounded-wait self-test; returns the library status (LOR_ETIMEOUT expected)."""
         return self.lib.lor_selftest_wait(self.ctx, polls)
+
+    def set_weighting(self, weighting):
+        """0: unit patch weights (the paper's method); 1: counting-matrix weights."""
+        self._check(self.lib.lor_set_weighting(self.ctx, int(weighting)))
 
     def set_prec(self, prec):
         self._check(self.lib.lor_set_prec(self.ctx, prec))

@@ -41,3 +41,22 @@ def test_weighted_pcg_iterations_match_oracle():
     ito = krylov.pcg(lambda u: cg.apply_A(K, N, u), B.apply, b.cpu().numpy(), rtol=1e-8)[1]
     assert rel <= 1e-8 and abs(it - ito) <= 1, (it, ito)
     s.close()
+
+
+def test_set_weighting_toggles_on_one_context():
+    from paper_1908_07071_gb300 import lor
+    verts, kappa = make_mesh(3, 3, seed=5, perturb=0.15)
+    p = 3
+    s = lor.Solver(verts, kappa, p)
+    m = Mesh(verts, kappa)
+    r = random_vector(s.nvec, 41)
+    rd = torch.from_numpy(r).cuda()
+    z = torch.empty(s.nvec, dtype=torch.float64, device="cuda")
+    for w, kind in ((1, "count"), (0, "none")):
+        s.set_weighting(w)
+        s.apply_P(rd, z)
+        zr = olor.LORPreconditioner(m, p, weighting=kind).apply(r)
+        assert np.abs(z.cpu().numpy() - zr).max() <= 1e-10 * np.abs(zr).max()
+    with pytest.raises(lor.LorError):
+        s.set_weighting(2)
+    s.close()
