@@ -244,8 +244,8 @@ def leg_batch(nsolves, rank):
 # ----------------------------------------------------------------- DG leg
 def leg_dg():
     """3D SIPG and BR2 on a 24^3 perturbed mesh, p=4, log-normal kappa: iterations of
-    B_DG-preconditioned CG for eta in {1,10,100,1000} x eta_min (FP64), and DG per-apply
-    throughput."""
+    B_DG-preconditioned CG for eta in {1,10,100,1000} x eta_min (FP64, mixed, and mixed with
+    the counting-matrix weighted patch sum), and DG per-apply throughput."""
     import torch
     from paper_1908_07071_gb300 import lor
     from paper_1908_07071_gb300.synthetic import make_mesh
@@ -285,6 +285,20 @@ def leg_dg():
             e1.record()
             torch.cuda.synchronize()
             row.update({"iterations_mixed": it2, "time_ms_mixed": e0.elapsed_time(e1), "rel_res_mixed": rel2})
+            # the same mixed solve with the counting-matrix weighted patch sum (option beyond the paper)
+            try:
+                s.set_weighting(1)
+                x3 = torch.zeros_like(b)
+                e0.record()
+                it3, rel3 = s.solve(b, x3)
+                e1.record()
+                torch.cuda.synchronize()
+                row.update({"iterations_mixed_count_weighted": it3, "time_ms_mixed_count_weighted": e0.elapsed_time(e1),
+                            "rel_res_mixed_count_weighted": rel3})
+            except lor.LorError as exc:
+                row["count_weighted_error"] = str(exc)
+            finally:
+                s.set_weighting(0)
             if mult == 10.0:
                 xa = torch.randn(s.nvec, dtype=torch.float64, device="cuda")
                 ya = torch.empty_like(xa)
