@@ -38,7 +38,9 @@ def test_create_validates_on_host(lib):
     st, ctx = _create(lib, opt, verts, kappa)
     assert st == lor.LOR_OK and ctx.value
     lib.lor_destroy(ctx)
-    for field, bad in (("p", 0), ("p", 9), ("dim", 4), ("nx", 0), ("rtol", 0.0), ("max_it", 0)):
+    assert opt.weighting == 0                       # the paper's unit patch weights by default
+    for field, bad in (("p", 0), ("p", 9), ("dim", 4), ("nx", 0), ("rtol", 0.0), ("max_it", 0),
+                       ("weighting", 2), ("weighting", -1)):
         o = lor.Options()
         ctypes.memmove(ctypes.byref(o), ctypes.byref(opt), ctypes.sizeof(o))
         setattr(o, field, bad)
@@ -61,4 +63,9 @@ def test_calls_before_setup_are_rejected(lib):
     assert lib.lor_apply_A(ctx, None, None, 0) == lor.LOR_ESTATE
     assert lib.lor_pcg_solve(ctx, None, None, None, None) == lor.LOR_ESTATE
     assert b"setup" in lib.lor_last_error(ctx)
+    assert lib.lor_device_status(ctx) == lor.LOR_ESTATE
+    assert lib.lor_selftest_wait(ctx, 16) == lor.LOR_ESTATE
+    # option switches are host state and may precede setup; bad values are refused
+    assert lib.lor_set_weighting(ctx, 1) == lor.LOR_OK
+    assert lib.lor_set_weighting(ctx, 3) == lor.LOR_EINVAL
     lib.lor_destroy(ctx)
