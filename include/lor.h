@@ -139,8 +139,10 @@ lor_status lor_set_prec(lor_ctx* ctx, int prec);
 
 /* Switches the patch-sum weighting of lor_options.weighting (0 unit weights,
  * 1 counting matrix) for later calls; the weights are evaluated inside the
- * patch kernel, so no setup is redone.  LOR_EINVAL for other values or if the
- * learned correction is enabled (it is trained for unit weights). */
+ * patch kernel, so no setup is redone.  A batch (lor_batch_create) keeps the
+ * setting its contexts had when its CUDA graph was captured (first
+ * lor_batch_solve).  LOR_EINVAL for other values or if the learned correction
+ * is enabled (it is trained for unit weights). */
 lor_status lor_set_weighting(lor_ctx* ctx, int weighting);
 
 /* Number of kernels this context has launched so far (all entry points). */
