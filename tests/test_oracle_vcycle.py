@@ -1,0 +1,92 @@
+"""Pins of the oracle's element-structured patch hierarchy and V(1,1) cycle (Section 3.3).
+
+Three facts fixed by the mathematics, each checked on interior, edge and corner
+patches of distorted 2D and 3D meshes:
+
+* the 1D prolongation interpolates linearly in the element reference coordinate, so
+  it reproduces constants and the reference coordinate itself;
+* the patch blocks of the global Galerkin levels are Galerkin on the patch: a coarse
+  hat function of an interior patch node vanishes on the patch boundary, so
+  P_j^T A_j^l P_j = A_j^{l+1} with P_j the patch block of the global prolongation;
+* the V(1,1) cycle with ILU(0) smoother M_l = L_l U_l and an exact solve on the
+  vertex level has the textbook error propagation
+  I - V_l A_l = (I - M_l^{-1} A_l)(I - P_l V_{l+1} P_l^T A_l)(I - M_l^{-1} A_l),
+  V_last = A_last^{-1}; a dropped residual update, a restriction by P instead of
+  P^T or a missing coarse correction all break it.
+"""
+import numpy as np
+import pytest
+
+from oracle import basis, lor
+from oracle.mesh import Mesh
+from paper_1908_07071_gb300.synthetic import make_mesh
+
+
+def _patches(dim, n, p, seed, mg=0):
+    v, k = make_mesh(dim, n, seed=seed, perturb=0.15)
+    B = lor.LORPreconditioner(Mesh(v, k), p, mg_levels=mg, coarse=False)
+    return B
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 8])
+def test_prolongation_reproduces_linears_in_reference_coordinate(p):
+    xg = basis.gll(p)[0]          # GLL points mapped to [0, 1]
+    sels = lor.level_selections(p)
+    nel = 3
+    for l in range(len(sels) - 1):
+        P = lor.prolong_1d(nel, p, sels[l], sels[l + 1])
+        # reference coordinate (element index + local GLL point) on both grids
+        xf = np.concatenate([[0.0]] + [e + xg[sels[l][1:]] for e in range(nel)])
+        xc = np.concatenate([[0.0]] + [e + xg[sels[l + 1][1:]] for e in range(nel)])
+        np.testing.assert_allclose(P @ np.ones(len(xc)), 1.0, atol=1e-14)
+        np.testing.assert_allclose(P @ xc, xf, atol=1e-13)
+        # kept points are injected, so every column has a unit entry
+        assert np.all(np.isclose(P, 1.0).sum(axis=0) == 1)
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, 3, 6), (3, 2, 4), (3, 3, 3)])
+def test_patch_levels_are_galerkin_on_the_patch(dim, n, p):
+    B = _patches(dim, n, p, seed=3)
+    checked = 0
+    for pt in B.patches:
+        lv = pt["levels"]
+        for l in range(len(lv) - 1):
+            A, P, Ac = lv[l]["A"], lv[l]["P"], lv[l + 1]["A"]
+            if Ac.shape[0] == 0:
+                continue
+            scale = np.abs(A).max()
+            np.testing.assert_allclose(P.T @ A @ P, Ac, atol=1e-12 * scale)
+            checked += 1
+    assert checked >= len(B.patches)
+
+
+def _vcycle_matrix(B, levels, l):
+    m = levels[l]["A"].shape[0]
+    return np.column_stack([B.vcycle(levels, l, c) for c in np.eye(m)]) if m else np.zeros((0, 0))
+
+
+@pytest.mark.parametrize("dim,n,p,mg", [(2, 3, 8, 0), (2, 2, 4, 2), (3, 2, 4, 0), (3, 2, 6, 0)])
+def test_vcycle_error_propagation_is_the_textbook_product(dim, n, p, mg):
+    B = _patches(dim, n, p, seed=5, mg=mg)
+    corner = tuple([0] * dim)
+    interior = tuple([1] * dim)
+    for pt in B.patches:
+        if pt["v"] not in (corner, interior):
+            continue
+        lv = pt["levels"]
+        L = len(lv)
+        A_last = lv[L - 1]["A"]
+        V_next = np.linalg.inv(A_last) if A_last.shape[0] else np.zeros((0, 0))
+        for l in range(L - 2, -1, -1):
+            A, P = lv[l]["A"], lv[l]["P"]
+            m = A.shape[0]
+            Lf, Uf = lv[l]["LU"]
+            S = np.eye(m) - np.linalg.solve(Lf @ Uf, A)
+            C = np.eye(m) - P @ V_next @ P.T @ A
+            E = S @ C @ S
+            V = _vcycle_matrix(B, lv, l)
+            np.testing.assert_allclose(np.eye(m) - V @ A, E, atol=1e-10)
+            V_next = V
+        # vertex level: an interior patch keeps its own vertex; the patch of a corner
+        # vertex keeps none (its vertex is a Dirichlet node), so it has no coarse correction
+        assert A_last.shape == ((1, 1) if pt["v"] == interior else (0, 0))
