@@ -8,6 +8,9 @@ patches of distorted 2D and 3D meshes:
 * the patch blocks of the global Galerkin levels are Galerkin on the patch: a coarse
   hat function of an interior patch node vanishes on the patch boundary, so
   P_j^T A_j^l P_j = A_j^{l+1} with P_j the patch block of the global prolongation;
+* the coarse-space basis P_0 (Section 3.2) is Q1 on each element of T_p evaluated at
+  the GLL nodes, and each coordinate of the multilinear element map is such a Q1
+  function, so P_0 maps the vertex coordinates onto the node coordinates;
 * the V(1,1) cycle with ILU(0) smoother M_l = L_l U_l and an exact solve on the
   vertex level has the textbook error propagation
   I - V_l A_l = (I - M_l^{-1} A_l)(I - P_l V_{l+1} P_l^T A_l)(I - M_l^{-1} A_l),
@@ -17,7 +20,7 @@ patches of distorted 2D and 3D meshes:
 import numpy as np
 import pytest
 
-from oracle import basis, lor
+from oracle import basis, cg, lor
 from oracle.mesh import Mesh
 from paper_1908_07071_gb300.synthetic import make_mesh
 
@@ -90,3 +93,17 @@ def test_vcycle_error_propagation_is_the_textbook_product(dim, n, p, mg):
         # vertex level: an interior patch keeps its own vertex; the patch of a corner
         # vertex keeps none (its vertex is a Dirichlet node), so it has no coarse correction
         assert A_last.shape == ((1, 1) if pt["v"] == interior else (0, 0))
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, 3, 5), (3, 2, 4)])
+def test_coarse_basis_maps_vertex_coordinates_to_node_coordinates(dim, n, p):
+    v, k = make_mesh(dim, n, seed=7, perturb=0.2)
+    m = Mesh(v, k)
+    B = lor.LORPreconditioner(m, p, patch_subset=[])
+    X = cg.node_coordinates(m, p)
+    for a in range(dim):
+        np.testing.assert_allclose(B.P0 @ m.vertices[a].ravel(), X[:, a], atol=1e-13)
+    np.testing.assert_allclose(B.P0 @ np.ones(B.P0.shape[1]), 1.0, atol=1e-14)
+    # without Dirichlet rows the coarse operator keeps the constants in its kernel
+    A0 = (B.P0.T @ B.K_h @ B.P0).toarray()
+    assert np.abs(A0 @ np.ones(A0.shape[0])).max() <= 1e-12 * np.abs(A0).max()
