@@ -64,7 +64,42 @@ def parse():
     ap.add_argument("--no-dg", action="store_true", help="skip the DG penalty-sweep leg")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--summarize-ncu", metavar="CSV",
+                    help="print per-kernel launches, total time and share of an ncu launch list "
+                         "(--metrics gpu__time_duration.sum --csv) and exit")
     return ap.parse_args()
+
+
+def summarize_ncu_launches(path: str) -> str:
+    """Per kernel of an ncu launch list: launches, total device time (ms) and share."""
+    import csv
+    import re
+    from collections import defaultdict
+    rows = list(csv.reader(open(path)))
+    hdr = None
+    for i, r in enumerate(rows):
+        if "Kernel Name" in r and "Metric Name" in r:
+            hdr, rows = r, rows[i + 1:]
+            break
+    if hdr is None:
+        raise ValueError(f"{path}: no ncu CSV header (Kernel Name, Metric Name)")
+    k_name, k_metric, k_val, k_unit = (hdr.index(x) for x in ("Kernel Name", "Metric Name", "Metric Value",
+                                                             "Metric Unit"))
+    to_ms = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0, "msecond": 1.0}
+    tot, cnt = defaultdict(float), defaultdict(int)
+    for r in rows:
+        if len(r) <= k_val or r[k_metric] != "gpu__time_duration.sum":
+            continue
+        name = re.sub(r"\(.*", "", r[k_name]).replace("void ", "").strip()
+        name = re.sub(r"<unnamed>::|\(anonymous namespace\)::", "", name)
+        tot[name] += float(r[k_val].replace(",", "")) * to_ms.get(r[k_unit], 1.0)
+        cnt[name] += 1
+    all_ms = sum(tot.values())
+    out = [f"{'kernel':70s} {'launches':>9s} {'total ms':>11s} {'share':>7s}"]
+    for name in sorted(tot, key=lambda n: -tot[n]):
+        out.append(f"{name[:70]:70s} {cnt[name]:9d} {tot[name]:11.3f} {100 * tot[name] / all_ms:6.2f}%")
+    out.append(f"{'all':70s} {sum(cnt.values()):9d} {all_ms:11.3f}")
+    return "\n".join(out)
 
 
 # --------------------------------------------------------------------- CPU leg
@@ -332,6 +367,9 @@ def peaks():
 
 def main():
     args = parse()
+    if args.summarize_ncu:
+        print(summarize_ncu_launches(args.summarize_ncu))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
