@@ -166,11 +166,61 @@ def ilu_solve(L, U, r):
 
 
 # ------------------------------------------------------------- patches (3.2)
-def patch_range_1d(v: int, nel: int, m: int):
-    """Global level indices of the open interior of the patch of vertex v (one axis)."""
-    lo = max(v - 1, 0) * m
-    hi = min(v + 1, nel) * m
+def patch_range_1d(v: int, nel: int, m: int, lo_k: int = 1, hi_k: int = 1):
+    """Global level indices of the open interior of the patch of vertex v (one axis).
+
+    The patch covers the elements v - lo_k, ..., v + hi_k - 1 of the axis (clamped to
+    the mesh); lo_k = hi_k = 1 is the vertex patch of Eq. (patch)."""
+    lo = max(v - lo_k, 0) * m
+    hi = min(v + hi_k, nel) * m
     return np.arange(lo + 1, hi)
+
+
+def isotropic_overlap_spans(mesh: Mesh, ratio: float = 0.5):
+    """Element spans of vertex patches enlarged so that their overlap stays isotropic.
+
+    Section 5.5 extends the patches that contain high-aspect-ratio elements so that the
+    overlap no longer shrinks with the aspect ratio (the partition-of-unity argument
+    behind the lemma on the local decomposition in Section 3.2 needs overlap of the
+    size of the elements, not of their thin side).  The paper does not state the rule;
+    reading: the isotropic size of vertex v is the longest mesh edge at v, and along
+    each axis and side the patch takes whole elements until the vertex it reaches lies
+    at least ratio x that size from v (or the boundary is reached).  On meshes whose
+    edges at a vertex differ by less than 1/ratio this is the vertex patch itself.
+    Returns {vertex multi-index: [(lo_k, hi_k) per axis]}.
+    """
+    d, n = mesh.dim, mesh.n
+
+    def X(idx):
+        return mesh.vertices[(slice(None),) + tuple(reversed(idx))]
+
+    spans = {}
+    for t in itertools.product(*[range(v + 1) for v in reversed(n)]):
+        v = tuple(reversed(t))
+        x0 = X(v)
+        edges = []
+        for a in range(d):
+            for s in (-1, 1):
+                w = list(v)
+                w[a] += s
+                if 0 <= w[a] <= n[a]:
+                    edges.append(np.linalg.norm(X(w) - x0))
+        target = ratio * max(edges)
+        per_axis = []
+        for a in range(d):
+            ks = []
+            for s in (-1, 1):
+                k = 1
+                while True:
+                    w = list(v)
+                    w[a] += s * k
+                    if w[a] <= 0 or w[a] >= n[a] or np.linalg.norm(X(w) - x0) >= target:
+                        break
+                    k += 1
+                ks.append(k)
+            per_axis.append(tuple(ks))
+        spans[v] = per_axis
+    return spans
 
 
 def box_indices(ranges, N):
@@ -197,8 +247,11 @@ class LORPreconditioner:
 
     def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0,
                  exact_local: bool = False, exact_coarse: bool = False, K_h=None,
-                 patch_subset=None, coarse=True, ordering: str = "lex", weighting: str = "none"):
+                 patch_subset=None, coarse=True, ordering: str = "lex", weighting: str = "none",
+                 patch_spans=None):
         """patch_subset: vertex multi-indices whose patches are built (default all);
+        patch_spans: {vertex: [(lo_k, hi_k) per axis]} element spans of enlarged patches
+        (`isotropic_overlap_spans`, Section 5.5); vertices not listed keep the vertex patch;
         coarse=False skips the coarse space (for checks of the patch part alone);
         ordering: ILU(0) ordering of every patch level, "lex" (patch-lexicographic),
         "mdf" or "rcm" (Section 3.4, `oracle.ordering`);
@@ -206,6 +259,7 @@ class LORPreconditioner:
         both sides by D^{-1/2}, D = number of patches containing each node (the counting
         matrix Section 5.1 names as future work)."""
         self.ordering = ordering
+        self.patch_spans = patch_spans or {}
         if weighting not in ("none", "count"):
             raise ValueError(f"unknown weighting {weighting!r}")
         self.weighting = weighting
@@ -242,8 +296,9 @@ class LORPreconditioner:
             if self.patch_subset is not None and tuple(v) not in self.patch_subset:
                 continue
             levels = []
+            span = self.patch_spans.get(tuple(v), [(1, 1)] * self.dim)
             for l in range(L):
-                ranges = [patch_range_1d(v[a], self.mesh.n[a], self.ms[l]) for a in range(self.dim)]
+                ranges = [patch_range_1d(v[a], self.mesh.n[a], self.ms[l], *span[a]) for a in range(self.dim)]
                 idx = box_indices(ranges, self.Ns[l])
                 Aj = self.A[l][idx][:, idx].toarray() if len(idx) else np.zeros((0, 0))
                 lev = {"ranges": ranges, "idx": idx, "A": Aj}
@@ -256,7 +311,8 @@ class LORPreconditioner:
                         lev["LU"] = ilu0(Aj[np.ix_(perm, perm)], pat[np.ix_(perm, perm)])
                         lev["perm"] = perm
                 if l < L - 1:
-                    rc = [patch_range_1d(v[a], self.mesh.n[a], self.ms[l + 1]) for a in range(self.dim)]
+                    rc = [patch_range_1d(v[a], self.mesh.n[a], self.ms[l + 1], *span[a])
+                          for a in range(self.dim)]
                     mats = [self.P1[l][a][np.ix_(ranges[a], rc[a])] for a in range(self.dim)]
                     lev["P"] = kron_nd(mats).toarray() if all(len(r) for r in ranges + rc) \
                         else np.zeros((len(idx), int(np.prod([len(r) for r in rc]))))

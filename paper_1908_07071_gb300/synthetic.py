@@ -115,6 +115,41 @@ def make_mesh(dim: int, n, seed: int = 0, perturb: float = 0.15,
     return np.ascontiguousarray(verts), np.ascontiguousarray(kappa)
 
 
+def make_strip_mesh(n: int, aspect: float, layers: int = 4, seed: int = 0, perturb: float = 0.0):
+    """2D unit-square mesh of n x n elements with a strip of thin elements (Section 5.5).
+
+    The `layers` element rows around y = 1/2 have height h/aspect (h = 1/n, the
+    element width), so their aspect ratio is `aspect`; the other rows split the rest
+    of [0,1] equally, half below and half above the strip.  Each interior vertex
+    column moves along x as a whole, by U(-perturb*h, perturb*h), so every element
+    stays a rectangle (a per-vertex shift would shear the thin elements by up to
+    2*perturb*aspect).
+    kappa = 1 (the constant-coefficient problem of that section).
+    Returns (vertices, kappa) in the layouts of the module docstring.
+    """
+    n, layers = int(n), int(layers)
+    if not 1 <= layers <= n - 2:
+        raise ValueError("need 1 <= layers <= n - 2")
+    h = 1.0 / n
+    delta = h / float(aspect)
+    y0 = 0.5 - 0.5 * layers * delta
+    y1 = 0.5 + 0.5 * layers * delta
+    if y0 <= 0.0:
+        raise ValueError("strip thicker than the domain")
+    nb = (n - layers) // 2
+    na = n - layers - nb
+    ys = np.concatenate([np.linspace(0.0, y0, nb + 1)[:-1], np.linspace(y0, y1, layers + 1),
+                         np.linspace(y1, 1.0, na + 1)[1:]])
+    xs = np.linspace(0.0, 1.0, n + 1)
+    verts = np.empty((2, n + 1, n + 1))
+    verts[0] = xs[None, :]
+    verts[1] = ys[:, None]
+    if perturb != 0.0:
+        u = uniform01(stream_key(seed, TAG_VERTS), n + 1)
+        verts[0, :, 1:-1] += ((2.0 * u[1:-1] - 1.0) * perturb * h)[None, :]
+    return np.ascontiguousarray(verts), np.ones((n, n))
+
+
 def random_vector(shape, seed: int, tag: int = 7) -> np.ndarray:
     """Seeded N(0,1) test vector (e.g. an input x for operator parity tests)."""
     cnt = int(np.prod(shape))
