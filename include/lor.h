@@ -75,9 +75,11 @@ typedef struct {
  * unit patch weights. */
 void lor_default_options(lor_options* opt);
 
-/* Creates a context for the mesh (Section 2).  Validates sizes, copies the host
- * mesh arrays to the device, checks every element for det J > 0 at its
- * quadrature points (LOR_EINVAL otherwise).  stream: a cudaStream_t or NULL. */
+/* Creates a context for the mesh (Section 2).  Validates the options and sizes
+ * (element count and vertex count x dim at most INT_MAX), copies the host mesh
+ * arrays into the context and rejects non-finite vertices and kappa <= 0
+ * (LOR_EINVAL); LOR_ENOMEM if the host copy cannot be allocated.  No CUDA call
+ * is made here.  stream: a cudaStream_t or NULL. */
 lor_status lor_create(lor_ctx** ctx, const lor_options* opt,
                       const double* vertices, const double* kappa, void* stream);
 
@@ -85,8 +87,11 @@ lor_status lor_create(lor_ctx** ctx, const lor_options* opt,
  * factors of the sum-factorized operator, the LOR matrix K_h as a 3^d-point
  * stencil, Galerkin level stencils of the element-structured hierarchy, the
  * lexicographic ILU(0) factors of every vertex patch at every level, and the
- * coarse-space hierarchy.  Allocates all device memory of the context.
- * LOR_EBREAKDOWN if any ILU(0) pivot is not positive. */
+ * coarse-space hierarchy.  Allocates all device memory of the context and
+ * uploads the mesh.  LOR_EINVAL if an element has det J <= 0 at a quadrature
+ * point, LOR_EBREAKDOWN if any ILU(0) pivot is not positive.  A failed setup
+ * is not retried: later lor_setup calls return LOR_ESTATE (destroy the
+ * context). */
 lor_status lor_setup(lor_ctx* ctx);
 
 typedef struct {

@@ -1,4 +1,5 @@
 // C ABI of the LOR solver (declared in include/lor.h).
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -135,6 +136,10 @@ lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* verti
   if (opt->disc != LOR_CG && (opt->dim != 3 || !(opt->eta > 0))) return LOR_EINVAL;
   if (!(opt->rtol > 0) || opt->max_it < 1) return LOR_EINVAL;
   if (opt->weighting != 0 && opt->weighting != 1) return LOR_EINVAL;
+  // element and vertex counts are ints in the kernels' index arithmetic
+  const long long nel_ll = (long long)opt->nx * opt->ny * (opt->dim == 3 ? opt->nz : 1);
+  const long long nv_ll = (long long)(opt->nx + 1) * (opt->ny + 1) * (opt->dim == 3 ? opt->nz + 1 : 1);
+  if (nel_ll > INT_MAX || nv_ll * opt->dim > INT_MAX) return LOR_EINVAL;
   lor_ctx* c = new (std::nothrow) lor_ctx();
   if (!c) return LOR_ENOMEM;
   c->opt = *opt;
@@ -145,9 +150,13 @@ lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* verti
   c->n[2] = opt->dim == 3 ? opt->nz : 1;
   c->nel = c->n[0] * c->n[1] * c->n[2];
   c->stream = (cudaStream_t)stream;
-  const long long NV = (long long)(c->n[0] + 1) * (c->n[1] + 1) * (c->dim == 3 ? c->n[2] + 1 : 1);
-  c->h_vert.assign(vertices, vertices + NV * c->dim);
-  c->h_kappa.assign(kappa, kappa + c->nel);
+  try {
+    c->h_vert.assign(vertices, vertices + nv_ll * c->dim);
+    c->h_kappa.assign(kappa, kappa + c->nel);
+  } catch (const std::bad_alloc&) {
+    delete c;
+    return LOR_ENOMEM;
+  }
   for (double k : c->h_kappa)
     if (!(k > 0) || !std::isfinite(k)) {
       delete c;
@@ -165,6 +174,9 @@ lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* verti
 lor_status lor_setup(lor_ctx* c) {
   if (!c) return LOR_EINVAL;
   if (c->setup_done) return lor_fail(c, LOR_ESTATE, "lor_setup called twice");
+  if (c->setup_started)
+    return lor_fail(c, LOR_ESTATE, "an earlier lor_setup failed; destroy the context and create a new one");
+  c->setup_started = true;
   lor_status s;
   if ((s = lor_setup_geometry(c))) return s;
   if ((s = lor_setup_stencils(c))) return s;

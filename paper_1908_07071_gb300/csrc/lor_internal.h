@@ -83,6 +83,7 @@ struct lor_ctx {
   cudaStream_t stream;
   std::string err;
   bool setup_done = false;
+  bool setup_started = false;   // a failed lor_setup leaves partial state: no retry
 
   // mesh
   double* d_vert = nullptr;   // SoA dim x NV

@@ -51,6 +51,11 @@ def test_create_validates_on_host(lib):
     nan_verts = verts.copy()
     nan_verts.flat[5] = np.nan
     assert _create(lib, opt, nan_verts, kappa)[0] == lor.LOR_EINVAL
+    # element counts beyond the kernels' int index range are refused before any array is read
+    big = lor.Options()
+    ctypes.memmove(ctypes.byref(big), ctypes.byref(opt), ctypes.sizeof(big))
+    big.nx = big.ny = big.nz = 1300                      # 2.2e9 elements
+    assert _create(lib, big, verts, kappa)[0] == lor.LOR_EINVAL
 
 
 def test_calls_before_setup_are_rejected(lib):
