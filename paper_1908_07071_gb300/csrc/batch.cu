@@ -314,7 +314,10 @@ lor_status lor_batch_solve(lor_batch* b, const double* const* d_b, double* const
     b->xs.assign(d_x, d_x + n);
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return LOR_ECUDA;
-    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LOR_ECUDA;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      return LOR_ECUDA;
+    }
     cudaEventRecord(b->fork, cs);
     lor_status st = LOR_OK;
     for (int s = 0; s < n && !st; ++s) {
@@ -327,8 +330,11 @@ lor_status lor_batch_solve(lor_batch* b, const double* const* d_b, double* const
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
-    if (st) return st;
-    if (e != cudaSuccess) { cudaGetLastError(); b->err = cudaGetErrorString(e); return LOR_ECUDA; }
+    if (st || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) { cudaGetLastError(); b->err = cudaGetErrorString(e); }
+      return st ? st : LOR_ECUDA;
+    }
     b->graph = g;
     size_t nodes = 0;
     cudaGraphGetNodes(g, nullptr, &nodes);
@@ -344,9 +350,14 @@ lor_status lor_batch_solve(lor_batch* b, const double* const* d_b, double* const
   int it = 0;
   bool any_flag = false;
   for (; it < maxit; ++it) {
-    if (cudaGraphLaunch(b->exec, b->main) != cudaSuccess) return LOR_ECUDA;
-    cudaMemcpyAsync(b->h_flags, b->d_flags, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, b->main);
-    if (cudaStreamSynchronize(b->main) != cudaSuccess) return LOR_ECUDA;
+    if (cudaGraphLaunch(b->exec, b->main) != cudaSuccess ||
+        cudaMemcpyAsync(b->h_flags, b->d_flags, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, b->main) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->main) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return LOR_ECUDA;
+    }
     bool all = true;
     for (int s = 0; s < n; ++s) {
       all = all && b->h_flags[2 * s] != 0.0;
