@@ -58,13 +58,18 @@ def tensor_points(dim, pts1d, w1d):
 
 
 def element_stiffness(corners, kappa, p, q=None):
-    """Dense K_e[a,b] = sum_q w_q |det J_q| kappa grad phi_a . grad phi_b."""
+    """Dense K_e[a,b] = sum_q w_q |det J_q| kappa grad phi_a . grad phi_b.
+
+    kappa: the element's constant, or a callable b(X) of the physical points X (Q, d)
+    (the variable coefficients of Section 5.2), evaluated at the quadrature points."""
     dim = corners.shape[1]
     q = p + 1 if q is None else q
     x1, w1 = gauss_legendre(q)
     pts, w = tensor_points(dim, x1, w1)
     _, dphi = tensor_basis(dim, p, x1)
-    _, J = multilinear(corners, pts)
+    Xq, J = multilinear(corners, pts)
+    if callable(kappa):
+        kappa = np.asarray(kappa(Xq), dtype=np.float64)
     detJ = np.linalg.det(J)
     Jinv = np.linalg.inv(J)                      # (Q, d, d)
     # physical gradient: grad_x phi = J^{-T} grad_xi phi
@@ -99,13 +104,15 @@ def boundary_mask(N):
     return m.ravel()
 
 
-def assemble_stiffness(mesh: Mesh, p: int):
-    """Assembled K_p over all grid nodes (no Dirichlet elimination), CSR."""
+def assemble_stiffness(mesh: Mesh, p: int, coef=None):
+    """Assembled K_p over all grid nodes (no Dirichlet elimination), CSR.
+
+    coef: optional callable b(X) replacing the per-element kappa (Section 5.2)."""
     N = node_shape(mesh.n, p)
     ntot = int(np.prod(N))
     rows, cols, vals = [], [], []
     for e in mesh.elements():
-        Ke = element_stiffness(mesh.corners(e), mesh.kappa_of(e), p)
+        Ke = element_stiffness(mesh.corners(e), mesh.kappa_of(e) if coef is None else coef, p)
         idx = element_nodes(e, p, N)
         rows.append(np.repeat(idx, len(idx)))
         cols.append(np.tile(idx, len(idx)))

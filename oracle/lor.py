@@ -42,7 +42,10 @@ COARSE_SWEEPS = 2
 
 # --------------------------------------------------------------------------- K_h
 def q1_stiffness_batch(corners, kappa):
-    """Q1 element stiffness for a batch of cells: corners (C, 2^d, d) -> (C, 2^d, 2^d)."""
+    """Q1 element stiffness for a batch of cells: corners (C, 2^d, d) -> (C, 2^d, 2^d).
+
+    kappa: (C,) constants per cell, or a callable b(X) of physical points (C, d)
+    evaluated at each cell's Gauss points (Section 5.2 coefficients)."""
     C, nc, d = corners.shape
     g = 0.5 - 0.5 / np.sqrt(3.0)
     g1 = np.array([g, 1.0 - g])
@@ -65,12 +68,21 @@ def q1_stiffness_batch(corners, kappa):
         detJ = np.linalg.det(J)
         Jinv = np.linalg.inv(J)
         gphys = np.einsum("Cba,cb->Cca", Jinv, dN)         # J^{-T} dN
-        K += (w * np.abs(detJ) * kappa)[:, None, None] * np.einsum("Cia,Cja->Cij", gphys, gphys)
+        if callable(kappa):
+            Nc = np.array([np.prod([xi[a] if (c >> a) & 1 else 1.0 - xi[a] for a in range(d)])
+                           for c in range(nc)])
+            kq = np.asarray(kappa(np.einsum("Cca,c->Ca", corners, Nc)), dtype=np.float64)
+        else:
+            kq = kappa
+        K += (w * np.abs(detJ) * kq)[:, None, None] * np.einsum("Cia,Cja->Cij", gphys, gphys)
     return K
 
 
-def assemble_lor(mesh: Mesh, p: int):
-    """K_h over all nodes of the GLL-refined grid (no Dirichlet elimination), CSR."""
+def assemble_lor(mesh: Mesh, p: int, coef=None):
+    """K_h over all nodes of the GLL-refined grid (no Dirichlet elimination), CSR.
+
+    coef: optional callable b(X) replacing the parent element's kappa; reading: it is
+    evaluated at the 2-point Gauss points of every LOR sub-cell, like the geometry."""
     d = mesh.dim
     N = node_shape(mesh.n, p)
     X = node_coordinates(mesh, p)
@@ -82,7 +94,7 @@ def assemble_lor(mesh: Mesh, p: int):
         off = np.array([(c >> a) & 1 for a in range(d)])
         corner_ids[:, c] = ((cells + off) * strides).sum(axis=1)
     elem = cells // p
-    kap = mesh.kappa[tuple(elem[:, a] for a in reversed(range(d)))]
+    kap = mesh.kappa[tuple(elem[:, a] for a in reversed(range(d)))] if coef is None else coef
     Kc = q1_stiffness_batch(X[corner_ids], kap)
     rows = np.repeat(corner_ids, 2 ** d, axis=1).ravel()
     cols = np.tile(corner_ids, (1, 2 ** d)).ravel()

@@ -78,8 +78,8 @@ def ilu_apply(L, U, r):
 class SinglePatchPreconditioner:
     """B(1) r = one V(1,1) cycle of the element-structured hierarchy on the whole domain."""
 
-    def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0):
-        self.base = LORPreconditioner(mesh, p, mg_levels=mg_levels, patch_subset=[])
+    def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0, K_h=None):
+        self.base = LORPreconditioner(mesh, p, mg_levels=mg_levels, patch_subset=[], K_h=K_h)
         b = self.base
         self.L = len(b.A)
         self.mask = [~boundary_mask(N).ravel() for N in b.Ns]

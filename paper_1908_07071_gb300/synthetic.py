@@ -150,6 +150,14 @@ def make_strip_mesh(n: int, aspect: float, layers: int = 4, seed: int = 0, pertu
     return np.ascontiguousarray(verts), np.ones((n, n))
 
 
+def two_valued_kappa(n, seed: int = 0, high: float = 10.0, low: float = 1.0) -> np.ndarray:
+    """Piecewise-constant coefficient taking `high` or `low` on each element with equal
+    probability (the discontinuous coefficient b_4 of Section 5.2); layout as kappa."""
+    shape_e = tuple(reversed([int(v) for v in n]))
+    u = uniform01(stream_key(seed, TAG_KAPPA), int(np.prod(shape_e))).reshape(shape_e)
+    return np.where(u < 0.5, float(high), float(low))
+
+
 def random_vector(shape, seed: int, tag: int = 7) -> np.ndarray:
     """Seeded N(0,1) test vector (e.g. an input x for operator parity tests)."""
     cnt = int(np.prod(shape))
