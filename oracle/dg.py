@@ -76,6 +76,7 @@ def face_points(d, a, side, x1):
 
 
 def element_volume(corners, p):
+    """|D| by (p+1)^d-point Gauss quadrature of |det J| (the h_F of the SIPG penalty, Section 2.1)."""
     x1, w1 = gauss_legendre(p + 1)
     pts, w = tensor_points(corners.shape[1], x1, w1)
     _, J = multilinear(corners, pts)
@@ -233,6 +234,7 @@ class DGPreconditioner:
         self.B = cg_prec
 
     def apply(self, r):
+        """diag(A_DG)^{-1} r on the element-boundary nodes V_B plus E B E^T r (Eq. (dg-as))."""
         z = np.where(self.vb, r / self.d, 0.0)
         return z + self.E @ self.B.apply(self.E.T @ r)
 

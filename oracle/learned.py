@@ -24,6 +24,8 @@ TAPS = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0,
 
 
 def init_params(seed=0, scale=0.1):
+    """Seeded weights of the 3-layer network; the last layer starts at zero, so the
+    untrained correction is zero and the plain V-cycle result is unchanged."""
     rng = np.random.default_rng(seed)
     return {
         "W1": rng.standard_normal((CH, 2, 27)) * scale, "b1": np.zeros(CH),
@@ -63,6 +65,8 @@ def conv_backward(x, W, g):
 
 
 def features(t, diag):
+    """Input channels: the D^{-1/2}-scaled residual normalised by its RMS (which makes
+    the correction 1-homogeneous in t) and log(diag A_j / its mean); also the scales."""
     s = 1.0 / np.sqrt(diag)
     st = s * t
     rho = np.sqrt(np.mean(st ** 2))

@@ -173,6 +173,7 @@ def ilu0(A, pattern):
 
 
 def ilu_solve(L, U, r):
+    """(L U)^{-1} r: forward then backward triangular solve (one ILU(0) smoothing, Section 3.4)."""
     w = sla.solve_triangular(L, r, lower=True, unit_diagonal=True)
     return sla.solve_triangular(U, w, lower=False)
 
@@ -359,6 +360,7 @@ class LORPreconditioner:
         return y
 
     def local_solve(self, j, r):
+        """R_j applied to the patch residual: one V(1,1) cycle (Section 3.3), or A_j^{-1}."""
         levels = self.patches[j]["levels"]
         if self.exact_local:
             A0 = levels[0]["A"]
@@ -411,6 +413,7 @@ class LORPreconditioner:
         self.cInv = np.linalg.inv(self.cA[-1].toarray()) if self.cA[-1].shape[0] else None
 
     def coarse_vcycle(self, l, r):
+        """One V-cycle on coarse level l (the R_0 reading in the module docstring)."""
         A = self.cA[l]
         if l == len(self.cA) - 1:
             return self.cInv @ r
@@ -432,6 +435,7 @@ class LORPreconditioner:
 
     # ------------------------------------------------------------------ apply
     def apply(self, r, parts=("patches", "coarse")):
+        """B r = sum_j R_j^T V_j(R_j r) + P_0 R_0 P_0^T r (Eq. (as)); Dirichlet entries of r are ignored."""
         r = np.asarray(r, dtype=np.float64)
         z = np.zeros_like(r)
         N0 = self.Ns[0]

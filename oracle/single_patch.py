@@ -71,6 +71,7 @@ def ilu0_csr(A, pattern):
 
 
 def ilu_apply(L, U, r):
+    """(L U)^{-1} r with the sparse factors (one ILU(0) smoothing, Section 3.4)."""
     w = spla.spsolve_triangular(L, r, lower=True, unit_diagonal=True)
     return spla.spsolve_triangular(U, w, lower=False)
 
@@ -94,6 +95,7 @@ class SinglePatchPreconditioner:
             self.LU.append(ilu0_csr(self.A[l], pat))
 
     def vcycle(self, l, r):
+        """V(1,1) on global level l (Section 3.3); R_0 on the vertex level."""
         if len(r) == 0:
             return r
         if l == self.L - 1:
@@ -107,6 +109,7 @@ class SinglePatchPreconditioner:
         return x + ilu_apply(Lf, Uf, r - A @ x)
 
     def apply(self, r):
+        """B(1) r on the full node grid; Dirichlet entries are ignored and returned as 0."""
         r = np.asarray(r, dtype=np.float64)
         z = np.zeros_like(r)
         z[self.mask[0]] = self.vcycle(0, r[self.mask[0]])
