@@ -57,17 +57,19 @@ def tensor_points(dim, pts1d, w1d):
     return pts, w
 
 
-def element_stiffness(corners, kappa, p, q=None):
+def element_stiffness(corners, kappa, p, q=None, geom=None):
     """Dense K_e[a,b] = sum_q w_q |det J_q| kappa grad phi_a . grad phi_b.
 
     kappa: the element's constant, or a callable b(X) of the physical points X (Q, d)
-    (the variable coefficients of Section 5.2), evaluated at the quadrature points."""
+    (the variable coefficients of Section 5.2), evaluated at the quadrature points.
+    geom: optional callable xi -> (X, J) replacing the multilinear map of corners
+    (curved elements, `Mesh.element_map`)."""
     dim = corners.shape[1]
     q = p + 1 if q is None else q
     x1, w1 = gauss_legendre(q)
     pts, w = tensor_points(dim, x1, w1)
     _, dphi = tensor_basis(dim, p, x1)
-    Xq, J = multilinear(corners, pts)
+    Xq, J = multilinear(corners, pts) if geom is None else geom(pts)
     if callable(kappa):
         kappa = np.asarray(kappa(Xq), dtype=np.float64)
     detJ = np.linalg.det(J)
@@ -76,6 +78,13 @@ def element_stiffness(corners, kappa, p, q=None):
     gphys = np.einsum("qba,bqn->aqn", Jinv, dphi)   # (d, Q, nb)
     wk = w * np.abs(detJ) * kappa
     return np.einsum("aqi,q,aqj->ij", gphys, wk, gphys)
+
+
+def _geom(mesh: Mesh, e, p):
+    """The element map of a curved element, None for the multilinear default."""
+    if mesh.warp is None:
+        return None
+    return lambda pts: mesh.element_map(e, pts, p)
 
 
 def element_nodes(e, p, N):
@@ -112,7 +121,8 @@ def assemble_stiffness(mesh: Mesh, p: int, coef=None):
     ntot = int(np.prod(N))
     rows, cols, vals = [], [], []
     for e in mesh.elements():
-        Ke = element_stiffness(mesh.corners(e), mesh.kappa_of(e) if coef is None else coef, p)
+        Ke = element_stiffness(mesh.corners(e), mesh.kappa_of(e) if coef is None else coef, p,
+                               geom=_geom(mesh, e, p))
         idx = element_nodes(e, p, N)
         rows.append(np.repeat(idx, len(idx)))
         cols.append(np.tile(idx, len(idx)))
@@ -165,7 +175,7 @@ def apply_A_rows(mesh: Mesh, p: int, x, rows):
         acc = 0.0
         for e in itertools.product(*cand):
             if e not in cache:
-                cache[e] = element_stiffness(mesh.corners(e), mesh.kappa_of(e), p)
+                cache[e] = element_stiffness(mesh.corners(e), mesh.kappa_of(e), p, geom=_geom(mesh, e, p))
             Ke = cache[e]
             idx = element_nodes(e, p, N)
             loc = int(np.nonzero(idx == r)[0][0])
@@ -184,7 +194,7 @@ def load_vector(mesh: Mesh, p: int, f, q=None):
     phi, _ = tensor_basis(mesh.dim, p, x1)
     b = np.zeros(ntot)
     for e in mesh.elements():
-        X, J = multilinear(mesh.corners(e), pts)
+        X, J = mesh.element_map(e, pts, p)
         fv = f(X)
         wq = w * np.abs(np.linalg.det(J)) * fv
         np.add.at(b, element_nodes(e, p, N), phi.T @ wq)
@@ -200,7 +210,7 @@ def node_coordinates(mesh: Mesh, p: int):
     pts, _ = tensor_points(mesh.dim, xg, np.ones(p + 1))
     X = np.zeros((ntot, mesh.dim))
     for e in mesh.elements():
-        Xe, _ = multilinear(mesh.corners(e), pts)
+        Xe, _ = mesh.element_map(e, pts, p)
         X[element_nodes(e, p, N)] = Xe
     return X
 
@@ -213,7 +223,7 @@ def l2_error(mesh: Mesh, p: int, u, exact):
     phi, _ = tensor_basis(mesh.dim, p, x1)
     err = 0.0
     for e in mesh.elements():
-        X, J = multilinear(mesh.corners(e), pts)
+        X, J = mesh.element_map(e, pts, p)
         uh = phi @ u[element_nodes(e, p, N)]
         err += np.sum(w * np.abs(np.linalg.det(J)) * (uh - exact(X)) ** 2)
     return np.sqrt(err)

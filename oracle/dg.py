@@ -95,6 +95,8 @@ def face_geometry(corners, a, side, pts, w):
 
 def assemble_dg(mesh: Mesh, p: int, eta: float, form: str = "ip"):
     """Assembled A_IP or A_BR2 (CSR) on the element-major DG space."""
+    if getattr(mesh, "warp", None) is not None:
+        raise NotImplementedError("the DG oracle takes multilinear elements only")
     d = mesh.dim
     n = mesh.n
     Q = p + 1

@@ -4,6 +4,11 @@ Section 2: every element D of T_p is the image of the unit cube [0,1]^d.  Here
 the map is the multilinear (bilinear/trilinear) interpolation of the element's
 2^d vertices (the reading used for all perturbed meshes).  Corner c of an
 element has offsets (c & 1, (c >> 1) & 1, (c >> 2) & 1) along (x, y, z).
+
+Curved elements (the curved meshes of Section 5.2): with a smooth map ``warp``
+the element map becomes isoparametric, the degree-p Lagrange interpolant at the
+(p+1)^d GLL points of warp(multilinear(xi)), so the high-order nodes lie on the
+curved geometry and the map is continuous across shared faces.
 """
 from __future__ import annotations
 
@@ -11,13 +16,19 @@ import itertools
 
 import numpy as np
 
+from .basis import gll, lagrange
+
 
 class Mesh:
-    """Structured-topology mesh with n = (nx, ny[, nz]) elements."""
+    """Structured-topology mesh with n = (nx, ny[, nz]) elements.
 
-    def __init__(self, vertices, kappa):
+    warp: optional callable X (Q, d) -> (Q, d) applied to the multilinear image;
+    the element map is then its isoparametric interpolant (module docstring)."""
+
+    def __init__(self, vertices, kappa, warp=None):
         self.vertices = np.asarray(vertices, dtype=np.float64)
         self.kappa = np.asarray(kappa, dtype=np.float64)
+        self.warp = warp
         self.dim = self.vertices.shape[0]
         self.n = tuple(reversed(self.kappa.shape))          # (nx, ny[, nz])
         assert len(self.n) == self.dim
@@ -42,7 +53,38 @@ class Mesh:
         return out
 
     def kappa_of(self, e):
+        """The coefficient kappa_e of element e."""
         return float(self.kappa[tuple(reversed(e))])
+
+    def element_map(self, e, xi, p):
+        """X (Q, d) and J (Q, d, d) of element e at reference points xi: the multilinear
+        map, or with a warp its degree-p isoparametric interpolant."""
+        if self.warp is None:
+            return multilinear(self.corners(e), xi)
+        return isoparametric(self.corners(e), self.warp, p, xi)
+
+
+def isoparametric(corners, warp, p, xi):
+    """Degree-p interpolant of warp(multilinear(corners, .)) at the GLL points, and its
+    Jacobian, at reference points xi (Q, d)."""
+    corners = np.asarray(corners)
+    xi = np.atleast_2d(xi)
+    Q, d = xi.shape
+    xg = gll(p)[0]
+    grids = np.meshgrid(*([xg] * d), indexing="ij")               # axis 0 slowest
+    nodes = np.stack([grids[d - 1 - a].ravel() for a in range(d)], axis=1)   # x fastest
+    Xn = np.asarray(warp(multilinear(corners, nodes)[0]), dtype=np.float64)  # ((p+1)^d, d)
+    B, D = zip(*[lagrange(xg, xi[:, a]) for a in range(d)])       # per axis (Q, p+1)
+    idx = np.stack([np.indices([p + 1] * d)[d - 1 - a].ravel() for a in range(d)], axis=1)
+    phi = np.ones((Q, len(nodes)))
+    dphi = np.ones((d, Q, len(nodes)))
+    for a in range(d):
+        phi *= B[a][:, idx[:, a]]
+        for b in range(d):
+            dphi[b] *= (D[a] if a == b else B[a])[:, idx[:, a]]
+    X = phi @ Xn
+    J = np.einsum("bqn,na->qab", dphi, Xn)
+    return X, J
 
 
 def multilinear(corners, xi):

@@ -150,6 +150,32 @@ def make_strip_mesh(n: int, aspect: float, layers: int = 4, seed: int = 0, pertu
     return np.ascontiguousarray(verts), np.ones((n, n))
 
 
+def make_quarter_hole_mesh(n: int, radius: float = 0.25):
+    """Curved 2D mesh of [0,1]^2 minus the quarter disk of `radius` at the origin (one
+    quarter of the square-with-a-hole geometry of Section 5.2), n x n elements.
+
+    The vertices are those of the uniform grid of the parameter square (s, t); the
+    returned `warp` maps (s, t) to the domain: angle theta = (pi/2) s, blended linearly
+    in t from the arc of `radius` to the outer boundary (x = 1 or y = 1) along the ray
+    at theta.  The outer boundary has its corner at s = 1/2, so n must be even (a
+    vertex line there keeps every element's warp smooth).
+    Returns (vertices, kappa = 1, warp).
+    """
+    if n % 2:
+        raise ValueError("n must be even")
+    verts, kappa = make_mesh(2, n, perturb=0.0, kappa_const=1.0)
+
+    def warp(S):
+        S = np.asarray(S, dtype=np.float64)
+        th = 0.5 * np.pi * S[:, 0]
+        t = S[:, 1][:, None]
+        ray = np.stack([np.cos(th), np.sin(th)], axis=1)
+        outer = ray / np.max(ray, axis=1, keepdims=True)
+        return (1.0 - t) * radius * ray + t * outer
+
+    return verts, kappa, warp
+
+
 def two_valued_kappa(n, seed: int = 0, high: float = 10.0, low: float = 1.0) -> np.ndarray:
     """Piecewise-constant coefficient taking `high` or `low` on each element with equal
     probability (the discontinuous coefficient b_4 of Section 5.2); layout as kappa."""
