@@ -176,6 +176,64 @@ def make_quarter_hole_mesh(n: int, radius: float = 0.25):
     return verts, kappa, warp
 
 
+def make_split_triangle_mesh(n: int, seed: int = 0, perturb: float = 0.15):
+    """Unstructured quadrilateral mesh of [0,1]^2 (a stand-in for the unstructured mesh (a)
+    of Section 5.2): an n x n grid of squares, each cut into two triangles (diagonals
+    alternating in a checkerboard), interior grid vertices moved by U(-perturb*h,
+    perturb*h) per coordinate, and every triangle split into three quadrilaterals
+    through its edge midpoints and centroid.  Interior vertices have 3 (centroids), 4
+    or 8 (grid vertices where four diagonals meet) elements around them.
+
+    Returns (vertices (nv, 2), quads (nq, 4) int64, kappa (nq,) = 1); quad corners are
+    listed in the reference-square order (0,0), (1,0), (0,1), (1,1) and every quad is
+    counter-clockwise.  Each quad's reference frame is turned by a seeded multiple of
+    90 degrees, so that neighbouring elements run along shared edges in both directions
+    (as element maps of a general mesh do).
+    """
+    n = int(n)
+    h = 1.0 / n
+    g = np.linspace(0.0, 1.0, n + 1)
+    P = np.stack(np.meshgrid(g, g, indexing="xy"), axis=-1).reshape(-1, 2)     # index j*(n+1)+i
+    if perturb != 0.0:
+        u = uniform01(stream_key(seed, TAG_VERTS), 2 * (n + 1) ** 2).reshape(-1, 2)
+        ij = np.stack(np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="xy"), axis=-1).reshape(-1, 2)
+        inner = np.all((ij > 0) & (ij < n), axis=1)
+        P[inner] += (2.0 * u[inner] - 1.0) * perturb * h
+    vid = lambda i, j: j * (n + 1) + i  # noqa: E731
+    tris = []
+    for j in range(n):
+        for i in range(n):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            if (i + j) % 2 == 0:
+                tris += [(a, b, c), (a, c, d)]
+            else:
+                tris += [(a, b, d), (b, c, d)]
+    verts = [tuple(x) for x in P]
+    mids = {}
+
+    def mid(u, v):
+        key = (min(u, v), max(u, v))
+        if key not in mids:
+            mids[key] = len(verts)
+            verts.append(tuple(0.5 * (P[u] + P[v])))
+        return mids[key]
+
+    ring = []                                                # corners in counter-clockwise order
+    for (a, b, c) in tris:                                   # counter-clockwise triangles
+        gc = len(verts)
+        verts.append(tuple((P[a] + P[b] + P[c]) / 3.0))
+        mab, mbc, mca = mid(a, b), mid(b, c), mid(c, a)
+        for (x, mx, my) in ((a, mab, mca), (b, mbc, mab), (c, mca, mbc)):
+            ring.append((x, mx, gc, my))
+    turn = (uniform01(stream_key(seed, TAG_KAPPA + 10), len(ring)) * 4).astype(int)
+    quads = []
+    for r, t in zip(ring, turn):
+        r = r[t:] + r[:t]
+        quads.append((r[0], r[1], r[3], r[2]))               # (0,0), (1,0), (0,1), (1,1)
+    return (np.ascontiguousarray(np.array(verts, dtype=np.float64)), np.array(quads, dtype=np.int64),
+            np.ones(len(quads)))
+
+
 def two_valued_kappa(n, seed: int = 0, high: float = 10.0, low: float = 1.0) -> np.ndarray:
     """Piecewise-constant coefficient taking `high` or `low` on each element with equal
     probability (the discontinuous coefficient b_4 of Section 5.2); layout as kappa."""
