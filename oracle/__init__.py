@@ -8,7 +8,7 @@ solver arithmetic.
 
 Modules (each function cites the passage of the paper it follows):
   basis   -- GLL / Gauss-Legendre rules and Lagrange bases (Sections 2, 3.1)
-  mesh    -- multilinear element maps (Section 2)
+  mesh    -- multilinear and isoparametric (curved) element maps (Sections 2, 5.2)
   cg      -- Q_p stiffness by dense quadrature, load vector (Eq. (fem), (system))
   lor     -- K_h, element-structured hierarchy, ordered ILU(0), vertex patches,
              coarse space, additive Schwarz B (Sections 3.1-3.4, Eq. (as), (patch))
@@ -16,6 +16,9 @@ Modules (each function cites the passage of the paper it follows):
   krylov  -- PCG / flexible CG and the Lanczos condition estimate
   learned -- FP64 reference of the per-patch convolutional smoother and its
              gradients (the learned form)
+  ordering     -- MDF and RCM orderings for ILU(0) (Section 3.4)
+  single_patch -- B(1): the whole domain as one patch (Section 5.1)
+  unstructured -- vertex patches on unstructured quadrilateral meshes (Section 5.2)
 
 Parity status: every function is pinned by a `-m "not gpu"` test against
 closed forms, textbook special cases or invariants, except where a module
