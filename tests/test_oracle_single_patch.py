@@ -165,3 +165,20 @@ def test_count_weighting_is_spd_and_reduces_iterations():
     M = np.column_stack([B2.apply(E[:, c])[inner] for c in range(n)])
     assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
     assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_count_weighting_gain_reverses_at_high_degree_in_2d():
+    """The counting-weight gain shrinks with p: on a Cartesian 4 x 4 mesh it helps at p = 4
+    and costs iterations at p = 16 (the weighted decomposition is not p-robust)."""
+    v, k = make_mesh(2, 4, seed=0, perturb=0.0, kappa_const=1.0)
+    m = Mesh(v, k)
+    its = {}
+    for p in (4, 16):
+        N = cg.node_shape(m.n, p)
+        K = cg.assemble_stiffness(m, p)
+        b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+        A = lambda u: cg.apply_A(K, N, u)  # noqa: E731
+        for w in ("none", "count"):
+            its[p, w] = krylov.pcg(A, olor.LORPreconditioner(m, p, weighting=w).apply, b, rtol=1e-8)[1]
+    assert its[4, "count"] <= 0.75 * its[4, "none"], its
+    assert its[16, "count"] > its[16, "none"], its
