@@ -268,12 +268,14 @@ class LORPreconditioner:
         coarse=False skips the coarse space (for checks of the patch part alone);
         ordering: ILU(0) ordering of every patch level, "lex" (patch-lexicographic),
         "mdf" or "rcm" (Section 3.4, `oracle.ordering`);
-        weighting: "none" (unit weights, Eq. (as)) or "count": the patch sum scaled on
+        weighting: "none" (unit weights, Eq. (as)), "count": the patch sum scaled on
         both sides by D^{-1/2}, D = number of patches containing each node (the counting
-        matrix Section 5.1 names as future work)."""
+        matrix Section 5.1 names as future work), or "pou": each patch scaled on both
+        sides by W_j = sqrt(theta_j), theta_j the Q1 vertex function of its vertex in
+        the element reference coordinates at the level-0 nodes (`pou_weights`)."""
         self.ordering = ordering
         self.patch_spans = patch_spans or {}
-        if weighting not in ("none", "count"):
+        if weighting not in ("none", "count", "pou"):
             raise ValueError(f"unknown weighting {weighting!r}")
         self.weighting = weighting
         self.patch_subset = None if patch_subset is None else set(map(tuple, patch_subset))
@@ -446,7 +448,12 @@ class LORPreconditioner:
             zp = np.zeros_like(r)
             for j in range(len(self.patches)):
                 idx = self.patches[j]["levels"][0]["idx"]
-                if len(idx):
+                if not len(idx):
+                    continue
+                if self.weighting == "pou":
+                    wj = self.pou_weights(j)
+                    zp[idx] += wj * self.local_solve(j, wj * rr[idx])
+                else:
                     zp[idx] += self.local_solve(j, rp[idx])
             z += zp if w is None else w * zp
         if "coarse" in parts and self.with_coarse:
@@ -455,6 +462,26 @@ class LORPreconditioner:
             ec[self.vmask] = self.coarse_solve(rc)
             z += self.P0 @ ec
         return z
+
+    def pou_weights(self, j):
+        """sqrt(theta_j) at the level-0 nodes of patch j (its box order).
+
+        theta_j is the Q1 (bilinear/trilinear) function of patch j's vertex v in the
+        element reference coordinates: along axis a, 1 - s on the element whose left
+        vertex is v and s on the element whose right vertex is v, with s the node's GLL
+        coordinate in [0, 1].  These functions sum to one at every node and vanish on
+        the patch boundary, so the weighted sum is a smooth partition of unity (the
+        ingredient of the stable decomposition in Section 3.2).  An option beyond the
+        paper, like the counting matrix."""
+        pt = self.patches[j]
+        v = pt["v"]
+        xg = gll(self.p)[0]
+        hats = []
+        for a, I in enumerate(pt["levels"][0]["ranges"]):
+            e, s = I // self.p, xg[I % self.p]
+            hats.append(np.where(e == v[a], 1.0 - s, s))
+        grids = np.meshgrid(*reversed(hats), indexing="ij")
+        return np.sqrt(np.prod([g.ravel() for g in grids], axis=0))
 
     def count_weights(self):
         """D^{-1/2} on the level-0 grid: D counts the built patches containing each node."""

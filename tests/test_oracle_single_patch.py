@@ -182,3 +182,53 @@ def test_count_weighting_gain_reverses_at_high_degree_in_2d():
             its[p, w] = krylov.pcg(A, olor.LORPreconditioner(m, p, weighting=w).apply, b, rtol=1e-8)[1]
     assert its[4, "count"] <= 0.75 * its[4, "none"], its
     assert its[16, "count"] > its[16, "none"], its
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, 3, 4), (3, 2, 3)])
+def test_pou_weights_are_a_partition_of_unity_and_b_is_spd(dim, n, p):
+    """weighting="pou": sum_j W_j^2 = 1 at every interior node (the Q1 vertex functions
+    sum to one and vanish on each patch boundary); B stays symmetric positive definite."""
+    v, k = make_mesh(dim, n, seed=0, perturb=0.15)
+    m = Mesh(v, k)
+    B = olor.LORPreconditioner(m, p, weighting="pou")
+    s = np.zeros(int(np.prod(B.Ns[0])))
+    for j, pt in enumerate(B.patches):
+        idx = pt["levels"][0]["idx"]
+        if len(idx):
+            w = B.pou_weights(j)
+            assert np.all(w > 0)
+            s[idx] += w ** 2
+    inner = ~cg.boundary_mask(B.Ns[0])
+    np.testing.assert_allclose(s[inner], 1.0, atol=1e-14)
+    if dim == 2:
+        idx = np.nonzero(inner)[0]
+        E = np.zeros((len(inner), len(idx)))
+        E[idx, np.arange(len(idx))] = 1.0
+        M = np.column_stack([B.apply(E[:, c])[inner] for c in range(len(idx))])
+        assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
+        assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_pou_weighting_is_p_robust_in_2d_and_beats_counting_weights_in_3d():
+    """Measured: Cartesian 4 x 4, p = 4 / 16: unit 25 / 39, counting 16 / 47, pou 16 / 23;
+    perturbed 3D Q4 on 3^3 with log-normal b: unit 66, counting 29, pou 27."""
+    v, k = make_mesh(2, 4, seed=0, perturb=0.0, kappa_const=1.0)
+    m = Mesh(v, k)
+    its = {}
+    for p in (4, 16):
+        N = cg.node_shape(m.n, p)
+        K = cg.assemble_stiffness(m, p)
+        b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+        A = lambda u: cg.apply_A(K, N, u)  # noqa: E731
+        its[p] = krylov.pcg(A, olor.LORPreconditioner(m, p, weighting="pou").apply, b, rtol=1e-8)[1]
+    assert its[16] <= 1.6 * its[4], its
+    v, k = make_mesh(3, 3, seed=0, perturb=0.15)
+    m = Mesh(v, k)
+    p = 4
+    N = cg.node_shape(m.n, p)
+    K = cg.assemble_stiffness(m, p)
+    b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+    A = lambda u: cg.apply_A(K, N, u)  # noqa: E731
+    got = {w: krylov.pcg(A, olor.LORPreconditioner(m, p, weighting=w).apply, b, rtol=1e-8)[1]
+           for w in ("none", "count", "pou")}
+    assert got["pou"] <= got["count"] and got["pou"] <= 0.5 * got["none"], got
