@@ -277,6 +277,10 @@ class LORPreconditioner:
         self.patch_spans = patch_spans or {}
         if weighting not in ("none", "count", "pou"):
             raise ValueError(f"unknown weighting {weighting!r}")
+        if weighting == "pou" and patch_spans:
+            # the vertex function of an enlarged patch is not its Q1 hat: the weights
+            # would not sum to one (and PCG does not converge with them)
+            raise ValueError("pou weights are defined for vertex patches only")
         self.weighting = weighting
         self.patch_subset = None if patch_subset is None else set(map(tuple, patch_subset))
         self.with_coarse = coarse

@@ -129,3 +129,10 @@ def test_iterations_flat_in_aspect_ratio_with_enlarged_patches():
     assert abs(its["enlarged+count", 1500.0] - its["enlarged+count", 15.0]) <= 2, its
     assert its["vertex", 1500.0] >= 3 * its["enlarged", 1500.0], its
     assert its["vertex", 1500.0] >= 2 * its["vertex", 15.0], its
+
+
+def test_pou_weights_refuse_enlarged_patches():
+    v, k = make_strip_mesh(6, 150.0, layers=2)
+    m = Mesh(v, k)
+    with pytest.raises(ValueError):
+        lor.LORPreconditioner(m, 2, patch_spans=lor.isotropic_overlap_spans(m), weighting="pou")
