@@ -320,20 +320,21 @@ def leg_dg():
             e1.record()
             torch.cuda.synchronize()
             row.update({"iterations_mixed": it2, "time_ms_mixed": e0.elapsed_time(e1), "rel_res_mixed": rel2})
-            # the same mixed solve with the counting-matrix weighted patch sum (option beyond the paper)
-            try:
-                s.set_weighting(1)
-                x3 = torch.zeros_like(b)
-                e0.record()
-                it3, rel3 = s.solve(b, x3)
-                e1.record()
-                torch.cuda.synchronize()
-                row.update({"iterations_mixed_count_weighted": it3, "time_ms_mixed_count_weighted": e0.elapsed_time(e1),
-                            "rel_res_mixed_count_weighted": rel3})
-            except lor.LorError as exc:
-                row["count_weighted_error"] = str(exc)
-            finally:
-                s.set_weighting(0)
+            # the same mixed solve with weighted patch sums (options beyond the paper)
+            for wmode, tag in ((1, "count_weighted"), (2, "pou_weighted")):
+                try:
+                    s.set_weighting(wmode)
+                    x3 = torch.zeros_like(b)
+                    e0.record()
+                    it3, rel3 = s.solve(b, x3)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    row.update({f"iterations_mixed_{tag}": it3, f"time_ms_mixed_{tag}": e0.elapsed_time(e1),
+                                f"rel_res_mixed_{tag}": rel3})
+                except lor.LorError as exc:
+                    row[f"{tag}_error"] = str(exc)
+                finally:
+                    s.set_weighting(0)
             if mult == 10.0:
                 xa = torch.randn(s.nvec, dtype=torch.float64, device="cuda")
                 ya = torch.empty_like(xa)
@@ -487,27 +488,29 @@ def main():
             extras["fp64_plain"] = {"time_to_tol_ms": f0.elapsed_time(f1), "iterations": it64,
                                     "rel_res": rel64, "chosen_vs_fp64_x_rel_diff": dx,
                                     "speedup_chosen_vs_fp64": f0.elapsed_time(f1) / ms_per_step}
-        # the chosen form with the counting-matrix weighted patch sum (an option beyond
-        # the paper's unit weights; context only, the headline keeps unit weights)
-        try:
-            s.set_weighting(1)
-            xw = torch.zeros_like(b)
-            s.solve(b, xw)
-            w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            xw.zero_()
-            w0.record(stream)
-            itw, relw = s.solve(b, xw)
-            w1.record(stream)
-            torch.cuda.synchronize()
-            extras["count_weighted"] = {"time_to_tol_ms": w0.elapsed_time(w1), "iterations": itw, "rel_res": relw,
-                                        "speedup_vs_unit_weights": ms_per_step / w0.elapsed_time(w1)}
-        except Exception as exc:   # an optional leg must not hide the main result
-            extras["count_weighted"] = {"error": f"{type(exc).__name__}: {exc}"}
-        finally:
+        # the chosen form with a weighted patch sum (options beyond the paper's unit
+        # weights; context only, the headline keeps unit weights): 1 counting matrix,
+        # 2 partition of unity
+        for wmode, key in ((1, "count_weighted"), (2, "pou_weighted")):
             try:
-                s.set_weighting(0)
-            except Exception:
-                pass
+                s.set_weighting(wmode)
+                xw = torch.zeros_like(b)
+                s.solve(b, xw)
+                w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                xw.zero_()
+                w0.record(stream)
+                itw, relw = s.solve(b, xw)
+                w1.record(stream)
+                torch.cuda.synchronize()
+                extras[key] = {"time_to_tol_ms": w0.elapsed_time(w1), "iterations": itw, "rel_res": relw,
+                               "speedup_vs_unit_weights": ms_per_step / w0.elapsed_time(w1)}
+            except Exception as exc:   # an optional leg must not hide the main result
+                extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
+            finally:
+                try:
+                    s.set_weighting(0)
+                except Exception:
+                    pass
 
     # roofline of the dominant kernel class inside the timed region
     pk = peaks()

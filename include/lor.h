@@ -67,7 +67,10 @@ typedef struct {
   int weighting;    /* patch sum of Eq. (as): 0 = unit weights (the paper's
                        method); 1 = scaled on both sides by D^{-1/2}, D the
                        number of patches containing each node (the counting
-                       matrix Section 5.1 leaves to future work)            */
+                       matrix Section 5.1 leaves to future work); 2 = patch j
+                       scaled on both sides by sqrt(theta_j), theta_j the Q1
+                       function of its vertex in element reference
+                       coordinates (a partition of unity over the patches) */
 } lor_options;
 
 /* Fills *opt with defaults: dim 3, p 4, 8^3 elements, CG, eta 1, full
@@ -143,7 +146,7 @@ lor_status lor_pcg_solve_host(lor_ctx* ctx, const double* h_b, double* h_x,
 lor_status lor_set_prec(lor_ctx* ctx, int prec);
 
 /* Switches the patch-sum weighting of lor_options.weighting (0 unit weights,
- * 1 counting matrix) for later calls; the weights are evaluated inside the
+ * 1 counting matrix, 2 partition of unity) for later calls; the weights are evaluated inside the
  * patch kernel, so no setup is redone.  A batch (lor_batch_create) keeps the
  * setting its contexts had when its CUDA graph was captured (first
  * lor_batch_solve).  LOR_EINVAL for other values or if the learned correction

@@ -70,7 +70,9 @@ struct PatchArgs {
   long long x0_stride;
   const int* porder;            // patch visiting order (grouped by box shape)
   const double* conv;           // optional: skip all work when *conv != 0 (converged batched solve)
-  int wp;                       // > 0: patch sum weighted by D^{-1/2} on both sides (wp = p), 0: unit weights
+  int wp;                       // > 0: patch sum weighted on both sides (wp = p), 0: unit weights
+  int wmode;                    //   1: counting matrix D^{-1/2}, 2: partition of unity sqrt(theta_v)
+  const void* hat;              //   vertex hat table of the coarse space (T), used by mode 2
   // patch-local mode (learned-correction training data): patches plist[0..nlist)
   // take their level-0 right-hand side from rloc and write x to xloc (lexicographic
   // box order, stride vstride per listed patch) instead of gathering / scattering
@@ -393,19 +395,47 @@ __device__ __forceinline__ T count_weight(int I, int J, int K, int p) {
   return T(1) / sqrt(T(1 << c));
 }
 
+// Weight of level-0 node (I, J, K) in the patch sum.  mode 1: the counting-matrix
+// weight above.  mode 2: the partition of unity sqrt(theta_v), theta_v the Q1
+// function of the patch's vertex v in the element reference coordinates.  Along
+// axis a it is the vertex hat, which the coarse-space table holds at positions
+// p + t, t = I - (v_a - 1) p in [1, 2p - 1] for every node of the patch; ho_a =
+// (2 - v_a) p turns the global index into that position.
+template <int DIM, typename T>
+__device__ __forceinline__ T node_weight(int mode, int I, int J, int K, int p, int ho0, int ho1, int ho2,
+                                         const T* __restrict__ hat) {
+  if (mode == 1) return count_weight<DIM, T>(I, J, K, p);
+  T h = hat[ho0 + I] * hat[ho1 + J];
+  if (DIM == 3) h *= hat[ho2 + K];
+  return sqrt(h);
+}
+
+// ho_a = (2 - v_a) p for the vertex v of patch j on an n0 x n1 (x n2) element grid
+// (vertices numbered x fastest).
+template <int DIM>
+__device__ __forceinline__ void hat_offsets(int j, int n0, int n1, int p, int* ho) {
+  const int v0 = j % (n0 + 1), v1 = (j / (n0 + 1)) % (n1 + 1);
+  ho[0] = (2 - v0) * p;
+  ho[1] = (2 - v1) * p;
+  ho[2] = DIM == 3 ? (2 - j / ((n0 + 1) * (n1 + 1))) * p : 0;
+}
+
 // Level-0 residual in place: t holds x on entry (rows of the box, zero guard
 // bands) and rhs - A x on exit.  Planes are done in order; plane k is computed
 // into tmp from prev (x of plane k-1, guarded) and t (planes k, k+1 still x),
 // then plane k's x moves to prev (and to xout, when given) and tmp into t.
-// wp > 0: the global right-hand side is weighted by D^{-1/2} (count_weight).
+// wp > 0: the global right-hand side is weighted (node_weight with mode wmode).
 template <int DIM, typename T>
 __device__ void resid0_inplace(const WLevel& b, const PLevel& lv, const T* __restrict__ rg0,
-                               const T* __restrict__ rloc, T* t, T* prev, T* tmp, T* xout, int wp) {
+                               const T* __restrict__ rloc, T* t, T* prev, T* tmp, T* xout, int wp, int wmode,
+                               int jp, int n0, int n1, const T* __restrict__ hat) {
   constexpr int NSP = lor_nsp(DIM);
   const int lane = threadIdx.x & 31;
   const int A = b.A, B = b.B, C = b.C, AB = A * B;
   const T* Sa = (const T*)lv.Sa;
   const int N0 = lv.N[0], N1 = lv.N[1];
+  int ho[3] = {0, 0, 0};
+  if (wmode == 2) hat_offsets<DIM>(jp, n0, n1, wp, ho);
   for (int k = 0; k < C; ++k) {
     BoxIter it;
     it.init(lane, A, B);   // walks plane-local rows (k component unused)
@@ -416,7 +446,7 @@ __device__ void resid0_inplace(const WLevel& b, const PLevel& lv, const T* __res
       T s[NSP];
       load_row<DIM, T>(Sa, G, s);
       T rhs = rloc ? rloc[lex] : rg0[G];
-      if (wp) rhs *= count_weight<DIM, T>(b.org[0] + i, b.org[1] + j, b.org[2] + k, wp);
+      if (wp) rhs *= node_weight<DIM, T>(wmode, b.org[0] + i, b.org[1] + j, b.org[2] + k, wp, ho[0], ho[1], ho[2], hat);
       tmp[p] = row_residual<DIM, T>(s, rhs, i, j, k, A, B, C, [&](int o, int dx, int dy, int dz) -> T {
         return dz < 0 ? prev[p + dy * A + dx] : t[lex + dz * AB + dy * A + dx];
       });
@@ -576,6 +606,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
   const long long step = (long long)gridDim.x * nw;
   int cur_sh = -1;
   const FT* F = (const FT*)a.F;
+  const T* hat = (const T*)a.hat;
   for (long long jo = gw; jo < nwork; jo += step) {
     const int j = a.plist ? a.plist[jo] : a.porder[jo];
     int v[3];
@@ -643,10 +674,14 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       const T* S = (const T*)lv0.S;
       BoxIter it;
       it.init(lane, b0.A, b0.B);
+      int ho[3] = {0, 0, 0};
+      if (a.wmode == 2) hat_offsets<DIM>(j, a.n[0], a.n[1], a.wp, ho);
       for (int lex = lane; lex < b0.rows; lex += 32, it.next()) {
         const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
         T rhs = rloc ? rloc[lex] : rg0[G];
-        if (a.wp) rhs *= count_weight<DIM, T>(b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp);
+        if (a.wp)
+          rhs *= node_weight<DIM, T>(a.wmode, b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp, ho[0], ho[1],
+                                     ho[2], hat);
         xslot[lex] = rhs / S[(long long)(a.NS / 2) * lv0.ntot + G];
         t0[lex] = T(0);
       }
@@ -659,13 +694,17 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
         constexpr int U = kRowsInFlight;
         BoxIter it;
         it.init(lane, b0.A, b0.B);
+        int ho[3] = {0, 0, 0};
+        if (a.wmode == 2) hat_offsets<DIM>(j, a.n[0], a.n[1], a.wp, ho);
         for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
           T v[U];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int lex = l0 + 32 * u;
             const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
-            const T w = a.wp ? count_weight<DIM, T>(b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp) : T(1);
+            const T w = a.wp ? node_weight<DIM, T>(a.wmode, b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp,
+                                                   ho[0], ho[1], ho[2], hat)
+                             : T(1);
             it.next();
             if (lex < b0.rows) v[u] = (rloc ? rloc[lex] : rg0[G]) * w;
           }
@@ -679,7 +718,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       ok = ilu_solve<DIM, T, FT, NBUF>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
       T* prev = vec + (b0.A + 1);                 // guarded plane buffers
       T* tmp = prev + AB0 + (b0.A + 1);
-      if (ok) resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, xslot, a.wp);
+      if (ok) resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, xslot, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
       if (ok && bottom > 0) {
         // ---- coarse levels
         restrict_level<DIM, T>(bx[0], bx[1], xf[type[0]], xf[type[1]], xf[type[2]], t0, vec + bx[1].ro);
@@ -782,7 +821,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
               if (l0 + 32 * u < b0.rows) t0[l0 + 32 * u] = xv[u];
           }
           __syncwarp();
-          resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, nullptr, a.wp);
+          resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, nullptr, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
         }
       }
       if (ok) ok = ilu_solve<DIM, T, FT, NBUF>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
@@ -807,13 +846,17 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       constexpr int U = kRowsInFlight;
       BoxIter it;
       it.init(lane, b0.A, b0.B);
+      int ho[3] = {0, 0, 0};
+      if (a.wmode == 2) hat_offsets<DIM>(j, a.n[0], a.n[1], a.wp, ho);
       for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
         T xv[U], w[U];
         int G[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           G[u] = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
-          w[u] = a.wp ? count_weight<DIM, T>(b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp) : T(1);
+          w[u] = a.wp ? node_weight<DIM, T>(a.wmode, b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp, ho[0],
+                                            ho[1], ho[2], hat)
+                      : T(1);
           it.next();
           if (l0 + 32 * u < b0.rows) xv[u] = xslot[l0 + 32 * u];
         }
@@ -832,7 +875,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
     if (a.tout && sh == 0) {   // residual left on an interior patch, for the learned correction
       T* prev = vec + (b0.A + 1);
       T* tmp = prev + AB0 + (b0.A + 1);
-      resid0_inplace<DIM, T>(b0, lv0, rg0, nullptr, t0, prev, tmp, nullptr, a.wp);
+      resid0_inplace<DIM, T>(b0, lv0, rg0, nullptr, t0, prev, tmp, nullptr, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
       T* dst = (T*)a.tout + jo * a.vstride;
       for (int lex = lane; lex < b0.rows; lex += 32) dst[lex] = t0[lex];
       __syncwarp();
@@ -1153,6 +1196,8 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
   a.conv = c->conv_flag;
   a.plist = nullptr; a.nlist = 0; a.rloc = nullptr; a.xloc = nullptr; a.vstride = 0; a.tout = nullptr;
   a.wp = c->opt.weighting ? c->p : 0;
+  a.wmode = c->opt.weighting;
+  a.hat = Sel<T>::p0w(c);
   const WarpLayout w = warp_layout<T, FT>(c);
   a.slot_bytes = w.slot_bytes;
   a.tab_ints = w.tab_ints;

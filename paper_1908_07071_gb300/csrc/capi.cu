@@ -135,7 +135,7 @@ lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* verti
   if (opt->disc != LOR_CG && opt->disc != LOR_DG_IP && opt->disc != LOR_DG_BR2) return LOR_EINVAL;
   if (opt->disc != LOR_CG && (opt->dim != 3 || !(opt->eta > 0))) return LOR_EINVAL;
   if (!(opt->rtol > 0) || opt->max_it < 1) return LOR_EINVAL;
-  if (opt->weighting != 0 && opt->weighting != 1) return LOR_EINVAL;
+  if (opt->weighting < 0 || opt->weighting > 2) return LOR_EINVAL;
   // element and vertex counts are ints in the kernels' index arithmetic
   const long long nel_ll = (long long)opt->nx * opt->ny * (opt->dim == 3 ? opt->nz : 1);
   const long long nv_ll = (long long)(opt->nx + 1) * (opt->ny + 1) * (opt->dim == 3 ? opt->nz + 1 : 1);
@@ -295,7 +295,7 @@ lor_status lor_pcg_solve_host(lor_ctx* c, const double* hb, double* hx, int* ite
 
 lor_status lor_set_weighting(lor_ctx* c, int weighting) {
   if (!c) return LOR_EINVAL;
-  if (weighting != 0 && weighting != 1) return lor_fail(c, LOR_EINVAL, "lor_set_weighting: 0 or 1");
+  if (weighting < 0 || weighting > 2) return lor_fail(c, LOR_EINVAL, "lor_set_weighting: 0, 1 or 2");
   if (weighting && c->learned_on) return lor_fail(c, LOR_EINVAL, "learned correction needs unit patch weights");
   c->opt.weighting = weighting;
   return LOR_OK;

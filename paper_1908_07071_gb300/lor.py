@@ -217,7 +217,8 @@ class Solver:
         return self.lib.lor_selftest_wait(self.ctx, polls)
 
     def set_weighting(self, weighting):
-        """0: unit patch weights (the paper's method); 1: counting-matrix weights."""
+        """0: unit patch weights (the paper's method); 1: counting-matrix weights;
+        2: partition-of-unity weights (square root of each patch's vertex function)."""
         self._check(self.lib.lor_set_weighting(self.ctx, int(weighting)))
 
     def set_prec(self, prec):

@@ -40,7 +40,7 @@ def test_create_validates_on_host(lib):
     lib.lor_destroy(ctx)
     assert opt.weighting == 0                       # the paper's unit patch weights by default
     for field, bad in (("p", 0), ("p", 9), ("dim", 4), ("nx", 0), ("rtol", 0.0), ("max_it", 0),
-                       ("weighting", 2), ("weighting", -1)):
+                       ("weighting", 3), ("weighting", -1)):
         o = lor.Options()
         ctypes.memmove(ctypes.byref(o), ctypes.byref(opt), ctypes.sizeof(o))
         setattr(o, field, bad)

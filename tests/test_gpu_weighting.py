@@ -58,5 +58,5 @@ def test_set_weighting_toggles_on_one_context():
         zr = olor.LORPreconditioner(m, p, weighting=kind).apply(r)
         assert np.abs(z.cpu().numpy() - zr).max() <= 1e-10 * np.abs(zr).max()
     with pytest.raises(lor.LorError):
-        s.set_weighting(2)
+        s.set_weighting(3)
     s.close()

@@ -232,3 +232,29 @@ def test_pou_weighting_is_p_robust_in_2d_and_beats_counting_weights_in_3d():
     got = {w: krylov.pcg(A, olor.LORPreconditioner(m, p, weighting=w).apply, b, rtol=1e-8)[1]
            for w in ("none", "count", "pou")}
     assert got["pou"] <= got["count"] and got["pou"] <= 0.5 * got["none"], got
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, (3, 4), 4), (3, 2, 3), (3, (2, 3, 2), 1)])
+def test_pou_weight_table_indexing(dim, n, p):
+    """The patch kernel evaluates the partition-of-unity weight of node I in the patch of
+    vertex v as sqrt(prod_a hat[(2 - v_a) p + I_a]), where hat is the coarse-space table
+    of the library: hat[p + t] is the vertex function at position t = 1 .. 2p-1 of the
+    two elements around a vertex (x_t rising, then 1 - x_{t-p} falling).  That index
+    arithmetic, written out here, must give the oracle's pou_weights on every patch."""
+    from oracle.basis import gll
+    v, k = make_mesh(dim, n, seed=0, perturb=0.15)
+    B = olor.LORPreconditioner(Mesh(v, k), p, weighting="pou", coarse=False)
+    x = gll(p)[0]
+    hat = np.zeros(3 * p)
+    hat[:p + 1] = x
+    for t in range(1, 2 * p):
+        hat[p + t] = x[t] if t <= p else 1.0 - x[t - p]
+    for j, pt in enumerate(B.patches):
+        ranges = pt["levels"][0]["ranges"]
+        if not all(len(r) for r in ranges):
+            continue
+        idx = [(2 - pt["v"][a]) * p + ranges[a] for a in range(dim)]
+        assert all(ix.min() >= p + 1 and ix.max() <= 3 * p - 1 for ix in idx)
+        grids = np.meshgrid(*[hat[ix] for ix in reversed(idx)], indexing="ij")
+        w = np.sqrt(np.prod([g.ravel() for g in grids], axis=0))
+        np.testing.assert_allclose(w, B.pou_weights(j), atol=1e-15)
