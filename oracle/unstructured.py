@@ -185,9 +185,13 @@ def coarse_basis(mesh: QuadMesh, p: int, lev0: Level):
 class UnstructuredLOR:
     """B = P_0 A_0^{-1} P_0^T + sum_j R_j^T V_j R_j (Eq. (as)) on a QuadMesh."""
 
-    def __init__(self, mesh: QuadMesh, p: int, local: str = "vcycle"):
-        if local not in ("vcycle", "exact"):
-            raise ValueError(local)
+    def __init__(self, mesh: QuadMesh, p: int, local: str = "vcycle", weighting: str = "none"):
+        """local: "vcycle" or "exact" patch solves; weighting: "none" (Eq. (as)) or "pou":
+        patch j scaled on both sides by sqrt(theta_j), theta_j = column j of P_0 (the
+        bilinear vertex function, a partition of unity over the patches)."""
+        if local not in ("vcycle", "exact") or weighting not in ("none", "pou"):
+            raise ValueError((local, weighting))
+        self.weighting = weighting
         self.mesh, self.p, self.local_kind = mesh, p, local
         sels = level_selections(p) if local == "vcycle" else [list(range(p + 1)), [0, p]]
         if local == "vcycle" and not all(_symmetric(s, p) for s in sels):
@@ -270,8 +274,10 @@ class UnstructuredLOR:
                 idx = lv[0]["idx"]
                 if not len(idx):
                     continue
-                rj = rr[idx]
-                z[idx] += np.linalg.solve(lv[0]["A"], rj) if self.local_kind == "exact" else self.vcycle(lv, 0, rj)
+                w = np.sqrt(self.P0[idx, pt["v"]].toarray().ravel()) if self.weighting == "pou" else 1.0
+                rj = w * rr[idx]
+                zj = np.linalg.solve(lv[0]["A"], rj) if self.local_kind == "exact" else self.vcycle(lv, 0, rj)
+                z[idx] += w * zj
         if "coarse" in parts and self.A0inv.shape[0]:
             ec = np.zeros(self.mesh.nv)
             ec[self.vin] = self.A0inv @ (self.P0.T @ rr)[self.vin]

@@ -258,3 +258,16 @@ def test_pou_weight_table_indexing(dim, n, p):
         grids = np.meshgrid(*[hat[ix] for ix in reversed(idx)], indexing="ij")
         w = np.sqrt(np.prod([g.ravel() for g in grids], axis=0))
         np.testing.assert_allclose(w, B.pou_weights(j), atol=1e-15)
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, (3, 4), 5), (3, 2, 4)])
+def test_pou_weights_are_square_roots_of_the_coarse_basis(dim, n, p):
+    """theta_j is the vertex function of patch j, i.e. column j of P_0 (built separately,
+    by tensor linear interpolation), so W_j = sqrt(P_0[idx_j, j])."""
+    v, k = make_mesh(dim, n, seed=2, perturb=0.15)
+    B = olor.LORPreconditioner(Mesh(v, k), p, weighting="pou")
+    P0 = B.P0.toarray()
+    for j, pt in enumerate(B.patches):
+        idx = pt["levels"][0]["idx"]
+        if len(idx):
+            np.testing.assert_allclose(B.pou_weights(j), np.sqrt(P0[idx, j]), atol=1e-14)

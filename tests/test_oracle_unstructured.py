@@ -167,3 +167,24 @@ def test_iterations_bounded_in_h_on_unstructured_meshes():
     for p in (2, 4):
         assert its[p, 4] <= 1.25 * its[p, 2] + 2, its
     assert its[4, 4] <= 45, its
+
+
+def test_pou_weights_on_unstructured_patches():
+    """weighting="pou": W_j = sqrt(P_0[:, j]) on the patch; sum_j W_j^2 = 1 at every interior
+    node, and fewer PCG iterations than unit weights (measured: p = 4, n = 2: 34 -> 21)."""
+    m = _unstructured(2, seed=0)
+    p = 4
+    Bw = un.UnstructuredLOR(m, p, weighting="pou")
+    s = np.zeros(Bw.levels[0].ntot)
+    for pt in Bw.patches:
+        idx = pt["levels"][0]["idx"]
+        s[idx] += Bw.P0[idx, pt["v"]].toarray().ravel()
+    inner = ~Bw.levels[0].boundary
+    np.testing.assert_allclose(s[inner], 1.0, atol=1e-14)
+    L0 = Bw.levels[0]
+    K = un.assemble_stiffness(m, p, L0)
+    b = np.where(inner, 1.0, 0.0)
+    A = lambda z: np.where(inner, K @ np.where(inner, z, 0.0), 0.0)  # noqa: E731
+    it_unit = krylov.pcg(A, un.UnstructuredLOR(m, p).apply, b, rtol=1e-8)[1]
+    it_pou = krylov.pcg(A, Bw.apply, b, rtol=1e-8)[1]
+    assert it_pou <= 0.75 * it_unit, (it_unit, it_pou)
