@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-dg", action="store_true", help="skip the DG penalty-sweep leg")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--weighting", type=int, default=0, choices=[0, 1, 2],
+                    help="patch-sum weighting of the timed form: 0 unit (the paper's method), 1 counting matrix, "
+                         "2 partition of unity")
     ap.add_argument("--summarize-ncu", metavar="CSV",
                     help="print per-kernel launches, total time and share of an ncu launch list "
                          "(--metrics gpu__time_duration.sum --csv) and exit")
@@ -397,7 +400,7 @@ def main():
     bf16 = args.form == "mixed-bf16"
     form = lor.LOR_FP64 if args.form == "fp64" else lor.LOR_MIXED
     t_setup = time.perf_counter()
-    s = lor.Solver(verts, kappa, p, prec=form, rtol=1e-8, factor_bf16=bf16)
+    s = lor.Solver(verts, kappa, p, prec=form, rtol=1e-8, factor_bf16=bf16, weighting=args.weighting)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     ndof = s.info.ndof
@@ -473,9 +476,10 @@ def main():
             ms = a0.elapsed_time(a1) / reps
             mdofs[name] = {"ms": ms, "MDOF/s": ndof / (ms * 1e-3) / 1e6}
         extras["per_apply"] = mdofs
-        # plain FP64 solve for comparison
-        if form != lor.LOR_FP64:
+        # plain FP64 solve for comparison (the paper's method: unit weights)
+        if form != lor.LOR_FP64 or args.weighting:
             s.set_prec(lor.LOR_FP64)
+            s.set_weighting(0)
             x64 = torch.zeros_like(b)
             s.solve(b, x64)
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -484,6 +488,7 @@ def main():
             f1.record(stream)
             torch.cuda.synchronize()
             s.set_prec(form)
+            s.set_weighting(args.weighting)
             dx = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
             extras["fp64_plain"] = {"time_to_tol_ms": f0.elapsed_time(f1), "iterations": it64,
                                     "rel_res": rel64, "chosen_vs_fp64_x_rel_diff": dx,
@@ -491,7 +496,7 @@ def main():
         # the chosen form with a weighted patch sum (options beyond the paper's unit
         # weights; context only, the headline keeps unit weights): 1 counting matrix,
         # 2 partition of unity
-        for wmode, key in ((1, "count_weighted"), (2, "pou_weighted")):
+        for wmode, key in ((1, "count_weighted"), (2, "pou_weighted")) if args.weighting == 0 else ():
             try:
                 s.set_weighting(wmode)
                 xw = torch.zeros_like(b)
@@ -547,7 +552,7 @@ def main():
     # The one capture of this configuration (profiles/patch_warp_q8n32_dram.md: 23.19 GB read +
     # 1.00 GB written) predates the patch-sum weighting option, so it is quoted, not reported.
     roof["traffic"] = None
-    if (names[dom], p, n, args.form) == ("patch_vcycle_fp32", 8, 32, "mixed-bf16"):
+    if (names[dom], p, n, args.form, args.weighting) == ("patch_vcycle_fp32", 8, 32, "mixed-bf16", 0):
         roof["traffic_last_capture"] = {"bytes": 23.19e9 + 1.00e9,
                                         "note": "captured before the weighting option changed the kernel"}
     roof["kernel"] = names[dom]
@@ -560,6 +565,7 @@ def main():
             "vs_baseline": None, "dtype": "f32+bf16/f64" if bf16 else ("f32/f64" if form != lor.LOR_FP64 else "f64"),
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "p": p, "n": n, "ndof": ndof, "form": args.form,
+                       "weighting": ["unit", "counting matrix", "partition of unity"][args.weighting],
                        "l2": "working set (ILU factors, stencils) >> 129 MB L2; no flush needed",
                        "parallelism": f"replicas x{world}"},
             "iterations": its[-1], "rel_res": rels[-1], "setup_s": t_setup, "gpu_launches": launches,
