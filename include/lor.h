@@ -145,6 +145,25 @@ lor_status lor_pcg_solve_host(lor_ctx* ctx, const double* h_b, double* h_x,
  * keeps FP64 and FP32 (and, if requested, bf16) data, so no setup is redone. */
 lor_status lor_set_prec(lor_ctx* ctx, int prec);
 
+/* Pointwise coefficients b(x) (Section 5.2, the coefficients b1-b3) in place of
+ * the per-element kappa, for CG contexts.  The coefficient is sampled at two
+ * point sets, both listed by lor_coefficient_points:
+ *   - the (p+1)^d Gauss-Legendre points of every element, where K_p is
+ *     integrated: nq = nel (p+1)^d points, element-major (elements x fastest),
+ *     q = qx + Q qy + Q^2 qz inside an element;
+ *   - the 2^d Gauss points of every sub-cell of the GLL-refined mesh, where K_h
+ *     is integrated (Section 3.1): nh = cells 2^d points, cells x fastest on the
+ *     (N-1)^d sub-cell grid, g = gx + 2 gy + 4 gz inside a cell.
+ * lor_coefficient_sizes gives nq and nh.  lor_coefficient_points writes the
+ * physical coordinates (dim doubles per point, point-major) into caller-owned
+ * HOST arrays xq and xh (either may be NULL); it makes no CUDA call and works
+ * before lor_setup.  lor_set_coefficient copies the HOST values b(xq) and b(xh);
+ * it must precede lor_setup (LOR_ESTATE after), and it refuses DG contexts, NULL
+ * arrays and values that are not positive and finite (LOR_EINVAL). */
+lor_status lor_coefficient_sizes(const lor_ctx* ctx, long long* nq, long long* nh);
+lor_status lor_coefficient_points(const lor_ctx* ctx, double* xq, double* xh);
+lor_status lor_set_coefficient(lor_ctx* ctx, const double* bq, const double* bh);
+
 /* Switches the patch-sum weighting of lor_options.weighting (0 unit weights,
  * 1 counting matrix, 2 partition of unity) for later calls; the weights are evaluated inside the
  * patch kernel, so no setup is redone.  A batch (lor_batch_create) keeps the

@@ -293,6 +293,44 @@ lor_status lor_pcg_solve_host(lor_ctx* c, const double* hb, double* hx, int* ite
   return s;
 }
 
+lor_status lor_coefficient_sizes(const lor_ctx* c, long long* nq, long long* nh) {
+  if (!c || !nq || !nh) return LOR_EINVAL;
+  lor_coef_sizes(c, nq, nh);
+  return LOR_OK;
+}
+
+lor_status lor_coefficient_points(const lor_ctx* c, double* xq, double* xh) {
+  if (!c) return LOR_EINVAL;
+  lor_coef_points(c, xq, xh);
+  return LOR_OK;
+}
+
+lor_status lor_set_coefficient(lor_ctx* c, const double* bq, const double* bh) {
+  if (!c) return LOR_EINVAL;
+  if (c->setup_started) return lor_fail(c, LOR_ESTATE, "lor_set_coefficient must precede lor_setup");
+  if (c->opt.disc != LOR_CG)
+    return lor_fail(c, LOR_EINVAL, "pointwise coefficients: CG only (the DG penalty takes kappa per element)");
+  if (!bq || !bh) return lor_fail(c, LOR_EINVAL, "lor_set_coefficient: null array");
+  long long nq = 0, nh = 0;
+  lor_coef_sizes(c, &nq, &nh);
+  try {
+    c->h_bq.assign(bq, bq + nq);
+    c->h_bh.assign(bh, bh + nh);
+  } catch (const std::bad_alloc&) {
+    c->h_bq.clear();
+    c->h_bh.clear();
+    return lor_fail(c, LOR_ENOMEM, "lor_set_coefficient: host copy");
+  }
+  for (const std::vector<double>* v : {&c->h_bq, &c->h_bh})
+    for (double x : *v)
+      if (!(x > 0) || !std::isfinite(x)) {
+        c->h_bq.clear();
+        c->h_bh.clear();
+        return lor_fail(c, LOR_EINVAL, "lor_set_coefficient: values must be positive and finite");
+      }
+  return LOR_OK;
+}
+
 lor_status lor_set_weighting(lor_ctx* c, int weighting) {
   if (!c) return LOR_EINVAL;
   if (weighting < 0 || weighting > 2) return lor_fail(c, LOR_EINVAL, "lor_set_weighting: 0, 1 or 2");

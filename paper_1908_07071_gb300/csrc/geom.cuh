@@ -1,16 +1,16 @@
-// Device helpers for multilinear element maps (Section 2: every element is the
+// Host and device helpers for multilinear element maps (Section 2: every element is the
 // image of the unit cube under the multilinear interpolation of its vertices).
 #pragma once
 
 namespace lorg {
 
-__device__ __forceinline__ double det3(const double J[3][3]) {
+__host__ __device__ __forceinline__ double det3(const double J[3][3]) {
   return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
          J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
 }
 
 // inverse of a dim x dim matrix (dim 2 or 3) by the adjugate
-__device__ __forceinline__ void inv_dd(int dim, const double J[3][3], double det, double Ji[3][3]) {
+__host__ __device__ __forceinline__ void inv_dd(int dim, const double J[3][3], double det, double Ji[3][3]) {
   if (dim == 3) {
     Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
     Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
@@ -29,7 +29,7 @@ __device__ __forceinline__ void inv_dd(int dim, const double J[3][3], double det
 
 // Multilinear map of the 2^dim points P[c][a] (corner c = cx + 2cy + 4cz) at xi:
 // X and J[a][b] = dX_a/dxi_b.
-__device__ __forceinline__ void multilinear(int dim, const double (*Pc)[3], const double* xi, double* X, double J[3][3]) {
+__host__ __device__ __forceinline__ void multilinear(int dim, const double (*Pc)[3], const double* xi, double* X, double J[3][3]) {
   for (int a = 0; a < 3; ++a) { X[a] = 0; for (int b = 0; b < 3; ++b) J[a][b] = 0; }
   const int nc = 1 << dim;
   for (int cc = 0; cc < nc; ++cc) {
@@ -50,7 +50,7 @@ __device__ __forceinline__ void multilinear(int dim, const double (*Pc)[3], cons
   }
 }
 
-__device__ __forceinline__ void element_corners(int dim, int nx, int ny, int ex, int ey, int ez, const double* vert,
+__host__ __device__ __forceinline__ void element_corners(int dim, int nx, int ny, int ex, int ey, int ez, const double* vert,
                                        long long NV, double (*Pc)[3]) {
   const int nc = 1 << dim;
   for (int cc = 0; cc < nc; ++cc) {

@@ -89,6 +89,11 @@ struct lor_ctx {
   double* d_vert = nullptr;   // SoA dim x NV
   double* d_kappa = nullptr;
   std::vector<double> h_vert, h_kappa;
+  // optional pointwise coefficient b(x) (lor_set_coefficient): values at the Gauss
+  // points of K_p ([element][q]) and of the LOR sub-cells of K_h ([cell][g])
+  std::vector<double> h_bq, h_bh;
+  double* d_bq = nullptr;
+  double* d_bh = nullptr;
 
   // 1D basis (host copies, device constant tables are uploaded per launch)
   double gll_x[LOR_MAXP + 1], gll_w[LOR_MAXP + 1];
@@ -249,6 +254,9 @@ lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, dou
 lor_status lor_setup_krylov(lor_ctx* c);
 BoxShape* lor_dev_shapes(lor_ctx* c);
 double* lor_basis64(lor_ctx* c, int which);
+// sizes and physical coordinates of the coefficient sample points (host; no CUDA call)
+void lor_coef_sizes(const lor_ctx* c, long long* nq, long long* nh);
+void lor_coef_points(const lor_ctx* c, double* xq, double* xh);
 float* lor_basis32(lor_ctx* c, int which);
 
 // event pair around a hot kernel launch (no-op unless profiling)

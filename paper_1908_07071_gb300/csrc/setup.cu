@@ -26,13 +26,75 @@ double* lor_basis64(lor_ctx* c, int which) { return (double*)c->allocs[0] + whic
 float* lor_basis32(lor_ctx* c, int which) { return (float*)c->allocs[1] + which * kBlk; }
 BoxShape* lor_dev_shapes(lor_ctx* c) { return c->d_shapes; }
 
+// Sample points of a pointwise coefficient (Section 5.2), in the layouts k_geom and
+// k_lor_stencil read: K_p Gauss points [element][q] (elements x fastest, q = qx +
+// Q qy + Q^2 qz, Q = p + 1 Gauss-Legendre points per axis) and the 2-point Gauss
+// points of the LOR sub-cells [cell][g] (cells x fastest on the GLL-refined grid,
+// g = gx + 2 gy + 4 gz), each as dim coordinates.
+void lor_coef_sizes(const lor_ctx* c, long long* nq, long long* nh) {
+  const int dim = c->dim, p = c->p;
+  long long q = 1, cells = 1;
+  for (int a = 0; a < dim; ++a) { q *= p + 1; cells *= (long long)c->n[a] * p; }
+  *nq = (long long)c->nel * q;
+  *nh = cells * (1LL << dim);
+}
+
+void lor_coef_points(const lor_ctx* c, double* xq, double* xh) {
+  const int dim = c->dim, p = c->p, Q = p + 1, nx = c->n[0], ny = c->n[1], nz = c->n[2];
+  double gllx[LOR_MAXP + 1], gllw[LOR_MAXP + 1], glx[LOR_MAXP + 2], glw[LOR_MAXP + 2];
+  lorh::gll(p, gllx, gllw);
+  lorh::gauss(Q, glx, glw);
+  const long long NV = (long long)(nx + 1) * (ny + 1) * (dim == 3 ? nz + 1 : 1);
+  const double* vert = c->h_vert.data();
+  const int Qd = dim == 3 ? Q * Q * Q : Q * Q;
+  double Pc[8][3], X[3], J[3][3];
+  if (xq) {
+    for (long long e = 0; e < c->nel; ++e) {
+      const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = dim == 3 ? (int)(e / ((long long)nx * ny)) : 0;
+      lorg::element_corners(dim, nx, ny, ex, ey, ez, vert, NV, Pc);
+      for (int q = 0; q < Qd; ++q) {
+        const double xi[3] = {glx[q % Q], glx[(q / Q) % Q], dim == 3 ? glx[q / (Q * Q)] : 0.0};
+        lorg::multilinear(dim, Pc, xi, X, J);
+        for (int a = 0; a < dim; ++a) xq[(e * Qd + q) * dim + a] = X[a];
+      }
+    }
+  }
+  if (xh) {
+    const int Nx = nx * p + 1, Ny = ny * p + 1, Nz = dim == 3 ? nz * p + 1 : 1;
+    const double gq = 0.5 - 0.5 / sqrt(3.0);
+    const double g1[2] = {gq, 1.0 - gq};
+    const int nc = 1 << dim;
+    // node position: the element map at the node's GLL point (as k_nodes)
+    auto node = [&](int I, int Jn, int K, double* out) {
+      const int ex = std::min(I / p, nx - 1), ey = std::min(Jn / p, ny - 1), ez = dim == 3 ? std::min(K / p, nz - 1) : 0;
+      const double xi[3] = {gllx[I - ex * p], gllx[Jn - ey * p], dim == 3 ? gllx[K - ez * p] : 0.0};
+      double P[8][3], JJ[3][3];
+      lorg::element_corners(dim, nx, ny, ex, ey, ez, vert, NV, P);
+      lorg::multilinear(dim, P, xi, out, JJ);
+    };
+    long long cidx = 0;
+    for (int oz = 0; oz < (dim == 3 ? Nz - 1 : 1); ++oz)
+      for (int oy = 0; oy < Ny - 1; ++oy)
+        for (int ox = 0; ox < Nx - 1; ++ox, ++cidx) {
+          double Cc[8][3] = {};
+          for (int t = 0; t < nc; ++t) node(ox + (t & 1), oy + ((t >> 1) & 1), oz + ((t >> 2) & 1), Cc[t]);
+          for (int g = 0; g < nc; ++g) {
+            const double xi[3] = {g1[g & 1], g1[(g >> 1) & 1], dim == 3 ? g1[(g >> 2) & 1] : 0.0};
+            lorg::multilinear(dim, Cc, xi, X, J);
+            for (int a = 0; a < dim; ++a) xh[(cidx * nc + g) * dim + a] = X[a];
+          }
+        }
+  }
+}
+
 namespace {
 
 // G[e][comp][q] = kappa_e w_q det J (J^{-1} J^{-T})_{ab}, comps (00,01,02,11,12,22) / (00,01,11)
+// bq (optional): the coefficient at every Gauss point ([e][q]) in place of kappa_e.
 __global__ void k_geom(int dim, int p, int nx, int ny, int nz, const double* __restrict__ vert,
-                       const double* __restrict__ kappa, const double* __restrict__ glx,
-                       const double* __restrict__ glw, double* __restrict__ G64, float* __restrict__ G32,
-                       int* status) {
+                       const double* __restrict__ kappa, const double* __restrict__ bq,
+                       const double* __restrict__ glx, const double* __restrict__ glw, double* __restrict__ G64,
+                       float* __restrict__ G32, int* status) {
   const int Q = p + 1;
   const int Qd = dim == 3 ? Q * Q * Q : Q * Q;
   const long long nel = (long long)nx * ny * (dim == 3 ? nz : 1);
@@ -53,7 +115,7 @@ __global__ void k_geom(int dim, int p, int nx, int ny, int nz, const double* __r
   double Ji[3][3];
   lorg::inv_dd(dim, J, det, Ji);
   const double w = glw[qx] * glw[qy] * (dim == 3 ? glw[qz] : 1.0);
-  const double s = kappa[e] * w * det;
+  const double s = (bq ? bq[gid] : kappa[e]) * w * det;
   const int ncomp = dim == 3 ? 6 : 3;
   const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
   const int ja[3] = {0, 0, 1}, jb[3] = {0, 1, 1};
@@ -86,8 +148,11 @@ __global__ void k_nodes(int dim, int p, int nx, int ny, int nz, const double* __
 }
 
 // K_h stencil row of every level-0 node (all 2^d sub-cells around it).
+// bh (optional): the coefficient at the 2^d Gauss points of every sub-cell
+// ([cell][g], cells x fastest, g = gx + 2 gy + 4 gz) in place of the parent's kappa.
 __global__ void k_lor_stencil(int dim, int p, int nx, int ny, int nz, const double* __restrict__ X,
-                              const double* __restrict__ kappa, double* __restrict__ S) {
+                              const double* __restrict__ kappa, const double* __restrict__ bh,
+                              double* __restrict__ S) {
   const int Nx = nx * p + 1, Ny = ny * p + 1, Nz = dim == 3 ? nz * p + 1 : 1;
   const long long ntot = (long long)Nx * Ny * Nz;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,7 +190,9 @@ __global__ void k_lor_stencil(int dim, int p, int nx, int ny, int nz, const doub
               const double det = dim == 3 ? lorg::det3(J) : (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
               double Ji[3][3];
               lorg::inv_dd(dim, J, det, Ji);
-              const double wq = (dim == 3 ? 0.125 : 0.25) * fabs(det) * kap;
+              const double bv =
+                  bh ? bh[(((long long)oz * (Ny - 1) + oy) * (Nx - 1) + ox) * nc + (gz * 4 + gy * 2 + gx)] : kap;
+              const double wq = (dim == 3 ? 0.125 : 0.25) * fabs(det) * bv;
               // reference gradients of the corner functions
               double gme[3];
               double gref[8][3];
@@ -426,6 +493,10 @@ lor_status lor_setup_geometry(lor_ctx* c) {
   // mesh
   if (upload(c, (void**)&c->d_vert, c->h_vert.data(), c->h_vert.size() * 8)) return LOR_ENOMEM;
   if (upload(c, (void**)&c->d_kappa, c->h_kappa.data(), c->h_kappa.size() * 8)) return LOR_ENOMEM;
+  if (!c->h_bq.empty()) {   // pointwise coefficient (lor_set_coefficient)
+    if (upload(c, (void**)&c->d_bq, c->h_bq.data(), c->h_bq.size() * 8)) return LOR_ENOMEM;
+    if (upload(c, (void**)&c->d_bh, c->h_bh.data(), c->h_bh.size() * 8)) return LOR_ENOMEM;
+  }
   // geometric factors
   const int Qd = c->dim == 3 ? Q * Q * Q : Q * Q;
   const int ncomp = c->dim == 3 ? 6 : 3;
@@ -435,8 +506,8 @@ lor_status lor_setup_geometry(lor_ctx* c) {
   if (!c->d_G64 || !c->d_G32) return lor_fail(c, LOR_ENOMEM, "alloc geometric factors");
   const long long tot = (long long)c->nel * Qd;
   k_geom<<<(unsigned)lor_ceil_div(tot, 128), 128, 0, c->stream>>>(
-      c->dim, p, c->n[0], c->n[1], c->n[2], c->d_vert, c->d_kappa, lor_basis64(c, 2), lor_basis64(c, 3),
-      c->d_G64, c->d_G32, c->d_status);
+      c->dim, p, c->n[0], c->n[1], c->n[2], c->d_vert, c->d_kappa, c->d_bq, lor_basis64(c, 2),
+      lor_basis64(c, 3), c->d_G64, c->d_G32, c->d_status);
   ++c->launches;
   if (lor_cuda_check(c, cudaGetLastError(), "geometry")) return LOR_ECUDA;
   return check_status(c, "geometry");
@@ -553,7 +624,7 @@ lor_status lor_setup_stencils(lor_ctx* c) {
     if (!c->d_S64[l] || !c->d_S32[l]) return lor_fail(c, LOR_ENOMEM, "alloc stencils");
   }
   k_lor_stencil<<<(unsigned)lor_ceil_div(nt0, 128), 128, 0, c->stream>>>(dim, p, c->n[0], c->n[1], c->n[2], c->d_X,
-                                                                           c->d_kappa, c->d_S64[0]);
+                                                                           c->d_kappa, c->d_bh, c->d_S64[0]);
   ++c->launches;
   if (lor_cuda_check(c, cudaGetLastError(), "lor stencil")) return LOR_ECUDA;
   for (int l = 0; l + 1 < c->L; ++l) {

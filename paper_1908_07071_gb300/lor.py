@@ -91,10 +91,14 @@ def load():
     lib.lor_selftest_wait.argtypes = [vp, i]
     lib.lor_set_prec.argtypes = [vp, i]
     lib.lor_set_weighting.argtypes = [vp, i]
+    lib.lor_coefficient_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.lor_coefficient_points.argtypes = [vp, vp, vp]
+    lib.lor_set_coefficient.argtypes = [vp, vp, vp]
     lib.lor_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.lor_profile.argtypes = [vp, i]
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
-    for name in ("lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
+    for name in ("lor_coefficient_sizes", "lor_coefficient_points", "lor_set_coefficient",
+                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -121,11 +125,29 @@ def _ptr(t, dtype, n, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def coefficient_points(lib, ctx, dim):
+    """Host coordinates of the coefficient sample points of a created context: the K_p
+    Gauss points (nq, dim) and the LOR sub-cell Gauss points (nh, dim)."""
+    nq, nh = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    st = lib.lor_coefficient_sizes(ctx, ctypes.byref(nq), ctypes.byref(nh))
+    if st != LOR_OK:
+        raise LorError(st, "lor_coefficient_sizes")
+    xq = np.empty((nq.value, dim))
+    xh = np.empty((nh.value, dim))
+    st = lib.lor_coefficient_points(ctx, xq.ctypes.data_as(ctypes.c_void_p), xh.ctypes.data_as(ctypes.c_void_p))
+    if st != LOR_OK:
+        raise LorError(st, "lor_coefficient_points")
+    return xq, xh
+
+
 class Solver:
     """One LOR-preconditioned problem on the current CUDA device and stream."""
 
     def __init__(self, vertices, kappa, p, *, mg_levels=0, prec=LOR_FP64, rtol=1e-8, max_it=1000,
-                 inner_rtol=1e-3, factor_bf16=False, disc=LOR_CG, eta=1.0, weighting=0, stream=None):
+                 inner_rtol=1e-3, factor_bf16=False, disc=LOR_CG, eta=1.0, weighting=0, coefficient=None,
+                 stream=None):
+        """coefficient: optional callable b(X) of physical points X (n, dim) -> (n,) replacing the
+        per-element kappa (CG only); it is evaluated at the points lor_coefficient_points lists."""
         import torch
         self.lib = load()
         vertices = np.ascontiguousarray(vertices, dtype=np.float64)
@@ -152,6 +174,14 @@ class Solver:
         if st != LOR_OK:
             raise LorError(st, "lor_create rejected the input")
         self.ctx = ctx
+        if coefficient is not None:
+            xq, xh = coefficient_points(self.lib, ctx, dim)
+            bq = np.ascontiguousarray(coefficient(xq), dtype=np.float64)
+            bh = np.ascontiguousarray(coefficient(xh), dtype=np.float64)
+            if bq.shape != (len(xq),) or bh.shape != (len(xh),):
+                raise ValueError("coefficient must map (n, dim) points to n values")
+            self._check(self.lib.lor_set_coefficient(ctx, bq.ctypes.data_as(ctypes.c_void_p),
+                                                     bh.ctypes.data_as(ctypes.c_void_p)))
         self._check(self.lib.lor_setup(ctx))
         self.info = Info()
         self._check(self.lib.lor_get_info(ctx, ctypes.byref(self.info)))

@@ -74,3 +74,59 @@ def test_calls_before_setup_are_rejected(lib):
     assert lib.lor_set_weighting(ctx, 1) == lor.LOR_OK
     assert lib.lor_set_weighting(ctx, 3) == lor.LOR_EINVAL
     lib.lor_destroy(ctx)
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, (3, 2), 3), (3, (2, 1, 2), 2)])
+def test_coefficient_points_match_the_oracle_quadrature(lib, dim, n, p):
+    """lor_coefficient_points (host only) lists the Gauss points of K_p per element and the
+    2-point Gauss points of every LOR sub-cell in the documented order; the oracle computes
+    the same points from its own element maps."""
+    import itertools
+    from oracle import cg
+    from oracle.basis import gauss_legendre
+    from oracle.mesh import Mesh, multilinear
+    verts, kappa = make_mesh(dim, n, seed=6, perturb=0.15)
+    opt = lor.Options()
+    lib.lor_default_options(ctypes.byref(opt))
+    nn = list(n) + [1] * (3 - len(n))
+    opt.dim, opt.p, opt.nx, opt.ny, opt.nz = dim, p, nn[0], nn[1], nn[2]
+    st, ctx = _create(lib, opt, verts, kappa)
+    assert st == lor.LOR_OK
+    xq, xh = lor.coefficient_points(lib, ctx, dim)
+    m = Mesh(verts, kappa)
+    x1, w1 = gauss_legendre(p + 1)
+    pts, _ = cg.tensor_points(dim, x1, w1)
+    ref_q = np.concatenate([m.element_map(e, pts, p)[0] for e in m.elements()])
+    np.testing.assert_allclose(xq, ref_q, atol=1e-14)
+    N = cg.node_shape(m.n, p)
+    X = cg.node_coordinates(m, p)
+    g = 0.5 - 0.5 / np.sqrt(3.0)
+    ref_h = []
+    for cell in itertools.product(*[range(v - 1) for v in reversed(N)]):
+        c = cell[::-1]                                             # (ox, oy[, oz]), x fastest
+        corners = []
+        for t in range(2 ** dim):
+            idx, stride = 0, 1
+            for a in range(dim):
+                idx += (c[a] + ((t >> a) & 1)) * stride
+                stride *= N[a]
+            corners.append(X[idx])
+        for gi in range(2 ** dim):
+            xi = np.array([[g, 1 - g][(gi >> a) & 1] for a in range(dim)])
+            ref_h.append(multilinear(np.array(corners), xi[None, :])[0][0])
+    np.testing.assert_allclose(xh, np.array(ref_h), atol=1e-14)
+    # values: positive and finite only, and CG contexts only
+    bq, bh = np.ones(len(xq)), np.ones(len(xh))
+    bad = bh.copy()
+    bad[3] = 0.0
+    vp = ctypes.c_void_p
+    assert lib.lor_set_coefficient(ctx, bq.ctypes.data_as(vp), bad.ctypes.data_as(vp)) == lor.LOR_EINVAL
+    assert lib.lor_set_coefficient(ctx, None, bh.ctypes.data_as(vp)) == lor.LOR_EINVAL
+    assert lib.lor_set_coefficient(ctx, bq.ctypes.data_as(vp), bh.ctypes.data_as(vp)) == lor.LOR_OK
+    lib.lor_destroy(ctx)
+    if dim == 3:
+        opt.disc, opt.eta = lor.LOR_DG_IP, 10.0
+        st, ctx = _create(lib, opt, verts, kappa)
+        assert st == lor.LOR_OK
+        assert lib.lor_set_coefficient(ctx, bq.ctypes.data_as(vp), bh.ctypes.data_as(vp)) == lor.LOR_EINVAL
+        lib.lor_destroy(ctx)
