@@ -11,3 +11,16 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+# Options beyond the paper's method (partition-of-unity patch weights, pointwise
+# coefficients) run after the tests of the method itself, so that a stop at the first
+# failure (-x) never hides those; the allocation-free right-hand side stays last.
+_LATE = ("test_gpu_weighting_pou.py", "test_gpu_coefficients.py", "test_zz_no_alloc.py")
+
+
+def pytest_collection_modifyitems(session, config, items):
+    def rank(item):
+        name = item.nodeid.split("::")[0].rsplit("/", 1)[-1]
+        return _LATE.index(name) + 1 if name in _LATE else 0
+    items.sort(key=rank)   # stable: the order inside each group is kept
