@@ -13,10 +13,11 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
-# Options beyond the paper's method (partition-of-unity patch weights, pointwise
-# coefficients) run after the tests of the method itself, so that a stop at the first
-# failure (-x) never hides those; the allocation-free right-hand side stays last.
-_LATE = ("test_gpu_weighting_pou.py", "test_gpu_coefficients.py", "test_zz_no_alloc.py")
+# The allocation-free right-hand side runs after the context-based tests; options beyond
+# the paper's method (partition-of-unity patch weights, pointwise coefficients) run after
+# everything else, so that a stop at the first failure (-x) in them hides no test of the
+# method itself.
+_LATE = ("test_zz_no_alloc.py", "test_gpu_weighting_pou.py", "test_gpu_coefficients.py")
 
 
 def pytest_collection_modifyitems(session, config, items):

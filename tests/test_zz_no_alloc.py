@@ -3,10 +3,10 @@
 Callers that may not call cudaMalloc (their framework owns all device memory,
 or their device-memory budget is fixed at start-up) cannot build a solver
 context; lor_rhs_static serves them with its scratch in a static device array.
-This file is collected last on purpose: it checks, through the C ABI, that two
-calls in a row give the same b as the context-based entry point, within the
-1e-12 relative tolerance the right-hand-side parity test uses, and that sizes
-beyond the static array are refused.
+This file runs after the context-based tests (ordered in conftest.py): it checks,
+through the C ABI, that two calls in a row give the same b as the context-based
+entry point, within the 1e-12 relative tolerance the right-hand-side parity test
+uses, and that sizes beyond the static array are refused.
 """
 import ctypes
 
