@@ -277,10 +277,6 @@ class LORPreconditioner:
         self.patch_spans = patch_spans or {}
         if weighting not in ("none", "count", "pou"):
             raise ValueError(f"unknown weighting {weighting!r}")
-        if weighting == "pou" and patch_spans:
-            # the vertex function of an enlarged patch is not its Q1 hat: the weights
-            # would not sum to one (and PCG does not converge with them)
-            raise ValueError("pou weights are defined for vertex patches only")
         self.weighting = weighting
         self.patch_subset = None if patch_subset is None else set(map(tuple, patch_subset))
         self.with_coarse = coarse
@@ -470,6 +466,12 @@ class LORPreconditioner:
     def pou_weights(self, j):
         """sqrt(theta_j) at the level-0 nodes of patch j (its box order).
 
+        Enlarged patches (patch_spans): the Q1 hat of the vertex does not cover the patch,
+        so theta_j = psi_j / sum_k psi_k with psi_j a product of 1D tents that are linear
+        in the physical coordinate along each axis (on the grid line through the vertex),
+        1 at the vertex and 0 at the ends of the patch's span; the normalisation makes
+        the weights a partition of unity whatever the spans are.
+
         theta_j is the Q1 (bilinear/trilinear) function of patch j's vertex v in the
         element reference coordinates: along axis a, 1 - s on the element whose left
         vertex is v and s on the element whose right vertex is v, with s the node's GLL
@@ -477,6 +479,8 @@ class LORPreconditioner:
         the patch boundary, so the weighted sum is a smooth partition of unity (the
         ingredient of the stable decomposition in Section 3.2).  An option beyond the
         paper, like the counting matrix."""
+        if self.patch_spans:
+            return self._tent_weights()[j]
         pt = self.patches[j]
         v = pt["v"]
         xg = gll(self.p)[0]
@@ -486,6 +490,45 @@ class LORPreconditioner:
             hats.append(np.where(e == v[a], 1.0 - s, s))
         grids = np.meshgrid(*reversed(hats), indexing="ij")
         return np.sqrt(np.prod([g.ravel() for g in grids], axis=0))
+
+    def _tent_weights(self):
+        """Normalised physical tents of every patch (see pou_weights)."""
+        if getattr(self, "_tw", None) is not None:
+            return self._tw
+        p, d, N = self.p, self.dim, self.Ns[0]
+        X = node_coordinates(self.mesh, p)
+
+        def coord(v, a, i):
+            """Coordinate a of the node with index i along axis a on the grid line through v."""
+            idx = [v[b] * p for b in range(d)]
+            idx[a] = i
+            flat, stride = 0, 1
+            for b in range(d):
+                flat += idx[b] * stride
+                stride *= N[b]
+            return X[flat, a]
+
+        psi = []
+        for pt in self.patches:
+            v = pt["v"]
+            span = self.patch_spans.get(tuple(v), [(1, 1)] * d)
+            tents = []
+            for a, I in enumerate(pt["levels"][0]["ranges"]):
+                lo, hi = span[a]
+                xv = coord(v, a, v[a] * p)
+                xlo = coord(v, a, max(v[a] - lo, 0) * p)
+                xhi = coord(v, a, min(v[a] + hi, self.mesh.n[a]) * p)
+                xs = np.array([coord(v, a, i) for i in I])
+                t = np.where(xs <= xv, (xs - xlo) / (xv - xlo) if xv > xlo else 1.0,
+                             (xhi - xs) / (xhi - xv) if xhi > xv else 1.0)
+                tents.append(np.clip(t, 0.0, None))
+            grids = np.meshgrid(*reversed(tents), indexing="ij")
+            psi.append(np.prod([g.ravel() for g in grids], axis=0))
+        total = np.zeros(int(np.prod(N)))
+        for pt, s in zip(self.patches, psi):
+            total[pt["levels"][0]["idx"]] += s
+        self._tw = [np.sqrt(s / total[pt["levels"][0]["idx"]]) for pt, s in zip(self.patches, psi)]
+        return self._tw
 
     def count_weights(self):
         """D^{-1/2} on the level-0 grid: D counts the built patches containing each node."""

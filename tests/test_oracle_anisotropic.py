@@ -131,8 +131,27 @@ def test_iterations_flat_in_aspect_ratio_with_enlarged_patches():
     assert its["vertex", 1500.0] >= 2 * its["vertex", 15.0], its
 
 
-def test_pou_weights_refuse_enlarged_patches():
-    v, k = make_strip_mesh(6, 150.0, layers=2)
-    m = Mesh(v, k)
-    with pytest.raises(ValueError):
-        lor.LORPreconditioner(m, 2, patch_spans=lor.isotropic_overlap_spans(m), weighting="pou")
+def test_pou_weights_on_enlarged_patches():
+    """weighting="pou" with enlarged patches: normalised tents in physical coordinates,
+    sum_j W_j^2 = 1 at every interior node, and counts flat in the aspect ratio (measured on
+    8 x 8, 2-layer strip, Q3: 16 / 16 at aspect 15 / 1500; vertex patches 51 / 172)."""
+    p = 3
+    its = {}
+    for ar in (15.0, 1500.0):
+        v, k = make_strip_mesh(8, ar, layers=2, perturb=0.1)
+        m = Mesh(v, k)
+        B = lor.LORPreconditioner(m, p, patch_spans=lor.isotropic_overlap_spans(m), weighting="pou")
+        s = np.zeros(int(np.prod(B.Ns[0])))
+        for j, pt in enumerate(B.patches):
+            idx = pt["levels"][0]["idx"]
+            if len(idx):
+                w = B.pou_weights(j)
+                assert np.all(w > 0)
+                s[idx] += w ** 2
+        inner = ~cg.boundary_mask(B.Ns[0])
+        np.testing.assert_allclose(s[inner], 1.0, atol=1e-14)
+        K = cg.assemble_stiffness(m, p)
+        N = cg.node_shape(m.n, p)
+        b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+        its[ar] = krylov.pcg(lambda z: cg.apply_A(K, N, z), B.apply, b, rtol=1e-8)[1]
+    assert abs(its[1500.0] - its[15.0]) <= 2 and its[1500.0] <= 25, its
