@@ -13,7 +13,8 @@
  *    coordinates are SoA float64: component c of vertex (i,j,k) at
  *    vertices[c*NV + (k*(ny+1)+j)*(nx+1)+i], NV = (nx+1)(ny+1)(nz+1).
  *    kappa[(ez*ny+ey)*nx+ex] > 0 is the piecewise-constant coefficient b of
- *    Eq. (poisson).  Both are HOST pointers, copied by lor_create.
+ *    Eq. (poisson) (lor_set_coefficient replaces it by a pointwise b(x)).
+ *    Both are HOST pointers, copied by lor_create.
  *  - CG vectors ("L-vectors"): float64 (or float32 where a call says so) on
  *    the full Q_p node grid Nx*Ny(*Nz), N = p*n+1 per direction, x fastest:
  *    node (I,J,K) at (K*Ny+J)*Nx+I.  Boundary (Dirichlet) entries of inputs are
