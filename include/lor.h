@@ -165,6 +165,18 @@ lor_status lor_coefficient_sizes(const lor_ctx* ctx, long long* nq, long long* n
 lor_status lor_coefficient_points(const lor_ctx* ctx, double* xq, double* xh);
 lor_status lor_set_coefficient(lor_ctx* ctx, const double* bq, const double* bh);
 
+/* Curved (isoparametric) elements, as in the curved meshes of Section 5.2, for CG
+ * contexts.  X (HOST, copied) gives the physical coordinates of every level-0 GLL
+ * node: X[a*ntot + (K*Ny+J)*Nx+I], ntot = Nx*Ny(*Nz), a < dim (the L-vector node
+ * order).  K_p then uses the degree-p isoparametric map of each element's nodes
+ * (its Jacobian at the Gauss points), and K_h the LOR sub-cells with these
+ * corners.  The coarse space and the patch weights stay defined in reference
+ * coordinates.  Must precede lor_setup (LOR_ESTATE after).  LOR_EINVAL for DG
+ * contexts, with lor_set_coefficient, for a NULL array or a non-finite
+ * coordinate; lor_setup reports a non-positive Jacobian as LOR_EINVAL.
+ * lor_rhs then refuses (LOR_EINVAL): the caller supplies b. */
+lor_status lor_set_node_coordinates(lor_ctx* ctx, const double* X);
+
 /* Switches the patch-sum weighting of lor_options.weighting (0 unit weights,
  * 1 counting matrix, 2 partition of unity) for later calls; the weights are evaluated inside the
  * patch kernel, so no setup is redone.  A batch (lor_batch_create) keeps the

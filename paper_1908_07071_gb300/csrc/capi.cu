@@ -231,6 +231,8 @@ lor_status lor_rhs(lor_ctx* c, int kind, double* d_b) {
   lor_status s = ready(c);
   if (s) return s;
   if (!d_b || kind < 0 || kind > 1) return lor_fail(c, LOR_EINVAL, "lor_rhs: bad argument");
+  if (!c->h_nodes.empty())
+    return lor_fail(c, LOR_EINVAL, "lor_rhs integrates on multilinear elements; curved meshes supply b");
   return lor_launch_rhs(c, kind, d_b);
 }
 
@@ -311,6 +313,8 @@ lor_status lor_set_coefficient(lor_ctx* c, const double* bq, const double* bh) {
   if (c->opt.disc != LOR_CG)
     return lor_fail(c, LOR_EINVAL, "pointwise coefficients: CG only (the DG penalty takes kappa per element)");
   if (!bq || !bh) return lor_fail(c, LOR_EINVAL, "lor_set_coefficient: null array");
+  if (!c->h_nodes.empty())
+    return lor_fail(c, LOR_EINVAL, "pointwise coefficients are sampled on multilinear elements, not curved ones");
   long long nq = 0, nh = 0;
   lor_coef_sizes(c, &nq, &nh);
   try {
@@ -328,6 +332,28 @@ lor_status lor_set_coefficient(lor_ctx* c, const double* bq, const double* bh) {
         c->h_bh.clear();
         return lor_fail(c, LOR_EINVAL, "lor_set_coefficient: values must be positive and finite");
       }
+  return LOR_OK;
+}
+
+lor_status lor_set_node_coordinates(lor_ctx* c, const double* X) {
+  if (!c) return LOR_EINVAL;
+  if (c->setup_started) return lor_fail(c, LOR_ESTATE, "lor_set_node_coordinates must precede lor_setup");
+  if (c->opt.disc != LOR_CG) return lor_fail(c, LOR_EINVAL, "curved elements: CG only");
+  if (!c->h_bq.empty()) return lor_fail(c, LOR_EINVAL, "curved elements do not combine with lor_set_coefficient");
+  if (!X) return lor_fail(c, LOR_EINVAL, "lor_set_node_coordinates: null array");
+  long long ntot = 1;
+  for (int a = 0; a < c->dim; ++a) ntot *= (long long)c->n[a] * c->p + 1;
+  try {
+    c->h_nodes.assign(X, X + ntot * c->dim);
+  } catch (const std::bad_alloc&) {
+    c->h_nodes.clear();
+    return lor_fail(c, LOR_ENOMEM, "lor_set_node_coordinates: host copy");
+  }
+  for (double x : c->h_nodes)
+    if (!std::isfinite(x)) {
+      c->h_nodes.clear();
+      return lor_fail(c, LOR_EINVAL, "lor_set_node_coordinates: non-finite coordinate");
+    }
   return LOR_OK;
 }
 

@@ -94,6 +94,8 @@ struct lor_ctx {
   std::vector<double> h_bq, h_bh;
   double* d_bq = nullptr;
   double* d_bh = nullptr;
+  // optional GLL node coordinates of curved elements (lor_set_node_coordinates), SoA dim x ntot
+  std::vector<double> h_nodes;
 
   // 1D basis (host copies, device constant tables are uploaded per launch)
   double gll_x[LOR_MAXP + 1], gll_w[LOR_MAXP + 1];

@@ -18,7 +18,8 @@
 
 // ------------------------------------------------------------------ basis block
 // Device layout of the small basis block: for precision 64: [B | Dq | glx | glw |
-// gllx], each (LOR_MAXP+2)^2 doubles; for 32: [B | Dq] floats.
+// gllx | Dn], each (LOR_MAXP+2)^2 doubles (Dn: derivative of the GLL Lagrange basis at
+// the Gauss points, [q][i]); for 32: [B | Dq] floats.
 static const int kBlk = (LOR_MAXP + 2) * (LOR_MAXP + 2);
 
 // The two blocks are the first two allocations of the context (lor_setup_geometry).
@@ -126,6 +127,58 @@ __global__ void k_geom(int dim, int p, int nx, int ny, int nz, const double* __r
     const long long o = e * ncomp * Qd + (long long)cpt * Qd + q;
     G64[o] = s * g;
     G32[o] = (float)(s * g);
+  }
+}
+
+// Curved (isoparametric) elements: G as k_geom, with J at each Gauss point from the
+// degree-p interpolant of the element's GLL node coordinates X (SoA dim x ntot):
+// J[a][b] = sum_n X_a(n) d(phi_n)/d(xi_b), phi_n the tensor GLL Lagrange basis.
+// B, D: the 1D basis and its derivative at the Gauss points ([q][i], Q x Q).
+__global__ void k_geom_iso(int dim, int p, int nx, int ny, int nz, const double* __restrict__ X,
+                           const double* __restrict__ kappa, const double* __restrict__ B,
+                           const double* __restrict__ D, const double* __restrict__ glw, double* __restrict__ G64,
+                           float* __restrict__ G32, int* status) {
+  const int Q = p + 1;
+  const int Qd = dim == 3 ? Q * Q * Q : Q * Q;
+  const long long nel = (long long)nx * ny * (dim == 3 ? nz : 1);
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nel * Qd) return;
+  const long long e = gid / Qd;
+  const int q = (int)(gid - e * Qd);
+  const int qx = q % Q, qy = (q / Q) % Q, qz = dim == 3 ? q / (Q * Q) : 0;
+  const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = dim == 3 ? (int)(e / ((long long)nx * ny)) : 0;
+  const int Nx = nx * p + 1, Ny = ny * p + 1;
+  const long long ntot = (long long)Nx * Ny * (dim == 3 ? nz * p + 1 : 1);
+  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  const int nk = dim == 3 ? Q : 1;
+  for (int k = 0; k < nk; ++k)
+    for (int j = 0; j < Q; ++j)
+      for (int i = 0; i < Q; ++i) {
+        const long long node = ((long long)(ez * p + k) * Ny + (ey * p + j)) * Nx + (ex * p + i);
+        const double bx = B[qx * Q + i], by = B[qy * Q + j], bz = dim == 3 ? B[qz * Q + k] : 1.0;
+        const double g[3] = {D[qx * Q + i] * by * bz, bx * D[qy * Q + j] * bz,
+                             dim == 3 ? bx * by * D[qz * Q + k] : 0.0};
+        for (int a = 0; a < dim; ++a) {
+          const double xa = X[a * ntot + node];
+          for (int b = 0; b < dim; ++b) J[a][b] += xa * g[b];
+        }
+      }
+  const double det = dim == 3 ? lorg::det3(J) : (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+  if (!(det > 0)) { atomicOr(status, 1); return; }
+  double Ji[3][3];
+  lorg::inv_dd(dim, J, det, Ji);
+  const double w = glw[qx] * glw[qy] * (dim == 3 ? glw[qz] : 1.0);
+  const double s = kappa[e] * w * det;
+  const int ncomp = dim == 3 ? 6 : 3;
+  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+  const int ja[3] = {0, 0, 1}, jb[3] = {0, 1, 1};
+  for (int cpt = 0; cpt < ncomp; ++cpt) {
+    const int a = dim == 3 ? ia[cpt] : ja[cpt], b = dim == 3 ? ib[cpt] : jb[cpt];
+    double gsum = 0;
+    for (int t = 0; t < dim; ++t) gsum += Ji[a][t] * Ji[b][t];
+    const long long o = e * ncomp * Qd + (long long)cpt * Qd + q;
+    G64[o] = s * gsum;
+    G32[o] = (float)(s * gsum);
   }
 }
 
@@ -465,7 +518,7 @@ static lor_status check_status(lor_ctx* c, const char* what) {
 lor_status lor_setup_geometry(lor_ctx* c) {
   const int p = c->p, Q = p + 1;
   // basis block (allocation 0: doubles, allocation 1: floats)
-  std::vector<double> h64(5 * kBlk, 0.0);
+  std::vector<double> h64(6 * kBlk, 0.0);
   std::vector<float> h32(2 * kBlk, 0.0f);
   lorh::gll(p, c->gll_x, c->gll_w);
   lorh::gauss(Q, c->gl_x, c->gl_w);
@@ -476,6 +529,7 @@ lor_status lor_setup_geometry(lor_ctx* c) {
   for (int i = 0; i < Q * Q; ++i) {
     h64[0 * kBlk + i] = c->B[i];
     h64[1 * kBlk + i] = c->Dq[i];
+    h64[5 * kBlk + i] = Dn[i];
     h32[0 * kBlk + i] = (float)c->B[i];
     h32[1 * kBlk + i] = (float)c->Dq[i];
   }
@@ -505,9 +559,18 @@ lor_status lor_setup_geometry(lor_ctx* c) {
   c->d_G32 = (float*)lor_alloc(c, ng * 4);
   if (!c->d_G64 || !c->d_G32) return lor_fail(c, LOR_ENOMEM, "alloc geometric factors");
   const long long tot = (long long)c->nel * Qd;
-  k_geom<<<(unsigned)lor_ceil_div(tot, 128), 128, 0, c->stream>>>(
-      c->dim, p, c->n[0], c->n[1], c->n[2], c->d_vert, c->d_kappa, c->d_bq, lor_basis64(c, 2),
-      lor_basis64(c, 3), c->d_G64, c->d_G32, c->d_status);
+  if (!c->h_nodes.empty()) {
+    // curved elements (lor_set_node_coordinates): the GLL node coordinates are given;
+    // the stencil setup uses them as they are, and K_p takes its isoparametric map
+    if (upload(c, (void**)&c->d_X, c->h_nodes.data(), c->h_nodes.size() * 8)) return LOR_ENOMEM;
+    k_geom_iso<<<(unsigned)lor_ceil_div(tot, 128), 128, 0, c->stream>>>(
+        c->dim, p, c->n[0], c->n[1], c->n[2], c->d_X, c->d_kappa, lor_basis64(c, 0), lor_basis64(c, 5),
+        lor_basis64(c, 3), c->d_G64, c->d_G32, c->d_status);
+  } else {
+    k_geom<<<(unsigned)lor_ceil_div(tot, 128), 128, 0, c->stream>>>(
+        c->dim, p, c->n[0], c->n[1], c->n[2], c->d_vert, c->d_kappa, c->d_bq, lor_basis64(c, 2),
+        lor_basis64(c, 3), c->d_G64, c->d_G32, c->d_status);
+  }
   ++c->launches;
   if (lor_cuda_check(c, cudaGetLastError(), "geometry")) return LOR_ECUDA;
   return check_status(c, "geometry");
@@ -612,11 +675,13 @@ lor_status lor_setup_stencils(lor_ctx* c) {
     g.ntot = (long long)g.N[0] * g.N[1] * g.N[2];
   }
   const long long nt0 = c->lev[0].ntot;
-  c->d_X = (double*)lor_alloc(c, nt0 * dim * 8);
-  if (!c->d_X) return lor_fail(c, LOR_ENOMEM, "alloc coordinates");
-  k_nodes<<<(unsigned)lor_ceil_div(nt0, 128), 128, 0, c->stream>>>(dim, p, c->n[0], c->n[1], c->n[2], c->d_vert,
-                                                                     lor_basis64(c, 4), c->d_X);
-  ++c->launches;
+  if (!c->d_X) {   // multilinear elements: the element map at the GLL points (curved: given)
+    c->d_X = (double*)lor_alloc(c, nt0 * dim * 8);
+    if (!c->d_X) return lor_fail(c, LOR_ENOMEM, "alloc coordinates");
+    k_nodes<<<(unsigned)lor_ceil_div(nt0, 128), 128, 0, c->stream>>>(dim, p, c->n[0], c->n[1], c->n[2], c->d_vert,
+                                                                       lor_basis64(c, 4), c->d_X);
+    ++c->launches;
+  }
   for (int l = 0; l < c->L; ++l) {
     const long long nt = c->lev[l].ntot;
     c->d_S64[l] = (double*)lor_alloc(c, nt * c->NS * 8);

@@ -94,10 +94,11 @@ def load():
     lib.lor_coefficient_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.lor_coefficient_points.argtypes = [vp, vp, vp]
     lib.lor_set_coefficient.argtypes = [vp, vp, vp]
+    lib.lor_set_node_coordinates.argtypes = [vp, vp]
     lib.lor_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.lor_profile.argtypes = [vp, i]
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
-    for name in ("lor_coefficient_sizes", "lor_coefficient_points", "lor_set_coefficient",
+    for name in ("lor_coefficient_sizes", "lor_coefficient_points", "lor_set_coefficient", "lor_set_node_coordinates",
                  "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
@@ -145,9 +146,11 @@ class Solver:
 
     def __init__(self, vertices, kappa, p, *, mg_levels=0, prec=LOR_FP64, rtol=1e-8, max_it=1000,
                  inner_rtol=1e-3, factor_bf16=False, disc=LOR_CG, eta=1.0, weighting=0, coefficient=None,
-                 stream=None):
+                 node_coordinates=None, stream=None):
         """coefficient: optional callable b(X) of physical points X (n, dim) -> (n,) replacing the
-        per-element kappa (CG only); it is evaluated at the points lor_coefficient_points lists."""
+        per-element kappa (CG only); it is evaluated at the points lor_coefficient_points lists.
+        node_coordinates: optional (ntot, dim) physical coordinates of the level-0 GLL nodes in
+        L-vector order, for curved (isoparametric) elements (CG only; rhs() then refuses)."""
         import torch
         self.lib = load()
         vertices = np.ascontiguousarray(vertices, dtype=np.float64)
@@ -174,6 +177,12 @@ class Solver:
         if st != LOR_OK:
             raise LorError(st, "lor_create rejected the input")
         self.ctx = ctx
+        if node_coordinates is not None:
+            Xn = np.ascontiguousarray(np.asarray(node_coordinates, dtype=np.float64).T)
+            ntot = int(np.prod([v * p + 1 for v in n]))
+            if Xn.shape != (dim, ntot):
+                raise ValueError(f"node_coordinates must have shape ({ntot}, {dim})")
+            self._check(self.lib.lor_set_node_coordinates(ctx, Xn.ctypes.data_as(ctypes.c_void_p)))
         if coefficient is not None:
             xq, xh = coefficient_points(self.lib, ctx, dim)
             bq = np.ascontiguousarray(coefficient(xq), dtype=np.float64)

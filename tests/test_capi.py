@@ -130,3 +130,29 @@ def test_coefficient_points_match_the_oracle_quadrature(lib, dim, n, p):
         assert st == lor.LOR_OK
         assert lib.lor_set_coefficient(ctx, bq.ctypes.data_as(vp), bh.ctypes.data_as(vp)) == lor.LOR_EINVAL
         lib.lor_destroy(ctx)
+
+
+def test_node_coordinates_validation(lib):
+    """lor_set_node_coordinates (curved elements): finite values, CG only, not together
+    with pointwise coefficients; all checked on the host before setup."""
+    verts, kappa = make_mesh(2, 2, seed=0)
+    opt = lor.Options()
+    lib.lor_default_options(ctypes.byref(opt))
+    opt.dim, opt.p, opt.nx, opt.ny = 2, 3, 2, 2
+    ntot = 7 * 7
+    vp = ctypes.c_void_p
+    X = np.zeros(2 * ntot)
+    st, ctx = _create(lib, opt, verts, kappa)
+    bad = X.copy()
+    bad[5] = np.inf
+    assert lib.lor_set_node_coordinates(ctx, bad.ctypes.data_as(vp)) == lor.LOR_EINVAL
+    assert lib.lor_set_node_coordinates(ctx, None) == lor.LOR_EINVAL
+    assert lib.lor_set_node_coordinates(ctx, X.ctypes.data_as(vp)) == lor.LOR_OK
+    xq, xh = lor.coefficient_points(lib, ctx, 2)
+    bq, bh = np.ones(len(xq)), np.ones(len(xh))
+    assert lib.lor_set_coefficient(ctx, bq.ctypes.data_as(vp), bh.ctypes.data_as(vp)) == lor.LOR_EINVAL
+    lib.lor_destroy(ctx)
+    st, ctx = _create(lib, opt, verts, kappa)
+    assert lib.lor_set_coefficient(ctx, bq.ctypes.data_as(vp), bh.ctypes.data_as(vp)) == lor.LOR_OK
+    assert lib.lor_set_node_coordinates(ctx, X.ctypes.data_as(vp)) == lor.LOR_EINVAL
+    lib.lor_destroy(ctx)
