@@ -174,7 +174,7 @@ lor_status lor_set_coefficient(lor_ctx* ctx, const double* bq, const double* bh)
  * coordinates.  Must precede lor_setup (LOR_ESTATE after).  LOR_EINVAL for DG
  * contexts, with lor_set_coefficient, for a NULL array or a non-finite
  * coordinate; lor_setup reports a non-positive Jacobian as LOR_EINVAL.
- * lor_rhs then refuses (LOR_EINVAL): the caller supplies b. */
+ * lor_rhs then integrates on the isoparametric elements. */
 lor_status lor_set_node_coordinates(lor_ctx* ctx, const double* X);
 
 /* Switches the patch-sum weighting of lor_options.weighting (0 unit weights,

@@ -395,6 +395,55 @@ __global__ void k_rhs_weights(int dim, int p, int nx, int ny, int nz, const doub
   W[gid] = w * fabs(det) * fval;
 }
 
+// Curved (isoparametric) elements: the same weights with the point and the Jacobian
+// from the degree-p interpolant of the element's GLL node coordinates X (SoA dim x
+// ntot); B, D: the 1D GLL basis and its derivative at the Gauss points ([q][i]).
+__global__ void k_rhs_weights_iso(int dim, int p, int nx, int ny, int nz, const double* __restrict__ Xn,
+                                  const double* __restrict__ B, const double* __restrict__ D,
+                                  const double* __restrict__ glw, int kind, double* __restrict__ W) {
+  const int Q = p + 1;
+  const int Qd = dim == 3 ? Q * Q * Q : Q * Q;
+  const long long nel = (long long)nx * ny * (dim == 3 ? nz : 1);
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nel * Qd) return;
+  const long long e = gid / Qd;
+  const int q = (int)(gid - e * Qd);
+  const int qx = q % Q, qy = (q / Q) % Q, qz = dim == 3 ? q / (Q * Q) : 0;
+  const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = dim == 3 ? (int)(e / ((long long)nx * ny)) : 0;
+  const int Nx = nx * p + 1, Ny = ny * p + 1;
+  const long long ntot = (long long)Nx * Ny * (dim == 3 ? nz * p + 1 : 1);
+  double X[3] = {0, 0, 0}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  const int nk = dim == 3 ? Q : 1;
+  for (int k = 0; k < nk; ++k)
+    for (int j = 0; j < Q; ++j)
+      for (int i = 0; i < Q; ++i) {
+        const long long node = ((long long)(ez * p + k) * Ny + (ey * p + j)) * Nx + (ex * p + i);
+        const double bx = B[qx * Q + i], by = B[qy * Q + j], bz = dim == 3 ? B[qz * Q + k] : 1.0;
+        const double g[3] = {D[qx * Q + i] * by * bz, bx * D[qy * Q + j] * bz,
+                             dim == 3 ? bx * by * D[qz * Q + k] : 0.0};
+        const double phi = bx * by * bz;
+        for (int a = 0; a < dim; ++a) {
+          const double xa = Xn[a * ntot + node];
+          X[a] += phi * xa;
+          for (int bb = 0; bb < dim; ++bb) J[a][bb] += xa * g[bb];
+        }
+      }
+  double det;
+  if (dim == 3)
+    det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+          J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  else
+    det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  double fval = 1.0;
+  if (kind == 1) {
+    const double pi = 3.14159265358979323846;
+    fval = dim * pi * pi;
+    for (int a = 0; a < dim; ++a) fval *= sin(pi * X[a]);
+  }
+  const double w = glw[qx] * glw[qy] * (dim == 3 ? glw[qz] : 1.0);
+  W[gid] = w * fabs(det) * fval;
+}
+
 __global__ void k_rhs_scatter(int dim, int p, int nx, int ny, int nz, const double* __restrict__ Bm,
                               const double* __restrict__ W, double* __restrict__ b) {
   const int Q = p + 1;
@@ -446,8 +495,13 @@ lor_status lor_launch_rhs_weights(lor_ctx* c, int kind, double* W) {
   const int Q = c->p + 1;
   const long long Qd = c->dim == 3 ? (long long)Q * Q * Q : (long long)Q * Q;
   const long long tot = (long long)c->nel * Qd;
-  k_rhs_weights<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(
-      c->dim, c->p, c->n[0], c->n[1], c->n[2], c->d_vert, lor_basis64(c, 2), lor_basis64(c, 3), kind, W);
+  if (!c->h_nodes.empty())   // curved elements (lor_set_node_coordinates)
+    k_rhs_weights_iso<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(
+        c->dim, c->p, c->n[0], c->n[1], c->n[2], c->d_X, lor_basis64(c, 0), lor_basis64(c, 5), lor_basis64(c, 3),
+        kind, W);
+  else
+    k_rhs_weights<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(
+        c->dim, c->p, c->n[0], c->n[1], c->n[2], c->d_vert, lor_basis64(c, 2), lor_basis64(c, 3), kind, W);
   ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "rhs weights");
 }

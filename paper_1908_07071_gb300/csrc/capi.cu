@@ -231,8 +231,6 @@ lor_status lor_rhs(lor_ctx* c, int kind, double* d_b) {
   lor_status s = ready(c);
   if (s) return s;
   if (!d_b || kind < 0 || kind > 1) return lor_fail(c, LOR_EINVAL, "lor_rhs: bad argument");
-  if (!c->h_nodes.empty())
-    return lor_fail(c, LOR_EINVAL, "lor_rhs integrates on multilinear elements; curved meshes supply b");
   return lor_launch_rhs(c, kind, d_b);
 }
 

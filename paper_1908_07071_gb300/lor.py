@@ -150,7 +150,7 @@ class Solver:
         """coefficient: optional callable b(X) of physical points X (n, dim) -> (n,) replacing the
         per-element kappa (CG only); it is evaluated at the points lor_coefficient_points lists.
         node_coordinates: optional (ntot, dim) physical coordinates of the level-0 GLL nodes in
-        L-vector order, for curved (isoparametric) elements (CG only; rhs() then refuses)."""
+        L-vector order, for curved (isoparametric) elements (CG only)."""
         import torch
         self.lib = load()
         vertices = np.ascontiguousarray(vertices, dtype=np.float64)

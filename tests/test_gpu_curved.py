@@ -1,8 +1,9 @@
 """Curved (isoparametric) elements on the GPU (lor_set_node_coordinates; the curved
 meshes of Section 5.2) against the oracle's isoparametric Mesh(warp=...): FP64
-apply_A and apply_P to 1e-10, PCG counts +-1, and lor_rhs refused (the caller
-supplies b).  The GLL node coordinates handed to the library are the oracle's own
-node positions of the warped mesh (an input, like the vertices)."""
+apply_A and apply_P to 1e-10, the load vector to 1e-12 (the rule and tolerance of
+the right-hand-side parity test), PCG counts +-1.  The GLL node coordinates handed
+to the library are the oracle's own node positions of the warped mesh (an input,
+like the vertices)."""
 import numpy as np
 import pytest
 import torch
@@ -47,8 +48,13 @@ def test_curved_apply_A_and_P_fp64_match_oracle(name):
     s.apply_P(xd, y)
     zo = B.apply(x)
     assert np.abs(y.cpu().numpy() - zo).max() <= 1e-10 * np.abs(zo).max()
-    with pytest.raises(lor.LorError):
-        s.rhs(torch.empty(s.nvec, dtype=torch.float64, device="cuda"), 0)
+    b = torch.empty(s.nvec, dtype=torch.float64, device="cuda")
+    dim = m.dim
+    for kind, f in ((0, lambda Xq: np.ones(len(Xq))),
+                    (1, lambda Xq: dim * np.pi ** 2 * np.prod(np.sin(np.pi * Xq), axis=1))):
+        s.rhs(b, kind)
+        ref = cg.load_vector(m, p, f, q=p + 1)
+        assert np.abs(b.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
     s.close()
 
 
@@ -59,8 +65,9 @@ def test_curved_pcg_iterations_match_oracle():
     s = lor.Solver(v, k, p, node_coordinates=cg.node_coordinates(m, p), rtol=1e-8)
     K = cg.assemble_stiffness(m, p)
     N = cg.node_shape(m.n, p)
-    bo = cg.load_vector(m, p, lambda Xq: np.ones(len(Xq)))
-    b = torch.from_numpy(bo).cuda()
+    b = torch.empty(s.nvec, dtype=torch.float64, device="cuda")
+    s.rhs(b, 0)
+    bo = b.cpu().numpy()
     x = torch.zeros_like(b)
     it, rel = s.solve(b, x)
     ito = krylov.pcg(lambda u: cg.apply_A(K, N, u), olor.LORPreconditioner(m, p).apply, bo, rtol=1e-8)[1]
