@@ -271,3 +271,20 @@ def test_pou_weights_are_square_roots_of_the_coarse_basis(dim, n, p):
         idx = pt["levels"][0]["idx"]
         if len(idx):
             np.testing.assert_allclose(B.pou_weights(j), np.sqrt(P0[idx, j]), atol=1e-14)
+
+
+def test_pou_weighted_vertex_patches_close_the_gap_to_one_patch():
+    """Section 5.1 reports vertex patches needing about twice the iterations of one patch
+    B(1).  Measured (Cartesian 4 x 4, Q4): B(1) 15, vertex patches with unit weights 25,
+    with partition-of-unity weights 16: the gap is the unit-weight overlap sum."""
+    v, k = make_mesh(2, 4, seed=0, perturb=0.0, kappa_const=1.0)
+    m = Mesh(v, k)
+    p = 4
+    K = cg.assemble_stiffness(m, p)
+    N = cg.node_shape(m.n, p)
+    b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+    A = lambda u: cg.apply_A(K, N, u)  # noqa: E731
+    one = krylov.pcg(A, SinglePatchPreconditioner(m, p).apply, b, rtol=1e-8)[1]
+    unit = krylov.pcg(A, olor.LORPreconditioner(m, p).apply, b, rtol=1e-8)[1]
+    pou = krylov.pcg(A, olor.LORPreconditioner(m, p, weighting="pou").apply, b, rtol=1e-8)[1]
+    assert unit >= 1.5 * one and pou <= 1.2 * one, (one, unit, pou)
