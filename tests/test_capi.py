@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library builds, loads, exports every
 function declared in include/lor.h, and rejects invalid input on the host."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -156,3 +157,48 @@ def test_node_coordinates_validation(lib):
     assert lib.lor_set_coefficient(ctx, bq.ctypes.data_as(vp), bh.ctypes.data_as(vp)) == lor.LOR_OK
     assert lib.lor_set_node_coordinates(ctx, X.ctypes.data_as(vp)) == lor.LOR_EINVAL
     lib.lor_destroy(ctx)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "lor.h"
+
+int main(void) {
+  lor_options o;
+  lor_default_options(&o);
+  o.dim = 2; o.p = 3; o.nx = 2; o.ny = 2;
+  double verts[2 * 9], kappa[4] = {1, 1, 1, 1};
+  for (int j = 0; j < 3; ++j)
+    for (int i = 0; i < 3; ++i) { verts[j * 3 + i] = 0.5 * i; verts[9 + j * 3 + i] = 0.5 * j; }
+  lor_ctx* ctx = NULL;
+  lor_status st = lor_create(&ctx, &o, verts, kappa, NULL);
+  long long nq = 0, nh = 0;
+  if (st == LOR_OK) st = lor_coefficient_sizes(ctx, &nq, &nh);
+  printf("%d %lld %lld\n", (int)st, nq, nh);
+  lor_destroy(ctx);
+  return st == LOR_OK ? 0 : 1;
+}
+"""
+
+
+def test_header_is_c99_and_links_from_c(lib, tmp_path):
+    """include/lor.h compiles as strict C99 and the library links and answers from C
+    (host-only calls: options, context creation, coefficient sizes)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_1908_07071_gb300.build import LIB
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(LIB)
+    cmd = [gcc, "-std=c99", "-pedantic", "-Wall", "-Werror", "-I", os.path.join(root, "include"), str(src),
+           "-o", str(exe), "-L", libdir, "-l:" + os.path.basename(LIB), "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.split() == ["0", str(4 * 16), str(36 * 4)]
