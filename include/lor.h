@@ -146,6 +146,25 @@ lor_status lor_pcg_solve_host(lor_ctx* ctx, const double* h_b, double* h_x,
  * keeps FP64 and FP32 (and, if requested, bf16) data, so no setup is redone. */
 lor_status lor_set_prec(lor_ctx* ctx, int prec);
 
+/* Checkpoint / resume of the FP64 PCG solve (an auxiliary service; not in the
+ * paper).  After lor_pcg_solve with LOR_FP64 returned LOR_OK or LOR_ENOCONV on
+ * this context (and before anything else uses its Krylov vectors: another
+ * solve or a batch), lor_pcg_state_save copies the iteration state into a
+ * caller-owned HOST buffer of lor_pcg_state_size bytes.  The state holds a
+ * header (problem sizes, iteration count, ||b||, r.z, r.r), then x (from d_x,
+ * the solve's solution), r = b - A x, z and the search direction p.
+ * lor_pcg_resume continues PCG from such a state, on a context set up for the
+ * same problem (dimension, degree, mesh sizes, discretization, learned
+ * correction on or off), for up to max_it more iterations.  d_b is the
+ * right-hand side and d_x receives the iterate.  *iters counts all iterations
+ * since the original start.  LOR_ESTATE if there is no state to save;
+ * LOR_EINVAL for a buffer that is too small, not a state, or a state of
+ * another problem; LOR_ENOCONV as lor_pcg_solve. */
+lor_status lor_pcg_state_size(const lor_ctx* ctx, size_t* bytes);
+lor_status lor_pcg_state_save(lor_ctx* ctx, const double* d_x, void* host, size_t bytes);
+lor_status lor_pcg_resume(lor_ctx* ctx, const void* host, size_t bytes, const double* d_b, double* d_x, int* iters,
+                          double* rel_res);
+
 /* Pointwise coefficients b(x) (Section 5.2, the coefficients b1-b3) in place of
  * the per-element kappa, for CG contexts.  The coefficient is sampled at two
  * point sets, both listed by lor_coefficient_points:

@@ -251,6 +251,7 @@ lor_status lor_batch_create(lor_batch** out, int n, lor_ctx** ctxs, void* stream
   *out = nullptr;
   for (int i = 0; i < n; ++i)
     if (!ctxs[i] || !ctxs[i]->setup_done || ctxs[i]->dg_state) return LOR_EINVAL;
+  for (int i = 0; i < n; ++i) ctxs[i]->pcg_state_ok = false;   // the batch reuses their Krylov vectors
   lor_batch* b = new lor_batch();
   b->n = n;
   b->c.assign(ctxs, ctxs + n);
@@ -284,6 +285,7 @@ lor_status lor_batch_solve(lor_batch* b, const double* const* d_b, double* const
                            double* rel_res) {
   if (!b || !d_b || !d_x) return LOR_EINVAL;
   const int n = b->n;
+  for (lor_ctx* c : b->c) c->pcg_state_ok = false;   // the batch reuses their Krylov vectors
   // per-solve start: r = b, x = 0, z = P r, p = z (on the main stream)
   for (int s = 0; s < n; ++s) {
     lor_ctx* c = b->c[s];

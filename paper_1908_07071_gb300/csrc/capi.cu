@@ -270,9 +270,36 @@ lor_status lor_pcg_solve(lor_ctx* c, const double* b, double* x, int* iters, dou
   lor_status s = ready(c);
   if (s) return s;
   if (!b || !x) return lor_fail(c, LOR_EINVAL, "lor_pcg_solve: null vector");
+  c->pcg_state_ok = false;   // an FP64 solve leaves a new resumable state
   s = c->opt.prec == LOR_MIXED ? lor_pcg_mixed(c, b, x, iters, rel_res) : lor_pcg64(c, b, x, iters, rel_res);
   if (s != LOR_OK && s != LOR_ENOCONV) return s;
   const lor_status d = lor_take_device_status(c);   // a timed-out patch V-cycle invalidates the result
+  return d != LOR_OK ? d : s;
+}
+
+lor_status lor_pcg_state_size(const lor_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return LOR_EINVAL;
+  if (!c->setup_done) return LOR_ESTATE;
+  *bytes = lor_pcg_state_bytes(c);
+  return LOR_OK;
+}
+
+lor_status lor_pcg_state_save(lor_ctx* c, const double* d_x, void* host, size_t bytes) {
+  lor_status s = ready(c);
+  if (s) return s;
+  if (!d_x || !host) return lor_fail(c, LOR_EINVAL, "lor_pcg_state_save: null pointer");
+  return lor_pcg_save(c, d_x, host, bytes);
+}
+
+lor_status lor_pcg_resume(lor_ctx* c, const void* host, size_t bytes, const double* d_b, double* d_x, int* iters,
+                          double* rel_res) {
+  lor_status s = ready(c);
+  if (s) return s;
+  if (!host || !d_b || !d_x) return lor_fail(c, LOR_EINVAL, "lor_pcg_resume: null pointer");
+  c->pcg_state_ok = false;
+  s = lor_pcg_resume_impl(c, host, bytes, d_b, d_x, iters, rel_res);
+  if (s != LOR_OK && s != LOR_ENOCONV) return s;
+  const lor_status d = lor_take_device_status(c);
   return d != LOR_OK ? d : s;
 }
 

@@ -11,6 +11,7 @@
 // relative tolerance inner_rtol; x += ||r|| d in FP64.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "lor_internal.h"
 
@@ -204,6 +205,10 @@ static lor_status read_scalars(lor_ctx* c) {
   return lor_cuda_check(c, e, "read scalars");
 }
 
+template <typename T, typename FA, typename FP>
+static lor_status pcg_iterate(lor_ctx* c, T* x, T* r, T* z, T* p, T* Ap, long long n, double tol_abs, int max_it,
+                              FA applyA, FP applyP, double rr, int* it_out, double* rr_out, bool record);
+
 // PCG on vectors of type T with operator/preconditioner callbacks.
 // x starts at 0, r = rhs.  Stops at ||r|| <= tol_abs.  Returns iterations via *it.
 template <typename T, typename FA, typename FP>
@@ -218,8 +223,17 @@ static lor_status pcg_core(lor_ctx* c, T* x, T* r, T* z, T* p, T* Ap, long long 
   k_copy<T><<<gb, kRedThreads, 0, c->stream>>>(p, z, n);
   ++c->launches;
   if (read_scalars(c)) return LOR_ECUDA;
-  double rr = c->h_scal[S_RR];
+  const double rr = c->h_scal[S_RR];
   if (record) c->hist.push_back(sqrt(rr));
+  return pcg_iterate<T>(c, x, r, z, p, Ap, n, tol_abs, max_it, applyA, applyP, rr, it_out, rr_out, record);
+}
+
+// PCG (flexible CG with the learned correction) iterations from a consistent state:
+// x, r, p, z = B r, device scalars S_RZ = r.z and S_RR = rr = r.r.  Stops at ||r|| <= tol_abs.
+template <typename T, typename FA, typename FP>
+static lor_status pcg_iterate(lor_ctx* c, T* x, T* r, T* z, T* p, T* Ap, long long n, double tol_abs, int max_it,
+                              FA applyA, FP applyP, double rr, int* it_out, double* rr_out, bool record) {
+  const unsigned gb = red_blocks(n);
   int it = 0;
   lor_status st = LOR_OK;
   while (it < max_it && sqrt(rr) > tol_abs) {
@@ -288,9 +302,97 @@ lor_status lor_pcg64(lor_ctx* c, const double* b, double* x, int* iters, double*
   if (st) return st;
   double rn = 0;
   if (true_residual(c, b, x, r, Ap, &rn)) return LOR_ECUDA;
+  // the iteration state (x, r = b - A x, z, p, r.z) stays in the Krylov vectors for lor_pcg_state_save
+  c->pcg_bnorm = bn;
+  c->pcg_iters = it;
+  c->pcg_state_ok = true;
   if (iters) *iters = it;
   if (relres) *relres = rn / bn;
   if (it >= c->opt.max_it && sqrt(rr) > c->opt.rtol * bn) return lor_fail(c, LOR_ENOCONV, "max_it reached");
+  return LOR_OK;
+}
+
+// ------------------------------------------------------------ checkpoint / resume
+// A saved FP64 PCG state: this header, then x, r, z, p (nv doubles each).  r is the
+// true residual b - A x of the last iterate (the solve ends with it), z = B r of the
+// recursion, p the next search direction and rz = r.z the matching scalar.
+namespace {
+struct PcgState {
+  char magic[8];
+  int dim, p, n[3], disc, flexible, pad;
+  long long nv;
+  long long iteration;
+  double bnorm, rz, rr;
+};
+const char kPcgMagic[8] = {'L', 'O', 'R', 'P', 'C', 'G', '1', 0};
+}  // namespace
+
+size_t lor_pcg_state_bytes(const lor_ctx* c) { return sizeof(PcgState) + 4 * (size_t)c->nv * sizeof(double); }
+
+lor_status lor_pcg_save(lor_ctx* c, const double* x, void* host, size_t bytes) {
+  if (!c->pcg_state_ok) return lor_fail(c, LOR_ESTATE, "no FP64 PCG state: run lor_pcg_solve (FP64) first");
+  if (bytes < lor_pcg_state_bytes(c)) return lor_fail(c, LOR_EINVAL, "lor_pcg_state_save: buffer too small");
+  if (read_scalars(c)) return LOR_ECUDA;
+  PcgState h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kPcgMagic, 8);
+  h.dim = c->dim; h.p = c->p;
+  for (int a = 0; a < 3; ++a) h.n[a] = c->n[a];
+  h.disc = c->opt.disc; h.flexible = c->learned_on ? 1 : 0;
+  h.nv = c->nv; h.iteration = c->pcg_iters;
+  h.bnorm = c->pcg_bnorm; h.rz = c->h_scal[S_RZ]; h.rr = c->h_scal[S_RR];
+  std::memcpy(host, &h, sizeof(h));
+  double* dst = (double*)((char*)host + sizeof(h));
+  const double* src[4] = {x, c->d_v64[0], c->d_v64[1], c->d_v64[2]};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(dst + (size_t)k * c->nv, src[k], c->nv * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return lor_cuda_check(c, e, "lor_pcg_state_save");
+}
+
+lor_status lor_pcg_resume_impl(lor_ctx* c, const void* host, size_t bytes, const double* b, double* x, int* iters,
+                               double* relres) {
+  PcgState h;
+  if (bytes < sizeof(h)) return lor_fail(c, LOR_EINVAL, "lor_pcg_resume: buffer too small");
+  std::memcpy(&h, host, sizeof(h));
+  if (std::memcmp(h.magic, kPcgMagic, 8) != 0) return lor_fail(c, LOR_EINVAL, "lor_pcg_resume: not a PCG state");
+  bool same = h.dim == c->dim && h.p == c->p && h.disc == c->opt.disc && h.nv == c->nv &&
+              h.flexible == (c->learned_on ? 1 : 0);
+  for (int a = 0; a < 3; ++a) same = same && h.n[a] == c->n[a];
+  if (!same) return lor_fail(c, LOR_EINVAL, "lor_pcg_resume: state of a different problem or preconditioner");
+  if (bytes < lor_pcg_state_bytes(c) || !(h.bnorm > 0) || !std::isfinite(h.rz) || !std::isfinite(h.rr))
+    return lor_fail(c, LOR_EINVAL, "lor_pcg_resume: truncated or invalid state");
+  const long long n = c->nv;
+  double *r = c->d_v64[0], *z = c->d_v64[1], *p = c->d_v64[2], *Ap = c->d_v64[3];
+  const double* src = (const double*)((const char*)host + sizeof(h));
+  double* dst[4] = {x, r, z, p};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(dst[k], src + (size_t)k * n, n * 8, cudaMemcpyHostToDevice, c->stream);
+  for (int k = 0; k < 16; ++k) c->h_scal[k] = 0.0;
+  c->h_scal[S_RZ] = h.rz;
+  c->h_scal[S_RR] = h.rr;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_scal, c->h_scal, 16 * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // h_scal is reused by the iteration
+  if (e != cudaSuccess) return lor_cuda_check(c, e, "lor_pcg_resume upload");
+  c->hist.clear();
+  c->hist.push_back(sqrt(h.rr));
+  auto A = [&](const double* in, double* out) { return lor_opA64(c, in, out); };
+  auto P = [&](const double* in, double* out) { return lor_opP64(c, in, out); };
+  int it = 0;
+  double rr = 0;
+  const double tol = c->opt.rtol * h.bnorm;
+  lor_status st = pcg_iterate<double>(c, x, r, z, p, Ap, n, tol, c->opt.max_it, A, P, h.rr, &it, &rr, true);
+  if (st) return st;
+  double rn = 0;
+  if (true_residual(c, b, x, r, Ap, &rn)) return LOR_ECUDA;
+  c->pcg_bnorm = h.bnorm;
+  c->pcg_iters = (int)(h.iteration + it);
+  c->pcg_state_ok = true;
+  if (iters) *iters = c->pcg_iters;
+  if (relres) *relres = rn / h.bnorm;
+  if (it >= c->opt.max_it && sqrt(rr) > tol) return lor_fail(c, LOR_ENOCONV, "max_it reached");
   return LOR_OK;
 }
 

@@ -196,6 +196,10 @@ struct lor_ctx {
   // DG discretization data (dg.cu); nullptr for continuous contexts
   void* dg_state = nullptr;
   long long nv = 0;            // length of the solver's vectors (CG grid or DG blocks)
+  // the last FP64 PCG solve left a resumable state in the Krylov vectors
+  bool pcg_state_ok = false;
+  double pcg_bnorm = 0.0;
+  int pcg_iters = 0;
   int tune_ne = 1;             // apply_A tile variant (elements per CTA), set by the autotuner
   const double* conv_flag = nullptr;   // batched solves: patch kernel returns early when *conv_flag != 0
   // learned correction (learned.cu)
@@ -253,6 +257,11 @@ lor_status lor_take_device_status(lor_ctx* c);
 // krylov.cu
 lor_status lor_pcg64(lor_ctx* c, const double* b, double* x, int* iters, double* relres);
 lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, double* relres);
+// checkpoint / resume of the FP64 PCG (lor_pcg_state_save, lor_pcg_resume)
+size_t lor_pcg_state_bytes(const lor_ctx* c);
+lor_status lor_pcg_save(lor_ctx* c, const double* x, void* host, size_t bytes);
+lor_status lor_pcg_resume_impl(lor_ctx* c, const void* host, size_t bytes, const double* b, double* x, int* iters,
+                               double* relres);
 lor_status lor_setup_krylov(lor_ctx* c);
 BoxShape* lor_dev_shapes(lor_ctx* c);
 double* lor_basis64(lor_ctx* c, int which);

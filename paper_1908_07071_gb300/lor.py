@@ -95,10 +95,14 @@ def load():
     lib.lor_coefficient_points.argtypes = [vp, vp, vp]
     lib.lor_set_coefficient.argtypes = [vp, vp, vp]
     lib.lor_set_node_coordinates.argtypes = [vp, vp]
+    lib.lor_pcg_state_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.lor_pcg_state_save.argtypes = [vp, vp, vp, ctypes.c_size_t]
+    lib.lor_pcg_resume.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(i), pd]
     lib.lor_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.lor_profile.argtypes = [vp, i]
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
     for name in ("lor_coefficient_sizes", "lor_coefficient_points", "lor_set_coefficient", "lor_set_node_coordinates",
+                 "lor_pcg_state_size", "lor_pcg_state_save", "lor_pcg_resume",
                  "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
@@ -245,6 +249,27 @@ class Solver:
         self._check(self.lib.lor_pcg_solve_host(self.ctx, b.ctypes.data_as(ctypes.c_void_p),
                                                 x.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it),
                                                 ctypes.byref(rr)))
+        return it.value, rr.value
+
+    def state_save(self, x):
+        """The FP64 PCG state of the last solve (x its solution) as a host byte array."""
+        import torch
+        nb = ctypes.c_size_t(0)
+        self._check(self.lib.lor_pcg_state_size(self.ctx, ctypes.byref(nb)))
+        buf = np.empty(nb.value, dtype=np.uint8)
+        self._check(self.lib.lor_pcg_state_save(self.ctx, _ptr(x, torch.float64, self.nvec, "x"),
+                                                buf.ctypes.data_as(ctypes.c_void_p), nb.value))
+        return buf
+
+    def resume(self, state, b, x):
+        """Continues PCG from `state` (state_save of the same problem); returns (iterations, rel_res)."""
+        import torch
+        state = np.ascontiguousarray(state, dtype=np.uint8)
+        it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(self.lib.lor_pcg_resume(self.ctx, state.ctypes.data_as(ctypes.c_void_p), state.size,
+                                            _ptr(b, torch.float64, self.nvec, "b"),
+                                            _ptr(x, torch.float64, self.nvec, "x"), ctypes.byref(it),
+                                            ctypes.byref(rr)))
         return it.value, rr.value
 
     def device_status(self):

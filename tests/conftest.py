@@ -15,9 +15,10 @@ def pytest_configure(config):
 
 # The allocation-free right-hand side runs after the context-based tests; options beyond
 # the paper's method (partition-of-unity patch weights, pointwise coefficients, curved
-# elements) run after everything else, so that a stop at the first failure (-x) in them
+# elements, checkpoint/resume) run after everything else, so that a stop at the first failure (-x) in them
 # hides no test of the method itself.
-_LATE = ("test_zz_no_alloc.py", "test_gpu_weighting_pou.py", "test_gpu_coefficients.py", "test_gpu_curved.py")
+_LATE = ("test_zz_no_alloc.py", "test_gpu_weighting_pou.py", "test_gpu_coefficients.py", "test_gpu_curved.py",
+         "test_gpu_checkpoint.py")
 
 
 def pytest_collection_modifyitems(session, config, items):

@@ -71,6 +71,12 @@ def test_calls_before_setup_are_rejected(lib):
     assert b"setup" in lib.lor_last_error(ctx)
     assert lib.lor_device_status(ctx) == lor.LOR_ESTATE
     assert lib.lor_selftest_wait(ctx, 16) == lor.LOR_ESTATE
+    nb = ctypes.c_size_t(0)
+    assert lib.lor_pcg_state_size(ctx, ctypes.byref(nb)) == lor.LOR_ESTATE
+    buf = np.zeros(64, dtype=np.uint8)
+    vp = ctypes.c_void_p
+    assert lib.lor_pcg_state_save(ctx, None, buf.ctypes.data_as(vp), 64) == lor.LOR_ESTATE
+    assert lib.lor_pcg_resume(ctx, buf.ctypes.data_as(vp), 64, None, None, None, None) == lor.LOR_ESTATE
     # option switches are host state and may precede setup; bad values are refused
     assert lib.lor_set_weighting(ctx, 1) == lor.LOR_OK
     assert lib.lor_set_weighting(ctx, 3) == lor.LOR_EINVAL
