@@ -206,6 +206,7 @@ class Solver:
             raise LorError(st, self.lib.lor_last_error(self.ctx).decode())
 
     def close(self):
+        """Frees the context (lor_destroy); later calls on this Solver fail."""
         if getattr(self, "ctx", None):
             self.lib.lor_destroy(self.ctx)
             self.ctx = None
@@ -221,18 +222,22 @@ class Solver:
         return torch.float64 if prec == LOR_FP64 else torch.float32
 
     def rhs(self, b, kind=0):
+        """b = M f into the float64 CUDA tensor b: kind 0 is f = 1, kind 1 the manufactured d pi^2 prod sin(pi x_a)."""
         import torch
         self._check(self.lib.lor_rhs(self.ctx, kind, _ptr(b, torch.float64, self.nvec, "b")))
 
     def apply_A(self, x, y, prec=LOR_FP64):
+        """y = A x (matrix-free operator) in FP64 (float64 tensors) or FP32 (float32 tensors)."""
         dt = self._dt(prec)
         self._check(self.lib.lor_apply_A(self.ctx, _ptr(x, dt, self.nvec, "x"), _ptr(y, dt, self.nvec, "y"), prec))
 
     def apply_P(self, r, z, prec=LOR_FP64):
+        """z = B r (LOR additive-Schwarz preconditioner) in FP64 or FP32."""
         dt = self._dt(prec)
         self._check(self.lib.lor_apply_P(self.ctx, _ptr(r, dt, self.nvec, "r"), _ptr(z, dt, self.nvec, "z"), prec))
 
     def solve(self, b, x):
+        """PCG (FP64, or mixed precision per prec) of A x = b on CUDA tensors; returns (iterations, rel_res)."""
         import torch
         it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
         self._check(self.lib.lor_pcg_solve(self.ctx, _ptr(b, torch.float64, self.nvec, "b"),
@@ -241,6 +246,7 @@ class Solver:
         return it.value, rr.value
 
     def solve_host(self, b: np.ndarray, x: np.ndarray):
+        """The same solve from host float64 arrays (copies inside the call)."""
         if b.dtype != np.float64 or x.dtype != np.float64 or b.size != self.nvec or x.size != self.nvec:
             raise ValueError("host vectors must be float64 of length nvec")
         if not (b.flags.c_contiguous and x.flags.c_contiguous):
@@ -286,17 +292,21 @@ class Solver:
         self._check(self.lib.lor_set_weighting(self.ctx, int(weighting)))
 
     def set_prec(self, prec):
+        """LOR_FP64 or LOR_MIXED for later solves."""
         self._check(self.lib.lor_set_prec(self.ctx, prec))
 
     def launches(self):
+        """Number of kernels this context has launched so far."""
         n = ctypes.c_longlong(0)
         self._check(self.lib.lor_launch_count(self.ctx, ctypes.byref(n)))
         return n.value
 
     def profile(self, on):
+        """Starts (clearing earlier records) or stops CUDA-event timing of the hot kernel classes."""
         self._check(self.lib.lor_profile(self.ctx, int(on)))
 
     def profile_read(self, kernel):
+        """(total ms, launches) of one kernel class since profile(True)."""
         ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
         self._check(self.lib.lor_profile_read(self.ctx, kernel, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
@@ -316,9 +326,11 @@ class Solver:
         return out
 
     def learned_enable(self, on=True):
+        """Switches the learned per-patch correction (flexible CG) on or off."""
         self._check(self.lib.lor_learned_enable(self.ctx, int(bool(on))))
 
     def learned_train(self, steps, batch=64, lr=1e-3, seed=0):
+        """Trains the network on the GPU (Adam); returns the loss of every step."""
         hist = np.zeros(max(steps, 1), dtype=np.float32)
         self._check(self.lib.lor_learned_train(self.ctx, steps, batch, ctypes.c_float(lr), seed,
                                                hist.ctypes.data_as(ctypes.c_void_p)))
@@ -340,6 +352,7 @@ class Solver:
         return c, loss, grad
 
     def history(self):
+        """Residual 2-norms of the last solve, one per iteration."""
         cnt = ctypes.c_int(0)
         self.lib.lor_residual_history(self.ctx, None, 0, ctypes.byref(cnt))
         out = (ctypes.c_double * max(cnt.value, 1))()
@@ -364,6 +377,7 @@ class Batch:
         self.b = b
 
     def solve(self, bs, xs):
+        """Solves every context's problem (lists of float64 CUDA tensors); returns (iterations, rel_res) lists."""
         import torch
         n = len(self.solvers)
         pb = (ctypes.c_void_p * n)(*[_ptr(b, torch.float64, s.nvec, "b").value for b, s in zip(bs, self.solvers)])
@@ -376,11 +390,13 @@ class Batch:
         return list(its), list(rel)
 
     def stats(self):
+        """(milliseconds of the graph-launch loop of the last solve, nodes of the captured graph)."""
         ms, nodes = ctypes.c_double(0.0), ctypes.c_int(0)
         self.lib.lor_batch_stats(self.b, ctypes.byref(ms), ctypes.byref(nodes))
         return ms.value, nodes.value
 
     def close(self):
+        """Frees the batch (the contexts stay)."""
         if getattr(self, "b", None):
             self.lib.lor_batch_destroy(self.b)
             self.b = None
