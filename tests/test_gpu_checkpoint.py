@@ -32,8 +32,10 @@ def test_pcg_checkpoint_and_resume():
     x2 = torch.zeros_like(b)
     it, rel = s2.resume(state, b, x2)
     assert rel <= 1e-8 and abs(it - it_ref) <= 1, (it, it_ref)
+    # both iterates have relative residual <= 1e-8, so they differ by at most
+    # cond(A) * 2e-8 = 5.6e-6 (cond(A) = 279 for this problem, from the oracle's eigenvalues)
     d = float(torch.linalg.norm(x2 - x_ref) / torch.linalg.norm(x_ref))
-    assert d <= 1e-6, d
+    assert d <= 1e-5, d
     # the resumed context holds a state again: a second resume finishes at once
     state2 = s2.state_save(x2)
     x3 = torch.zeros_like(b)
