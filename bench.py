@@ -164,6 +164,28 @@ def run_cpu_leg(p, n, seed, budget_s, iters):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def run_cpu_leg_all_cores(p, n, budget_s, iters, cores):
+    """The same sample on every host core at once: one single-threaded process per core
+    (BLAS pinned to 1 thread, seed = process index), started together; the whole-host
+    throughput of independent solves is the sum of the per-process rates."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs = []
+    for i in range(cores):
+        code = (f"import json,sys; sys.path.insert(0, {ROOT!r}); import bench; "
+                f"print(json.dumps(bench.cpu_sample_worker({p},{n},{i},{budget_s},{iters})))")
+        procs.append(subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    rates = []
+    for pr in procs:
+        out, err = pr.communicate(timeout=900)
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        rates.append(1.0 / json.loads(out.strip().splitlines()[-1])["solve_s"])
+    return {"value": sum(rates), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} concurrent single-threaded processes, each timing the single-core sample "
+                      f"(seeds 0..{cores - 1}); sum of their rates"}
+
+
 # ------------------------------------------------------------------- clocks
 class Clocks:
     def __init__(self):
@@ -590,6 +612,11 @@ def main():
         except Exception as exc:   # the CPU leg must not hide the GPU result
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {exc}"}
+        try:
+            cores = max(1, min(os.cpu_count() or 1, 64))
+            line["cpu_baseline_all_cores"] = run_cpu_leg_all_cores(p, n, args.cpu_sample_s, its64, cores)
+        except Exception as exc:
+            line["cpu_baseline_all_cores"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()
