@@ -53,3 +53,14 @@ def test_ncu_launch_list_summary(tmp_path):
     dot = rows["k_dot<float,"]
     assert dot[-3:] == ["1", "0.500", "11.11%"]
     assert rows["all"][-2:] == ["3", "4.500"]
+
+
+def test_all_cores_cpu_baseline_sums_concurrent_samples():
+    """run_cpu_leg_all_cores: one single-threaded oracle sample per process, run together;
+    the reported throughput is the sum of the per-process rates (replica semantics)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.run_cpu_leg_all_cores(2, 3, 0.3, 20, 2)
+    one = bench.run_cpu_leg(2, 3, 0, 0.3, 20)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
+    assert 0.5 / one["solve_s"] < r["value"] < 4.0 / one["solve_s"], (r["value"], 1.0 / one["solve_s"])
