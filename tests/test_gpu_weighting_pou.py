@@ -55,3 +55,22 @@ def test_pou_mixed_precision_reaches_tolerance():
     it, rel = s.solve(b, x)
     assert rel <= 1e-8 and it > 0
     s.close()
+
+
+@pytest.mark.parametrize("form,n,p,eta", [("ip", 2, 2, 4.0), ("br2", (2, 3, 2), 3, 6.0)])
+def test_pou_dg_apply_P_fp64_matches_oracle(form, n, p, eta):
+    """The DG preconditioner wraps the CG one, so the weighting applies there too."""
+    from oracle import dg as odg
+    from paper_1908_07071_gb300 import lor
+    v, k = make_mesh(3, n, seed=0, perturb=0.15)
+    m = Mesh(v, k)
+    disc = lor.LOR_DG_IP if form == "ip" else lor.LOR_DG_BR2
+    s = lor.Solver(v, k, p, disc=disc, eta=eta, weighting=2)
+    A = odg.assemble_dg(m, p, eta, form=form)
+    P = odg.DGPreconditioner(m, p, A, olor.LORPreconditioner(m, p, weighting="pou"))
+    r = random_vector(s.nvec, 33)
+    ref = P.apply(r)
+    z = torch.full((s.nvec,), np.nan, dtype=torch.float64, device="cuda")
+    s.apply_P(torch.from_numpy(r).cuda(), z)
+    assert np.abs(z.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+    s.close()
