@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "lor_internal.h"
+#include "geom.cuh"
 
 namespace {
 
@@ -412,22 +413,8 @@ __global__ void k_rhs_weights_iso(int dim, int p, int nx, int ny, int nz, const 
   const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = dim == 3 ? (int)(e / ((long long)nx * ny)) : 0;
   const int Nx = nx * p + 1, Ny = ny * p + 1;
   const long long ntot = (long long)Nx * Ny * (dim == 3 ? nz * p + 1 : 1);
-  double X[3] = {0, 0, 0}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  const int nk = dim == 3 ? Q : 1;
-  for (int k = 0; k < nk; ++k)
-    for (int j = 0; j < Q; ++j)
-      for (int i = 0; i < Q; ++i) {
-        const long long node = ((long long)(ez * p + k) * Ny + (ey * p + j)) * Nx + (ex * p + i);
-        const double bx = B[qx * Q + i], by = B[qy * Q + j], bz = dim == 3 ? B[qz * Q + k] : 1.0;
-        const double g[3] = {D[qx * Q + i] * by * bz, bx * D[qy * Q + j] * bz,
-                             dim == 3 ? bx * by * D[qz * Q + k] : 0.0};
-        const double phi = bx * by * bz;
-        for (int a = 0; a < dim; ++a) {
-          const double xa = Xn[a * ntot + node];
-          X[a] += phi * xa;
-          for (int bb = 0; bb < dim; ++bb) J[a][bb] += xa * g[bb];
-        }
-      }
+  double X[3], J[3][3];
+  lorg::iso_map(dim, p, ex, ey, ez, qx, qy, qz, Nx, Ny, ntot, Xn, B, D, X, J);
   double det;
   if (dim == 3)
     det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +

@@ -61,4 +61,30 @@ __host__ __device__ __forceinline__ void element_corners(int dim, int nx, int ny
 }
 
 
+// Isoparametric (curved) element map: the degree-p interpolant of the element's GLL
+// node coordinates Xn (SoA dim x ntot on the Nx x Ny (x Nz) node grid) at the Gauss
+// point (qx, qy, qz) of element (ex, ey, ez).  B, D: the 1D GLL basis and its
+// derivative at the Gauss points ([q][i], Q = p + 1).  Returns X and J[a][b] = dX_a/dxi_b.
+__device__ __forceinline__ void iso_map(int dim, int p, int ex, int ey, int ez, int qx, int qy, int qz, int Nx,
+                                        int Ny, long long ntot, const double* Xn, const double* B,
+                                        const double* D, double* X, double J[3][3]) {
+  const int Q = p + 1;
+  for (int a = 0; a < 3; ++a) { X[a] = 0; for (int b = 0; b < 3; ++b) J[a][b] = 0; }
+  const int nk = dim == 3 ? Q : 1;
+  for (int k = 0; k < nk; ++k)
+    for (int j = 0; j < Q; ++j)
+      for (int i = 0; i < Q; ++i) {
+        const long long node = ((long long)(ez * p + k) * Ny + (ey * p + j)) * Nx + (ex * p + i);
+        const double bx = B[qx * Q + i], by = B[qy * Q + j], bz = dim == 3 ? B[qz * Q + k] : 1.0;
+        const double g[3] = {D[qx * Q + i] * by * bz, bx * D[qy * Q + j] * bz,
+                             dim == 3 ? bx * by * D[qz * Q + k] : 0.0};
+        const double phi = bx * by * bz;
+        for (int a = 0; a < dim; ++a) {
+          const double xa = Xn[a * ntot + node];
+          X[a] += phi * xa;
+          for (int b = 0; b < dim; ++b) J[a][b] += xa * g[b];
+        }
+      }
+}
+
 }  // namespace lorg

@@ -149,20 +149,8 @@ __global__ void k_geom_iso(int dim, int p, int nx, int ny, int nz, const double*
   const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = dim == 3 ? (int)(e / ((long long)nx * ny)) : 0;
   const int Nx = nx * p + 1, Ny = ny * p + 1;
   const long long ntot = (long long)Nx * Ny * (dim == 3 ? nz * p + 1 : 1);
-  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  const int nk = dim == 3 ? Q : 1;
-  for (int k = 0; k < nk; ++k)
-    for (int j = 0; j < Q; ++j)
-      for (int i = 0; i < Q; ++i) {
-        const long long node = ((long long)(ez * p + k) * Ny + (ey * p + j)) * Nx + (ex * p + i);
-        const double bx = B[qx * Q + i], by = B[qy * Q + j], bz = dim == 3 ? B[qz * Q + k] : 1.0;
-        const double g[3] = {D[qx * Q + i] * by * bz, bx * D[qy * Q + j] * bz,
-                             dim == 3 ? bx * by * D[qz * Q + k] : 0.0};
-        for (int a = 0; a < dim; ++a) {
-          const double xa = X[a * ntot + node];
-          for (int b = 0; b < dim; ++b) J[a][b] += xa * g[b];
-        }
-      }
+  double Xq[3], J[3][3];
+  lorg::iso_map(dim, p, ex, ey, ez, qx, qy, qz, Nx, Ny, ntot, X, B, D, Xq, J);
   const double det = dim == 3 ? lorg::det3(J) : (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
   if (!(det > 0)) { atomicOr(status, 1); return; }
   double Ji[3][3];
