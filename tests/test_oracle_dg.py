@@ -131,3 +131,27 @@ def test_spd_threshold_and_eta_robust_iterations(form):
         b = dg.load_vector_dg(m, p, lambda X: np.ones(len(X)))
         its.append(krylov.pcg(lambda u: A @ u, P.apply, b, rtol=1e-8)[1])
     assert max(its) <= 1.6 * min(its) + 2, its
+
+
+def test_dg_counts_bounded_under_h_refinement_table7():
+    """Section 5.3, Table 7: BR2 counts do not grow under h-refinement (25, 24, 23, 22 on
+    mesh (a), golden file).  B_DG with B(1) inside on perturbed 3^2 and 6^2 meshes of
+    [-1,1]^2 (Q4, eta = 10): measured 19 and 19 (12^2: 18); with vertex patches 36, 38, 39."""
+    import os
+    from oracle.single_patch import SinglePatchPreconditioner
+    gold = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden",
+                                                  "table7_br2_h_refinement.txt")) if not l.startswith("#")]
+    paper = [int(r[1]) for r in gold]
+    assert paper == sorted(paper, reverse=True)             # the paper's counts fall with h
+    p = 4
+    its = {}
+    for n in (3, 6):
+        v, k = make_mesh(2, n, seed=0, perturb=0.15, kappa_const=1.0)
+        m = Mesh(2 * v - 1, k)
+        A = dg.assemble_dg(m, p, 10.0, "br2")
+        b = dg.load_vector_dg(m, p, lambda X: np.ones(len(X)))
+        for name, inner in (("B(1)", SinglePatchPreconditioner(m, p)), ("B(V)", lor.LORPreconditioner(m, p))):
+            its[name, n] = krylov.pcg(lambda z: A @ z, dg.DGPreconditioner(m, p, A, inner).apply, b, rtol=1e-8)[1]
+    assert abs(its["B(1)", 6] - its["B(1)", 3]) <= 2, its
+    assert its["B(V)", 6] <= 1.15 * its["B(V)", 3], its
+    assert 0.7 * paper[0] <= its["B(1)", 3] <= 1.3 * paper[0], (its, paper)
