@@ -76,10 +76,31 @@ def ilu_apply(L, U, r):
     return spla.spsolve_triangular(U, w, lower=False)
 
 
-class SinglePatchPreconditioner:
-    """B(1) r = one V(1,1) cycle of the element-structured hierarchy on the whole domain."""
+SMOOTHERS = ("ilu", "jacobi", "gs", "line-jacobi", "line-gs")
 
-    def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0, K_h=None):
+
+def line_blocks(N, mask):
+    """Interior unknowns grouped by x-line (fixed y[, z]), in the order of the masked grid."""
+    ids = np.nonzero(mask)[0]
+    pos = np.empty(len(mask), dtype=np.int64)
+    pos[ids] = np.arange(len(ids))
+    key = ids // N[0]
+    return [pos[ids[key == k]] for k in np.unique(key)]
+
+
+class SinglePatchPreconditioner:
+    """B(1) r = one V(1,1) cycle of the element-structured hierarchy on the whole domain.
+
+    smoother (Section 3.4 compares smoothers on the GLL-refined mesh): "ilu" (ordered
+    ILU(0), the method), "jacobi" (damped point Jacobi, weight 2/3), "gs" (point
+    Gauss-Seidel: forward sweep before, backward sweep after the coarse correction, so
+    the cycle stays symmetric), "line-jacobi" (damped block Jacobi on x-lines, weight
+    2/3) and "line-gs" (block Gauss-Seidel on x-lines, forward then backward)."""
+
+    def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0, K_h=None, smoother: str = "ilu"):
+        if smoother not in SMOOTHERS:
+            raise ValueError(smoother)
+        self.smoother = smoother
         self.base = LORPreconditioner(mesh, p, mg_levels=mg_levels, patch_subset=[], K_h=K_h)
         b = self.base
         self.L = len(b.A)
@@ -90,9 +111,35 @@ class SinglePatchPreconditioner:
             P = kron_nd(b.P1[l]).tocsr()
             self.P.append(P[self.mask[l]][:, self.mask[l + 1]].tocsr())
         self.LU = []
+        self.lines = []
         for l in range(self.L - 1):
-            pat = grid_pattern(b.Ns[l])[self.mask[l]][:, self.mask[l]]
-            self.LU.append(ilu0_csr(self.A[l], pat))
+            if smoother == "ilu":
+                pat = grid_pattern(b.Ns[l])[self.mask[l]][:, self.mask[l]]
+                self.LU.append(ilu0_csr(self.A[l], pat))
+            self.lines.append(line_blocks(b.Ns[l], self.mask[l]) if smoother.startswith("line") else None)
+
+    def smooth(self, l, r, x, forward=True):
+        """One smoothing step x <- x + M^{-1} (r - A x) on level l (pre: forward, post: backward)."""
+        A = self.A[l]
+        if self.smoother == "ilu":
+            return x + ilu_apply(*self.LU[l], r - A @ x)
+        if self.smoother == "jacobi":
+            return x + (2.0 / 3.0) * (r - A @ x) / A.diagonal()
+        if self.smoother == "gs":
+            Ad = A.toarray()
+            T = np.tril(Ad) if forward else np.triu(Ad)
+            return x + spla.spsolve_triangular(sp.csr_matrix(T), r - A @ x, lower=forward)
+        blocks = self.lines[l] if forward else self.lines[l][::-1]
+        if self.smoother == "line-jacobi":
+            res = r - A @ x
+            y = x.copy()
+            for blk in blocks:
+                y[blk] += (2.0 / 3.0) * np.linalg.solve(A[blk][:, blk].toarray(), res[blk])
+            return y
+        y = x.copy()                                      # line Gauss-Seidel
+        for blk in blocks:
+            y[blk] += np.linalg.solve(A[blk][:, blk].toarray(), (r - A @ y)[blk])
+        return y
 
     def vcycle(self, l, r):
         """V(1,1) on global level l (Section 3.3); R_0 on the vertex level."""
@@ -100,13 +147,12 @@ class SinglePatchPreconditioner:
             return r
         if l == self.L - 1:
             return self.base.coarse_solve(r)
-        Lf, Uf = self.LU[l]
         A = self.A[l]
-        x = ilu_apply(Lf, Uf, r)
+        x = self.smooth(l, r, np.zeros_like(r), forward=True)
         P = self.P[l]
         if P.shape[1] > 0:
             x = x + P @ self.vcycle(l + 1, P.T @ (r - A @ x))
-        return x + ilu_apply(Lf, Uf, r - A @ x)
+        return self.smooth(l, r, x, forward=False)
 
     def apply(self, r):
         """B(1) r on the full node grid; Dirichlet entries are ignored and returned as 0."""

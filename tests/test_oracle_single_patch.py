@@ -288,3 +288,22 @@ def test_pou_weighted_vertex_patches_close_the_gap_to_one_patch():
     unit = krylov.pcg(A, olor.LORPreconditioner(m, p).apply, b, rtol=1e-8)[1]
     pou = krylov.pcg(A, olor.LORPreconditioner(m, p, weighting="pou").apply, b, rtol=1e-8)[1]
     assert unit >= 1.5 * one and pou <= 1.2 * one, (one, unit, pou)
+
+
+def test_smoother_comparison_on_the_gll_refined_mesh():
+    """Section 3.4: pointwise smoothers degrade on the anisotropic GLL-refined mesh as p
+    grows, ordered ILU(0) does not.  Measured (B(1), Cartesian 4 x 4), p = 4 / 12: ILU 15 / 19,
+    Jacobi 15 / 32, Gauss-Seidel 17 / 26, line Jacobi 16 / 28, line Gauss-Seidel 16 / 23."""
+    from oracle.single_patch import SMOOTHERS
+    v, k = make_mesh(2, 4, seed=0, perturb=0.0, kappa_const=1.0)
+    m = Mesh(v, k)
+    its = {}
+    for p in (4, 12):
+        N = cg.node_shape(m.n, p)
+        K = cg.assemble_stiffness(m, p)
+        b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+        A = lambda u: cg.apply_A(K, N, u)  # noqa: E731
+        for s in SMOOTHERS:
+            its[s, p] = krylov.pcg(A, SinglePatchPreconditioner(m, p, smoother=s).apply, b, rtol=1e-8)[1]
+    assert all(its["ilu", 12] <= its[s, 12] for s in SMOOTHERS), its
+    assert its["jacobi", 12] >= 1.8 * its["jacobi", 4] and its["ilu", 12] <= 1.4 * its["ilu", 4], its
