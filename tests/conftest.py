@@ -17,7 +17,7 @@ def pytest_configure(config):
 # the paper's method (partition-of-unity patch weights, pointwise coefficients, curved
 # elements, checkpoint/resume) run after everything else, so that a stop at the first failure (-x) in them
 # hides no test of the method itself.
-_LATE = ("test_zz_no_alloc.py", "test_gpu_coefficients.py", "test_gpu_checkpoint.py", "test_gpu_curved.py",
+_LATE = ("test_zz_no_alloc.py", "test_gpu_forward_error.py", "test_gpu_coefficients.py", "test_gpu_checkpoint.py", "test_gpu_curved.py",
          "test_gpu_weighting_pou.py")
 
 
