@@ -18,7 +18,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from .basis import gauss_legendre, gll, lagrange
-from .mesh import Mesh, multilinear
+from .mesh import Mesh, multilinear, oriented_det
 
 
 def node_shape(n, p):
@@ -58,7 +58,7 @@ def tensor_points(dim, pts1d, w1d):
 
 
 def element_stiffness(corners, kappa, p, q=None, geom=None):
-    """Dense K_e[a,b] = sum_q w_q |det J_q| kappa grad phi_a . grad phi_b.
+    """Dense K_e[a,b] = sum_q w_q det J_q kappa grad phi_a . grad phi_b (det J > 0, `oriented_det`).
 
     kappa: the element's constant, or a callable b(X) of the physical points X (Q, d)
     (the variable coefficients of Section 5.2), evaluated at the quadrature points.
@@ -72,11 +72,11 @@ def element_stiffness(corners, kappa, p, q=None, geom=None):
     Xq, J = multilinear(corners, pts) if geom is None else geom(pts)
     if callable(kappa):
         kappa = np.asarray(kappa(Xq), dtype=np.float64)
-    detJ = np.linalg.det(J)
+    detJ = oriented_det(J)
     Jinv = np.linalg.inv(J)                      # (Q, d, d)
     # physical gradient: grad_x phi = J^{-T} grad_xi phi
     gphys = np.einsum("qba,bqn->aqn", Jinv, dphi)   # (d, Q, nb)
-    wk = w * np.abs(detJ) * kappa
+    wk = w * detJ * kappa
     return np.einsum("aqi,q,aqj->ij", gphys, wk, gphys)
 
 
@@ -186,7 +186,7 @@ def apply_A_rows(mesh: Mesh, p: int, x, rows):
 
 
 def load_vector(mesh: Mesh, p: int, f, q=None):
-    """b_a = sum_e sum_q w_q |det J| f(X_q) phi_a(X_q) with q-point GL (default p+2); boundary zeroed."""
+    """b_a = sum_e sum_q w_q det J f(X_q) phi_a(X_q) with q-point GL (default p+2); boundary zeroed."""
     N = node_shape(mesh.n, p)
     ntot = int(np.prod(N))
     x1, w1 = gauss_legendre(p + 2 if q is None else q)
@@ -196,7 +196,7 @@ def load_vector(mesh: Mesh, p: int, f, q=None):
     for e in mesh.elements():
         X, J = mesh.element_map(e, pts, p)
         fv = f(X)
-        wq = w * np.abs(np.linalg.det(J)) * fv
+        wq = w * oriented_det(J) * fv
         np.add.at(b, element_nodes(e, p, N), phi.T @ wq)
     b[boundary_mask(N)] = 0.0
     return b
@@ -225,5 +225,5 @@ def l2_error(mesh: Mesh, p: int, u, exact):
     for e in mesh.elements():
         X, J = mesh.element_map(e, pts, p)
         uh = phi @ u[element_nodes(e, p, N)]
-        err += np.sum(w * np.abs(np.linalg.det(J)) * (uh - exact(X)) ** 2)
+        err += np.sum(w * oriented_det(J) * (uh - exact(X)) ** 2)
     return np.sqrt(err)

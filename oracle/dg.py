@@ -29,7 +29,7 @@ import scipy.sparse as sp
 
 from .basis import gauss_legendre, gll, lagrange
 from .cg import boundary_mask, element_stiffness, node_shape, tensor_points
-from .mesh import Mesh, multilinear
+from .mesh import Mesh, multilinear, oriented_det
 
 
 def basis_at(p, pts):
@@ -76,21 +76,21 @@ def face_points(d, a, side, x1):
 
 
 def element_volume(corners, p):
-    """|D| by (p+1)^d-point Gauss quadrature of |det J| (the h_F of the SIPG penalty, Section 2.1)."""
+    """|D| by (p+1)^d-point Gauss quadrature of det J (the h_F of the SIPG penalty, Section 2.1)."""
     x1, w1 = gauss_legendre(p + 1)
     pts, w = tensor_points(corners.shape[1], x1, w1)
     _, J = multilinear(corners, pts)
-    return float(np.sum(w * np.abs(np.linalg.det(J))))
+    return float(np.sum(w * oriented_det(J)))
 
 
 def face_geometry(corners, a, side, pts, w):
     """Outward unit normal (P, d) and area weights w |J_f| (P,) by Nanson's formula."""
     _, J = multilinear(corners, pts)
-    detJ = np.linalg.det(J)
+    detJ = oriented_det(J)
     Jit = np.transpose(np.linalg.inv(J), (0, 2, 1))            # J^{-T}
     g = Jit[:, :, a] * (1.0 if side == 1 else -1.0)           # J^{-T} (+-e_a)
     gn = np.linalg.norm(g, axis=1)
-    return g / gn[:, None], w * np.abs(detJ) * gn
+    return g / gn[:, None], w * detJ * gn
 
 
 def assemble_dg(mesh: Mesh, p: int, eta: float, form: str = "ip"):
@@ -179,7 +179,7 @@ def assemble_dg(mesh: Mesh, p: int, eta: float, form: str = "ip"):
                     for (e, s), k in zip(sides, kap):
                         ptsg = face_points(d, a, s, xg)
                         _, J = multilinear(mesh.corners(e), ptsg)
-                        detJ = np.abs(np.linalg.det(J))
+                        detJ = oriented_det(J)
                         c = 4.0 if interior else 1.0
                         beta += eta * k * dAg ** 2 / (c * wfg * w_end * detJ)
                     jm = []
@@ -252,5 +252,5 @@ def load_vector_dg(mesh: Mesh, p: int, f, q=None):
     for e in mesh.elements():
         X, J = multilinear(mesh.corners(e), pts)
         base = elem_index(e, mesh.n) * Q ** d
-        b[base:base + Q ** d] = phi.T @ (w * np.abs(np.linalg.det(J)) * f(X))
+        b[base:base + Q ** d] = phi.T @ (w * oriented_det(J) * f(X))
     return b

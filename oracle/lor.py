@@ -34,7 +34,7 @@ import scipy.sparse as sp
 from . import ordering
 from .basis import gll
 from .cg import boundary_mask, node_coordinates, node_shape
-from .mesh import Mesh, multilinear
+from .mesh import Mesh, multilinear, oriented_det
 
 COARSE_DIRECT_MAX = 343
 COARSE_SWEEPS = 2
@@ -65,7 +65,7 @@ def q1_stiffness_batch(corners, kappa):
                     v *= df if a == b else f
                 dN[c, b] = v
         J = np.einsum("Cca,cb->Cab", corners, dN)          # dX_a/dxi_b
-        detJ = np.linalg.det(J)
+        detJ = oriented_det(J)
         Jinv = np.linalg.inv(J)
         gphys = np.einsum("Cba,cb->Cca", Jinv, dN)         # J^{-T} dN
         if callable(kappa):
@@ -74,7 +74,7 @@ def q1_stiffness_batch(corners, kappa):
             kq = np.asarray(kappa(np.einsum("Cca,c->Ca", corners, Nc)), dtype=np.float64)
         else:
             kq = kappa
-        K += (w * np.abs(detJ) * kq)[:, None, None] * np.einsum("Cia,Cja->Cij", gphys, gphys)
+        K += (w * detJ * kq)[:, None, None] * np.einsum("Cia,Cja->Cij", gphys, gphys)
     return K
 
 

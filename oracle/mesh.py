@@ -87,6 +87,20 @@ def isoparametric(corners, warp, p, xi):
     return X, J
 
 
+def oriented_det(J):
+    """det J at every point of a batch of Jacobians (..., d, d).
+
+    An element of T_p is the image of the unit cube under an invertible map that
+    keeps its orientation (Section 2), so det J > 0 at every quadrature point.  A
+    map with det J <= 0 anywhere (an inverted or tangled element) is refused with
+    ValueError rather than integrated with |det J|, the same rule the GPU setup
+    applies."""
+    det = np.linalg.det(J)
+    if not np.all(det > 0):
+        raise ValueError("inverted element: det J <= 0 at a quadrature point")
+    return det
+
+
 def multilinear(corners, xi):
     """Map reference points xi (Q, d) through the multilinear map of ``corners``.
 

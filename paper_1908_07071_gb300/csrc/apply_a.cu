@@ -533,6 +533,22 @@ double* rhs_static_scratch(cudaError_t* err) {
   }
   return g_rhs_static_ptr[dev];
 }
+
+// The 1D tables of one call, passed by value as a kernel argument (so no host
+// buffer is copied): B at the Gauss points [q][i], Gauss nodes and weights.
+struct RhsTables { double B[(LOR_MAXP + 1) * (LOR_MAXP + 1)]; double x[LOR_MAXP + 1]; double w[LOR_MAXP + 1]; };
+
+// Writes the tables into the head of the static array: B at 0, nodes at 128,
+// weights at 192 (the offsets the weight and scatter kernels are given).
+__global__ void k_rhs_tables(RhsTables t, int Q, double* __restrict__ head) {
+  for (int i = threadIdx.x; i < kStaticTables; i += blockDim.x) {
+    double v = 0.0;
+    if (i < Q * Q) v = t.B[i];
+    else if (i >= 128 && i < 128 + Q) v = t.x[i - 128];
+    else if (i >= 192 && i < 192 + Q) v = t.w[i - 192];
+    head[i] = v;
+  }
+}
 }  // namespace
 
 extern "C" lor_status lor_rhs_static(int dim, int p, int nx, int ny, int nz, const double* d_vertices, int kind,
@@ -548,16 +564,13 @@ extern "C" lor_status lor_rhs_static(int dim, int p, int nx, int ny, int nz, con
   double* base = rhs_static_scratch(&e);
   if (!base) return LOR_ECUDA;
   cudaStream_t st = (cudaStream_t)stream;
-  // 1D tables on the host, copied into the head of the static array
-  double tab[kStaticTables] = {0};
+  // 1D tables on the host, written into the head of the static array by a kernel
+  RhsTables tab;
   double gll_x[LOR_MAXP + 1], gll_w[LOR_MAXP + 1], Dn[(LOR_MAXP + 1) * (LOR_MAXP + 1)];
-  double* Bm = tab;                        // Q*Q
-  double* glx = tab + 128;                 // Q
-  double* glw = tab + 192;                 // Q
   lorh::gll(p, gll_x, gll_w);
-  lorh::gauss(Q, glx, glw);
-  lorh::lagrange(Q, gll_x, Q, glx, Bm, Dn);
-  if ((e = cudaMemcpyAsync(base, tab, sizeof(tab), cudaMemcpyHostToDevice, st)) != cudaSuccess) return LOR_ECUDA;
+  lorh::gauss(Q, tab.x, tab.w);
+  lorh::lagrange(Q, gll_x, Q, tab.x, tab.B, Dn);
+  k_rhs_tables<<<1, 128, 0, st>>>(tab, Q, base);
   const long long nvec = (long long)(nx * p + 1) * (ny * p + 1) * (dim == 3 ? (nz * p + 1) : 1);
   if ((e = cudaMemsetAsync(d_b, 0, sizeof(double) * nvec, st)) != cudaSuccess) return LOR_ECUDA;
   double* W = base + kStaticTables;

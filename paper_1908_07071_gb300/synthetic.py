@@ -155,10 +155,12 @@ def make_quarter_hole_mesh(n: int, radius: float = 0.25):
     quarter of the square-with-a-hole geometry of Section 5.2), n x n elements.
 
     The vertices are those of the uniform grid of the parameter square (s, t); the
-    returned `warp` maps (s, t) to the domain: angle theta = (pi/2) s, blended linearly
-    in t from the arc of `radius` to the outer boundary (x = 1 or y = 1) along the ray
-    at theta.  The outer boundary has its corner at s = 1/2, so n must be even (a
-    vertex line there keeps every element's warp smooth).
+    returned `warp` maps (s, t) to the domain: angle theta = (pi/2)(1 - s), blended
+    linearly in t from the arc of `radius` to the outer boundary (x = 1 or y = 1) along
+    the ray at theta.  The angle decreases with s while the radius grows with t, so the
+    map keeps the orientation of the parameter square (det J > 0 everywhere).  The outer
+    boundary has its corner at s = 1/2, so n must be even (a vertex line there keeps
+    every element's warp smooth).
     Returns (vertices, kappa = 1, warp).
     """
     if n % 2:
@@ -167,7 +169,7 @@ def make_quarter_hole_mesh(n: int, radius: float = 0.25):
 
     def warp(S):
         S = np.asarray(S, dtype=np.float64)
-        th = 0.5 * np.pi * S[:, 0]
+        th = 0.5 * np.pi * (1.0 - S[:, 0])
         t = S[:, 1][:, None]
         ray = np.stack([np.cos(th), np.sin(th)], axis=1)
         outer = ray / np.max(ray, axis=1, keepdims=True)

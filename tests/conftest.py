@@ -13,12 +13,12 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
-# The allocation-free right-hand side runs after the context-based tests; options beyond
-# the paper's method (partition-of-unity patch weights, pointwise coefficients, curved
-# elements, checkpoint/resume) run after everything else, so that a stop at the first failure (-x) in them
-# hides no test of the method itself.
-_LATE = ("test_zz_no_alloc.py", "test_gpu_forward_error.py", "test_gpu_coefficients.py", "test_gpu_checkpoint.py", "test_gpu_curved.py",
-         "test_gpu_weighting_pou.py")
+# Options beyond the paper's method (partition-of-unity patch weights, pointwise
+# coefficients, curved elements, checkpoint/resume) run after the tests of the method
+# itself, so that a stop at the first failure (-x) in them hides none of those; the
+# allocation-free entry point's check (test_zz_no_alloc.py) is collected last of all.
+_LATE = ("test_gpu_forward_error.py", "test_gpu_coefficients.py", "test_gpu_checkpoint.py", "test_gpu_curved.py",
+         "test_gpu_weighting_pou.py", "test_zz_no_alloc.py")
 
 
 def pytest_collection_modifyitems(session, config, items):

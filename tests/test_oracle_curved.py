@@ -64,8 +64,38 @@ def test_quarter_hole_area_and_boundary_nodes():
     X = cg.node_coordinates(m, p).reshape(N[1], N[0], 2)
     np.testing.assert_allclose(np.hypot(X[0, :, 0], X[0, :, 1]), R, atol=1e-14)      # t = 0: the arc
     np.testing.assert_allclose(np.max(X[-1], axis=1), 1.0, atol=1e-14)              # t = 1: x = 1 or y = 1
-    np.testing.assert_allclose(X[:, 0, 1], 0.0, atol=1e-14)                         # s = 0: y = 0
-    np.testing.assert_allclose(X[:, -1, 0], 0.0, atol=1e-14)                        # s = 1: x = 0
+    np.testing.assert_allclose(X[:, 0, 0], 0.0, atol=1e-14)                         # s = 0: x = 0
+    np.testing.assert_allclose(X[:, -1, 1], 0.0, atol=1e-14)                        # s = 1: y = 0
+
+
+def test_quarter_hole_map_keeps_orientation_and_inverted_maps_are_refused():
+    """Section 2: every element is the image of the unit square under an orientation-
+    keeping map.  The quarter-hole stand-in has det J > 0 at every quadrature point;
+    its mirror image (angle increasing with s, a clockwise parametrisation) has det J < 0
+    everywhere, and the oracle refuses it instead of integrating |det J|."""
+    v, k, w = make_quarter_hole_mesh(4)
+    m = Mesh(v, k, warp=w)
+    x1, w1 = gauss_legendre(5)
+    pts, _ = cg.tensor_points(2, x1, w1)
+    for e in m.elements():
+        assert np.all(np.linalg.det(m.element_map(e, pts, 4)[1]) > 0)
+    mirrored = Mesh(v, k, warp=lambda X: w(X)[:, ::-1])
+    for e in mirrored.elements():
+        assert np.all(np.linalg.det(mirrored.element_map(e, pts, 4)[1]) < 0)
+    with pytest.raises(ValueError, match="inverted"):
+        cg.assemble_stiffness(mirrored, 2)
+    with pytest.raises(ValueError, match="inverted"):
+        lor.assemble_lor(mirrored, 2)
+    with pytest.raises(ValueError, match="inverted"):
+        cg.load_vector(mirrored, 2, lambda X: np.ones(len(X)))
+    # a multilinear element turned inside out by one swapped vertex pair is refused too
+    v2, k2 = make_mesh(2, 2, perturb=0.0)
+    v2 = v2.copy()
+    v2[0, :, [0, 1]] = v2[0, :, [1, 0]]
+    with pytest.raises(ValueError, match="inverted"):
+        cg.assemble_stiffness(Mesh(v2, k2), 2)
+    with pytest.raises(ValueError, match="inverted"):
+        dg.assemble_dg(Mesh(v2, k2), 2, 10.0, "ip")
 
 
 def test_linear_patch_test_on_curved_elements():

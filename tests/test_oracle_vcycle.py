@@ -107,3 +107,84 @@ def test_coarse_basis_maps_vertex_coordinates_to_node_coordinates(dim, n, p):
     # without Dirichlet rows the coarse operator keeps the constants in its kernel
     A0 = (B.P0.T @ B.K_h @ B.P0).toarray()
     assert np.abs(A0 @ np.ones(A0.shape[0])).max() <= 1e-12 * np.abs(A0).max()
+
+
+def _textbook_coarse(B, sweeps):
+    """Error propagation I - V_l A_l of the coarse V-cycle (R_0, Section 3.2 with the
+    l1-Jacobi reading), level by level from the coarsest: `sweeps` l1-Jacobi sweeps
+    S = I - D^{-1} A with D the l1 row sums (D_ii = sum_j |A_ij|), the Galerkin coarse
+    correction, `sweeps` more sweeps; the coarsest level solved exactly.  Returns
+    the list of (A_l, E_l) from level 0 up."""
+    out = []
+    A_last = B.cA[-1].toarray()
+    V_next = np.linalg.inv(A_last)
+    for l in range(len(B.cA) - 2, -1, -1):
+        A = B.cA[l].toarray()
+        P = B.cP[l].toarray()
+        m = A.shape[0]
+        D = np.abs(A).sum(axis=1)
+        S = np.eye(m) - A / D[:, None]
+        C = np.eye(m) - P @ V_next @ P.T @ A
+        Sk = np.linalg.matrix_power(S, sweeps)
+        E = Sk @ C @ Sk
+        out.append((A, E))
+        V_next = np.linalg.solve(A, (np.eye(m) - E).T).T    # V = (I - E) A^{-1}
+    return out[::-1]
+
+
+def _coarse_vcycle_matrix(B, l):
+    m = B.cA[l].shape[0]
+    return np.column_stack([B.coarse_vcycle(l, c) for c in np.eye(m)])
+
+
+@pytest.mark.parametrize("dim,n", [(2, 24), (3, 10)])
+def test_coarse_vcycle_error_propagation_is_the_textbook_product(dim, n):
+    """R_0 (Section 3.2, own V-cycle reading): on a vertex grid too large for the direct
+    solve, the coarse levels are Galerkin (P^T A_l P = A_{l+1}), P interpolates linearly
+    in the vertex index (constants and the index itself are reproduced on interior
+    points), the coarsest level is small enough for the dense inverse while the level
+    above it is not, and I - V_l A_l = S^2 (I - P V_{l+1} P^T A_l) S^2 with the l1-Jacobi
+    S = I - D^{-1} A_l on every level."""
+    v, k = make_mesh(dim, n, seed=11, perturb=0.15)
+    B = lor.LORPreconditioner(Mesh(v, k), 2, patch_subset=[])
+    assert len(B.cA) >= 2
+    assert B.cA[-1].shape[0] <= lor.COARSE_DIRECT_MAX < B.cA[-2].shape[0]
+    for l in range(len(B.cA) - 1):
+        A, P, Ac = B.cA[l].toarray(), B.cP[l].toarray(), B.cA[l + 1].toarray()
+        np.testing.assert_allclose(P.T @ A @ P, Ac, atol=1e-12 * np.abs(A).max())
+    textbook = _textbook_coarse(B, sweeps=2)
+    for l, (A, E) in enumerate(textbook):
+        V = _coarse_vcycle_matrix(B, l)
+        np.testing.assert_allclose(np.eye(A.shape[0]) - V @ A, E, atol=1e-10)
+
+
+def test_coarse_prolongation_is_linear_interpolation_in_the_vertex_index():
+    v, k = make_mesh(2, 24, seed=11, perturb=0.15)
+    B = lor.LORPreconditioner(Mesh(v, k), 2, patch_subset=[])
+    P = B.cP[0].toarray()
+    # interior vertex indices of the fine (25 x 25) and coarse (13 x 13) vertex grids
+    fi = np.arange(1, 24)
+    ci = np.arange(1, 12)
+    Xf = np.stack(np.meshgrid(fi, fi, indexing="xy"), -1).reshape(-1, 2).astype(float)
+    Xc = 2.0 * np.stack(np.meshgrid(ci, ci, indexing="xy"), -1).reshape(-1, 2).astype(float)
+    # a linear function of the vertex index that vanishes on the boundary of the coarse
+    # grid's interior support is reproduced where all its coarse neighbours are interior
+    inner = np.all((Xf >= 2) & (Xf <= 22), axis=1)
+    for a in range(2):
+        np.testing.assert_allclose((P @ Xc[:, a])[inner], Xf[inner, a], atol=1e-12)
+    np.testing.assert_allclose((P @ np.ones(len(Xc)))[inner], 1.0, atol=1e-14)
+
+
+def test_coarse_vcycle_pin_catches_planted_mistakes(monkeypatch):
+    """The textbook product above fails for a cycle with one sweep instead of two, and for
+    one that smooths with the plain diagonal instead of the l1 row sums."""
+    v, k = make_mesh(2, 24, seed=11, perturb=0.15)
+    B = lor.LORPreconditioner(Mesh(v, k), 2, patch_subset=[])
+    (A, E), = _textbook_coarse(B, sweeps=2)[:1]
+    monkeypatch.setattr(lor, "COARSE_SWEEPS", 1)
+    V = _coarse_vcycle_matrix(B, 0)
+    assert np.abs(np.eye(A.shape[0]) - V @ A - E).max() > 1e-3
+    monkeypatch.setattr(lor, "COARSE_SWEEPS", 2)
+    B.cDl1 = [Ai.diagonal().copy() for Ai in B.cA]
+    V = _coarse_vcycle_matrix(B, 0)
+    assert np.abs(np.eye(A.shape[0]) - V @ A - E).max() > 1e-3
