@@ -7,8 +7,11 @@
 //   E_e    : gather of the element's nodes from the structured node grid.
 // One thread per (x,y) node column of an element (3D: the z column lives in
 // registers, x/y contractions go through shared memory); several elements per
-// CTA for small p.  Element-interior outputs are stored, shared ones added with
-// atomics; global boundary (Dirichlet) nodes read as 0 and are never written.
+// CTA for small p.  The elements run in 2^d colour classes (element index parity
+// per axis), one launch per class in a fixed order: elements of one class share
+// no node, so element-interior outputs are stored and shared ones added without
+// atomics, and y is the same bit for bit on every run.  Global boundary
+// (Dirichlet) nodes read as 0 and are never written.
 #include <mutex>
 
 #include "lor_internal.h"
@@ -35,8 +38,10 @@ struct TileNE {
 // DGM = false: continuous Q_p on the structured node grid (gather/scatter,
 // Dirichlet nodes masked).  DGM = true: element-local DG blocks of (p+1)^3
 // values (element e at e*(p+1)^3), no masking, outputs stored (not added).
+// color >= 0: the elements of colour class color (bit a = element index parity
+// along axis a); color < 0: all elements (DG blocks, which share no node).
 template <int P, typename T, bool DGM, int NE>
-__global__ void __launch_bounds__(1024) k_apply3d(int nx, int ny, int nz, const T* __restrict__ Bg,
+__global__ void __launch_bounds__(1024) k_apply3d(int nx, int ny, int nz, int color, const T* __restrict__ Bg,
                                                   const T* __restrict__ Dg, const T* __restrict__ G,
                                                   const T* __restrict__ x, T* __restrict__ y) {
   constexpr int Q = P + 1;
@@ -47,12 +52,22 @@ __global__ void __launch_bounds__(1024) k_apply3d(int nx, int ny, int nz, const 
   const int el = tid / Q2, rem = tid - el * Q2;
   const int tx = rem % Q, ty = rem / Q;
   for (int i = tid; i < Q2; i += blockDim.x) { sB[i] = Bg[i]; sD[i] = Dg[i]; }
-  const long long nel = (long long)nx * ny * nz;
-  const long long e = (long long)blockIdx.x * NE + el;
-  const bool live = (el < NE) && (e < nel);
+  const long long ie = (long long)blockIdx.x * NE + el;
   const int Nx = nx * P + 1, Ny = ny * P + 1, Nz = nz * P + 1;
   int ex = 0, ey = 0, ez = 0;
-  if (live) { ex = (int)(e % nx); ey = (int)((e / nx) % ny); ez = (int)(e / ((long long)nx * ny)); }
+  bool live;
+  if (color < 0) {
+    live = (el < NE) && (ie < (long long)nx * ny * nz);
+    if (live) { ex = (int)(ie % nx); ey = (int)((ie / nx) % ny); ez = (int)(ie / ((long long)nx * ny)); }
+  } else {
+    const int cx = color & 1, cy = (color >> 1) & 1, cz = (color >> 2) & 1;
+    const int mx = (nx - cx + 1) / 2, my = (ny - cy + 1) / 2, mz = (nz - cz + 1) / 2;
+    live = (el < NE) && (ie < (long long)mx * my * mz);
+    if (live) {
+      ex = 2 * (int)(ie % mx) + cx; ey = 2 * (int)((ie / mx) % my) + cy; ez = 2 * (int)(ie / ((long long)mx * my)) + cz;
+    }
+  }
+  const long long e = ((long long)ez * ny + ey) * nx + ex;
   const int I = ex * P + tx, Jn = ey * P + ty;
   const bool bxy = !DGM && (I == 0 || I == Nx - 1 || Jn == 0 || Jn == Ny - 1);
   T u[Q], v[Q];
@@ -192,12 +207,12 @@ __global__ void __launch_bounds__(1024) k_apply3d(int nx, int ny, int nz, const 
     if (bxy || K == 0 || K == Nz - 1) continue;
     T* dst = y + ((long long)K * Ny + Jn) * Nx + I;
     if (inx && iny && k > 0 && k < P) *dst = a;
-    else atomicAdd(dst, a);
+    else *dst += a;   // no other element of this colour class touches the node
   }
 }
 
 template <int P, typename T>
-__global__ void __launch_bounds__(256) k_apply2d(int nx, int ny, const T* __restrict__ Bg,
+__global__ void __launch_bounds__(256) k_apply2d(int nx, int ny, int color, const T* __restrict__ Bg,
                                                  const T* __restrict__ Dg, const T* __restrict__ G,
                                                  const T* __restrict__ x, T* __restrict__ y) {
   constexpr int Q = P + 1;
@@ -209,12 +224,14 @@ __global__ void __launch_bounds__(256) k_apply2d(int nx, int ny, const T* __rest
   const int el = tid / Q2, rem = tid - el * Q2;
   const int tx = rem % Q, ty = rem / Q;
   for (int i = tid; i < Q2; i += blockDim.x) { sB[i] = Bg[i]; sD[i] = Dg[i]; }
-  const long long nel = (long long)nx * ny;
-  const long long e = (long long)blockIdx.x * NE + el;
-  const bool live = (el < NE) && (e < nel);
+  const long long ie = (long long)blockIdx.x * NE + el;
+  const int cx = color & 1, cy = (color >> 1) & 1;
+  const int mx = (nx - cx + 1) / 2, my = (ny - cy + 1) / 2;
+  const bool live = (el < NE) && (ie < (long long)mx * my);
   const int Nx = nx * P + 1, Ny = ny * P + 1;
   int ex = 0, ey = 0;
-  if (live) { ex = (int)(e % nx); ey = (int)(e / nx); }
+  if (live) { ex = 2 * (int)(ie % mx) + cx; ey = 2 * (int)(ie / mx) + cy; }
+  const long long e = (long long)ey * nx + ex;
   const int I = ex * P + tx, Jn = ey * P + ty;
   const bool bnd = (I == 0 || I == Nx - 1 || Jn == 0 || Jn == Ny - 1);
   T* S1 = s1[el < NE ? el : 0];
@@ -269,7 +286,7 @@ __global__ void __launch_bounds__(256) k_apply2d(int nx, int ny, const T* __rest
   if (!live || bnd) return;
   T* dst = y + (long long)Jn * Nx + I;
   if (tx > 0 && tx < P && ty > 0 && ty < P) *dst = out;
-  else atomicAdd(dst, out);
+  else *dst += out;   // no other element of this colour class touches the node
 }
 
 template <typename T>
@@ -286,12 +303,17 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   const int pk = sizeof(T) == 8 ? 2 : 3;
   lor_prof_begin(c, pk);
+  const int ncolor = c->dim == 3 ? 8 : 4;
+  for (int color = 0; color < ncolor; ++color) {
+    const int cx = color & 1, cy = (color >> 1) & 1, cz = (color >> 2) & 1;
+    const long long ncls = (long long)((nx - cx + 1) / 2) * ((ny - cy + 1) / 2) * (c->dim == 3 ? (nz - cz + 1) / 2 : 1);
+    if (ncls == 0) continue;
 #define LOR_VAR3(PP, V)                                                                     \
   {                                                                                         \
     constexpr int NE = TileNE<PP, T, V>::v;                                                 \
     const int threads = NE * (PP + 1) * (PP + 1);                                           \
-    const long long blocks = lor_ceil_div((long long)c->nel, NE);                           \
-    k_apply3d<PP, T, false, NE><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, B, D, G, x, y); \
+    const long long blocks = lor_ceil_div(ncls, NE);                                        \
+    k_apply3d<PP, T, false, NE><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, color, B, D, G, x, y); \
   }
 #define LOR_CASE3(PP)                                                                       \
   case PP: {                                                                                \
@@ -302,18 +324,19 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
     } else {                                                                                \
       constexpr int NE = ElemsPerBlock<PP>::v2;                                             \
       const int threads = NE * (PP + 1) * (PP + 1);                                         \
-      const long long blocks = lor_ceil_div((long long)c->nel, NE);                         \
-      k_apply2d<PP, T><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, B, D, G, x, y); \
+      const long long blocks = lor_ceil_div(ncls, NE);                                      \
+      k_apply2d<PP, T><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, color, B, D, G, x, y); \
     }                                                                                       \
   } break;
-  switch (c->p) {
-    LOR_CASE3(1) LOR_CASE3(2) LOR_CASE3(3) LOR_CASE3(4)
-    LOR_CASE3(5) LOR_CASE3(6) LOR_CASE3(7) LOR_CASE3(8)
-    default: return lor_fail(c, LOR_EINVAL, "unsupported p");
-  }
+    switch (c->p) {
+      LOR_CASE3(1) LOR_CASE3(2) LOR_CASE3(3) LOR_CASE3(4)
+      LOR_CASE3(5) LOR_CASE3(6) LOR_CASE3(7) LOR_CASE3(8)
+      default: return lor_fail(c, LOR_EINVAL, "unsupported p");
+    }
 #undef LOR_CASE3
 #undef LOR_VAR3
-  ++c->launches;
+    ++c->launches;
+  }
   lor_prof_end(c, pk);
   return lor_cuda_check(c, cudaGetLastError(), "apply_A launch");
 }
@@ -326,7 +349,7 @@ lor_status launch_apply_dgvol(lor_ctx* c, const T* B, const T* D, const T* G, co
     constexpr int NE = TileNE<PP, T, V>::v;                                                   \
     const int threads = NE * (PP + 1) * (PP + 1);                                             \
     const long long blocks = lor_ceil_div((long long)c->nel, NE);                             \
-    k_apply3d<PP, T, true, NE><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, B, D, G, x, y); \
+    k_apply3d<PP, T, true, NE><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, -1, B, D, G, x, y); \
   }
 #define LOR_CASEDG(PP)                                                                        \
   case PP: {                                                                                  \
@@ -431,15 +454,22 @@ __global__ void k_rhs_weights_iso(int dim, int p, int nx, int ny, int nz, const 
   W[gid] = w * fabs(det) * fval;
 }
 
-__global__ void k_rhs_scatter(int dim, int p, int nx, int ny, int nz, const double* __restrict__ Bm,
+// b += sum over the elements of colour class `color` (element index parity per
+// axis, as in the operator kernels): elements of one class share no node, so the
+// node sums are plain adds, and the classes run in a fixed order.
+__global__ void k_rhs_scatter(int dim, int p, int nx, int ny, int nz, int color, const double* __restrict__ Bm,
                               const double* __restrict__ W, double* __restrict__ b) {
   const int Q = p + 1;
   const int Qd = dim == 3 ? Q * Q * Q : Q * Q;
-  const long long nel = (long long)nx * ny * (dim == 3 ? nz : 1);
+  const int cx = color & 1, cy = (color >> 1) & 1, cz = (color >> 2) & 1;
+  const int mx = (nx - cx + 1) / 2, my = (ny - cy + 1) / 2, mz = dim == 3 ? (nz - cz + 1) / 2 : 1;
+  const long long ncls = (long long)mx * my * mz;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= nel * Qd) return;
-  const long long e = gid / Qd;
-  const int a = (int)(gid - e * Qd);
+  if (gid >= ncls * Qd) return;
+  const long long ie = gid / Qd;
+  const int a = (int)(gid - ie * Qd);
+  const long long e = ((long long)(dim == 3 ? 2 * (int)(ie / ((long long)mx * my)) + cz : 0) * ny +
+                       (2 * (int)((ie / mx) % my) + cy)) * nx + (2 * (int)(ie % mx) + cx);
   const int i = a % Q, j = (a / Q) % Q, k = dim == 3 ? a / (Q * Q) : 0;
   double s = 0.0;
   const double* We = W + e * Qd;
@@ -454,7 +484,7 @@ __global__ void k_rhs_scatter(int dim, int p, int nx, int ny, int nz, const doub
   const int I = ex * p + i, Jn = ey * p + j, K = ez * p + k;
   if (I == 0 || I == Nx - 1 || Jn == 0 || Jn == Ny - 1) return;
   if (dim == 3 && (K == 0 || K == Nz - 1)) return;
-  atomicAdd(b + ((long long)K * Ny + Jn) * Nx + I, s);
+  b[((long long)K * Ny + Jn) * Nx + I] += s;
 }
 
 }  // namespace
@@ -502,9 +532,11 @@ lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b) {
   cudaError_t e = cudaMemsetAsync(b, 0, sizeof(double) * c->lev[0].ntot, c->stream);
   if (e != cudaSuccess) return lor_cuda_check(c, e, "rhs memset");
   if (lor_launch_rhs_weights(c, kind, W)) return LOR_ECUDA;
-  const unsigned blocks = (unsigned)lor_ceil_div(tot, 256);
-  k_rhs_scatter<<<blocks, 256, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1], c->n[2], lor_basis64(c, 0), W, b);
-  ++c->launches;
+  for (int color = 0; color < (c->dim == 3 ? 8 : 4); ++color) {
+    k_rhs_scatter<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1], c->n[2],
+                                                                          color, lor_basis64(c, 0), W, b);
+    ++c->launches;
+  }
   return lor_cuda_check(c, cudaGetLastError(), "rhs launch");
 }
 
@@ -576,6 +608,7 @@ extern "C" lor_status lor_rhs_static(int dim, int p, int nx, int ny, int nz, con
   double* W = base + kStaticTables;
   const unsigned blocks = (unsigned)lor_ceil_div(nel * Qd, 256);
   k_rhs_weights<<<blocks, 256, 0, st>>>(dim, p, nx, ny, zz, d_vertices, base + 128, base + 192, kind, W);
-  k_rhs_scatter<<<blocks, 256, 0, st>>>(dim, p, nx, ny, zz, base, W, d_b);
+  for (int color = 0; color < (dim == 3 ? 8 : 4); ++color)
+    k_rhs_scatter<<<blocks, 256, 0, st>>>(dim, p, nx, ny, zz, color, base, W, d_b);
   return cudaGetLastError() == cudaSuccess ? LOR_OK : LOR_ECUDA;
 }

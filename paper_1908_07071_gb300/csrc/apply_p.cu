@@ -9,7 +9,10 @@
 // backward sweeps over factor records streamed by bulk copies), 3^d-point
 // residual with the level's Galerkin LOR stencil, tensor restriction, exact
 // solve on the vertex level (<= 1 unknown), then prolongation, residual and
-// post-smoothing on the way up, and a scatter-add of x_j into z.  Many patches
+// post-smoothing on the way up; x_j goes to the patch's own slice of a
+// per-patch buffer, and a gather kernel sums the slices of the (at most 2^d)
+// patches containing each node in a fixed order, so z is reproducible bit for
+// bit.  Many patches
 // are in flight per SM (one per warp), so the latency-bound sweeps of one patch
 // overlap those of the others.  Vectors live in zero-padded boxes so that
 // factor reads need no bounds checks (factors of out-of-box couplings are
@@ -58,7 +61,8 @@ struct PatchArgs {
   const long long* facoff;      // [L][J] record offsets
   const void* F;
   const void* r;
-  void* z;
+  void* zp;                     // per-patch outputs (T): patch j at zp + j * zstride, lexicographic box order
+  long long zstride;
   int* status;
   int slot_bytes;               // ring slot size (bytes, multiple of 16)
   int tab_ints;                 // per-warp shared-memory ints reserved for wavefront tables
@@ -841,7 +845,9 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       for (int lex = lane; lex < b0.rows; lex += 32) dst[lex] = xslot[lex] + t0[lex];
       continue;
     }
-    T* z = (T*)a.z;
+    // the weighted R_j^T x_j goes to the patch's own output slice (lexicographic
+    // box order); k_patch_sum adds the slices node by node in a fixed order
+    T* zj = (T*)a.zp + (long long)j * a.zstride;
     {
       constexpr int U = kRowsInFlight;
       BoxIter it;
@@ -850,13 +856,12 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       if (a.wmode == 2) hat_offsets<DIM>(j, a.n[0], a.n[1], a.wp, ho);
       for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
         T xv[U], w[U];
-        int G[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          G[u] = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
-          w[u] = a.wp ? node_weight<DIM, T>(a.wmode, b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp, ho[0],
-                                            ho[1], ho[2], hat)
-                      : T(1);
+          w[u] = a.wp && l0 + 32 * u < b0.rows
+                     ? node_weight<DIM, T>(a.wmode, b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp, ho[0],
+                                           ho[1], ho[2], hat)
+                     : T(1);
           it.next();
           if (l0 + 32 * u < b0.rows) xv[u] = xslot[l0 + 32 * u];
         }
@@ -865,7 +870,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           const int lex = l0 + 32 * u;
           if (lex < b0.rows) {
             const T xj = xv[u] + t0[lex];
-            atomicAdd(z + G[u], w[u] * xj);
+            zj[lex] = w[u] * xj;
             if (a.tout && sh == 0) t0[lex] = xj;
           }
         }
@@ -881,6 +886,51 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       __syncwarp();
     }
   }
+}
+
+// z[node] = sum over the (at most 2^d) vertex patches containing the interior node
+// of their output slices, in a fixed order (vertex index ascending along x, then
+// y, then z); boundary nodes get 0.  Patch j covers, along each axis, the nodes
+// org + [0, len) of its box: org = (v-1) p + 1 and len = 2p - 1 for an interior
+// vertex v, org = 1, len = p - 1 at v = 0 and org = (n-1) p + 1, len = p - 1 at v = n.
+template <typename T>
+__global__ void k_patch_sum(int dim, int p, int nx, int ny, int nz, const T* __restrict__ zp, long long zstride,
+                            const double* __restrict__ conv, T* __restrict__ z) {
+  const int Nx = nx * p + 1, Ny = ny * p + 1, Nz = dim == 3 ? nz * p + 1 : 1;
+  const long long nt = (long long)Nx * Ny * Nz;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nt) return;
+  if (conv && *conv != 0.0) { z[gid] = T(0); return; }   // converged batched solve: the patch kernel did nothing
+  const int I[3] = {(int)(gid % Nx), (int)((gid / Nx) % Ny), (int)(gid / ((long long)Nx * Ny))};
+  const int n[3] = {nx, ny, nz};
+  const int N[3] = {Nx, Ny, Nz};
+  for (int a = 0; a < dim; ++a)
+    if (I[a] == 0 || I[a] == N[a] - 1) { z[gid] = T(0); return; }
+  // per axis: candidate vertices, the node's local index in each, and the box length
+  int cv[3][2], cl[3][2], cn[3][2], cnt[3] = {1, 1, 1};
+  for (int a = 0; a < 3; ++a) { cv[a][0] = 0; cl[a][0] = 0; cn[a][0] = 1; }
+  for (int a = 0; a < dim; ++a) {
+    const int q = I[a] / p, rem = I[a] - q * p;
+    const int v0 = rem == 0 ? q : q, v1 = q + 1;
+    cnt[a] = rem == 0 ? 1 : 2;
+    const int vs[2] = {v0, v1};
+    for (int s = 0; s < cnt[a]; ++s) {
+      const int v = vs[s];
+      const int org = (v > 0 ? (v - 1) * p : 0) + 1;
+      cv[a][s] = v;
+      cl[a][s] = I[a] - org;
+      cn[a][s] = (v == 0 || v == n[a]) ? p - 1 : 2 * p - 1;
+    }
+  }
+  T s = T(0);
+  for (int c2 = 0; c2 < cnt[2]; ++c2)
+    for (int c1 = 0; c1 < cnt[1]; ++c1)
+      for (int c0 = 0; c0 < cnt[0]; ++c0) {
+        const long long jp = ((long long)cv[2][c2] * (ny + 1) + cv[1][c1]) * (nx + 1) + cv[0][c0];
+        const long long lex = ((long long)cl[2][c2] * cn[1][c1] + cl[1][c1]) * cn[0][c0] + cl[0][c0];
+        s += zp[jp * zstride + lex];
+      }
+  z[gid] = s;
 }
 
 // ------------------------------------------------------------------ coarse space
@@ -1190,7 +1240,8 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
   a.shapes = lor_dev_shapes(c);
   a.fpad = c->d_fpad; a.chunk = c->d_chunk;
   a.facoff = c->d_facoff;
-  a.F = F; a.r = nullptr; a.z = nullptr;
+  a.F = F; a.r = nullptr;
+  a.zp = c->d_zp;
   a.status = c->d_status;
   a.porder = c->d_porder;
   a.conv = c->conv_flag;
@@ -1207,6 +1258,7 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
   a.ovl_n = w.ovl_n;
   a.xs = c->d_xs;
   a.x0_stride = w.x0_stride;
+  a.zstride = w.x0_stride;
 }
 
 // Launch shape of the patch kernel: warps per CTA (shared memory) and resident
@@ -1258,11 +1310,9 @@ lor_status launch_patch_kernel(lor_ctx* c, PatchArgs& a) {
 template <typename T, typename FT>
 lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
   const long long nvec = c->lev[0].ntot;
-  cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * nvec, c->stream);
-  if (e != cudaSuccess) return lor_cuda_check(c, e, "apply_P memset");
   PatchArgs a;
   fill_patch_args<T, FT>(c, a, F);
-  a.r = r; a.z = z;
+  a.r = r;
   if (c->learned_on && sizeof(T) == 4) {
     a.tout = c->learned_tout;
     a.vstride = c->shapes[0].rows;
@@ -1271,6 +1321,10 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
   lor_prof_begin(c, pk);
   if (launch_patch_kernel<T, FT>(c, a)) return LOR_ECUDA;
   lor_prof_end(c, pk);
+  // z = sum_j R_j^T x_j, node by node in a fixed order
+  k_patch_sum<T><<<(unsigned)lor_ceil_div(nvec, 256), 256, 0, c->stream>>>(
+      c->dim, c->p, c->n[0], c->n[1], c->n[2], (const T*)c->d_zp, a.zstride, c->conv_flag, z);
+  ++c->launches;
   if (c->learned_on && sizeof(T) == 4) {
     if (lor_learned_apply(c, (float*)z)) return LOR_ECUDA;
   }
@@ -1350,7 +1404,8 @@ lor_status lor_patch_local32(lor_ctx* c, const int* plist, int nlist, const floa
 }
 
 // Checks that the patch kernel fits (every precision this context can run) and
-// allocates the per-warp level-0 iterate slots for the largest launch.
+// allocates the per-warp level-0 iterate slots for the largest launch and the
+// per-patch output slices (J slices of x0_stride values, float64-sized).
 lor_status lor_patch_prepare(lor_ctx* c) {
   long long need = 0;
   int nw = 0, grid = 0;
@@ -1368,5 +1423,8 @@ lor_status lor_patch_prepare(lor_ctx* c) {
   c->xs_bytes = need;
   c->d_xs = lor_alloc(c, (size_t)std::max<long long>(need, 8));
   if (!c->d_xs) return lor_fail(c, LOR_ENOMEM, "alloc patch iterate slots");
+  const long long zbytes = (long long)c->J * warp_layout<double, double>(c).x0_stride * 8;
+  c->d_zp = lor_alloc(c, (size_t)std::max<long long>(zbytes, 8));
+  if (!c->d_zp) return lor_fail(c, LOR_ENOMEM, "alloc patch outputs");
   return LOR_OK;
 }

@@ -51,6 +51,33 @@ __device__ __forceinline__ void face_decode(int f, const int* n, int* a, int* ia
   }
 }
 
+// Face colour classes: faces with normal axis a whose position ia along a has the
+// parity par.  Two faces of one class never touch the same element (face ia lies
+// between elements ia-1 and ia along a), so a kernel over one class may add into
+// element nodes without atomics; the 6 classes run one after another in a fixed
+// order, which makes the sums the same bit for bit on every run.
+struct FaceClass { int a, par, m; long long count; int off; };
+
+__host__ __device__ inline FaceClass face_class(const int* n, int a, int par) {
+  FaceClass k;
+  k.a = a; k.par = par;
+  const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+  k.m = (n[a] + 1 - par + 1) / 2;                   // positions ia = par, par + 2, ... <= n[a]
+  k.count = (long long)k.m * n[b] * n[c];
+  k.off = 0;
+  for (int ax = 0; ax < a; ++ax) {
+    const int bb = ax == 0 ? 1 : 0, cc = ax == 2 ? 1 : 2;
+    k.off += (n[ax] + 1) * n[bb] * n[cc];
+  }
+  return k;
+}
+
+// face index (face_decode numbering) of the idx-th face of class k
+__device__ __forceinline__ int class_face(const FaceClass& k, const int* n, long long idx) {
+  const int ia = k.par + 2 * (int)(idx % k.m);
+  return k.off + ia + (n[k.a] + 1) * (int)(idx / k.m);
+}
+
 __device__ __forceinline__ int elem_id(const int* n, int a, int ia, int tb, int tc) {
   int e3[3];
   const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
@@ -275,14 +302,18 @@ __global__ void k_face_flux(int p, int nface, int br2, FaceData<T> fd, Tab tb, c
   bq[2 * Q2 + q] = -half * jump;   // gradient test coefficient (times c_k . grad phi)
 }
 
-// per (face, side, element node): apply the transposed trace / normal derivative
+// per (face of class k, side, element node): apply the transposed trace / normal
+// derivative, added into the element node (no other face of the class touches it)
 template <typename T>
-__global__ void k_face_scatter(int p, int nface, FaceData<T> fd, Tab tb, const T* __restrict__ buf, T* y) {
+__global__ void k_face_scatter(int p, FaceClass fk, int n0, int n1, int n2, FaceData<T> fd, Tab tb,
+                               const T* __restrict__ buf, T* y) {
   const int Q = p + 1, Q2 = Q * Q, Q3 = Q2 * Q;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)nface * 2 * Q3) return;
-  const int f = (int)(gid / (2 * Q3));
-  const int r = (int)(gid - (long long)f * 2 * Q3);
+  if (gid >= fk.count * 2 * Q3) return;
+  const int n[3] = {n0, n1, n2};
+  const long long fi = gid / (2 * Q3);
+  const int f = class_face(fk, n, fi);
+  const int r = (int)(gid - fi * 2 * Q3);
   const int s = r / Q3, node = r % Q3;
   const FaceTopo t = fd.topo[f];
   if (s == 1 && t.eS < 0) return;
@@ -310,16 +341,19 @@ __global__ void k_face_scatter(int p, int nface, FaceData<T> fd, Tab tb, const T
       if (i == end) v += sv[q] * bb * bc + sg[q] * (cb[q] * D[q1 * Q + j] * bc + cc[q] * bb * D[q2 * Q + k]);
       acc += v;
     }
-  atomicAdd(y + (long long)e * Q3 + loc3(Q, t.a, i, j, k), acc);
+  y[(long long)e * Q3 + loc3(Q, t.a, i, j, k)] += acc;
 }
 
-// BR2 nodal penalty at the GLL face nodes
+// BR2 nodal penalty at the GLL face nodes of the faces of class k
 template <typename T>
-__global__ void k_face_br2(int p, int nface, FaceData<T> fd, const T* __restrict__ x, T* y) {
+__global__ void k_face_br2(int p, FaceClass fk, int n0, int n1, int n2, FaceData<T> fd, const T* __restrict__ x,
+                           T* y) {
   const int Q = p + 1, Q2 = Q * Q, Q3 = Q2 * Q;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)nface * Q2) return;
-  const int f = (int)(gid / Q2), q = (int)(gid - (long long)f * Q2);
+  if (gid >= fk.count * Q2) return;
+  const int n[3] = {n0, n1, n2};
+  const long long fi = gid / Q2;
+  const int f = class_face(fk, n, fi), q = (int)(gid - fi * Q2);
   const int j = q % Q, k = q / Q;
   const FaceTopo t = fd.topo[f];
   const long long iF = (long long)t.eF * Q3 + loc3(Q, t.a, t.endF, j, k);
@@ -330,8 +364,8 @@ __global__ void k_face_br2(int p, int nface, FaceData<T> fd, const T* __restrict
     jump -= x[iS];
   }
   const T v = fd.beta[(long long)f * Q2 + q] * jump;
-  atomicAdd(y + iF, v);
-  if (iS >= 0) atomicAdd(y + iS, -v);
+  y[iF] += v;
+  if (iS >= 0) y[iS] -= v;
 }
 
 // diagonal of A_DG: volume part per node, face part per (face, side, face node)
@@ -355,13 +389,16 @@ __global__ void k_diag_volume(int p, int nel, const double* __restrict__ B, cons
   diag[gid] = s;
 }
 
-__global__ void k_diag_face(int p, int nface, int br2, FaceData<double> fd, const double* __restrict__ B,
-                            const double* __restrict__ D, const double* __restrict__ Dn, double* diag) {
+__global__ void k_diag_face(int p, FaceClass fk, int n0, int n1, int n2, int br2, FaceData<double> fd,
+                            const double* __restrict__ B, const double* __restrict__ D, const double* __restrict__ Dn,
+                            double* diag) {
   const int Q = p + 1, Q2 = Q * Q, Q3 = Q2 * Q;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)nface * 2 * Q2) return;
-  const int f = (int)(gid / (2 * Q2));
-  const int r = (int)(gid - (long long)f * 2 * Q2);
+  if (gid >= fk.count * 2 * Q2) return;
+  const int n[3] = {n0, n1, n2};
+  const long long fi = gid / (2 * Q2);
+  const int f = class_face(fk, n, fi);
+  const int r = (int)(gid - fi * 2 * Q2);
   const int s = r / Q2, jk = r % Q2;
   const FaceTopo t = fd.topo[f];
   if (s == 1 && t.eS < 0) return;
@@ -383,21 +420,43 @@ __global__ void k_diag_face(int p, int nface, int br2, FaceData<double> fd, cons
       if (!br2) acc += fd.sigma[f] * fd.W[(long long)f * Q2 + q] * phi * phi;
     }
   if (br2) acc += fd.beta[(long long)f * Q2 + jk];
-  atomicAdd(diag + (long long)e * Q3 + loc3(Q, t.a, end, j, k), acc);
+  diag[(long long)e * Q3 + loc3(Q, t.a, end, j, k)] += acc;
 }
 
-// E^T: DG block values summed into the conforming node grid
+// E^T: DG block values summed into the conforming node grid.  One thread per
+// grid node adds the block values of the (at most 8) elements sharing it, in a
+// fixed order (element index ascending along x, then y, then z).
 template <typename T>
 __global__ void k_dg_to_cg(int p, int nx, int ny, int nz, const T* __restrict__ xd, T* xc) {
   const int Q = p + 1, Q3 = Q * Q * Q;
+  const int Nx = nx * p + 1, Ny = ny * p + 1, Nz = nz * p + 1;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)nx * ny * nz * Q3) return;
-  const long long e = gid / Q3;
-  const int n = (int)(gid - e * Q3);
-  const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((long long)nx * ny));
-  const int Nx = nx * p + 1, Ny = ny * p + 1;
-  const long long g = ((long long)(ez * p + n / (Q * Q)) * Ny + (ey * p + (n / Q) % Q)) * Nx + (ex * p + n % Q);
-  atomicAdd(xc + g, xd[gid]);
+  if (gid >= (long long)Nx * Ny * Nz) return;
+  const int I = (int)(gid % Nx), Jn = (int)((gid / Nx) % Ny), K = (int)(gid / ((long long)Nx * Ny));
+  // per axis: the elements containing the node (the one before a shared plane first)
+  const int e0x = I % p == 0 && I > 0 ? I / p - 1 : min(I / p, nx - 1);
+  const int e1x = I % p == 0 && I > 0 && I / p < nx ? I / p : -1;
+  const int e0y = Jn % p == 0 && Jn > 0 ? Jn / p - 1 : min(Jn / p, ny - 1);
+  const int e1y = Jn % p == 0 && Jn > 0 && Jn / p < ny ? Jn / p : -1;
+  const int e0z = K % p == 0 && K > 0 ? K / p - 1 : min(K / p, nz - 1);
+  const int e1z = K % p == 0 && K > 0 && K / p < nz ? K / p : -1;
+  T s = T(0);
+  for (int cz = 0; cz < 2; ++cz) {
+    const int ez = cz ? e1z : e0z;
+    if (ez < 0) continue;
+    for (int cy = 0; cy < 2; ++cy) {
+      const int ey = cy ? e1y : e0y;
+      if (ey < 0) continue;
+      for (int cx = 0; cx < 2; ++cx) {
+        const int ex = cx ? e1x : e0x;
+        if (ex < 0) continue;
+        const long long e = ((long long)ez * ny + ey) * nx + ex;
+        const int li = I - ex * p, lj = Jn - ey * p, lk = K - ez * p;
+        s += xd[e * Q3 + (lk * Q + lj) * Q + li];
+      }
+    }
+  }
+  xc[gid] = s;
 }
 
 // z_dg = [element-boundary node] r / diag + E zc
@@ -550,9 +609,15 @@ lor_status lor_setup_dg(lor_ctx* c) {
   k_diag_volume<<<(unsigned)lor_ceil_div(ndg, 128), 128, 0, c->stream>>>(p, c->nel, s->tab64, s->tab64 + Q2,
                                                                           c->d_G64, diag);
   ++c->launches;
-  k_diag_face<<<(unsigned)lor_ceil_div(nf * 2 * Q2, 128), 128, 0, c->stream>>>(
-      p, (int)nf, c->opt.disc == LOR_DG_BR2, face_data<double>(c), s->tab64, s->tab64 + Q2, s->tab64 + 2 * Q2, diag);
-  ++c->launches;
+  for (int a = 0; a < 3; ++a)
+    for (int par = 0; par < 2; ++par) {
+      const FaceClass fk = face_class(c->n, a, par);
+      if (fk.count == 0) continue;
+      k_diag_face<<<(unsigned)lor_ceil_div(fk.count * 2 * Q2, 128), 128, 0, c->stream>>>(
+          p, fk, c->n[0], c->n[1], c->n[2], c->opt.disc == LOR_DG_BR2, face_data<double>(c), s->tab64, s->tab64 + Q2,
+          s->tab64 + 2 * Q2, diag);
+      ++c->launches;
+    }
   k_inv_to<<<(unsigned)lor_ceil_div(ndg, 256), 256, 0, c->stream>>>(diag, s->dinv64, s->dinv32, ndg);
   ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "DG setup");
@@ -575,13 +640,21 @@ static lor_status apply_A_dg(lor_ctx* c, const T* x, T* y) {
   T* buf = dgbuf<T>(c);
   k_face_flux<T><<<(unsigned)lor_ceil_div(nf * Q2, 128), 128, 0, c->stream>>>(p, (int)nf, br2, face_data<T>(c),
                                                                                 tabs<T>(c, Q), x, buf);
-  k_face_scatter<T><<<(unsigned)lor_ceil_div(nf * 2 * Q3, 128), 128, 0, c->stream>>>(p, (int)nf, face_data<T>(c),
-                                                                                       tabs<T>(c, Q), buf, y);
-  c->launches += 2;
-  if (br2) {
-    k_face_br2<T><<<(unsigned)lor_ceil_div(nf * Q2, 128), 128, 0, c->stream>>>(p, (int)nf, face_data<T>(c), x, y);
-    ++c->launches;
-  }
+  ++c->launches;
+  // face classes one after another (no two faces of a class share an element)
+  for (int a = 0; a < 3; ++a)
+    for (int par = 0; par < 2; ++par) {
+      const FaceClass fk = face_class(c->n, a, par);
+      if (fk.count == 0) continue;
+      k_face_scatter<T><<<(unsigned)lor_ceil_div(fk.count * 2 * Q3, 128), 128, 0, c->stream>>>(
+          p, fk, c->n[0], c->n[1], c->n[2], face_data<T>(c), tabs<T>(c, Q), buf, y);
+      ++c->launches;
+      if (br2) {
+        k_face_br2<T><<<(unsigned)lor_ceil_div(fk.count * Q2, 128), 128, 0, c->stream>>>(
+            p, fk, c->n[0], c->n[1], c->n[2], face_data<T>(c), x, y);
+        ++c->launches;
+      }
+    }
   return lor_cuda_check(c, cudaGetLastError(), "DG apply");
 }
 
@@ -592,9 +665,8 @@ template <typename T>
 static lor_status apply_P_dg(lor_ctx* c, const T* r, T* z, T* cgin, T* cgout, const T* dinv) {
   const int p = c->p, Q = p + 1;
   const long long ndg = (long long)c->nel * Q * Q * Q;
-  cudaError_t e = cudaMemsetAsync(cgin, 0, sizeof(T) * c->lev[0].ntot, c->stream);
-  if (e != cudaSuccess) return lor_cuda_check(c, e, "DG precond memset");
-  k_dg_to_cg<T><<<(unsigned)lor_ceil_div(ndg, 256), 256, 0, c->stream>>>(p, c->n[0], c->n[1], c->n[2], r, cgin);
+  k_dg_to_cg<T><<<(unsigned)lor_ceil_div(c->lev[0].ntot, 256), 256, 0, c->stream>>>(p, c->n[0], c->n[1], c->n[2], r,
+                                                                                      cgin);
   ++c->launches;
   lor_status st = sizeof(T) == 8 ? lor_launch_apply_P64(c, (const double*)cgin, (double*)cgout)
                                  : lor_launch_apply_P32(c, (const float*)cgin, (float*)cgout);

@@ -149,6 +149,9 @@ struct lor_ctx {
   // resident warp; small enough to stay in L2)
   void* d_xs = nullptr;
   long long xs_bytes = 0;
+  // per-patch outputs of the patch kernel (J slices of level-0 box rows, sized for
+  // float64), summed node by node into z by a gather kernel
+  void* d_zp = nullptr;
   int maxfront = 0;           // largest padded front over all levels/shapes (records)
   int maxchunk[3] = {0, 0, 0};   // largest chunk (records) for 2-, 4-, 8-byte factors
   int* d_status = nullptr;    // device error word

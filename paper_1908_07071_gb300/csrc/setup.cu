@@ -882,10 +882,12 @@ lor_status lor_setup_patches(lor_ctx* c) {
     }
   tot *= lor_rec(dim);   // values
   if (upload(c, (void**)&c->d_facoff, off.data(), off.size() * 8)) return LOR_ENOMEM;
+  // FP64 records for the FP64 path, and the one reduced-precision copy the FP32
+  // path reads (bf16 if requested, else FP32)
   c->d_F64 = (double*)lor_alloc(c, std::max<long long>(tot, 1) * 8);
-  c->d_F32 = (float*)lor_alloc(c, std::max<long long>(tot, 1) * 4);
   if (c->opt.factor_bf16) c->d_F16 = (__nv_bfloat16*)lor_alloc(c, std::max<long long>(tot, 1) * 2);
-  if (!c->d_F64 || !c->d_F32 || (c->opt.factor_bf16 && !c->d_F16)) return lor_fail(c, LOR_ENOMEM, "alloc factors");
+  else c->d_F32 = (float*)lor_alloc(c, std::max<long long>(tot, 1) * 4);
+  if (!c->d_F64 || !(c->d_F16 || c->d_F32)) return lor_fail(c, LOR_ENOMEM, "alloc factors");
   // ILU(0) per level (the last level is solved exactly and needs no factors)
   for (int l = 0; l + 1 < c->L; ++l) {
     IluArgs a;
@@ -903,12 +905,11 @@ lor_status lor_setup_patches(lor_ctx* c) {
     if (lor_cuda_check(c, cudaGetLastError(), "ilu0")) return LOR_ECUDA;
   }
   if (tot > 0) {   // p = 1: the patch box is the vertex level, solved exactly, no factors
-    k_fac_to32<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F32, tot, lor_rec(dim));
-    ++c->launches;
-    if (c->d_F16) {
+    if (c->d_F32)
+      k_fac_to32<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F32, tot, lor_rec(dim));
+    else
       k_fac_to16<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F16, tot, lor_rec(dim));
-      ++c->launches;
-    }
+    ++c->launches;
     if (lor_cuda_check(c, cudaGetLastError(), "factor conversion")) return LOR_ECUDA;
   }
   return check_status(c, "ilu0");
