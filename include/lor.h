@@ -117,6 +117,20 @@ lor_status lor_get_info(const lor_ctx* ctx, lor_info* info);
  * float64 L-vector (or DG vector for DG contexts). */
 lor_status lor_rhs(lor_ctx* ctx, int kind, double* d_b);
 
+/* The load vector of the caller's right-hand side f (Eq. (system): f is an input
+ * of the problem, b_i = integral of f phi_i), integrated with the (p+1)^d
+ * Gauss-Legendre points of every element under the element map the operator
+ * uses (multilinear, or the isoparametric interpolant of lor_set_node_coordinates).
+ * lor_quadrature_points writes the physical coordinates of those points into the
+ * caller's HOST array xq (nel (p+1)^d points x dim doubles, point-major; elements
+ * x fastest, point q = qx + Q qy + Q^2 qz inside an element, Q = p+1); it makes no
+ * CUDA call and works before lor_setup.  lor_rhs_f takes f at those points as a
+ * DEVICE float64 array d_fq (same order) and writes b into d_b (an L-vector with
+ * zero boundary entries, or a DG vector for DG contexts).  LOR_EINVAL for NULL
+ * arrays, LOR_ESTATE before lor_setup. */
+lor_status lor_quadrature_points(const lor_ctx* ctx, double* xq);
+lor_status lor_rhs_f(lor_ctx* ctx, const double* d_fq, double* d_b);
+
 /* y = A x, the matrix-free sum-factorized operator (Section 2; Eq. (ip)/(br2)
  * for DG contexts).  prec LOR_FP64: x, y float64; LOR_FP32: x, y float32. */
 lor_status lor_apply_A(lor_ctx* ctx, const void* d_x, void* d_y, int prec);

@@ -487,6 +487,12 @@ __global__ void k_rhs_scatter(int dim, int p, int nx, int ny, int nz, int color,
   b[((long long)K * Ny + Jn) * Nx + I] += s;
 }
 
+// W[q] *= f[q]: the caller's f at the quadrature points times the f = 1 weights
+__global__ void k_scale_by(double* __restrict__ W, const double* __restrict__ f, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) W[i] *= f[i];
+}
+
 }  // namespace
 
 // Basis tables live in a small device block allocated in lor_setup_geometry:
@@ -523,15 +529,20 @@ lor_status lor_launch_rhs_weights(lor_ctx* c, int kind, double* W) {
   return lor_cuda_check(c, cudaGetLastError(), "rhs weights");
 }
 
-lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b) {
+lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b, const double* fq) {
   const int Q = c->p + 1;
   const long long Qd = c->dim == 3 ? (long long)Q * Q * Q : (long long)Q * Q;
   const long long tot = (long long)c->nel * Qd;
   double* W = (double*)c->d_v64[7];   // scratch: Krylov vector 7 holds >= nel*(p+1)^d (lor_setup_krylov)
-  if (c->dg_state) return lor_launch_rhs_dg(c, kind, b, W);
+  // quadrature weights w_q det J_q f(x_q): f from the kind, or the caller's values
+  if (lor_launch_rhs_weights(c, fq ? 0 : kind, W)) return LOR_ECUDA;
+  if (fq) {
+    k_scale_by<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(W, fq, tot);
+    ++c->launches;
+  }
+  if (c->dg_state) return lor_launch_rhs_dg(c, b, W);
   cudaError_t e = cudaMemsetAsync(b, 0, sizeof(double) * c->lev[0].ntot, c->stream);
   if (e != cudaSuccess) return lor_cuda_check(c, e, "rhs memset");
-  if (lor_launch_rhs_weights(c, kind, W)) return LOR_ECUDA;
   for (int color = 0; color < (c->dim == 3 ? 8 : 4); ++color) {
     k_rhs_scatter<<<(unsigned)lor_ceil_div(tot, 256), 256, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1], c->n[2],
                                                                           color, lor_basis64(c, 0), W, b);

@@ -234,6 +234,19 @@ lor_status lor_rhs(lor_ctx* c, int kind, double* d_b) {
   return lor_launch_rhs(c, kind, d_b);
 }
 
+lor_status lor_quadrature_points(const lor_ctx* c, double* xq) {
+  if (!c || !xq) return LOR_EINVAL;
+  lor_quad_points(c, xq);
+  return LOR_OK;
+}
+
+lor_status lor_rhs_f(lor_ctx* c, const double* d_fq, double* d_b) {
+  lor_status s = ready(c);
+  if (s) return s;
+  if (!d_fq || !d_b) return lor_fail(c, LOR_EINVAL, "lor_rhs_f: null vector");
+  return lor_launch_rhs(c, 0, d_b, d_fq);
+}
+
 lor_status lor_apply_A(lor_ctx* c, const void* x, void* y, int prec) {
   lor_status s = ready(c);
   if (s) return s;

@@ -686,10 +686,7 @@ lor_status lor_launch_apply_P_dg32(lor_ctx* c, const float* r, float* z) {
   return apply_P_dg<float>(c, r, z, s->cgin32, s->cgout32, s->dinv32);
 }
 
-lor_status lor_launch_rhs_dg(lor_ctx* c, int kind, double* b, double* W) {
-  extern lor_status lor_launch_rhs_weights(lor_ctx*, int, double*);
-  lor_status st = lor_launch_rhs_weights(c, kind, W);
-  if (st) return st;
+lor_status lor_launch_rhs_dg(lor_ctx* c, double* b, const double* W) {
   const int Q = c->p + 1;
   const long long ndg = (long long)c->nel * Q * Q * Q;
   k_rhs_dg<<<(unsigned)lor_ceil_div(ndg, 128), 128, 0, c->stream>>>(c->p, c->nel, lor_basis64(c, 0), W, b);

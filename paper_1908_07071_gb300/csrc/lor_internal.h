@@ -228,7 +228,9 @@ lor_status lor_setup_coarse(lor_ctx* c);
 // apply_a.cu
 lor_status lor_launch_apply_A64(lor_ctx* c, const double* x, double* y);
 lor_status lor_launch_apply_A32(lor_ctx* c, const float* x, float* y);
-lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b);
+// b = M f with f from `kind` (0: 1, 1: manufactured) or, when fq is given, the
+// caller's values at the quadrature points (device, nel (p+1)^d, lor_quadrature_points order)
+lor_status lor_launch_rhs(lor_ctx* c, int kind, double* b, const double* fq = nullptr);
 lor_status lor_launch_rhs_weights(lor_ctx* c, int kind, double* W);
 lor_status lor_launch_dgvol64(lor_ctx* c, const double* x, double* y);
 lor_status lor_launch_dgvol32(lor_ctx* c, const float* x, float* y);
@@ -238,7 +240,7 @@ lor_status lor_launch_apply_A_dg64(lor_ctx* c, const double* x, double* y);
 lor_status lor_launch_apply_A_dg32(lor_ctx* c, const float* x, float* y);
 lor_status lor_launch_apply_P_dg64(lor_ctx* c, const double* r, double* z);
 lor_status lor_launch_apply_P_dg32(lor_ctx* c, const float* r, float* z);
-lor_status lor_launch_rhs_dg(lor_ctx* c, int kind, double* b, double* W);
+lor_status lor_launch_rhs_dg(lor_ctx* c, double* b, const double* W);
 void lor_free_dg(lor_ctx* c);
 void lor_free_learned(lor_ctx* c);
 lor_status lor_learned_apply(lor_ctx* c, float* z);
@@ -271,6 +273,10 @@ double* lor_basis64(lor_ctx* c, int which);
 // sizes and physical coordinates of the coefficient sample points (host; no CUDA call)
 void lor_coef_sizes(const lor_ctx* c, long long* nq, long long* nh);
 void lor_coef_points(const lor_ctx* c, double* xq, double* xh);
+// physical coordinates of the (p+1)^d Gauss points of every element under the
+// element map the operator uses (multilinear, or the isoparametric interpolant of
+// the given node coordinates); host only
+void lor_quad_points(const lor_ctx* c, double* xq);
 float* lor_basis32(lor_ctx* c, int which);
 
 // event pair around a hot kernel launch (no-op unless profiling)

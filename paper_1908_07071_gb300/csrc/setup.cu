@@ -88,6 +88,39 @@ void lor_coef_points(const lor_ctx* c, double* xq, double* xh) {
   }
 }
 
+void lor_quad_points(const lor_ctx* c, double* xq) {
+  if (c->h_nodes.empty()) {   // multilinear elements: the K_p sample points
+    lor_coef_points(c, xq, nullptr);
+    return;
+  }
+  // curved elements: the degree-p interpolant of the GLL node coordinates
+  const int dim = c->dim, p = c->p, Q = p + 1, nx = c->n[0], ny = c->n[1];
+  double gllx[LOR_MAXP + 1], gllw[LOR_MAXP + 1], glx[LOR_MAXP + 2], glw[LOR_MAXP + 2];
+  double Bq[(LOR_MAXP + 1) * (LOR_MAXP + 1)], Dq[(LOR_MAXP + 1) * (LOR_MAXP + 1)];
+  lorh::gll(p, gllx, gllw);
+  lorh::gauss(Q, glx, glw);
+  lorh::lagrange(Q, gllx, Q, glx, Bq, Dq);   // Bq[q * Q + i] = l_i(gl_q)
+  const int Nx = nx * p + 1, Ny = ny * p + 1;
+  const long long ntot = (long long)Nx * Ny * (dim == 3 ? (long long)c->n[2] * p + 1 : 1);
+  const int Qd = dim == 3 ? Q * Q * Q : Q * Q;
+  const double* X = c->h_nodes.data();
+  for (long long e = 0; e < c->nel; ++e) {
+    const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = dim == 3 ? (int)(e / ((long long)nx * ny)) : 0;
+    for (int q = 0; q < Qd; ++q) {
+      const int qx = q % Q, qy = (q / Q) % Q, qz = dim == 3 ? q / (Q * Q) : 0;
+      double acc[3] = {0.0, 0.0, 0.0};
+      for (int k = 0; k < (dim == 3 ? Q : 1); ++k)
+        for (int j = 0; j < Q; ++j)
+          for (int i = 0; i < Q; ++i) {
+            const double phi = Bq[qx * Q + i] * Bq[qy * Q + j] * (dim == 3 ? Bq[qz * Q + k] : 1.0);
+            const long long node = ((long long)(ez * p + k) * Ny + (ey * p + j)) * Nx + (ex * p + i);
+            for (int a = 0; a < dim; ++a) acc[a] += phi * X[a * ntot + node];
+          }
+      for (int a = 0; a < dim; ++a) xq[(e * Qd + q) * dim + a] = acc[a];
+    }
+  }
+}
+
 namespace {
 
 // G[e][comp][q] = kappa_e w_q det J (J^{-1} J^{-T})_{ab}, comps (00,01,02,11,12,22) / (00,01,11)

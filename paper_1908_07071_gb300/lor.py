@@ -63,6 +63,8 @@ def load():
     lib.lor_setup.argtypes = [vp]
     lib.lor_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.lor_rhs.argtypes = [vp, i, vp]
+    lib.lor_rhs_f.argtypes = [vp, vp, vp]
+    lib.lor_quadrature_points.argtypes = [vp, vp]
     lib.lor_apply_A.argtypes = [vp, vp, vp, i]
     lib.lor_apply_P.argtypes = [vp, vp, vp, i]
     lib.lor_pcg_solve.argtypes = [vp, vp, vp, pi, pd]
@@ -103,7 +105,7 @@ def load():
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
     for name in ("lor_coefficient_sizes", "lor_coefficient_points", "lor_set_coefficient", "lor_set_node_coordinates",
                  "lor_pcg_state_size", "lor_pcg_state_save", "lor_pcg_resume",
-                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_apply_A", "lor_apply_P",
+                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -225,6 +227,21 @@ class Solver:
         """b = M f into the float64 CUDA tensor b: kind 0 is f = 1, kind 1 the manufactured d pi^2 prod sin(pi x_a)."""
         import torch
         self._check(self.lib.lor_rhs(self.ctx, kind, _ptr(b, torch.float64, self.nvec, "b")))
+
+    def quadrature_points(self):
+        """Physical coordinates (nel (p+1)^d, dim) of the Gauss points at which rhs_f takes f."""
+        Q = self.p + 1
+        nq = int(np.prod(self.n)) * Q ** self.dim
+        xq = np.empty(nq * self.dim)
+        self._check(self.lib.lor_quadrature_points(self.ctx, xq.ctypes.data_as(ctypes.c_void_p)))
+        return xq.reshape(nq, self.dim)
+
+    def rhs_f(self, fq, b):
+        """b = M f from f at quadrature_points() (float64 CUDA tensor fq) into the float64 CUDA tensor b."""
+        import torch
+        Q = self.p + 1
+        nq = int(np.prod(self.n)) * Q ** self.dim
+        self._check(self.lib.lor_rhs_f(self.ctx, _ptr(fq, torch.float64, nq, "fq"), _ptr(b, torch.float64, self.nvec, "b")))
 
     def apply_A(self, x, y, prec=LOR_FP64):
         """y = A x (matrix-free operator) in FP64 (float64 tensors) or FP32 (float32 tensors)."""

@@ -208,3 +208,43 @@ def test_header_is_c99_and_links_from_c(lib, tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.split() == ["0", str(4 * 16), str(36 * 4)]
+
+
+def test_quadrature_points_match_the_oracle_element_maps(lib):
+    """lor_quadrature_points (host only, before setup) lists the (p+1)^d Gauss points of every
+    element in the order lor_rhs_f reads f: elements x fastest, q = qx + Q qy + Q^2 qz; on
+    multilinear elements they are the oracle's multilinear maps of the Gauss points, on curved
+    elements the oracle's isoparametric maps (Section 5.2's curved mesh stand-in)."""
+    from oracle import cg
+    from oracle.basis import gauss_legendre
+    from oracle.mesh import Mesh
+    from paper_1908_07071_gb300.synthetic import make_quarter_hole_mesh
+    cases = []
+    v3, k3 = make_mesh(3, (2, 3, 2), seed=2, perturb=0.15)
+    cases.append((Mesh(v3, k3), 3, None))
+    vq, kq, warp = make_quarter_hole_mesh(4)
+    mq = Mesh(vq, kq, warp=warp)
+    cases.append((mq, 4, cg.node_coordinates(mq, 4)))
+    for m, p, X in cases:
+        opt = lor.Options()
+        lib.lor_default_options(ctypes.byref(opt))
+        opt.dim, opt.p = m.dim, p
+        opt.nx, opt.ny = m.n[0], m.n[1]
+        opt.nz = m.n[2] if m.dim == 3 else 1
+        st, ctx = _create(lib, opt, np.ascontiguousarray(m.vertices), np.ascontiguousarray(m.kappa))
+        assert st == lor.LOR_OK
+        if X is not None:
+            Xs = np.ascontiguousarray(X.T)
+            assert lib.lor_set_node_coordinates(ctx, Xs.ctypes.data_as(ctypes.c_void_p)) == lor.LOR_OK
+        Q = p + 1
+        nq = m.nel * Q ** m.dim
+        xq = np.empty(nq * m.dim)
+        assert lib.lor_quadrature_points(ctx, xq.ctypes.data_as(ctypes.c_void_p)) == lor.LOR_OK
+        xq = xq.reshape(m.nel, Q ** m.dim, m.dim)
+        x1, w1 = gauss_legendre(Q)
+        pts, _ = cg.tensor_points(m.dim, x1, w1)
+        for ie, e in enumerate(m.elements()):
+            Xo, _ = m.element_map(e, pts, p)
+            np.testing.assert_allclose(xq[ie], Xo, atol=1e-13)
+        assert lib.lor_quadrature_points(ctx, None) == lor.LOR_EINVAL
+        lib.lor_destroy(ctx)
