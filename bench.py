@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "3D Q_p PCG time-to-1e-8 and MDOF/s per apply: plain FP64 vs chosen form"
 REF_ITERS = 152   # FP64 PCG iterations to 1e-8 on the Q8 32^3 workload (measured on GB300)
+# DRAM bytes (read + written) of one patch-kernel launch on Q8 32^3, mixed bf16: the ncu
+# capture of one launch on Q8 12^3 scaled by the factor rows (profiles/patch_warp_q8_dram.md);
+# measured on the kernel as built
+PATCH_TRAFFIC_Q8N32 = 22.8e9
 WORKLOAD = "3D CG Q8, 32^3 perturbed hex mesh (+-0.15h), log-normal kappa (sigma 1), f=1, rtol 1e-8"
 
 
@@ -374,6 +378,16 @@ def leg_dg():
                     torch.cuda.synchronize()
                     ms = e0.elapsed_time(e1) / 5
                     per[name] = {"ms": ms, "MDOF/s": s.nvec / (ms * 1e-3) / 1e6}
+                # DG apply_A FP64 against the FP64 peak: volume sum factorization plus the
+                # face terms, ((p+1)^3 + 3 (p+1)^2) multiply-adds per face point and side
+                Qd, nel_dg = 5, 24 ** 3
+                nface = 3 * 25 * 24 * 24
+                fl = nel_dg * (24 * Qd ** 4 + 18 * Qd ** 3) + nface * 2 * Qd ** 2 * 2 * (Qd ** 3 + 3 * Qd ** 2)
+                ach = fl / (per["apply_A_fp64"]["ms"] * 1e-3) / 1e12
+                pk64 = lor.measure_fp64_peak()
+                per["apply_A_fp64"]["roofline"] = {"bound": "alu", "achieved": ach, "peak": pk64, "unit": "TFLOP/s",
+                                                   "frac": ach / pk64, "peak_kind": "measured (project FP64 FMA probe)",
+                                                   "work": f"{fl:.4g} flop per apply"}
                 row["per_apply"] = per
             rows.append(row)
             s.close()
@@ -542,6 +556,7 @@ def main():
     # roofline of the dominant kernel class inside the timed region
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
+    fp64_peak = lor.measure_fp64_peak()   # TFLOP/s, the project's FP64 FMA probe on this GPU
     names = {0: "patch_vcycle_fp64", 1: "patch_vcycle_fp32", 2: "apply_A_fp64", 3: "apply_A_fp32",
              4: "coarse_fp64", 5: "coarse_fp32"}
     dom = max(prof, key=lambda k: prof[k][0])
@@ -562,25 +577,38 @@ def main():
                 "peak_kind": "measured" if "hbm_gbs" in pk else "fallback"}
     elif dom == 2:
         flops = nel * (24 * Q ** 4 + 18 * Q ** 3)
-        fp64_peak = 1.26   # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
         roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-                "peak_kind": "derived"}
+                "peak_kind": "measured (project FP64 FMA probe)"}
     else:
         bts = nel * 6 * Q ** 3 * (8 if dom == 4 else 4) + 3 * s.nvec * 4
         roof = {"bound": "hbm", "achieved": bts / per_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_kind": "measured" if "hbm_gbs" in pk else "fallback"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    # DRAM bytes per launch come only from an ncu capture of the kernel as it is built now.
-    # The one capture of this configuration (profiles/patch_warp_q8n32_dram.md: 23.19 GB read +
-    # 1.00 GB written) predates the patch-sum weighting option, so it is quoted, not reported.
+    # DRAM bytes per launch from the ncu capture of this kernel as it is built now
+    # (profiles/patch_warp_q8_dram.md: one launch on Q8 12^3, scaled to 32^3 by the factor rows)
     roof["traffic"] = None
     if (names[dom], p, n, args.form, args.weighting) == ("patch_vcycle_fp32", 8, 32, "mixed-bf16", 0):
-        roof["traffic_last_capture"] = {"bytes": 23.19e9 + 1.00e9,
-                                        "note": "captured before the weighting option changed the kernel"}
+        roof["traffic"] = PATCH_TRAFFIC_Q8N32
     roof["kernel"] = names[dom]
     roof["launch_ms"] = per_launch_s * 1e3
     roof["launches_in_timed_region"] = nl
     roof["kernel_time_share"] = {names[k]: round(prof[k][0] / max(elapsed * 1e3, 1e-9), 4) for k in prof if prof[k][1]}
+    # the other hot kernels against their own bounds (per-apply timings above)
+    others = {}
+    pa = extras.get("per_apply", {})
+    if "apply_A_fp64" in pa:
+        fl = nel * (24 * Q ** 4 + 18 * Q ** 3)
+        ach = fl / (pa["apply_A_fp64"]["ms"] * 1e-3) / 1e12
+        others["apply_A_fp64"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                  "frac": ach / fp64_peak, "peak_kind": "measured (project FP64 FMA probe)",
+                                  "work": f"{fl:.4g} flop per apply (24 Q^4 + 18 Q^3 per element)"}
+    if "apply_A_fp32" in pa:
+        bts = nel * 6 * Q ** 3 * 4 + 3 * s.nvec * 4
+        ach = bts / (pa["apply_A_fp32"]["ms"] * 1e-3) / 1e9
+        others["apply_A_fp32"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                                  "peak_kind": "measured" if "hbm_gbs" in pk else "fallback",
+                                  "work": f"{bts:.4g} B per apply (6 geometric factors per Gauss point, x read, y RMW)"}
+    roof["others"] = others
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -320,6 +320,13 @@ lor_status lor_device_status(lor_ctx* ctx);
  * lor_device_status; LOR_OK would mean the wait did not time out. */
 lor_status lor_selftest_wait(lor_ctx* ctx, int polls);
 
+/* FP64 FMA throughput of the current device (no paper counterpart; the
+ * denominator of the FP64 operator's roofline): a kernel of independent FP64
+ * FMA chains on every SM, best of three timed launches, in TFLOP/s (an FMA
+ * counts 2 flops).  Needs no context; runs on the legacy default stream and
+ * synchronizes it.  LOR_EINVAL for NULL, LOR_ECUDA if a CUDA call fails. */
+lor_status lor_measure_fp64_peak(double* tflops);
+
 const char* lor_last_error(const lor_ctx* ctx);
 void lor_destroy(lor_ctx* ctx);
 

@@ -442,3 +442,50 @@ lor_status lor_pcg_mixed(lor_ctx* c, const double* b, double* x, int* iters, dou
   if (rn > c->opt.rtol * bn) return lor_fail(c, LOR_ENOCONV, "mixed precision: max_it reached");
   return LOR_OK;
 }
+
+// ------------------------------------------------- FP64 FMA throughput probe
+// Eight independent FMA chains per thread, enough warps to fill every SM: the
+// kernel issues nothing but FP64 FMAs, so its rate is the FP64 pipe's peak (the
+// denominator of the roofline of the FP64 operator apply).
+namespace {
+__device__ double g_dfma_sink;   // written only if the chains reach an impossible value; keeps them live
+__global__ void k_dfma_probe(int iters, double seed) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed * (threadIdx.x + 1) + k;
+  const double m = 0.9999999, c = 1e-9;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+  }
+  double s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == 1234.5678) g_dfma_sink = s;   // never true for these inputs
+}
+}  // namespace
+
+extern "C" lor_status lor_measure_fp64_peak(double* tflops) {
+  if (!tflops) return LOR_EINVAL;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return LOR_ECUDA;
+  const int blocks = nsm * 8, threads = 256, iters = 1 << 15;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LOR_ECUDA;
+  double best = 0.0;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, 0);
+    k_dfma_probe<<<blocks, threads>>>(iters, 1e-12);
+    cudaEventRecord(e1, 0);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+    if (ms > 0) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *tflops = best;
+  return cudaGetLastError() == cudaSuccess && best > 0 ? LOR_OK : LOR_ECUDA;
+}

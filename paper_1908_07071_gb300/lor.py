@@ -30,6 +30,15 @@ class LorError(RuntimeError):
         self.status = status
 
 
+def measure_fp64_peak():
+    """FP64 FMA throughput of the current CUDA device in TFLOP/s (lor_measure_fp64_peak)."""
+    v = ctypes.c_double(0.0)
+    st = load().lor_measure_fp64_peak(ctypes.byref(v))
+    if st != LOR_OK:
+        raise LorError(st, "FP64 peak probe failed")
+    return v.value
+
+
 class Options(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("p", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("disc", ctypes.c_int), ("eta", ctypes.c_double),
@@ -64,6 +73,7 @@ def load():
     lib.lor_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.lor_rhs.argtypes = [vp, i, vp]
     lib.lor_rhs_f.argtypes = [vp, vp, vp]
+    lib.lor_measure_fp64_peak.argtypes = [pd]
     lib.lor_quadrature_points.argtypes = [vp, vp]
     lib.lor_apply_A.argtypes = [vp, vp, vp, i]
     lib.lor_apply_P.argtypes = [vp, vp, vp, i]
@@ -105,7 +115,7 @@ def load():
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
     for name in ("lor_coefficient_sizes", "lor_coefficient_points", "lor_set_coefficient", "lor_set_node_coordinates",
                  "lor_pcg_state_size", "lor_pcg_state_save", "lor_pcg_resume",
-                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
+                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_measure_fp64_peak", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
