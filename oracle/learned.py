@@ -74,29 +74,40 @@ def features(t, diag):
     return np.stack([st / rho, f]), s, rho
 
 
-def forward(P, t, diag):
-    """Correction c (same shape as t) and the cache for backward."""
+def forward(P, t, diag, act="fp64"):
+    """Correction c (same shape as t) and the cache for backward.
+
+    act="bf16": the arithmetic of a bf16 implementation with FP32 (here FP64)
+    accumulation, which stores the network's input features and its pre-activations
+    in bfloat16: each layer's input is rounded to bf16 (the features; relu of the
+    rounded pre-activations is already bf16), the output layer is not."""
+    rnd = bf16_round if act == "bf16" else (lambda a: a)
     x0, s, rho = features(t, diag)
-    z1 = conv(x0, P["W1"], P["b1"])
+    x0 = rnd(x0)
+    z1 = rnd(conv(x0, P["W1"], P["b1"]))
     a1 = np.maximum(z1, 0)
-    z2 = conv(a1, P["W2"], P["b2"])
+    z2 = rnd(conv(a1, P["W2"], P["b2"]))
     a2 = np.maximum(z2, 0)
     y = conv(a2, P["W3"], P["b3"])[0]
     return rho * s * y, (x0, z1, a1, z2, a2, s, rho)
 
 
-def loss_and_grad(P, t, delta, apply_A, diag):
-    """L for one patch and dL/dparams.  apply_A(v) applies A_j to a box-shaped v."""
-    c, (x0, z1, a1, z2, a2, s, rho) = forward(P, t, diag)
+def loss_and_grad(P, t, delta, apply_A, diag, act="fp64"):
+    """L for one patch and dL/dparams.  apply_A(v) applies A_j to a box-shaped v.
+    act="bf16" also rounds the back-propagated gradients to bf16 where such an
+    implementation stores them: the output gradient and the gradients behind each
+    ReLU."""
+    rnd = bf16_round if act == "bf16" else (lambda a: a)
+    c, (x0, z1, a1, z2, a2, s, rho) = forward(P, t, diag, act)
     d = delta - c
     Ad = apply_A(d)
     norm = float(np.sum(delta * t))          # delta^T A delta, since t = A delta
     L = float(np.sum(d * Ad)) / norm
-    gy = (-2.0 * rho * s * Ad / norm)[None]
+    gy = rnd((-2.0 * rho * s * Ad / norm)[None])
     ga2, gW3, gb3 = conv_backward(a2, P["W3"], gy)
-    gz2 = ga2 * (z2 > 0)
+    gz2 = rnd(ga2 * (z2 > 0))
     ga1, gW2, gb2 = conv_backward(a1, P["W2"], gz2)
-    gz1 = ga1 * (z1 > 0)
+    gz1 = rnd(ga1 * (z1 > 0))
     _, gW1, gb1 = conv_backward(x0, P["W1"], gz1)
     return L, {"W1": gW1, "b1": gb1, "W2": gW2, "b2": gb2, "W3": gW3, "b3": gb3}
 

@@ -257,3 +257,19 @@ def batch_plan(nsolves: int, seed: int = 0, nmin: int = 4, nmax: int = 16,
     ns = nmin + np.minimum((u[:, 0] * (nmax - nmin + 1)).astype(int), nmax - nmin)
     ps = pmin + np.minimum((u[:, 1] * (pmax - pmin + 1)).astype(int), pmax - pmin)
     return [(int(a), int(b)) for a, b in zip(ns, ps)]
+
+
+TAG_NET = 11
+
+
+def learned_init_params(seed: int = 0, scale: float = 0.1) -> np.ndarray:
+    """Seeded starting parameters of the per-patch network (flat float32 vector in the
+    layout lor_learned_params takes: W1[16][2][27] b1[16] W2[16][16][27] b2[16]
+    W3[1][16][27] b3[1]): normal weights of standard deviation `scale` (scale/4 for the
+    16->16 layer), zero biases, and a zero output layer, so that the untrained
+    correction is zero."""
+    ch = 16
+    n1, n2, n3 = ch * 2 * 27, ch * ch * 27, ch * 27
+    z = normal(stream_key(seed, TAG_NET), n1 + n2)
+    return np.concatenate([z[:n1] * scale, np.zeros(ch), z[n1:] * scale / 4, np.zeros(ch),
+                           np.zeros(n3), np.zeros(1)]).astype(np.float32)

@@ -1,7 +1,20 @@
-"""Batched serving: uneven solves advanced together in one CUDA graph (GPU)."""
+"""Batched serving: uneven solves advanced together in one CUDA graph (GPU).
+
+Each member of a batch is checked against the oracle: its iteration count against
+the oracle's flexible PCG with the FP64 preconditioner (the batch runs the
+preconditioner in FP32, so the counts may differ by one; bf16 factors perturb B
+by up to 2^-9 relative per factor entry, stated bound two), and its solution
+against a direct solve of the assembled Dirichlet system, bounded by cond(A) times
+the residuals of the two (cond(A) from the oracle's extreme eigenvalues).  A
+second call replays the captured graph and must give the same bits, which rules
+out state leaking from one solve into the next."""
 import numpy as np
 import pytest
+import scipy.sparse.linalg as spl
 
+from oracle import cg, krylov
+from oracle import lor as olor
+from oracle.mesh import Mesh
 from paper_1908_07071_gb300.synthetic import batch_plan, make_mesh
 
 torch = pytest.importorskip("torch")
@@ -14,6 +27,50 @@ def _built():
         pytest.skip("no CUDA device")
     from paper_1908_07071_gb300.build import build_library
     build_library()
+
+
+def test_batch_members_match_the_oracle():
+    from paper_1908_07071_gb300 import lor
+    rtol = 1e-8
+    plan = batch_plan(6, seed=3, nmin=2, nmax=4, pmin=2, pmax=5)
+    solvers, bs, refs = [], [], []
+    for s_i, (n, p) in enumerate(plan):
+        v, k = make_mesh(3, n, seed=s_i, perturb=0.15)
+        m = Mesh(v, k)
+        K = cg.assemble_stiffness(m, p)
+        N = cg.node_shape(m.n, p)
+        B = olor.LORPreconditioner(m, p)
+        b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+        _, it_or, _, _ = krylov.pcg(lambda u: cg.apply_A(K, N, u), B.apply, b, rtol=rtol, flexible=True)
+        mask = ~cg.boundary_mask(N)
+        Ai = cg.dirichlet_operator(K, N)[mask][:, mask].tocsc()
+        xd = np.zeros_like(b)
+        xd[mask] = spl.spsolve(Ai, b[mask])
+        lmax = spl.eigsh(Ai, k=1, which="LA", return_eigenvectors=False)[0]
+        lmin = spl.eigsh(Ai, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+        bf16 = s_i % 2 == 1
+        solvers.append(lor.Solver(v, k, p, rtol=rtol, factor_bf16=bf16))
+        bs.append(torch.from_numpy(b).cuda())
+        refs.append((it_or, xd, lmax / lmin, bf16))
+    batch = lor.Batch(solvers)
+    xs = [torch.full_like(b, np.nan) for b in bs]
+    its, rels = batch.solve(bs, xs)
+    first = [x.clone() for x in xs]
+    for s_i, (it_or, xd, cond, bf16) in enumerate(refs):
+        print(f"member {plan[s_i]} bf16={bf16}: batch {its[s_i]} iterations, oracle {it_or}")
+        assert rels[s_i] <= rtol, (s_i, rels[s_i])
+        assert abs(its[s_i] - it_or) <= (2 if bf16 else 1), (s_i, its[s_i], it_or)
+        d = np.linalg.norm(xs[s_i].cpu().numpy() - xd) / np.linalg.norm(xd)
+        assert d <= cond * 2 * rtol, (s_i, d, cond)     # residuals of both solves <= rtol
+    for x in xs:
+        x.fill_(float("nan"))
+    its2, rels2 = batch.solve(bs, xs)
+    assert its2 == its and rels2 == rels
+    for x, x0 in zip(xs, first):
+        assert torch.equal(x, x0)
+    batch.close()
+    for s in solvers:
+        s.close()
 
 
 def test_batch_matches_individual_solves():
@@ -37,7 +94,9 @@ def test_batch_matches_individual_solves():
         its, rels = batch.solve(bs, xs)
         for s_i in range(len(plan)):
             assert rels[s_i] <= 1e-8, (s_i, rels[s_i])
-            assert its[s_i] <= 1.5 * refits[s_i] + 5, (its[s_i], refits[s_i])
+            # FCG with the FP32 preconditioner against FP64 PCG (bf16 factors on every
+            # other member): the counts may differ by a few iterations
+            assert abs(its[s_i] - refits[s_i]) <= max(2, refits[s_i] // 10), (its[s_i], refits[s_i])
             d = torch.linalg.norm(xs[s_i] - ref[s_i]) / torch.linalg.norm(ref[s_i])
             assert float(d) < 1e-5, (s_i, float(d))
     ms, nodes = batch.stats()

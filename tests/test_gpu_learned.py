@@ -58,9 +58,11 @@ def test_forward_loss_gradient_parity():
         A = B.patches[j]["levels"][0]["A"]
         delta = rng.standard_normal(V)
         t = A @ delta
+        # the oracle in the kernels' declared arithmetic: bf16 weights, bf16 features,
+        # pre-activations and back-propagated gradients, wide accumulation
         Lr, G = L.loss_and_grad(Pq, t.reshape(shape), delta.reshape(shape),
-                                lambda x, A=A: (A @ x.ravel()).reshape(shape), np.diag(A).reshape(shape))
-        c, _ = L.forward(Pq, t.reshape(shape), np.diag(A).reshape(shape))
+                                lambda x, A=A: (A @ x.ravel()).reshape(shape), np.diag(A).reshape(shape), act="bf16")
+        c, _ = L.forward(Pq, t.reshape(shape), np.diag(A).reshape(shape), act="bf16")
         ts.append(t)
         ds.append(delta)
         refs.append((Lr, G, c.ravel()))
@@ -71,9 +73,11 @@ def test_forward_loss_gradient_parity():
     c = c.cpu().numpy()
     loss = loss.cpu().numpy()
     Gsum = _unflat(grad)
+    # differences left: FP32 against FP64 accumulation, and the rare value whose bf16
+    # rounding falls on the other side of a rounding boundary in FP32
     for q, (Lr, G, cr) in enumerate(refs):
-        assert abs(loss[q] - Lr) <= 1e-4 * abs(Lr), (loss[q], Lr)
-        assert np.abs(c[q] - cr).max() <= 1e-4 * np.abs(cr).max()
+        assert abs(loss[q] - Lr) <= 1e-3 * abs(Lr), (loss[q], Lr)
+        assert np.abs(c[q] - cr).max() <= 1e-3 * np.abs(cr).max()
     for name in Gsum:
         ref = sum(r[1][name] for r in refs)
         assert np.abs(Gsum[name] - ref).max() <= 2e-3 * np.abs(ref).max() + 1e-7, name
@@ -98,5 +102,9 @@ def test_training_lowers_loss_and_correction_in_fcg():
     print(f"mixed-precision FCG iterations: plain {it_plain}, learned {it_l}; "
           f"loss {hist[:5].mean():.3f} -> {hist[-20:].mean():.3f}")
     assert rel_l <= 1e-8 and rel_plain <= 1e-8
-    assert it_l <= 1.1 * it_plain + 2
+    # the correction may not cost iterations; it cannot save any here either: its best
+    # case is an exact solve on every patch, and exact patch solves leave the PCG count
+    # of the additive preconditioner unchanged (the oracle pin
+    # test_exact_patch_solves_bound_the_learned_gain)
+    assert it_l <= it_plain
     s.close()

@@ -71,3 +71,49 @@ def test_bf16_rounding():
     r = L.bf16_round(vals)
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -7 and r[3] == -2.5
     assert abs(r[4] - 3.140625) < 1e-12
+
+
+def test_bf16_activation_mode():
+    """act="bf16" (the arithmetic of the tensor-core kernels): the cached features and
+    pre-activations are bfloat16 numbers, and the correction, the loss and the gradient
+    stay within the bf16 rounding error of the FP64 mode."""
+    P = L.init_params(seed=3, scale=0.3)
+    P["W3"] = np.random.default_rng(4).standard_normal(P["W3"].shape) * 0.1
+    t, delta, apply_A, diag = _problem(seed=2)
+    c64, _ = L.forward(P, t, diag)
+    c16, (x0, z1, a1, z2, a2, s, rho) = L.forward(P, t, diag, act="bf16")
+    for a in (x0, z1, z2):
+        np.testing.assert_array_equal(L.bf16_round(a), a)
+    assert np.abs(c16 - c64).max() <= 0.03 * np.abs(c64).max()
+    assert np.abs(c16 - c64).max() > 0                       # the rounding is really applied
+    L64, G64 = L.loss_and_grad(P, t, delta, apply_A, diag)
+    L16, G16 = L.loss_and_grad(P, t, delta, apply_A, diag, act="bf16")
+    assert abs(L16 - L64) <= 0.01 * abs(L64)
+    # gradients are sums over the patch with cancellation, so compare them as vectors
+    g64 = np.concatenate([G64[k].ravel() for k in sorted(G64)])
+    g16 = np.concatenate([G16[k].ravel() for k in sorted(G16)])
+    assert np.linalg.norm(g16 - g64) <= 0.1 * np.linalg.norm(g64)
+    assert g16 @ g64 >= 0.99 * np.linalg.norm(g16) * np.linalg.norm(g64)
+
+
+@pytest.mark.parametrize("n,p", [(4, 3), (3, 4)])
+def test_exact_patch_solves_bound_the_learned_gain(n, p):
+    """The learned correction adds to each patch's V-cycle result an estimate of the
+    error that cycle leaves on the patch; at best it makes every patch solve exact.
+    With exact patch solves the additive preconditioner needs as many PCG iterations
+    as with the V(1,1) cycle (within one), so the learned form can shorten the solve
+    only through a cheaper cycle, never through fewer iterations."""
+    from oracle import cg, krylov
+    from oracle import lor as olor
+    from oracle.mesh import Mesh
+    from paper_1908_07071_gb300.synthetic import make_mesh
+    v, k = make_mesh(3, n, seed=11, perturb=0.15)
+    m = Mesh(v, k)
+    K = cg.assemble_stiffness(m, p)
+    N = cg.node_shape(m.n, p)
+    b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+    its = []
+    for exact in (False, True):
+        B = olor.LORPreconditioner(m, p, exact_local=exact)
+        its.append(krylov.pcg(lambda u: cg.apply_A(K, N, u), B.apply, b, rtol=1e-8)[1])
+    assert abs(its[0] - its[1]) <= 1, its
