@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-solve batched leg")
     ap.add_argument("--no-dg", action="store_true", help="skip the DG penalty-sweep leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction leg (Q6 32^3)")
+    ap.add_argument("--no-schwarz", action="store_true", help="skip the B(1) / B(V) / hybrid comparison leg")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--weighting", type=int, default=0, choices=[0, 1, 2],
@@ -398,6 +399,63 @@ def leg_dg():
     return out
 
 
+def leg_schwarz(n: int = 12, degrees=(2, 4, 6, 8)):
+    """B(1) (the whole domain as one patch) against B(V) (one patch per vertex, additive
+    coarse space) and the hybrid form (coarse space multiplicative), the comparison of
+    Section 5.1 / Table 2 on the GPU: 3D CG on a 12^3 perturbed hex mesh, log-normal
+    kappa, f=1, FP64 PCG to 1e-8, p in {2,4,6,8}; and DG BR2 (eta 10) at p=4 with the
+    three forms inside the DG preconditioner.  Reports iterations, time to tolerance and
+    milliseconds per preconditioner apply (CUDA events, 5 applies after a warm-up)."""
+    import torch
+    from paper_1908_07071_gb300 import lor
+    from paper_1908_07071_gb300.synthetic import make_mesh
+    v, k = make_mesh(3, n, seed=0, perturb=0.15)
+    forms = (("B(V)", 0), ("hybrid", 1), ("B(1)", 2))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run(s):
+        b = torch.empty(s.nvec, dtype=torch.float64, device="cuda")
+        s.rhs(b, 0)
+        row = {}
+        for name, mode in forms:
+            s.set_schwarz(mode)
+            x = torch.zeros_like(b)
+            e0.record()
+            it, rel = s.solve(b, x)
+            e1.record()
+            torch.cuda.synchronize()
+            z = torch.empty_like(b)
+            s.apply_P(b, z)
+            e0.record()
+            for _ in range(5):
+                s.apply_P(b, z)
+            e1.record()
+            torch.cuda.synchronize()
+            row[name] = {"iterations": it, "rel_res": rel, "time_to_tol_ms": None, "ms_per_apply": e0.elapsed_time(e1) / 5}
+            x.zero_()
+            e0.record()
+            it, rel = s.solve(b, x)
+            e1.record()
+            torch.cuda.synchronize()
+            row[name]["time_to_tol_ms"] = e0.elapsed_time(e1)
+        s.set_schwarz(0)
+        return row
+
+    out = {"workload": f"3D CG on a {n}^3 perturbed hex mesh, log-normal kappa, f=1, FP64 PCG to 1e-8; "
+                       f"DG BR2 eta=10 p=4 on the same mesh", "cg": [], "dg_br2": None}
+    for p in degrees:
+        s = lor.Solver(v, k, p, rtol=1e-8)
+        row = {"p": p, "ndof": s.info.ndof}
+        row.update(run(s))
+        out["cg"].append(row)
+        s.close()
+    s = lor.Solver(v, k, 4, disc=lor.LOR_DG_BR2, eta=10.0, rtol=1e-8)
+    out["dg_br2"] = {"p": 4, "ndof": s.info.ndof}
+    out["dg_br2"].update(run(s))
+    s.close()
+    return out
+
+
 def leg_learned(n: int = 32, p: int = 6, train_n: int = 16, steps: int = 300):
     """The learned form (configuration 5): 3D CG Q6 on a 32^3 perturbed mesh, log-normal
     kappa.  The per-patch network is trained on the GPU on a mesh of the same family
@@ -683,6 +741,11 @@ def main():
             line["learned"] = leg_learned()
         except Exception as exc:
             line["learned"] = {"error": f"{type(exc).__name__}: {exc}"}
+    if not args.no_schwarz:
+        try:
+            line["schwarz"] = leg_schwarz()
+        except Exception as exc:
+            line["schwarz"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0 and not args.no_extras:
         its64 = extras.get("fp64_plain", {}).get("iterations", 60)
         try:

@@ -218,6 +218,30 @@ lor_status lor_set_node_coordinates(lor_ctx* ctx, const double* X);
  * is enabled (it is trained for unit weights). */
 lor_status lor_set_weighting(lor_ctx* ctx, int weighting);
 
+/* Selects how apply_P combines the coarse space with the patches: 0 = additive,
+ * B = P_0 R_0 P_0^T + sum_j R_j^T V_j R_j (Eq. (as), the default); 1 = hybrid,
+ * the coarse correction multiplicative and the patches additive among
+ * themselves (the variant Section 5.1 leaves to future work), in the symmetric
+ * form B_hyb = B_0 + (I - B_0 K_h) B_loc (I - K_h B_0), B_0 = P_0 R_0 P_0^T,
+ * B_loc the patch sum and K_h the LOR matrix on the interior nodes.  B_hyb is
+ * B_0 plus a congruence of B_loc, so it is symmetric positive definite and PCG
+ * applies.  An apply in hybrid form costs the additive one plus a second coarse
+ * V-cycle and two K_h stencil products.  2 = B(1), the whole domain as one patch
+ * (Section 5.1, Table 2): one V(1,1) cycle of the element-structured hierarchy
+ * on the global level grids, one lexicographic ILU(0) smoothing before and one
+ * after the coarse-level correction on every level above the vertex level, and
+ * the coarse solver R_0 on the vertex level.  Its ILU(0) factors are computed
+ * when the mode is first selected (hyperplane-parallel factorization on the
+ * device; LOR_EBREAKDOWN on a non-positive pivot) and its sweeps run one launch
+ * per hyperplane i + 2j + 4k of each level grid.  The first switch to 1 or 2
+ * allocates that form's work space (three float64 vectors of nvec entries for
+ * 1; factors of 3^d float64 and float32 values per level-grid node and six
+ * vectors per level for 2; LOR_ENOMEM if that fails); the setting holds for
+ * every later apply_P and solve, and for the DG preconditioner's conforming
+ * part.  LOR_ESTATE before lor_setup; LOR_EINVAL for other values or with the
+ * learned correction enabled (it is trained for the additive form). */
+lor_status lor_set_schwarz(lor_ctx* ctx, int mode);
+
 /* Number of kernels this context has launched so far (all entry points). */
 lor_status lor_launch_count(const lor_ctx* ctx, long long* count);
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblor.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "setup.cu", "apply_a.cu", "apply_p.cu", "krylov.cu", "dg.cu", "batch.cu", "learned.cu", "host_basis.cpp"]
+SOURCES = ["capi.cu", "setup.cu", "apply_a.cu", "apply_p.cu", "krylov.cu", "dg.cu", "batch.cu", "learned.cu", "single.cu", "host_basis.cpp"]
 
 
 def _nvcc():

@@ -43,7 +43,9 @@ struct TileNE {
 template <int P, typename T, bool DGM, int NE>
 __global__ void __launch_bounds__(1024) k_apply3d(int nx, int ny, int nz, int color, const T* __restrict__ Bg,
                                                   const T* __restrict__ Dg, const T* __restrict__ G,
-                                                  const T* __restrict__ x, T* __restrict__ y) {
+                                                  const T* __restrict__ x, T* __restrict__ y,
+                                                  const double* __restrict__ conv) {
+  if (conv && *conv != 0.0) return;   // converged member of a batched solve: nothing to do
   constexpr int Q = P + 1;
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
   __shared__ T sB[Q2], sD[Q2];
@@ -214,7 +216,9 @@ __global__ void __launch_bounds__(1024) k_apply3d(int nx, int ny, int nz, int co
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_apply2d(int nx, int ny, int color, const T* __restrict__ Bg,
                                                  const T* __restrict__ Dg, const T* __restrict__ G,
-                                                 const T* __restrict__ x, T* __restrict__ y) {
+                                                 const T* __restrict__ x, T* __restrict__ y,
+                                                 const double* __restrict__ conv) {
+  if (conv && *conv != 0.0) return;   // converged member of a batched solve: nothing to do
   constexpr int Q = P + 1;
   constexpr int Q2 = Q * Q;
   constexpr int NE = ElemsPerBlock<P>::v2;
@@ -313,7 +317,7 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
     constexpr int NE = TileNE<PP, T, V>::v;                                                 \
     const int threads = NE * (PP + 1) * (PP + 1);                                           \
     const long long blocks = lor_ceil_div(ncls, NE);                                        \
-    k_apply3d<PP, T, false, NE><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, color, B, D, G, x, y); \
+    k_apply3d<PP, T, false, NE><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, color, B, D, G, x, y, c->conv_flag); \
   }
 #define LOR_CASE3(PP)                                                                       \
   case PP: {                                                                                \
@@ -325,7 +329,7 @@ lor_status launch_apply(lor_ctx* c, const T* B, const T* D, const T* G, const T*
       constexpr int NE = ElemsPerBlock<PP>::v2;                                             \
       const int threads = NE * (PP + 1) * (PP + 1);                                         \
       const long long blocks = lor_ceil_div(ncls, NE);                                      \
-      k_apply2d<PP, T><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, color, B, D, G, x, y); \
+      k_apply2d<PP, T><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, color, B, D, G, x, y, c->conv_flag); \
     }                                                                                       \
   } break;
     switch (c->p) {
@@ -349,7 +353,7 @@ lor_status launch_apply_dgvol(lor_ctx* c, const T* B, const T* D, const T* G, co
     constexpr int NE = TileNE<PP, T, V>::v;                                                   \
     const int threads = NE * (PP + 1) * (PP + 1);                                             \
     const long long blocks = lor_ceil_div((long long)c->nel, NE);                             \
-    k_apply3d<PP, T, true, NE><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, -1, B, D, G, x, y); \
+    k_apply3d<PP, T, true, NE><<<(unsigned)blocks, threads, 0, c->stream>>>(nx, ny, nz, -1, B, D, G, x, y, nullptr); \
   }
 #define LOR_CASEDG(PP)                                                                        \
   case PP: {                                                                                  \

@@ -942,7 +942,8 @@ __global__ void k_patch_sum(int dim, int p, int nx, int ny, int nz, const T* __r
 // the two elements around the vertex.
 template <typename T>
 __global__ void k_p0t_pass(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int d2, int ax, int p,
-                           int Vn, const T* __restrict__ w) {
+                           int Vn, const T* __restrict__ w, const double* __restrict__ conv) {
+  if (conv && *conv != 0.0) return;   // converged batched solve
   const int o0 = ax == 0 ? Vn : d0, o1 = ax == 1 ? Vn : d1, o2 = ax == 2 ? Vn : d2;
   const long long no = (long long)o0 * o1 * o2;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -961,7 +962,8 @@ __global__ void k_p0t_pass(const T* __restrict__ in, T* __restrict__ out, int d0
 // z[F] += sum_V P0[F][V] e[V] for interior fine nodes (weights in the path precision)
 template <typename T>
 __global__ void k_coarse_prolong0(int dim, int p, int nx, int ny, int nz, const T* __restrict__ gllx,
-                                  const T* __restrict__ e, T* __restrict__ z) {
+                                  const T* __restrict__ e, T sgn, T* __restrict__ z, const double* __restrict__ conv) {
+  if (conv && *conv != 0.0) return;   // converged batched solve: z stays 0
   const int Nx = nx * p + 1, Ny = ny * p + 1, Nz = dim == 3 ? nz * p + 1 : 1;
   const long long nt = (long long)Nx * Ny * Nz;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -979,7 +981,37 @@ __global__ void k_coarse_prolong0(int dim, int p, int nx, int ny, int nz, const 
     if (dim == 3) w *= bz ? xi[2] : T(1) - xi[2];
     s += w * e[((long long)(ez + bz) * Vy + (ey + by)) * Vx + (ex + bx)];
   }
-  z[gid] += s;
+  z[gid] += sgn * s;
+}
+
+// y = b - K_h x (or y = K_h x when b is null) on the interior level-0 nodes, K_h the
+// LOR stencil with the Dirichlet rows and columns dropped; y = 0 on the boundary.
+template <typename T>
+__global__ void k_kh_apply(int dim, int Nx, int Ny, int Nz, const T* __restrict__ S, const T* __restrict__ x,
+                           const T* __restrict__ b, T* __restrict__ y) {
+  const long long nt = (long long)Nx * Ny * Nz;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nt) return;
+  const int I = (int)(gid % Nx), Jn = (int)((gid / Nx) % Ny), K = (int)(gid / ((long long)Nx * Ny));
+  if (I == 0 || I == Nx - 1 || Jn == 0 || Jn == Ny - 1 || (dim == 3 && (K == 0 || K == Nz - 1))) {
+    y[gid] = T(0);
+    return;
+  }
+  const int NS = dim == 3 ? 27 : 9;
+  T s = 0;
+  for (int o = 0; o < NS; ++o) {
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = dim == 3 ? o / 9 - 1 : 0;
+    const int I2 = I + dx, J2 = Jn + dy, K2 = K + dz;
+    if (I2 == 0 || I2 == Nx - 1 || J2 == 0 || J2 == Ny - 1 || (dim == 3 && (K2 == 0 || K2 == Nz - 1))) continue;
+    s += S[(long long)o * nt + gid] * x[gid + ((long long)dz * Ny + dy) * Nx + dx];
+  }
+  y[gid] = b ? b[gid] - s : s;
+}
+
+template <typename T>
+__global__ void k_add2(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ z, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = a[i] + b[i];
 }
 
 __device__ __forceinline__ bool grid_bnd(int dim, const int* N, int I, int J, int K) {
@@ -1307,8 +1339,9 @@ lor_status launch_patch_kernel(lor_ctx* c, PatchArgs& a) {
   return lor_cuda_check(c, cudaGetLastError(), "patch vcycle");
 }
 
+// z = sum_j R_j^T V_j(R_j r) (plus the learned correction when it is on)
 template <typename T, typename FT>
-lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
+lor_status patch_part(lor_ctx* c, const T* r, T* z, const FT* F) {
   const long long nvec = c->lev[0].ntot;
   PatchArgs a;
   fill_patch_args<T, FT>(c, a, F);
@@ -1328,6 +1361,14 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
   if (c->learned_on && sizeof(T) == 4) {
     if (lor_learned_apply(c, (float*)z)) return LOR_ECUDA;
   }
+  return LOR_OK;
+}
+
+// z += sgn P_0 R_0 P_0^T r (the coarse space of Eq. (as))
+template <typename T>
+lor_status coarse_part(lor_ctx* c, const T* r, T* z, T sgn) {
+  const long long nvec = c->lev[0].ntot;
+  const int pk = sizeof(T) == 8 ? 0 : 1;
   lor_prof_begin(c, pk + 4);
   // coarse space: rc = P_0^T r by separable passes (x, y[, z])
   {
@@ -1338,23 +1379,57 @@ lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
     T* t2 = Sel<T>::p0t(c, 1);
     T* rc = Sel<T>::cw(c, 0, 0);
     long long m = (long long)g0.N[2] * g0.N[1] * V0;
-    k_p0t_pass<T><<<(unsigned)lor_ceil_div(m, 256), 256, 0, c->stream>>>(r, t1, g0.N[0], g0.N[1], g0.N[2], 0, p, V0, w);
+    k_p0t_pass<T><<<(unsigned)lor_ceil_div(m, 256), 256, 0, c->stream>>>(r, t1, g0.N[0], g0.N[1], g0.N[2], 0, p, V0, w, c->conv_flag);
     m = (long long)g0.N[2] * V1 * V0;
     k_p0t_pass<T><<<(unsigned)lor_ceil_div(m, 256), 256, 0, c->stream>>>(t1, c->dim == 3 ? t2 : rc, V0, g0.N[1], g0.N[2], 1,
-                                                                          p, V1, w);
+                                                                          p, V1, w, c->conv_flag);
     c->launches += 2;
     if (c->dim == 3) {
       m = (long long)V2 * V1 * V0;
-      k_p0t_pass<T><<<(unsigned)lor_ceil_div(m, 256), 256, 0, c->stream>>>(t2, rc, V0, V1, g0.N[2], 2, p, V2, w);
+      k_p0t_pass<T><<<(unsigned)lor_ceil_div(m, 256), 256, 0, c->stream>>>(t2, rc, V0, V1, g0.N[2], 2, p, V2, w, c->conv_flag);
       ++c->launches;
     }
   }
   T* ec = coarse_vcycle<T>(c, 0);
   k_coarse_prolong0<T><<<(unsigned)lor_ceil_div(nvec, 256), 256, 0, c->stream>>>(c->dim, c->p, c->n[0], c->n[1],
-                                                                                   c->n[2], Sel<T>::p0w(c), ec, z);
+                                                                                   c->n[2], Sel<T>::p0w(c), ec, sgn, z,
+                                                                                   c->conv_flag);
   ++c->launches;
   lor_prof_end(c, pk + 4);
   return lor_cuda_check(c, cudaGetLastError(), "coarse space");
+}
+
+// B r with the coarse space additive (Eq. (as)), or hybrid: the coarse correction
+// multiplicative and the patches additive among themselves, in the symmetric form
+//   B_hyb = B_0 + (I - B_0 K_h) B_loc (I - K_h B_0),
+// B_0 = P_0 R_0 P_0^T, B_loc the patch sum, K_h the LOR matrix on the interior nodes
+// (the variant Section 5.1 leaves to future work).  Hybrid steps: z0 = B_0 r,
+// t = r - K_h z0, z1 = B_loc t, z = z0 + z1 - B_0 (K_h z1).
+template <typename T, typename FT>
+lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {
+  if (c->schwarz == 2) return lor_single_apply<T>(c, r, z);
+  if (c->schwarz == 0) {
+    if (patch_part<T, FT>(c, r, z, F)) return LOR_ECUDA;
+    return coarse_part<T>(c, r, z, T(1));
+  }
+  const LevelGrid& g0 = c->lev[0];
+  const long long nvec = g0.ntot;
+  if (!c->d_hyb) return lor_fail(c, LOR_ESTATE, "hybrid Schwarz workspace missing");
+  T* z0 = (T*)c->d_hyb;
+  T* t = z0 + nvec;
+  T* z1 = t + nvec;
+  const T* S = (const T*)Sel<T>::S(c, 0);
+  const unsigned nb = (unsigned)lor_ceil_div(nvec, 256);
+  const int Nz = c->dim == 3 ? g0.N[2] : 1;
+  cudaMemsetAsync(z0, 0, nvec * sizeof(T), c->stream);
+  if (coarse_part<T>(c, r, z0, T(1))) return LOR_ECUDA;
+  k_kh_apply<T><<<nb, 256, 0, c->stream>>>(c->dim, g0.N[0], g0.N[1], Nz, S, z0, r, t);
+  ++c->launches;
+  if (patch_part<T, FT>(c, t, z1, F)) return LOR_ECUDA;
+  k_kh_apply<T><<<nb, 256, 0, c->stream>>>(c->dim, g0.N[0], g0.N[1], Nz, S, z1, nullptr, t);
+  k_add2<T><<<nb, 256, 0, c->stream>>>(z0, z1, z, nvec);
+  c->launches += 2;
+  return coarse_part<T>(c, t, z, T(-1));
 }
 
 // Self-test of the bounded waits: one warp waits on an mbarrier at which nothing
@@ -1372,6 +1447,21 @@ __global__ void k_wait_selftest(int polls, int* status) {
 }
 
 }  // namespace
+
+template <typename T>
+T* lor_coarse_rhs(lor_ctx* c) {
+  return Sel<T>::cw(c, 0, 0);
+}
+
+template <typename T>
+T* lor_coarse_solve(lor_ctx* c) {
+  return coarse_vcycle<T>(c, 0);
+}
+
+template double* lor_coarse_rhs<double>(lor_ctx*);
+template float* lor_coarse_rhs<float>(lor_ctx*);
+template double* lor_coarse_solve<double>(lor_ctx*);
+template float* lor_coarse_solve<float>(lor_ctx*);
 
 lor_status lor_launch_wait_selftest(lor_ctx* c, int polls) {
   k_wait_selftest<<<1, 32, 0, c->stream>>>(polls, c->d_status);

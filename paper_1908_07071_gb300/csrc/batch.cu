@@ -101,10 +101,13 @@ __global__ void k_b_setconv(double* scal, double rtol) {
   scal[B_FLAG] = 0.0;
 }
 
+// Every kernel of the captured iteration skips its vector work once the solve has
+// converged (scal[B_CONV] != 0, set at the end of the update that reached rtol);
+// the reductions still finish, with zero sums, so the scalars stay frozen.
 __global__ void __launch_bounds__(256) k_b_dot(const double* a, const double* b, long long n, double* part,
                                                unsigned* count, double* scal, int op) {
   double s = 0;
-  GRID_STRIDE(i, n) s += a[i] * b[i];
+  if (scal[B_CONV] == 0.0) GRID_STRIDE(i, n) s += a[i] * b[i];
   finish2(s, 0.0, part, count, scal, op);
 }
 
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(256) k_b_update(double* x, double* r, const do
                                                   long long n, double* part, unsigned* count, double* scal) {
   const double al = scal[B_ALPHA];
   double s = 0;
-  GRID_STRIDE(i, n) {
+  if (scal[B_CONV] == 0.0) GRID_STRIDE(i, n) {
     x[i] += al * p[i];
     const double ri = r[i] - al * Ap[i];
     r[i] = ri;
@@ -121,7 +124,8 @@ __global__ void __launch_bounds__(256) k_b_update(double* x, double* r, const do
   finish2(s, 0.0, part, count, scal, F_UPDATE);
 }
 
-__global__ void k_b_down(float* d, const double* s, long long n) {
+__global__ void k_b_down(float* d, const double* s, long long n, const double* scal) {
+  if (scal && scal[B_CONV] != 0.0) return;
   GRID_STRIDE(i, n) d[i] = (float)s[i];
 }
 
@@ -129,7 +133,7 @@ __global__ void k_b_down(float* d, const double* s, long long n) {
 __global__ void __launch_bounds__(256) k_b_up_dots(double* z, const float* z32, const double* r, long long n,
                                                    double* part, unsigned* count, double* scal, int op) {
   double a = 0, b = 0;
-  GRID_STRIDE(i, n) {
+  if (scal[B_CONV] == 0.0) GRID_STRIDE(i, n) {
     const double zn = (double)z32[i];
     a += r[i] * zn;
     b += r[i] * z[i];
@@ -139,6 +143,7 @@ __global__ void __launch_bounds__(256) k_b_up_dots(double* z, const float* z32, 
 }
 
 __global__ void k_b_xpay(double* p, const double* z, long long n, const double* scal, int copy) {
+  if (!copy && scal[B_CONV] != 0.0) return;
   const double be = copy ? 0.0 : scal[B_BETA];
   GRID_STRIDE(i, n) p[i] = z[i] + be * p[i];
 }
@@ -192,16 +197,16 @@ static lor_status enqueue_iteration(lor_ctx* c, double* x, cudaStream_t st) {
   double *r = c->d_v64[0], *z = c->d_v64[1], *p = c->d_v64[2], *Ap = c->d_v64[3];
   float *r32 = c->d_v32[1], *z32 = c->d_v32[2];
   double* sc = scal_of(c);
+  c->conv_flag = sc + B_CONV;   // a converged solve's operator kernels return at once
   lor_status s = lor_opA64(c, p, Ap);
   if (!s) {
     k_b_dot<<<rblocks(n), kRT, 0, st>>>(p, Ap, n, c->d_part, c->d_count, sc, F_ALPHA);
     k_b_update<<<rblocks(n), kRT, 0, st>>>(x, r, p, Ap, n, c->d_part, c->d_count, sc);
-    k_b_down<<<rblocks(n), kRT, 0, st>>>(r32, r, n);
+    k_b_down<<<rblocks(n), kRT, 0, st>>>(r32, r, n, sc);
     c->launches += 3;
-    c->conv_flag = sc + B_CONV;
     s = lor_opP32(c, r32, z32);
-    c->conv_flag = nullptr;
   }
+  c->conv_flag = nullptr;
   if (!s) {
     k_b_up_dots<<<rblocks(n), kRT, 0, st>>>(z, z32, r, n, c->d_part, c->d_count, sc, F_BETA);
     k_b_xpay<<<rblocks(n), kRT, 0, st>>>(p, z, n, sc, 0);
@@ -298,7 +303,7 @@ lor_status lor_batch_solve(lor_batch* b, const double* const* d_b, double* const
     cudaMemsetAsync(sc, 0, 16 * 8, b->main);
     k_b_init<<<rblocks(nv), kRT, 0, b->main>>>(d_x[s], r, d_b[s], bmask(c), nv, c->d_part, c->d_count, sc);
     k_b_setconv<<<1, 1, 0, b->main>>>(sc, c->opt.rtol);
-    k_b_down<<<rblocks(nv), kRT, 0, b->main>>>(r32, r, nv);
+    k_b_down<<<rblocks(nv), kRT, 0, b->main>>>(r32, r, nv, nullptr);
     lor_status st = lor_opP32(c, r32, z32);
     cudaMemsetAsync(z, 0, nv * 8, b->main);
     k_b_up_dots<<<rblocks(nv), kRT, 0, b->main>>>(z, z32, r, nv, c->d_part, c->d_count, sc, F_RZ);

@@ -395,6 +395,24 @@ lor_status lor_set_node_coordinates(lor_ctx* c, const double* X) {
   return LOR_OK;
 }
 
+lor_status lor_set_schwarz(lor_ctx* c, int mode) {
+  if (!c || !c->setup_done) return LOR_ESTATE;
+  if (mode < 0 || mode > 2)
+    return lor_fail(c, LOR_EINVAL, "lor_set_schwarz: 0 (additive), 1 (hybrid) or 2 (single patch)");
+  if (mode != 0 && c->learned_on) return lor_fail(c, LOR_EINVAL, "learned correction needs the additive form");
+  if (mode == 2) {
+    const lor_status st = lor_single_prepare(c);
+    if (st) return st;
+  }
+  if (mode == 1 && !c->d_hyb) {
+    c->d_hyb = lor_alloc(c, (size_t)3 * c->lev[0].ntot * sizeof(double));
+    if (!c->d_hyb) return lor_fail(c, LOR_ENOMEM, "alloc hybrid Schwarz work vectors");
+  }
+  c->schwarz = mode;
+  c->pcg_state_ok = false;
+  return LOR_OK;
+}
+
 lor_status lor_set_weighting(lor_ctx* c, int weighting) {
   if (!c) return LOR_EINVAL;
   if (weighting < 0 || weighting > 2) return lor_fail(c, LOR_EINVAL, "lor_set_weighting: 0, 1 or 2");
@@ -432,6 +450,7 @@ void lor_destroy(lor_ctx* c) {
   else cudaDeviceSynchronize();
   if (c->dg_state) lor_free_dg(c);
   if (c->learned) lor_free_learned(c);
+  if (c->single) lor_free_single(c);
   for (void* p : c->allocs) cudaFree(p);
   for (int k = 0; k < 6; ++k)
     for (cudaEvent_t e : c->ev[k]) cudaEventDestroy(e);

@@ -660,6 +660,7 @@ lor_status lor_learned_enable(lor_ctx* c, int on) {
   if (!c || !c->setup_done) return LOR_EINVAL;
   // the correction is trained on the residuals of the unit-weight patch cycle
   if (on && c->opt.weighting) return lor_fail(c, LOR_EINVAL, "learned correction needs unit patch weights");
+  if (on && c->schwarz) return lor_fail(c, LOR_EINVAL, "learned correction needs the additive form");
   lor_status st = learned_init(c);
   if (st) return st;
   c->learned_on = on != 0 && LS(c)->nint > 0;

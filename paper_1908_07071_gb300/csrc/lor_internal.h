@@ -152,6 +152,10 @@ struct lor_ctx {
   // per-patch outputs of the patch kernel (J slices of level-0 box rows, sized for
   // float64), summed node by node into z by a gather kernel
   void* d_zp = nullptr;
+  // coarse-space combination of apply_P: 0 additive (Eq. (as)), 1 hybrid (coarse
+  // multiplicative); the hybrid form's three level-0 work vectors (float64-sized)
+  int schwarz = 0;
+  void* d_hyb = nullptr;
   int maxfront = 0;           // largest padded front over all levels/shapes (records)
   int maxchunk[3] = {0, 0, 0};   // largest chunk (records) for 2-, 4-, 8-byte factors
   int* d_status = nullptr;    // device error word
@@ -206,6 +210,8 @@ struct lor_ctx {
   int tune_ne = 1;             // apply_A tile variant (elements per CTA), set by the autotuner
   const double* conv_flag = nullptr;   // batched solves: patch kernel returns early when *conv_flag != 0
   // learned correction (learned.cu)
+  // single-patch preconditioner B(1) (single.cu), built by lor_set_schwarz(ctx, 2)
+  void* single = nullptr;
   void* learned = nullptr;
   bool learned_on = false;
   float* learned_tout = nullptr;       // level-0 residuals of interior patches after the cycle
@@ -243,6 +249,13 @@ lor_status lor_launch_apply_P_dg32(lor_ctx* c, const float* r, float* z);
 lor_status lor_launch_rhs_dg(lor_ctx* c, double* b, const double* W);
 void lor_free_dg(lor_ctx* c);
 void lor_free_learned(lor_ctx* c);
+void lor_free_single(lor_ctx* c);
+lor_status lor_single_prepare(lor_ctx* c);
+template <typename T> lor_status lor_single_apply(lor_ctx* c, const T* r, T* z);
+// coarse solver R_0: its right-hand side buffer (the full vertex grid) and one solve,
+// returning the buffer that holds the result (apply_p.cu)
+template <typename T> T* lor_coarse_rhs(lor_ctx* c);
+template <typename T> T* lor_coarse_solve(lor_ctx* c);
 lor_status lor_learned_apply(lor_ctx* c, float* z);
 lor_status lor_patch_local32(lor_ctx* c, const int* plist, int nlist, const float* rloc, float* xloc, int vstride);
 // operator / preconditioner of the context's discretization (CG or DG)

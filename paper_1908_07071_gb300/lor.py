@@ -103,6 +103,7 @@ def load():
     lib.lor_selftest_wait.argtypes = [vp, i]
     lib.lor_set_prec.argtypes = [vp, i]
     lib.lor_set_weighting.argtypes = [vp, i]
+    lib.lor_set_schwarz.argtypes = [vp, i]
     lib.lor_coefficient_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.lor_coefficient_points.argtypes = [vp, vp, vp]
     lib.lor_set_coefficient.argtypes = [vp, vp, vp]
@@ -115,7 +116,7 @@ def load():
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
     for name in ("lor_coefficient_sizes", "lor_coefficient_points", "lor_set_coefficient", "lor_set_node_coordinates",
                  "lor_pcg_state_size", "lor_pcg_state_save", "lor_pcg_resume",
-                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_measure_fp64_peak", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
+                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_set_schwarz", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_measure_fp64_peak", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -312,6 +313,10 @@ class Solver:
     def selftest_wait(self, polls=1 << 12):
         """Runs the bounded-wait self-test; returns the library status (LOR_ETIMEOUT expected)."""
         return self.lib.lor_selftest_wait(self.ctx, polls)
+
+    def set_schwarz(self, mode):
+        """0: additive coarse space (Eq. (as)); 1: hybrid, coarse correction multiplicative."""
+        self._check(self.lib.lor_set_schwarz(self.ctx, int(mode)))
 
     def set_weighting(self, weighting):
         """0: unit patch weights (the paper's method); 1: counting-matrix weights;
