@@ -402,7 +402,7 @@ def leg_dg():
 def leg_schwarz(n: int = 12, degrees=(2, 4, 6, 8)):
     """B(1) (the whole domain as one patch) against B(V) (one patch per vertex, additive
     coarse space) and the hybrid form (coarse space multiplicative), the comparison of
-    Section 5.1 / Table 2 on the GPU: 3D CG on a 12^3 perturbed hex mesh, log-normal
+    Section 4.1 / Table 2 on the GPU: 3D CG on a 12^3 perturbed hex mesh, log-normal
     kappa, f=1, FP64 PCG to 1e-8, p in {2,4,6,8}; and DG BR2 (eta 10) at p=4 with the
     three forms inside the DG preconditioner.  Reports iterations, time to tolerance and
     milliseconds per preconditioner apply (CUDA events, 5 applies after a warm-up)."""

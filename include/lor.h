@@ -68,7 +68,7 @@ typedef struct {
   int weighting;    /* patch sum of Eq. (as): 0 = unit weights (the paper's
                        method); 1 = scaled on both sides by D^{-1/2}, D the
                        number of patches containing each node (the counting
-                       matrix Section 5.1 leaves to future work); 2 = patch j
+                       matrix Section 4.1 leaves to future work); 2 = patch j
                        scaled on both sides by sqrt(theta_j), theta_j the Q1
                        function of its vertex in element reference
                        coordinates (a partition of unity over the patches) */
@@ -143,7 +143,7 @@ lor_status lor_apply_A(lor_ctx* ctx, const void* d_x, void* d_y, int prec);
 lor_status lor_apply_P(lor_ctx* ctx, const void* d_r, void* d_z, int prec);
 
 /* Solves A x = b by preconditioned CG from x0 = 0 to ||r|| <= rtol ||b||
- * (Section 5).  LOR_FP64: plain FP64 PCG.  LOR_MIXED: iterative refinement
+ * (Section 4).  LOR_FP64: plain FP64 PCG.  LOR_MIXED: iterative refinement
  * with FP64 residuals b - A x and FP64 corrections; each correction is a PCG
  * solve with FP32 operator and preconditioner and FP64 inner products.
  * d_b, d_x: device float64 L-vectors.  iters: total (inner) iterations;
@@ -179,7 +179,7 @@ lor_status lor_pcg_state_save(lor_ctx* ctx, const double* d_x, void* host, size_
 lor_status lor_pcg_resume(lor_ctx* ctx, const void* host, size_t bytes, const double* d_b, double* d_x, int* iters,
                           double* rel_res);
 
-/* Pointwise coefficients b(x) (Section 5.2, the coefficients b1-b3) in place of
+/* Pointwise coefficients b(x) (Section 4.2, the coefficients b1-b3) in place of
  * the per-element kappa, for CG contexts.  The coefficient is sampled at two
  * point sets, both listed by lor_coefficient_points:
  *   - the (p+1)^d Gauss-Legendre points of every element, where K_p is
@@ -198,7 +198,7 @@ lor_status lor_coefficient_sizes(const lor_ctx* ctx, long long* nq, long long* n
 lor_status lor_coefficient_points(const lor_ctx* ctx, double* xq, double* xh);
 lor_status lor_set_coefficient(lor_ctx* ctx, const double* bq, const double* bh);
 
-/* Curved (isoparametric) elements, as in the curved meshes of Section 5.2, for CG
+/* Curved (isoparametric) elements, as in the curved meshes of Section 4.2, for CG
  * contexts.  X (HOST, copied) gives the physical coordinates of every level-0 GLL
  * node: X[a*ntot + (K*Ny+J)*Nx+I], ntot = Nx*Ny(*Nz), a < dim (the L-vector node
  * order).  K_p then uses the degree-p isoparametric map of each element's nodes
@@ -209,6 +209,40 @@ lor_status lor_set_coefficient(lor_ctx* ctx, const double* bq, const double* bh)
  * coordinate; lor_setup reports a non-positive Jacobian as LOR_EINVAL.
  * lor_rhs then integrates on the isoparametric elements. */
 lor_status lor_set_node_coordinates(lor_ctx* ctx, const double* X);
+
+/* Selects the ILU(0) ordering of every patch level (Section 3.4): 0 =
+ * lexicographic (x fastest; the default), 1 = reverse Cuthill-McKee of the
+ * 3^d-point pattern of the patch box (breadth-first from the node of smallest
+ * (degree, index), neighbours by increasing (degree, index), reversed), 2 =
+ * minimum discarded fill of the patch matrix (the node whose elimination would
+ * discard the smallest 2-norm of fill is ordered next, ties by smallest index;
+ * the kept fill updates the remaining matrix).  Orderings 1 and 2 are computed
+ * on the host during lor_setup together with the ILU(0) factors in that order,
+ * one patch per host thread at a time (MDF costs about 26^2 operations per
+ * remaining neighbour per elimination step, seconds per thousand patches at
+ * p = 4); their sweeps follow the dependency levels of the order, in fronts of
+ * at most 32 rows, with records that hold all 3^d - 1 couplings of a row.  Must
+ * precede lor_setup (LOR_ESTATE after); LOR_EINVAL for other values.  A
+ * non-positive pivot of the ordered factorization makes lor_setup return
+ * LOR_EBREAKDOWN. */
+lor_status lor_set_ordering(lor_ctx* ctx, int ordering);
+
+/* Host-only utility (no context, no CUDA call): the ordering lor_set_ordering
+ * uses, for one box of A x B x C nodes (C = 1 in 2D; at most 2^20 nodes) with the
+ * 3^d-point pattern.  a27: per node (x fastest) its 3^d stencil values in
+ * stencil-offset order ((dz+1)*9 + (dy+1)*3 + (dx+1); zero for neighbours
+ * outside the box), read only for MDF (ordering 2).  perm (A*B*C ints, host):
+ * perm[q] = box index of the q-th node.  LOR_EBREAKDOWN if MDF meets a
+ * non-positive pivot, LOR_EINVAL for bad sizes or ordering. */
+lor_status lor_box_ordering(int dim, int A, int B, int C, int ordering, const double* a27, int* perm);
+
+/* The ILU(0) order of one patch level: perm[q] = box index (x fastest within the
+ * patch box) of the q-th row, for level 0 <= level < levels - 1 (the vertex level
+ * is solved exactly) and patch 0 <= patch < npatch (vertex (i,j,k) is patch
+ * (k*(ny+1)+j)*(nx+1)+i).  *count = rows of the box; perm may be NULL to query
+ * it, else cap >= *count (LOR_EINVAL otherwise).  Host memory, filled from the
+ * context's host copy; the identity for the lexicographic ordering. */
+lor_status lor_patch_ordering(lor_ctx* ctx, int level, long long patch, int* perm, int cap, int* count);
 
 /* Switches the patch-sum weighting of lor_options.weighting (0 unit weights,
  * 1 counting matrix, 2 partition of unity) for later calls; the weights are evaluated inside the
@@ -221,13 +255,13 @@ lor_status lor_set_weighting(lor_ctx* ctx, int weighting);
 /* Selects how apply_P combines the coarse space with the patches: 0 = additive,
  * B = P_0 R_0 P_0^T + sum_j R_j^T V_j R_j (Eq. (as), the default); 1 = hybrid,
  * the coarse correction multiplicative and the patches additive among
- * themselves (the variant Section 5.1 leaves to future work), in the symmetric
+ * themselves (the variant Section 4.1 leaves to future work), in the symmetric
  * form B_hyb = B_0 + (I - B_0 K_h) B_loc (I - K_h B_0), B_0 = P_0 R_0 P_0^T,
  * B_loc the patch sum and K_h the LOR matrix on the interior nodes.  B_hyb is
  * B_0 plus a congruence of B_loc, so it is symmetric positive definite and PCG
  * applies.  An apply in hybrid form costs the additive one plus a second coarse
  * V-cycle and two K_h stencil products.  2 = B(1), the whole domain as one patch
- * (Section 5.1, Table 2): one V(1,1) cycle of the element-structured hierarchy
+ * (Section 4.1, Table 2): one V(1,1) cycle of the element-structured hierarchy
  * on the global level grids, one lexicographic ILU(0) smoothing before and one
  * after the coarse-level correction on every level above the vertex level, and
  * the coarse solver R_0 on the vertex level.  Its ILU(0) factors are computed

@@ -17,8 +17,8 @@ Modules (each function cites the passage of the paper it follows):
   learned -- FP64 reference of the per-patch convolutional smoother and its
              gradients (the learned form)
   ordering     -- MDF and RCM orderings for ILU(0) (Section 3.4)
-  single_patch -- B(1): the whole domain as one patch (Section 5.1)
-  unstructured -- vertex patches on unstructured quadrilateral meshes (Section 5.2)
+  single_patch -- B(1): the whole domain as one patch (Section 4.1)
+  unstructured -- vertex patches on unstructured quadrilateral meshes (Section 4.2)
 
 Parity status: every function is pinned by a `-m "not gpu"` test against
 closed forms, textbook special cases or invariants, except where a module

@@ -61,7 +61,7 @@ def element_stiffness(corners, kappa, p, q=None, geom=None):
     """Dense K_e[a,b] = sum_q w_q det J_q kappa grad phi_a . grad phi_b (det J > 0, `oriented_det`).
 
     kappa: the element's constant, or a callable b(X) of the physical points X (Q, d)
-    (the variable coefficients of Section 5.2), evaluated at the quadrature points.
+    (the variable coefficients of Section 4.2), evaluated at the quadrature points.
     geom: optional callable xi -> (X, J) replacing the multilinear map of corners
     (curved elements, `Mesh.element_map`)."""
     dim = corners.shape[1]
@@ -116,7 +116,7 @@ def boundary_mask(N):
 def assemble_stiffness(mesh: Mesh, p: int, coef=None):
     """Assembled K_p over all grid nodes (no Dirichlet elimination), CSR.
 
-    coef: optional callable b(X) replacing the per-element kappa (Section 5.2)."""
+    coef: optional callable b(X) replacing the per-element kappa (Section 4.2)."""
     N = node_shape(mesh.n, p)
     ntot = int(np.prod(N))
     rows, cols, vals = [], [], []

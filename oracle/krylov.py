@@ -1,6 +1,6 @@
 """Preconditioned and flexible conjugate gradients (oracle; FP64).
 
-Section 3.2 uses the preconditioner inside CG; Section 5 stops once the
+Section 3.2 uses the preconditioner inside CG; Section 4 stops once the
 residual is reduced by a fixed factor.  Reading: x0 = 0 and the stopping test
 ||r_k||_2 <= rtol ||b||_2 on the true (unpreconditioned) residual 2-norm.
 Flexible CG (Notay, SIAM J. Sci. Comput. 22(4), 2000) uses the

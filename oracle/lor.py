@@ -20,7 +20,7 @@ Follows Section 3 step by step, with dense/sparse library primitives only:
   Reading (R_0): the paper uses one BoomerAMG V-cycle, a third-party system;
   here R_0 is one V-cycle on the coarse vertex grid: keep-even-plus-last 2x
   coarsening, index-space linear interpolation, Galerkin operators, two sweeps of
-  l1-scaled Jacobi before and after (the relaxation BoomerAMG offers, Section 5.4),
+  l1-scaled Jacobi before and after (the relaxation BoomerAMG offers, Section 4.4),
   and an exact dense solve once at most 343 unknowns remain.
 """
 from __future__ import annotations
@@ -45,7 +45,7 @@ def q1_stiffness_batch(corners, kappa):
     """Q1 element stiffness for a batch of cells: corners (C, 2^d, d) -> (C, 2^d, 2^d).
 
     kappa: (C,) constants per cell, or a callable b(X) of physical points (C, d)
-    evaluated at each cell's Gauss points (Section 5.2 coefficients)."""
+    evaluated at each cell's Gauss points (Section 4.2 coefficients)."""
     C, nc, d = corners.shape
     g = 0.5 - 0.5 / np.sqrt(3.0)
     g1 = np.array([g, 1.0 - g])
@@ -192,7 +192,7 @@ def patch_range_1d(v: int, nel: int, m: int, lo_k: int = 1, hi_k: int = 1):
 def isotropic_overlap_spans(mesh: Mesh, ratio: float = 0.5):
     """Element spans of vertex patches enlarged so that their overlap stays isotropic.
 
-    Section 5.5 extends the patches that contain high-aspect-ratio elements so that the
+    Section 4.5 extends the patches that contain high-aspect-ratio elements so that the
     overlap no longer shrinks with the aspect ratio (the partition-of-unity argument
     behind the lemma on the local decomposition in Section 3.2 needs overlap of the
     size of the elements, not of their thin side).  The paper does not state the rule;
@@ -264,13 +264,13 @@ class LORPreconditioner:
                  patch_spans=None):
         """patch_subset: vertex multi-indices whose patches are built (default all);
         patch_spans: {vertex: [(lo_k, hi_k) per axis]} element spans of enlarged patches
-        (`isotropic_overlap_spans`, Section 5.5); vertices not listed keep the vertex patch;
+        (`isotropic_overlap_spans`, Section 4.5); vertices not listed keep the vertex patch;
         coarse=False skips the coarse space (for checks of the patch part alone);
         ordering: ILU(0) ordering of every patch level, "lex" (patch-lexicographic),
         "mdf" or "rcm" (Section 3.4, `oracle.ordering`);
         weighting: "none" (unit weights, Eq. (as)), "count": the patch sum scaled on
         both sides by D^{-1/2}, D = number of patches containing each node (the counting
-        matrix Section 5.1 names as future work), or "pou": each patch scaled on both
+        matrix Section 4.1 names as future work), or "pou": each patch scaled on both
         sides by W_j = sqrt(theta_j), theta_j the Q1 vertex function of its vertex in
         the element reference coordinates at the level-0 nodes (`pou_weights`)."""
         self.ordering = ordering
@@ -541,7 +541,7 @@ class LORPreconditioner:
 
     def apply_hybrid(self, r):
         """Hybrid Schwarz: the coarse correction applied multiplicatively, the patches
-        additively among themselves (the variant Section 5.1 names as future work after
+        additively among themselves (the variant Section 4.1 names as future work after
         Lottes and Fischer), in the symmetric form
             B_hyb = B_0 + (I - B_0 K_h) B_loc (I - K_h B_0),
         B_loc = sum_j R_j^T V_j R_j, B_0 = P_0 R_0 P_0^T, K_h on the interior nodes.

@@ -5,7 +5,7 @@ the map is the multilinear (bilinear/trilinear) interpolation of the element's
 2^d vertices (the reading used for all perturbed meshes).  Corner c of an
 element has offsets (c & 1, (c >> 1) & 1, (c >> 2) & 1) along (x, y, z).
 
-Curved elements (the curved meshes of Section 5.2): with a smooth map ``warp``
+Curved elements (the curved meshes of Section 4.2): with a smooth map ``warp``
 the element map becomes isoparametric, the degree-p Lagrange interpolant at the
 (p+1)^d GLL points of warp(multilinear(xi)), so the high-order nodes lie on the
 curved geometry and the map is continuous across shared faces.

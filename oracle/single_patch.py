@@ -1,6 +1,6 @@
 """B(1): the whole domain as one additive-Schwarz patch.  TEST INFRASTRUCTURE ONLY.
 
-Section 5.1 first studies the local multigrid solver with a single patch for the
+Section 4.1 first studies the local multigrid solver with a single patch for the
 entire domain: the high-order system is preconditioned by one element-structured
 V-cycle (Section 3.3) on the low-order refined system K_h, with one ordered ILU(0)
 sweep (forward and backward) as pre- and post-smoother at every level, coarsening

@@ -1,7 +1,7 @@
 """Q_p, LOR and vertex-patch additive Schwarz on unstructured quadrilateral meshes
 (oracle; FP64; 2D).  TEST INFRASTRUCTURE ONLY.
 
-Section 5.2 runs the method on unstructured quadrilateral meshes: the patch of a
+Section 4.2 runs the method on unstructured quadrilateral meshes: the patch of a
 vertex is the union of the elements around it (any number of them), each element
 is refined at its own GLL points, and the element-structured hierarchy coarsens
 every element separately (Section 3.3).  This module restates the pieces for

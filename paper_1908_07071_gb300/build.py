@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblor.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "setup.cu", "apply_a.cu", "apply_p.cu", "krylov.cu", "dg.cu", "batch.cu", "learned.cu", "single.cu", "host_basis.cpp"]
+SOURCES = ["capi.cu", "setup.cu", "apply_a.cu", "apply_p.cu", "krylov.cu", "dg.cu", "batch.cu", "learned.cu", "single.cu", "host_basis.cpp",
+           "orderings.cpp"]
 
 
 def _nvcc():
@@ -29,8 +30,9 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "--expt-relaxed-constexpr", "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cpp"):
-        cmd = [_nvcc(), "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-x", "cu", *ARCH,
-               "-c", os.path.join(CSRC, src), "-o", obj]
+        # host code; no floating-point contraction, so products and sums round one by one
+        cmd = [_nvcc(), "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-x", "cu",
+               *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose_ptxas and src.endswith(".cu"):
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)

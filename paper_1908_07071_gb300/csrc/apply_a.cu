@@ -1,4 +1,4 @@
-// Matrix-free sum-factorized Q_p stiffness apply (Section 2; Section 3.5 Table 1:
+// Matrix-free sum-factorized Q_p stiffness apply (Section 2; Section 3.6 Table 1:
 // O(p^{d+1}) work per element).  y = sum_e E_e^T B^T G_e B E_e x with
 //   B      : interpolation from the (p+1) GLL nodes to the q = p+1 Gauss points,
 //            followed by the collocated Gauss-point derivative Dq (so that

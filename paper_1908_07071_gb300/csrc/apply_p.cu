@@ -58,6 +58,7 @@ struct PatchArgs {
   const BoxShape* shapes;       // [L][8]
   const int* fpad;
   const int* chunk;
+  const GenSched* gsched;       // ordered patch levels: per-patch schedules [L][J] (else null)
   const long long* facoff;      // [L][J] record offsets
   const void* F;
   const void* r;
@@ -182,21 +183,31 @@ __device__ __forceinline__ int rec_index(const FT* rec) {
 // scaled by 1/u_ii) couplings.  Rows of one front never couple, so every load
 // of the front is issued before its first store; the row indices of the next
 // front (records nrec[u], read only if nxt) are loaded in the same round.
-template <int DIM, bool BACK, typename T, typename FT, int NR>
+// Value of slot o of a record in shared memory (ordered records are read in place).
+template <typename T, typename FT>
+__device__ __forceinline__ T rec_val(const FT* rec, int o) {
+  if constexpr (sizeof(FT) == 2) return (T)__bfloat162float(rec[o]);
+  else return (T)rec[o];
+}
+
+template <int DIM, bool BACK, typename T, typename FT, int NR, bool GEN>
 __device__ __forceinline__ void sweep_front(const FT* const* rec, int* li, const FT* const* nrec, bool nxt, int A,
                                             int AB, T* t) {
   constexpr int NS = DIM == 3 ? 27 : 9;
   constexpr int C = NS / 2;
-  constexpr int R = lor_rec(DIM);
-  RecRegs<R, FT> rr[NR];
-  T tv[NR][C + 1];
+  // lexicographic records: the 13 (4) lower or upper couplings; ordered records:
+  // all 26 (8) couplings, zero where the neighbour is on the other side of the row
+  constexpr int NC = GEN ? NS - 1 : C;
+  constexpr int R = GEN ? lor_rec_gen(DIM) : lor_rec(DIM);
+  RecRegs<GEN ? 4 : R, FT> rr[NR];
+  T tv[NR][NC + 1];
 #pragma unroll
   for (int u = 0; u < NR; ++u) {
-    rr[u].load(rec[u]);
-    tv[u][C] = t[li[u]];
+    if constexpr (!GEN) rr[u].load(rec[u]);
+    tv[u][NC] = t[li[u]];
 #pragma unroll
-    for (int o = 0; o < C; ++o) {
-      const int so = BACK ? C + 1 + o : o;                 // stencil offset index
+    for (int o = 0; o < NC; ++o) {
+      const int so = GEN ? (o < C ? o : o + 1) : (BACK ? C + 1 + o : o);   // stencil offset index
       const int dx = so % 3 - 1, dy = (so / 3) % 3 - 1, dz = DIM == 3 ? so / 9 - 1 : 0;
       tv[u][o] = t[li[u] + dz * AB + dy * A + dx];
     }
@@ -206,13 +217,19 @@ __device__ __forceinline__ void sweep_front(const FT* const* rec, int* li, const
   for (int u = 0; u < NR; ++u) ln[u] = nxt ? rec_index<R, FT>(nrec[u]) : 0;
 #pragma unroll
   for (int u = 0; u < NR; ++u) {
-    T s0 = tv[u][C], s1 = T(0);
+    T s0 = tv[u][NC], s1 = T(0);
 #pragma unroll
-    for (int o = 0; o < C; ++o) {
-      const T v = rr[u].template val<T>(o) * tv[u][o];
+    for (int o = 0; o < NC; ++o) {
+      T w;
+      if constexpr (GEN) w = rec_val<T, FT>(rec[u], o);
+      else w = rr[u].template val<T>(o);
+      const T v = w * tv[u][o];
       if (o & 1) s1 -= v; else s0 -= v;
     }
-    t[li[u]] = BACK ? (s0 + s1) * rr[u].template val<T>(R - 2) : s0 + s1;
+    T dinv;
+    if constexpr (GEN) dinv = rec_val<T, FT>(rec[u], R - 2);
+    else dinv = rr[u].template val<T>(R - 2);
+    t[li[u]] = BACK ? (s0 + s1) * dinv : s0 + s1;
   }
 #pragma unroll
   for (int u = 0; u < NR; ++u) li[u] = ln[u];
@@ -230,11 +247,11 @@ __device__ __forceinline__ void sweep_front(const FT* const* rec, int* li, const
 // separates fronts.  t has a zero guard band, so neighbour reads need no
 // clamping (multipliers of out-of-box neighbours are stored as 0).  BACK
 // selects the backward sweep (U part, fronts in reverse, scaled by 1/u_ii).
-template <int DIM, bool BACK, typename T, typename FT, int NBUF>
+template <int DIM, bool BACK, typename T, typename FT, int NBUF, bool GEN>
 __device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __restrict__ fp,
                                       const int* __restrict__ ch, int nc, int A, int AB, int dummy,
                                       const FT* zrec, T* t, Ring<FT, NBUF>& rg) {
-  constexpr int R = lor_rec(DIM);
+  constexpr int R = GEN ? lor_rec_gen(DIM) : lor_rec(DIM);
   const int lane = threadIdx.x & 31;
   if (lane == 0) {
     for (int c = 0; c < NBUF - 1 && c < nc; ++c) {
@@ -285,9 +302,9 @@ __device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __
       const FT* nrec[2] = {lane < en - bn ? blk + (bn + lane) * R : zrec,
                            lane + 32 < en - bn ? blk + (bn + lane + 32) * R : zrec};
       if (n > 32) {   // warp-uniform
-        sweep_front<DIM, BACK, T, FT, 2>(rec, li, nrec, more, A, AB, t);
+        sweep_front<DIM, BACK, T, FT, 2, GEN>(rec, li, nrec, more, A, AB, t);
       } else {
-        sweep_front<DIM, BACK, T, FT, 1>(rec, li, nrec, more, A, AB, t);
+        sweep_front<DIM, BACK, T, FT, 1, GEN>(rec, li, nrec, more, A, AB, t);
         li[1] = more ? rec_index<R, FT>(nrec[1]) : dummy;
       }
       if (more) {
@@ -307,15 +324,16 @@ __device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __
 template <typename FT>
 constexpr int elem_class() { return sizeof(FT) == 2 ? 0 : (sizeof(FT) == 4 ? 1 : 2); }
 
-template <int DIM, typename T, typename FT, int NBUF>
+template <int DIM, typename T, typename FT, int NBUF, bool GEN>
 __device__ __forceinline__ bool ilu_solve(const BoxShape& bs, const int* fp, const int* ch, const FT* FL, T* t,
                                           Ring<FT, NBUF>& rg, const FT* zrec) {
   constexpr int ES = elem_class<FT>();
+  constexpr int R = GEN ? lor_rec_gen(DIM) : lor_rec(DIM);
   const int A = bs.dims[0], AB = bs.dims[0] * bs.dims[1];
-  bool ok = sweep<DIM, false, T, FT, NBUF>(FL, fp, ch, bs.nchunk[ES], A, AB, bs.rows, zrec, t, rg);
+  bool ok = sweep<DIM, false, T, FT, NBUF, GEN>(FL, fp, ch, bs.nchunk[ES], A, AB, bs.rows, zrec, t, rg);
   if (ok)
-    ok = sweep<DIM, true, T, FT, NBUF>(FL + (long long)bs.rpad * lor_rec(DIM), fp, ch, bs.nchunk[ES], A, AB, bs.rows,
-                                        zrec, t, rg);
+    ok = sweep<DIM, true, T, FT, NBUF, GEN>(FL + (long long)bs.rpad * R, fp, ch, bs.nchunk[ES], A, AB, bs.rows, zrec,
+                                             t, rg);
   __syncwarp();
   return ok;
 }
@@ -546,7 +564,11 @@ constexpr int kRowsInFlight = 4;
 // Per-warp shared-memory block (byte offsets): mbarriers, a zero factor record,
 // level metadata of the current box shape, the bulk-copy ring, the wavefront
 // tables of the shape, and the vectors.
-constexpr int kWarpBars = 0, kWarpZrec = 32, kWarpMeta = 160, kWarpShape = 288, kWarpRing = 768;
+// The zero record spans the widest record (32 doubles of an ordered FP64 level).
+constexpr int kWarpBars = 0, kWarpZrec = 32, kWarpMeta = 288, kWarpShape = 352, kWarpRing = 768;
+static_assert(kWarpMeta - kWarpZrec >= 32 * 8, "zero record smaller than an ordered FP64 record");
+static_assert(kWarpShape - kWarpMeta >= 2 * LOR_MAXLEV * 4, "level metadata does not fit");
+static_assert(kWarpRing - kWarpShape >= LOR_MAXLEV * (int)sizeof(BoxShape), "box shapes do not fit");
 
 // The patch kernel.  Each warp runs whole V-cycles for its own patches (one
 // after another, no block barriers):
@@ -557,10 +579,10 @@ constexpr int kWarpBars = 0, kWarpZrec = 32, kWarpMeta = 160, kWarpShape = 288, 
 // ILU, x <- t, t <- r - A x, r_{l+1} <- R t; the vertex level is solved exactly
 // (<= 1 unknown), a truncated box (boundary patch whose vertex level is empty)
 // is smoothed by ILU twice instead; up: x += P x_{l+1}, t <- r - A x, ILU, x += t.
-template <int DIM, typename T, typename FT, int NBUF>
+template <int DIM, typename T, typename FT, int NBUF, bool GEN>
 __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
   constexpr int ES = elem_class<FT>();
-  constexpr int R = lor_rec(DIM);
+  constexpr int R = GEN ? lor_rec_gen(DIM) : lor_rec(DIM);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (a.conv && *a.conv != 0.0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -598,7 +620,8 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
   BoxShape* bsh = (BoxShape*)(wb + kWarpShape);
   int* ip = (int*)(wb + kWarpRing + (size_t)NBUF * a.slot_bytes);
   T* vec = (T*)(ip + a.tab_ints);
-  if (lane < 32) ((unsigned*)(wb + kWarpZrec))[lane] = 0u;
+  ((unsigned*)(wb + kWarpZrec))[lane] = 0u;
+  ((unsigned*)(wb + kWarpZrec))[lane + 32] = 0u;
   if (lane == 0) {
     for (int s = 0; s < NBUF; ++s) mbar_init(rg.bar + s, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -622,13 +645,20 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       type[t] = (v[t] == 0 || v[t] == a.n[t]) ? 1 : 0;
       sh |= type[t] << t;
     }
-    if (sh != cur_sh) {
-      // wavefront tables of every level of this shape
+    if (GEN || sh != cur_sh) {
+      // wavefront tables of every level of this shape (ordered levels: of this patch)
       __syncwarp();
       if (lane == 0) {
         int ioff = 0;
         for (int l = 0; l < a.L; ++l) {
           bsh[l] = a.shapes[l * 8 + sh];
+          if (GEN) {
+            const GenSched g = a.gsched[(long long)l * a.J + j];
+            bsh[l].nfront = g.nfront;
+            bsh[l].rpad = g.rpad;
+            bsh[l].front_off = g.front_off;
+            for (int e = 0; e < 3; ++e) { bsh[l].nchunk[e] = g.nchunk[e]; bsh[l].chunk_off[e] = g.chunk_off[e]; }
+          }
           meta[l] = ioff; ioff += bsh[l].nfront + 1;
           meta[LOR_MAXLEV + l] = ioff; ioff += bsh[l].nchunk[ES] + 1;
         }
@@ -719,7 +749,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       }
       __syncwarp();
       const FT* FL0 = F + a.facoff[j] * R;
-      ok = ilu_solve<DIM, T, FT, NBUF>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
+      ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
       T* prev = vec + (b0.A + 1);                 // guarded plane buffers
       T* tmp = prev + AB0 + (b0.A + 1);
       if (ok) resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, xslot, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
@@ -734,7 +764,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           const FT* FL = F + a.facoff[(long long)l * a.J + j] * R;
           for (int q = lane; q < b.rows; q += 32) t[q] = r[q];
           __syncwarp();
-          ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+          ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
           if (!ok) break;
           for (int q = lane; q < b.rows; q += 32) x[q] = t[q];
           __syncwarp();
@@ -760,12 +790,12 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
             const FT* FL = F + a.facoff[(long long)l * a.J + j] * R;
             for (int q = lane; q < b.rows; q += 32) t[q] = r[q];
             __syncwarp();
-            ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+            ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
             if (ok) {
               for (int q = lane; q < b.rows; q += 32) x[q] = t[q];
               __syncwarp();
               resid_level<DIM, T>(b, lv, r, x, t);
-              ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+              ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
             }
             if (ok) {
               for (int q = lane; q < b.rows; q += 32) x[q] += t[q];
@@ -785,7 +815,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
                                           xc, it.i, it.j, it.k);
           __syncwarp();
           resid_level<DIM, T>(b, a.lv[l], r, x, t);
-          ok = ilu_solve<DIM, T, FT, NBUF>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+          ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
           if (!ok) break;
           for (int q = lane; q < b.rows; q += 32) x[q] += t[q];
           __syncwarp();
@@ -828,7 +858,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, nullptr, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
         }
       }
-      if (ok) ok = ilu_solve<DIM, T, FT, NBUF>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
+      if (ok) ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
     }
     if (!ok) {
       // a bulk copy did not arrive in time: report, drain what is still in flight, leave
@@ -1231,6 +1261,10 @@ WarpLayout warp_layout(const lor_ctx* c) {
     for (int l = 0; l < c->L; ++l) t += c->shapes[l * 8 + s].nfront + 1 + c->shapes[l * 8 + s].nchunk[es] + 1;
     tab = std::max(tab, t);
   }
+  if (c->ordering) {   // ordered records and per-patch schedules
+    w.slot_bytes = std::max(c->gen_maxchunk[es], 1) * lor_rec_gen(c->dim) * (int)sizeof(FT);
+    tab = std::max(tab, c->gen_tab_ints);
+  }
   w.tab_ints = (tab + 3) / 4 * 4;
   const BoxShape& b0 = c->shapes[0];
   const int A = b0.dims[0], B = b0.dims[1];
@@ -1271,6 +1305,8 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
   }
   a.shapes = lor_dev_shapes(c);
   a.fpad = c->d_fpad; a.chunk = c->d_chunk;
+  a.gsched = nullptr;
+  if (c->ordering) { a.fpad = c->d_gfpad; a.chunk = c->d_gchunk; a.gsched = c->d_gsched; }
   a.facoff = c->d_facoff;
   a.F = F; a.r = nullptr;
   a.zp = c->d_zp;
@@ -1308,15 +1344,10 @@ bool patch_launch_shape(const lor_ctx* c, int* nw, int* grid, size_t* smem) {
   *smem = (size_t)w.xf_bytes + (size_t)*nw * w.warp_bytes;
   constexpr int NB = ring_depth<FT>();
   int per_sm = 0;
-  if (c->dim == 3) {
-    auto kern = k_patch_warp<3, T, FT, NB>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * *nw, *smem);
-  } else {
-    auto kern = k_patch_warp<2, T, FT, NB>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * *nw, *smem);
-  }
+  auto kern = c->dim == 3 ? (c->ordering ? k_patch_warp<3, T, FT, NB, true> : k_patch_warp<3, T, FT, NB, false>)
+                          : (c->ordering ? k_patch_warp<2, T, FT, NB, true> : k_patch_warp<2, T, FT, NB, false>);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * *nw, *smem);
   *grid = std::max(per_sm, 1) * nsm;
   return true;
 }
@@ -1333,8 +1364,13 @@ lor_status launch_patch_kernel(lor_ctx* c, PatchArgs& a) {
   if ((long long)grid * nw * a.x0_stride * (long long)sizeof(T) > c->xs_bytes)
     return lor_fail(c, LOR_ESTATE, "patch iterate slots too small");
   constexpr int NB = ring_depth<FT>();
-  if (c->dim == 3) k_patch_warp<3, T, FT, NB><<<grid, 32 * nw, smem, c->stream>>>(a);
-  else k_patch_warp<2, T, FT, NB><<<grid, 32 * nw, smem, c->stream>>>(a);
+  if (c->ordering) {
+    if (c->dim == 3) k_patch_warp<3, T, FT, NB, true><<<grid, 32 * nw, smem, c->stream>>>(a);
+    else k_patch_warp<2, T, FT, NB, true><<<grid, 32 * nw, smem, c->stream>>>(a);
+  } else {
+    if (c->dim == 3) k_patch_warp<3, T, FT, NB, false><<<grid, 32 * nw, smem, c->stream>>>(a);
+    else k_patch_warp<2, T, FT, NB, false><<<grid, 32 * nw, smem, c->stream>>>(a);
+  }
   ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "patch vcycle");
 }
@@ -1403,7 +1439,7 @@ lor_status coarse_part(lor_ctx* c, const T* r, T* z, T sgn) {
 // multiplicative and the patches additive among themselves, in the symmetric form
 //   B_hyb = B_0 + (I - B_0 K_h) B_loc (I - K_h B_0),
 // B_0 = P_0 R_0 P_0^T, B_loc the patch sum, K_h the LOR matrix on the interior nodes
-// (the variant Section 5.1 leaves to future work).  Hybrid steps: z0 = B_0 r,
+// (the variant Section 4.1 leaves to future work).  Hybrid steps: z0 = B_0 r,
 // t = r - K_h z0, z1 = B_loc t, z = z0 + z1 - B_0 (K_h z1).
 template <typename T, typename FT>
 lor_status launch_apply_P(lor_ctx* c, const T* r, T* z, const FT* F) {

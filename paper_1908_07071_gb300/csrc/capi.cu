@@ -373,6 +373,60 @@ lor_status lor_set_coefficient(lor_ctx* c, const double* bq, const double* bh) {
   return LOR_OK;
 }
 
+lor_status lor_set_ordering(lor_ctx* c, int ordering) {
+  if (!c) return LOR_EINVAL;
+  if (c->setup_started) return lor_fail(c, LOR_ESTATE, "lor_set_ordering must precede lor_setup");
+  if (ordering < 0 || ordering > 2) return lor_fail(c, LOR_EINVAL, "lor_set_ordering: 0 (lexicographic), 1 (RCM) or 2 (MDF)");
+  c->ordering = ordering;
+  return LOR_OK;
+}
+
+lor_status lor_box_ordering(int dim, int A, int B, int C, int ordering, const double* a27, int* perm) {
+  if ((dim != 2 && dim != 3) || A < 1 || B < 1 || C < 1 || (dim == 2 && C != 1) || !perm) return LOR_EINVAL;
+  if (ordering < 0 || ordering > 2 || (ordering == 2 && !a27)) return LOR_EINVAL;
+  const long long n = (long long)A * B * C;
+  if (n > (1 << 20)) return LOR_EINVAL;
+  std::vector<int> out;
+  try {
+    if (ordering == 0) {
+      out.resize(n);
+      for (long long q = 0; q < n; ++q) out[q] = (int)q;
+    } else if (ordering == 1) {
+      lorh::rcm_box(dim, A, B, C, out);
+    } else {
+      const int NS = dim == 3 ? 27 : 9;
+      std::vector<double> a(a27, a27 + n * NS);
+      if (!lorh::mdf_box(dim, A, B, C, a, out)) return LOR_EBREAKDOWN;
+    }
+  } catch (const std::bad_alloc&) {
+    return LOR_ENOMEM;
+  }
+  for (long long q = 0; q < n; ++q) perm[q] = out[q];
+  return LOR_OK;
+}
+
+lor_status lor_patch_ordering(lor_ctx* c, int level, long long patch, int* perm, int cap, int* count) {
+  if (!c || !count) return LOR_EINVAL;
+  if (!c->setup_done) return lor_fail(c, LOR_ESTATE, "lor_patch_ordering: call lor_setup first");
+  if (level < 0 || level + 1 >= c->L || patch < 0 || patch >= c->J)
+    return lor_fail(c, LOR_EINVAL, "lor_patch_ordering: level or patch out of range");
+  const int n0 = c->n[0] + 1, n1 = c->n[1] + 1;
+  const int v[3] = {(int)(patch % n0), (int)((patch / n0) % n1), c->dim == 3 ? (int)(patch / ((long long)n0 * n1)) : 0};
+  int sh = 0;
+  for (int a = 0; a < c->dim; ++a) sh |= ((v[a] == 0 || v[a] == c->n[a]) ? 1 : 0) << a;
+  const int rows = c->shapes[level * 8 + sh].rows;
+  *count = rows;
+  if (!perm) return LOR_OK;
+  if (cap < rows) return lor_fail(c, LOR_EINVAL, "lor_patch_ordering: buffer too small");
+  if (c->ordering == 0) {
+    for (int q = 0; q < rows; ++q) perm[q] = q;
+  } else {
+    const std::vector<int>& h = c->h_perm[(size_t)level * c->J + patch];
+    for (int q = 0; q < rows; ++q) perm[q] = h[q];
+  }
+  return LOR_OK;
+}
+
 lor_status lor_set_node_coordinates(lor_ctx* c, const double* X) {
   if (!c) return LOR_EINVAL;
   if (c->setup_started) return lor_fail(c, LOR_ESTATE, "lor_set_node_coordinates must precede lor_setup");

@@ -1,4 +1,4 @@
-// Preconditioned conjugate gradients (Section 3.2 uses B inside CG; Section 5
+// Preconditioned conjugate gradients (Section 3.2 uses B inside CG; Section 4
 // stops on a residual reduction).  All inner products accumulate in FP64 with a
 // deterministic two-stage reduction (fixed grid, per-block partials, the last
 // block sums the partials in order), so repeated solves are bit-identical.

@@ -23,6 +23,19 @@ void gauss(int q, double* x, double* w);
 void lagrange(int m, const double* nodes, int nt, const double* t, double* B, double* D);
 // Element-structured hierarchy (Section 3.3): GLL-index subsets per level.
 std::vector<std::vector<int>> level_selections(int p, int mg_levels);
+// Orderings of a patch-level box (A x B x C nodes, 3^d-point pattern) for ILU(0)
+// (Section 3.4), as permutations new position -> box index (orderings.cpp):
+// reverse Cuthill-McKee of the pattern, and minimum discarded fill of the matrix
+// a27 (per node its 3^d stencil values, zero outside the box; false on a
+// non-positive pivot).
+void rcm_box(int dim, int A, int B, int C, std::vector<int>& perm);
+bool mdf_box(int dim, int A, int B, int C, const std::vector<double>& a27, std::vector<int>& perm);
+// ILU(0) of a27 in the order perm, in place in box-index layout (lu: per node the
+// multipliers at earlier neighbours, u_ij at later ones and u_ii at the centre),
+// and the level of every node in the dependency schedule of the order (0 for
+// nodes without earlier neighbours).  False on a non-positive pivot.
+bool ilu0_ordered(int dim, int A, int B, int C, const std::vector<double>& a27, const std::vector<int>& perm,
+                  std::vector<double>& lu, std::vector<int>& level);
 }  // namespace lorh
 
 // ---------------------------------------------------------- device-side tables
@@ -59,6 +72,23 @@ struct LevelGrid {
 // record is all zero except its index, which points at the first guard cell
 // after the box (index = rows), so a sweep may process it like a real row.
 __host__ __device__ constexpr int lor_rec(int dim) { return dim == 3 ? 16 : 8; }
+
+// Records of an algebraically ordered patch level (RCM or MDF, Section 3.4): any
+// neighbour may precede a row in the order, so a record holds all 26 (3D) / 8 (2D)
+// couplings in stencil-offset order without the centre: the L record the
+// multipliers of the earlier neighbours (0 at the later ones), the U record the
+// coefficients of the later neighbours, and 1/u_ii in slot rec-2; slot rec-1 holds
+// the row index as in the lexicographic records.  Rows are grouped by their level
+// in the dependency schedule of the order, each level split into fronts of at most
+// 32 rows (rows of one level never couple), fronts padded to 4 records.
+__host__ __device__ constexpr int lor_rec_gen(int dim) { return dim == 3 ? 32 : 16; }
+
+// Per-patch, per-level schedule of an ordered patch level: fronts and bulk-copy
+// chunks as in BoxShape, offsets into ctx->d_gfpad / d_gchunk.
+struct GenSched {
+  int nfront, rpad, front_off;
+  int nchunk[3], chunk_off[3];
+};
 // row length of the row-major stencil copies: 3^dim padded to a multiple of 4
 __host__ __device__ constexpr int lor_nsp(int dim) { return dim == 3 ? 28 : 12; }
 struct BoxShape {
@@ -157,6 +187,16 @@ struct lor_ctx {
   int schwarz = 0;
   void* d_hyb = nullptr;
   int maxfront = 0;           // largest padded front over all levels/shapes (records)
+  // ILU(0) ordering of the patch levels: 0 lexicographic (wavefront records), 1 RCM,
+  // 2 MDF (ordered records, per-patch schedules; host permutations kept for
+  // lor_patch_ordering)
+  int ordering = 0;
+  GenSched* d_gsched = nullptr;            // [level][J]
+  int* d_gfpad = nullptr;
+  int* d_gchunk = nullptr;
+  int gen_tab_ints = 0;                    // largest per-patch table (ints) over all levels
+  int gen_maxchunk[3] = {0, 0, 0};
+  std::vector<std::vector<int>> h_perm;    // [level * J + j] new position -> box index
   int maxchunk[3] = {0, 0, 0};   // largest chunk (records) for 2-, 4-, 8-byte factors
   int* d_status = nullptr;    // device error word
 

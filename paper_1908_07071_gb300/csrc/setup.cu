@@ -13,6 +13,10 @@
 #include <cstring>
 #include <vector>
 
+#include <atomic>
+#include <cstring>
+#include <thread>
+
 #include "lor_internal.h"
 #include "geom.cuh"
 
@@ -27,7 +31,7 @@ double* lor_basis64(lor_ctx* c, int which) { return (double*)c->allocs[0] + whic
 float* lor_basis32(lor_ctx* c, int which) { return (float*)c->allocs[1] + which * kBlk; }
 BoxShape* lor_dev_shapes(lor_ctx* c) { return c->d_shapes; }
 
-// Sample points of a pointwise coefficient (Section 5.2), in the layouts k_geom and
+// Sample points of a pointwise coefficient (Section 4.2), in the layouts k_geom and
 // k_lor_stencil read: K_p Gauss points [element][q] (elements x fastest, q = qx +
 // Q qy + Q^2 qz, Q = p + 1 Gauss-Legendre points per axis) and the 2-point Gauss
 // points of the LOR sub-cells [cell][g] (cells x fastest on the GLL-refined grid,
@@ -751,6 +755,196 @@ static int axis_len(int type, int m) { return type == 0 ? 2 * m - 1 : m - 1; }
 // front is a chunk of its own
 static const int kChunkBytes[3] = {4096, 4096, 8192};
 
+// Factors of algebraically ordered patch levels (RCM or MDF, Section 3.4), built on
+// the host: per patch and level the box matrix from the level stencil, the
+// ordering, ILU(0) in that order, the dependency levels of the order (fronts of at
+// most 32 rows) and the records (lor_rec_gen layout).  Patches are spread over the
+// host threads; the permutations are kept for lor_patch_ordering.
+static lor_status setup_ordered_factors(lor_ctx* c) {
+  const int dim = c->dim, NS = c->NS, C = NS / 2, R = lor_rec_gen(dim), L = c->L, J = c->J;
+  std::vector<std::vector<double>> hS(L);
+  for (int l = 0; l + 1 < L; ++l) {
+    hS[l].resize((size_t)NS * c->lev[l].ntot);
+    cudaError_t e = cudaMemcpyAsync(hS[l].data(), c->d_S64[l], hS[l].size() * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return lor_cuda_check(c, e, "ordered factors: stencil copy");
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return lor_cuda_check(c, e, "ordered factors: stencil copy");
+  struct Out {
+    std::vector<double> rec;             // 2 * rpad records (L part, then U part)
+    std::vector<int> fpad;               // record offset of every front (nfront + 1)
+    std::vector<int> chunk[3];           // front index of every chunk start (nchunk + 1)
+    int nfront = 0, rpad = 0, rows = 0;
+    bool ok = true;
+  };
+  std::vector<Out> out((size_t)L * J);
+  c->h_perm.assign((size_t)L * J, std::vector<int>());
+  // RCM depends on the pattern only: one permutation per (level, shape)
+  std::vector<std::vector<int>> rcm((size_t)L * 8);
+  if (c->ordering == 1)
+    for (int l = 0; l + 1 < L; ++l)
+      for (int sh = 0; sh < (1 << dim); ++sh) {
+        const BoxShape& bs = c->shapes[l * 8 + sh];
+        if (bs.rows) lorh::rcm_box(dim, bs.dims[0], bs.dims[1], bs.dims[2], rcm[(size_t)l * 8 + sh]);
+      }
+  std::atomic<long long> next(0);
+  const long long ntask = (long long)std::max(L - 1, 0) * J;
+  auto work = [&]() {
+    for (;;) {
+      const long long task = next++;
+      if (task >= ntask) return;
+      const int l = (int)(task / J), j = (int)(task % J);
+      const int v[3] = {j % (c->n[0] + 1), (j / (c->n[0] + 1)) % (c->n[1] + 1),
+                        dim == 3 ? j / ((c->n[0] + 1) * (c->n[1] + 1)) : 0};
+      int sh = 0;
+      for (int a = 0; a < dim; ++a) sh |= ((v[a] == 0 || v[a] == c->n[a]) ? 1 : 0) << a;
+      const BoxShape& bs = c->shapes[l * 8 + sh];
+      Out& o = out[(size_t)l * J + j];
+      o.rows = bs.rows;
+      o.fpad.assign(1, 0);
+      for (int es = 0; es < 3; ++es) o.chunk[es].assign(1, 0);
+      if (bs.rows == 0) continue;
+      const int A = bs.dims[0], B = bs.dims[1], Cd = bs.dims[2], n = bs.rows;
+      const LevelGrid& g = c->lev[l];
+      int org[3];
+      for (int t = 0; t < 3; ++t) org[t] = t < dim ? (v[t] > 0 ? v[t] - 1 : 0) * g.m + 1 : 0;
+      std::vector<double> a27((size_t)n * NS, 0.0);
+      for (int lex = 0; lex < n; ++lex) {
+        const int i = lex % A, jj = (lex / A) % B, k = lex / (A * B);
+        const long long G = ((long long)(org[2] + k) * g.N[1] + (org[1] + jj)) * g.N[0] + (org[0] + i);
+        for (int q = 0; q < NS; ++q) {
+          const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = dim == 3 ? q / 9 - 1 : 0;
+          const int ni = i + dx, nj = jj + dy, nk = k + dz;
+          if (ni >= 0 && ni < A && nj >= 0 && nj < B && nk >= 0 && nk < Cd)
+            a27[(size_t)lex * NS + q] = hS[l][(size_t)q * g.ntot + G];
+        }
+      }
+      std::vector<int>& perm = c->h_perm[(size_t)l * J + j];
+      if (c->ordering == 1) perm = rcm[(size_t)l * 8 + sh];
+      else if (!lorh::mdf_box(dim, A, B, Cd, a27, perm)) { o.ok = false; continue; }
+      std::vector<double> lu;
+      std::vector<int> level;
+      if (!lorh::ilu0_ordered(dim, A, B, Cd, a27, perm, lu, level)) { o.ok = false; continue; }
+      std::vector<int> pos(n);
+      for (int q = 0; q < n; ++q) pos[perm[q]] = q;
+      int nlev = 0;
+      for (int q = 0; q < n; ++q) nlev = std::max(nlev, level[q] + 1);
+      std::vector<std::vector<int>> bylev(nlev);
+      for (int q = 0; q < n; ++q) bylev[level[perm[q]]].push_back(perm[q]);
+      std::vector<std::vector<int>> fronts;
+      for (auto& lv : bylev)
+        for (size_t s0 = 0; s0 < lv.size(); s0 += 32)
+          fronts.emplace_back(lv.begin() + s0, lv.begin() + std::min(lv.size(), s0 + 32));
+      int rec = 0;
+      for (auto& f : fronts) { rec += (int)((f.size() + 3) / 4 * 4); o.fpad.push_back(rec); }
+      o.nfront = (int)fronts.size();
+      o.rpad = rec;
+      o.rec.assign((size_t)2 * rec * R, 0.0);
+      for (int q = 0; q < 2 * rec; ++q) {   // padding records: index = the guard cell after the box
+        long long idx = n;
+        std::memcpy(&o.rec[(size_t)q * R + R - 1], &idx, 8);
+      }
+      int q = 0;
+      for (size_t fi = 0; fi < fronts.size(); ++fi) {
+        q = o.fpad[fi];
+        for (int i : fronts[fi]) {
+          double* Lr = &o.rec[(size_t)q * R];
+          double* Ur = &o.rec[(size_t)(rec + q) * R];
+          const int x = i % A, y = (i / A) % B, z = i / (A * B);
+          for (int s2 = 0; s2 < NS - 1; ++s2) {
+            const int so = s2 < C ? s2 : s2 + 1;
+            const int dx = so % 3 - 1, dy = (so / 3) % 3 - 1, dz = dim == 3 ? so / 9 - 1 : 0;
+            const int X = x + dx, Y = y + dy, Z = z + dz;
+            if (X < 0 || X >= A || Y < 0 || Y >= B || Z < 0 || Z >= Cd) continue;
+            const int nbi = (Z * B + Y) * A + X;
+            const double val = lu[(size_t)i * NS + so];
+            if (pos[nbi] < pos[i]) Lr[s2] = val;
+            else Ur[s2] = val;
+          }
+          Ur[R - 2] = 1.0 / lu[(size_t)i * NS + C];
+          const long long idx = i;
+          std::memcpy(&Lr[R - 1], &idx, 8);
+          std::memcpy(&Ur[R - 1], &idx, 8);
+          ++q;
+        }
+      }
+      for (int es = 0; es < 3; ++es) {   // chunks of whole fronts, as for the wavefront records
+        const int cap = kChunkBytes[es] / (R * (2 << es));
+        int fa = 0;
+        while (fa < o.nfront) {
+          int fb = fa + 1;
+          while (fb < o.nfront && o.fpad[fb + 1] - o.fpad[fa] <= cap) ++fb;
+          o.chunk[es].push_back(fb);
+          fa = fb;
+        }
+      }
+    }
+  };
+  {
+    const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nth; ++t) pool.emplace_back(work);
+    for (auto& th : pool) th.join();
+  }
+  for (const Out& o : out)
+    if (!o.ok) return lor_fail(c, LOR_EBREAKDOWN, "ordered ILU(0) breakdown: non-positive pivot");
+  // concatenate: record offsets, schedules, front and chunk tables
+  std::vector<long long> off((size_t)L * J);
+  std::vector<GenSched> gs((size_t)L * J);
+  std::vector<int> gfpad, gchunk;
+  long long tot = 0;
+  c->gen_tab_ints = 0;
+  for (int es = 0; es < 3; ++es) c->gen_maxchunk[es] = 0;
+  std::vector<int> tab(J, 0);
+  for (int l = 0; l < L; ++l)
+    for (int j = 0; j < J; ++j) {
+      const size_t t = (size_t)l * J + j;
+      const Out& o = out[t];
+      GenSched& g = gs[t];
+      off[t] = tot;
+      g.nfront = o.nfront;
+      g.rpad = o.rpad;
+      g.front_off = (int)gfpad.size();
+      if (o.fpad.empty()) gfpad.push_back(0);
+      else gfpad.insert(gfpad.end(), o.fpad.begin(), o.fpad.end());
+      int maxc = 0;
+      for (int es = 0; es < 3; ++es) {
+        g.chunk_off[es] = (int)gchunk.size();
+        if (o.chunk[es].empty()) { gchunk.push_back(0); g.nchunk[es] = 0; continue; }
+        g.nchunk[es] = (int)o.chunk[es].size() - 1;
+        gchunk.insert(gchunk.end(), o.chunk[es].begin(), o.chunk[es].end());
+        for (int k = 0; k < g.nchunk[es]; ++k)
+          c->gen_maxchunk[es] = std::max(c->gen_maxchunk[es], o.fpad[o.chunk[es][k + 1]] - o.fpad[o.chunk[es][k]]);
+        maxc = std::max(maxc, g.nchunk[es]);
+      }
+      tab[j] += g.nfront + 1 + maxc + 1;
+      tot += 2LL * o.rpad;
+      if (l + 1 < L) c->fac_rows += o.rows;
+    }
+  for (int j = 0; j < J; ++j) c->gen_tab_ints = std::max(c->gen_tab_ints, tab[j]);
+  const long long nval = tot * R;
+  std::vector<double> all((size_t)std::max<long long>(nval, 1), 0.0);
+  for (size_t t = 0; t < out.size(); ++t)
+    if (!out[t].rec.empty()) std::memcpy(&all[(size_t)off[t] * R], out[t].rec.data(), out[t].rec.size() * 8);
+  if (upload(c, (void**)&c->d_facoff, off.data(), off.size() * 8)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_gsched, gs.data(), gs.size() * sizeof(GenSched))) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_gfpad, gfpad.data(), gfpad.size() * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_gchunk, gchunk.data(), gchunk.size() * 4)) return LOR_ENOMEM;
+  if (upload(c, (void**)&c->d_F64, all.data(), all.size() * 8)) return LOR_ENOMEM;
+  if (c->opt.factor_bf16) c->d_F16 = (__nv_bfloat16*)lor_alloc(c, all.size() * 2);
+  else c->d_F32 = (float*)lor_alloc(c, all.size() * 4);
+  if (!(c->d_F16 || c->d_F32)) return lor_fail(c, LOR_ENOMEM, "alloc factors");
+  if (nval > 0) {
+    if (c->d_F32) k_fac_to32<<<(unsigned)lor_ceil_div(nval, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F32, nval, R);
+    else k_fac_to16<<<(unsigned)lor_ceil_div(nval, 256), 256, 0, c->stream>>>(c->d_F64, c->d_F16, nval, R);
+    ++c->launches;
+  }
+  // the upload's host buffers go out of scope here: finish the copies first
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return lor_cuda_check(c, e, "ordered factors");
+  return lor_cuda_check(c, cudaGetLastError(), "ordered factors");
+}
+
 lor_status lor_setup_patches(lor_ctx* c) {
   const int dim = c->dim;
   c->J = 1;
@@ -899,6 +1093,7 @@ lor_status lor_setup_patches(lor_ctx* c) {
     if ((long long)order.size() != c->J) return lor_fail(c, LOR_EINVAL, "patch order incomplete");
     if (upload(c, (void**)&c->d_porder, order.data(), order.size() * 4)) return LOR_ENOMEM;
   }
+  if (c->ordering) return setup_ordered_factors(c);
   // factor storage offsets (records; a patch level holds 2*rpad records)
   std::vector<long long> off((size_t)c->L * c->J);
   long long tot = 0;

@@ -1,4 +1,4 @@
-// B(1): the whole domain as one additive-Schwarz patch (Section 5.1, Table 2).
+// B(1): the whole domain as one additive-Schwarz patch (Section 4.1, Table 2).
 //
 // One V(1,1) cycle of the element-structured hierarchy (Section 3.3) on the global
 // LOR levels: on every level l below the vertex level, one ordered ILU(0) smoothing

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "lor.h")
 LOR_OK, LOR_EINVAL, LOR_ENOMEM, LOR_ECUDA, LOR_EBREAKDOWN, LOR_ENAN, LOR_ENOCONV, LOR_ETIMEOUT, LOR_ESTATE = range(9)
 LOR_CG, LOR_DG_IP, LOR_DG_BR2 = 0, 1, 2
 LOR_FP64, LOR_FP32, LOR_MIXED = 0, 1, 2
+ORDER_LEX, ORDER_RCM, ORDER_MDF = 0, 1, 2
 STATUS_NAMES = {0: "LOR_OK", 1: "LOR_EINVAL", 2: "LOR_ENOMEM", 3: "LOR_ECUDA", 4: "LOR_EBREAKDOWN",
                 5: "LOR_ENAN", 6: "LOR_ENOCONV", 7: "LOR_ETIMEOUT", 8: "LOR_ESTATE"}
 
@@ -37,6 +38,26 @@ def measure_fp64_peak():
     if st != LOR_OK:
         raise LorError(st, "FP64 peak probe failed")
     return v.value
+
+
+def box_ordering(dims, ordering, a27=None):
+    """ILU(0) ordering of a box of dims = (A, B[, C]) nodes (lor_box_ordering, host only):
+    box indices in elimination order.  a27: (nodes, 3^d) stencil values, needed for MDF."""
+    dim = len(dims)
+    A, B = int(dims[0]), int(dims[1])
+    C = int(dims[2]) if dim == 3 else 1
+    n = A * B * C
+    perm = np.zeros(n, dtype=np.int32)
+    buf = None
+    if a27 is not None:
+        buf = np.ascontiguousarray(a27, dtype=np.float64)
+        if buf.shape != (n, 27 if dim == 3 else 9):
+            raise ValueError("a27 must have shape (nodes, 3^d)")
+    st = load().lor_box_ordering(dim, A, B, C, int(ordering), None if buf is None else buf.ctypes.data_as(ctypes.c_void_p),
+                                 perm.ctypes.data_as(ctypes.c_void_p))
+    if st != LOR_OK:
+        raise LorError(st, "lor_box_ordering failed")
+    return perm.astype(np.int64)
 
 
 class Options(ctypes.Structure):
@@ -104,6 +125,9 @@ def load():
     lib.lor_set_prec.argtypes = [vp, i]
     lib.lor_set_weighting.argtypes = [vp, i]
     lib.lor_set_schwarz.argtypes = [vp, i]
+    lib.lor_set_ordering.argtypes = [vp, i]
+    lib.lor_box_ordering.argtypes = [i, i, i, i, i, vp, vp]
+    lib.lor_patch_ordering.argtypes = [vp, i, ctypes.c_longlong, vp, i, ctypes.POINTER(i)]
     lib.lor_coefficient_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.lor_coefficient_points.argtypes = [vp, vp, vp]
     lib.lor_set_coefficient.argtypes = [vp, vp, vp]
@@ -116,7 +140,7 @@ def load():
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
     for name in ("lor_coefficient_sizes", "lor_coefficient_points", "lor_set_coefficient", "lor_set_node_coordinates",
                  "lor_pcg_state_size", "lor_pcg_state_save", "lor_pcg_resume",
-                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_set_schwarz", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_measure_fp64_peak", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
+                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_set_schwarz", "lor_set_ordering", "lor_box_ordering", "lor_patch_ordering", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_measure_fp64_peak", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -163,11 +187,13 @@ class Solver:
 
     def __init__(self, vertices, kappa, p, *, mg_levels=0, prec=LOR_FP64, rtol=1e-8, max_it=1000,
                  inner_rtol=1e-3, factor_bf16=False, disc=LOR_CG, eta=1.0, weighting=0, coefficient=None,
-                 node_coordinates=None, stream=None):
+                 node_coordinates=None, ordering=0, stream=None):
         """coefficient: optional callable b(X) of physical points X (n, dim) -> (n,) replacing the
         per-element kappa (CG only); it is evaluated at the points lor_coefficient_points lists.
         node_coordinates: optional (ntot, dim) physical coordinates of the level-0 GLL nodes in
-        L-vector order, for curved (isoparametric) elements (CG only)."""
+        L-vector order, for curved (isoparametric) elements (CG only).
+        ordering: ILU(0) ordering of the patch levels, 0 lexicographic, 1 RCM, 2 MDF
+        (ORDER_LEX / ORDER_RCM / ORDER_MDF)."""
         import torch
         self.lib = load()
         vertices = np.ascontiguousarray(vertices, dtype=np.float64)
@@ -194,6 +220,8 @@ class Solver:
         if st != LOR_OK:
             raise LorError(st, "lor_create rejected the input")
         self.ctx = ctx
+        if ordering:
+            self._check(self.lib.lor_set_ordering(ctx, int(ordering)))
         if node_coordinates is not None:
             Xn = np.ascontiguousarray(np.asarray(node_coordinates, dtype=np.float64).T)
             ntot = int(np.prod([v * p + 1 for v in n]))
@@ -313,6 +341,15 @@ class Solver:
     def selftest_wait(self, polls=1 << 12):
         """Runs the bounded-wait self-test; returns the library status (LOR_ETIMEOUT expected)."""
         return self.lib.lor_selftest_wait(self.ctx, polls)
+
+    def patch_ordering(self, level, patch):
+        """ILU(0) order of one patch level: box indices of its rows in elimination order."""
+        cnt = ctypes.c_int(0)
+        self._check(self.lib.lor_patch_ordering(self.ctx, int(level), int(patch), None, 0, ctypes.byref(cnt)))
+        out = np.zeros(max(cnt.value, 1), dtype=np.int32)
+        self._check(self.lib.lor_patch_ordering(self.ctx, int(level), int(patch), out.ctypes.data_as(ctypes.c_void_p),
+                                                cnt.value, ctypes.byref(cnt)))
+        return out[:cnt.value].astype(np.int64)
 
     def set_schwarz(self, mode):
         """0: additive coarse space (Eq. (as)); 1: hybrid, coarse correction multiplicative."""

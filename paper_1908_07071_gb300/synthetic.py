@@ -116,7 +116,7 @@ def make_mesh(dim: int, n, seed: int = 0, perturb: float = 0.15,
 
 
 def make_strip_mesh(n: int, aspect: float, layers: int = 4, seed: int = 0, perturb: float = 0.0):
-    """2D unit-square mesh of n x n elements with a strip of thin elements (Section 5.5).
+    """2D unit-square mesh of n x n elements with a strip of thin elements (Section 4.5).
 
     The `layers` element rows around y = 1/2 have height h/aspect (h = 1/n, the
     element width), so their aspect ratio is `aspect`; the other rows split the rest
@@ -152,7 +152,7 @@ def make_strip_mesh(n: int, aspect: float, layers: int = 4, seed: int = 0, pertu
 
 def make_quarter_hole_mesh(n: int, radius: float = 0.25):
     """Curved 2D mesh of [0,1]^2 minus the quarter disk of `radius` at the origin (one
-    quarter of the square-with-a-hole geometry of Section 5.2), n x n elements.
+    quarter of the square-with-a-hole geometry of Section 4.2), n x n elements.
 
     The vertices are those of the uniform grid of the parameter square (s, t); the
     returned `warp` maps (s, t) to the domain: angle theta = (pi/2)(1 - s), blended
@@ -180,7 +180,7 @@ def make_quarter_hole_mesh(n: int, radius: float = 0.25):
 
 def make_split_triangle_mesh(n: int, seed: int = 0, perturb: float = 0.15):
     """Unstructured quadrilateral mesh of [0,1]^2 (a stand-in for the unstructured mesh (a)
-    of Section 5.2): an n x n grid of squares, each cut into two triangles (diagonals
+    of Section 4.2): an n x n grid of squares, each cut into two triangles (diagonals
     alternating in a checkerboard), interior grid vertices moved by U(-perturb*h,
     perturb*h) per coordinate, and every triangle split into three quadrilaterals
     through its edge midpoints and centroid.  Interior vertices have 3 (centroids), 4
@@ -238,7 +238,7 @@ def make_split_triangle_mesh(n: int, seed: int = 0, perturb: float = 0.15):
 
 def two_valued_kappa(n, seed: int = 0, high: float = 10.0, low: float = 1.0) -> np.ndarray:
     """Piecewise-constant coefficient taking `high` or `low` on each element with equal
-    probability (the discontinuous coefficient b_4 of Section 5.2); layout as kappa."""
+    probability (the discontinuous coefficient b_4 of Section 4.2); layout as kappa."""
     shape_e = tuple(reversed([int(v) for v in n]))
     u = uniform01(stream_key(seed, TAG_KAPPA), int(np.prod(shape_e))).reshape(shape_e)
     return np.where(u < 0.5, float(high), float(low))

@@ -214,7 +214,7 @@ def test_quadrature_points_match_the_oracle_element_maps(lib):
     """lor_quadrature_points (host only, before setup) lists the (p+1)^d Gauss points of every
     element in the order lor_rhs_f reads f: elements x fastest, q = qx + Q qy + Q^2 qz; on
     multilinear elements they are the oracle's multilinear maps of the Gauss points, on curved
-    elements the oracle's isoparametric maps (Section 5.2's curved mesh stand-in)."""
+    elements the oracle's isoparametric maps (Section 4.2's curved mesh stand-in)."""
     from oracle import cg
     from oracle.basis import gauss_legendre
     from oracle.mesh import Mesh

@@ -1,4 +1,4 @@
-"""Pointwise coefficients b(x) on the GPU (lor_set_coefficient; Section 5.2, b1-b3)
+"""Pointwise coefficients b(x) on the GPU (lor_set_coefficient; Section 4.2, b1-b3)
 against the oracle's K_p and K_h with the same b: FP64 apply_A and apply_P to 1e-10,
 PCG counts +-1.  The library samples b at the points lor_coefficient_points lists
 (checked against the oracle's quadrature points in test_capi.py)."""

@@ -1,5 +1,5 @@
 """Curved (isoparametric) elements on the GPU (lor_set_node_coordinates; the curved
-meshes of Section 5.2) against the oracle's isoparametric Mesh(warp=...): FP64
+meshes of Section 4.2) against the oracle's isoparametric Mesh(warp=...): FP64
 apply_A and apply_P to 1e-10, the load vector to 1e-12 (the rule and tolerance of
 the right-hand-side parity test), PCG counts +-1.  The GLL node coordinates handed
 to the library are the oracle's own node positions of the warped mesh (an input,

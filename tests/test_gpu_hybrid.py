@@ -1,6 +1,6 @@
 """Hybrid Schwarz on the GPU (lor_set_schwarz(ctx, 1)): the coarse correction applied
 multiplicatively in the symmetric form B_0 + (I - B_0 K_h) B_loc (I - K_h B_0), the
-patches additive among themselves (Section 5.1 names the variant as future work).
+patches additive among themselves (Section 4.1 names the variant as future work).
 Compared with the oracle's apply_hybrid: FP64 to 1e-10 relative (max-norm), FP32
 within the bounds of the additive FP32 test, and the FP64 PCG count within one
 iteration of the oracle's."""

@@ -1,0 +1,105 @@
+"""Algebraically ordered ILU(0) smoothing on the GPU (lor_set_ordering, Section 3.4):
+reverse Cuthill-McKee and minimum discarded fill orders of every patch level, with
+the patch kernel sweeping the dependency levels of the order.  The permutations the
+library used equal the oracle's node for node; B r in FP64 equals the oracle's
+LORPreconditioner(ordering=...) to 1e-10 relative (max-norm), the FP32 path stays
+within the bounds of the lexicographic FP32 test, and PCG counts are within one
+iteration of the oracle's."""
+import numpy as np
+import pytest
+
+from oracle import cg, krylov
+from oracle import lor as olor
+from oracle.mesh import Mesh
+from paper_1908_07071_gb300.synthetic import make_mesh, random_vector
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+CASES = [  # (dim, n, p, mg_levels), ordering; the oracle's MDF takes minutes beyond p = 4 in 3D
+    ((2, 3, 4, 0), "rcm"), ((2, 3, 4, 0), "mdf"),
+    ((2, (3, 4), 6, 0), "rcm"), ((2, (3, 4), 6, 0), "mdf"),
+    ((3, 2, 3, 0), "rcm"), ((3, 2, 3, 0), "mdf"),
+    ((3, (2, 3, 4), 3, 0), "rcm"), ((3, (2, 3, 4), 3, 0), "mdf"),
+    ((3, 3, 2, 0), "rcm"), ((3, 3, 2, 0), "mdf"),
+    ((3, 2, 6, 2), "rcm"),
+    ((3, 2, 8, 0), "rcm"),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_07071_gb300.build import build_library
+    build_library()
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("case,kind", CASES, ids=str)
+def test_ordered_apply_P_matches_oracle(case, kind):
+    from paper_1908_07071_gb300 import lor
+    dim, n, p, mg = case
+    code = {"rcm": lor.ORDER_RCM, "mdf": lor.ORDER_MDF}[kind]
+    v, k = make_mesh(dim, n, seed=5, perturb=0.15)
+    B = olor.LORPreconditioner(Mesh(v, k), p, mg_levels=mg, ordering=kind)
+    r = None
+    for bf16 in (False, True):
+        s = lor.Solver(v, k, p, mg_levels=mg, ordering=code, factor_bf16=bf16)
+        if not bf16:
+            # the orders the library used, patch by patch and level by level
+            for j, P in enumerate(B.patches):
+                for l, lev in enumerate(P["levels"][:-1]):
+                    if "perm" in lev:
+                        np.testing.assert_array_equal(s.patch_ordering(l, j), lev["perm"])
+            r = random_vector(s.nvec, 29)
+            z_ref = B.apply(r)
+            z = torch.full((s.nvec,), np.nan, dtype=torch.float64, device="cuda")
+            s.apply_P(torch.from_numpy(r).cuda(), z)
+            assert _rel(z.cpu().numpy(), z_ref) < 1e-10
+        z32 = torch.empty(s.nvec, dtype=torch.float32, device="cuda")
+        s.apply_P(torch.from_numpy(r).float().cuda(), z32, prec=lor.LOR_FP32)
+        err = _rel(z32.double().cpu().numpy(), B.apply(r))
+        assert err < (8 * 2.0 ** -8 if bf16 else 50 * U32 * 1e3), err
+        s.close()
+
+
+@pytest.mark.parametrize("kind", ["rcm", "mdf"])
+def test_ordered_pcg_matches_oracle(kind):
+    from paper_1908_07071_gb300 import lor
+    code = {"rcm": lor.ORDER_RCM, "mdf": lor.ORDER_MDF}[kind]
+    v, k = make_mesh(3, 3, seed=5, perturb=0.15)
+    m = Mesh(v, k)
+    p = 4
+    rtol = 1e-10
+    K = cg.assemble_stiffness(m, p)
+    N = cg.node_shape(m.n, p)
+    B = olor.LORPreconditioner(m, p, ordering=kind)
+    b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
+    x_or, it_or, _, coef = krylov.pcg(lambda u: cg.apply_A(K, N, u), B.apply, b, rtol=rtol)
+    s = lor.Solver(v, k, p, rtol=rtol, ordering=code)
+    x = torch.zeros(s.nvec, dtype=torch.float64, device="cuda")
+    it, rel = s.solve(torch.from_numpy(b).cuda(), x)
+    print(f"{kind} PCG: GPU {it}, oracle {it_or}")
+    assert abs(it - it_or) <= 1, (it, it_or)
+    assert rel <= rtol
+    lo, hi = krylov.lanczos_condition(*coef)
+    assert np.linalg.norm(x.cpu().numpy() - x_or) / np.linalg.norm(x_or) <= hi / lo * 2 * rtol * 10
+    s.close()
+
+
+def test_ordering_is_set_before_setup_only():
+    from paper_1908_07071_gb300 import lor
+    v, k = make_mesh(3, 2, seed=5, perturb=0.15)
+    with pytest.raises(lor.LorError) as err:
+        lor.Solver(v, k, 3, ordering=3)
+    assert err.value.status == lor.LOR_EINVAL
+    s = lor.Solver(v, k, 3)
+    assert s.lib.lor_set_ordering(s.ctx, 1) == lor.LOR_ESTATE
+    np.testing.assert_array_equal(s.patch_ordering(0, 13), np.arange(125))   # lexicographic: identity
+    s.close()

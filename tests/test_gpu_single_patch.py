@@ -1,6 +1,6 @@
 """B(1) on the GPU (lor_set_schwarz(ctx, 2)): the whole domain as one patch, one
 V(1,1) cycle of the element-structured hierarchy with lexicographic ILU(0)
-smoothing on the global level grids and R_0 on the vertex level (Section 5.1,
+smoothing on the global level grids and R_0 on the vertex level (Section 4.1,
 Table 2).  Compared with the oracle's SinglePatchPreconditioner: FP64 to 1e-10
 relative (max-norm), FP32 within the bound of the additive FP32 test, and the FP64
 PCG count within one iteration of the oracle's."""

@@ -1,4 +1,4 @@
-"""Anisotropic strip meshes and vertex patches enlarged for isotropic overlap (Section 5.5).
+"""Anisotropic strip meshes and vertex patches enlarged for isotropic overlap (Section 4.5).
 
 Pins: the strip mesh has the stated element sizes; the enlargement rule is the
 vertex patch itself on shape-regular meshes and covers the thin strip on strip
@@ -6,7 +6,7 @@ meshes; enlarged patches keep the hierarchy Galerkin and the V(1,1) error
 propagation textbook; with exact local and coarse solves the patch sum obeys the
 colouring bound of additive Schwarz (patches of one colour share no coupling, so
 their corrections are A-orthogonal projections); and the iteration counts behave as
-Section 5.5 reports: flat in the aspect ratio with enlarged patches, growing without.
+Section 4.5 reports: flat in the aspect ratio with enlarged patches, growing without.
 """
 import numpy as np
 import pytest
@@ -110,7 +110,7 @@ def test_enlarged_patches_obey_the_colouring_bound():
 
 
 def test_iterations_flat_in_aspect_ratio_with_enlarged_patches():
-    """Section 5.5: with isotropic overlap the CG counts stay constant in the aspect ratio
+    """Section 4.5: with isotropic overlap the CG counts stay constant in the aspect ratio
     of the strip; plain vertex patches degrade.  Q3 on 8 x 8 elements, a 2-layer strip."""
     p = 3
     its = {}

@@ -1,4 +1,4 @@
-"""Variable coefficients b(x) (Section 5.2) in the oracle: the coefficient is evaluated
+"""Variable coefficients b(x) (Section 4.2) in the oracle: the coefficient is evaluated
 at the physical quadrature points of K_p and at the 2-point Gauss points of every LOR
 sub-cell of K_h.
 
@@ -127,6 +127,6 @@ def test_iteration_counts_vs_table4(p):
         ps, pv = paper[(p, name)]
         assert abs(single - ps) <= max(2, 0.15 * ps), (name, single, ps)
         assert 0.9 * pv <= vertex <= 1.3 * pv, (name, vertex, pv)
-    # vertex patches need about twice the single patch's iterations (Section 5.2)
+    # vertex patches need about twice the single patch's iterations (Section 4.2)
     for name, (s, vv) in ours.items():
         assert 1.4 * s <= vv <= 2.6 * s, (name, s, vv)

@@ -1,4 +1,4 @@
-"""Curved (isoparametric) elements in the oracle (the curved mesh of Section 5.2).
+"""Curved (isoparametric) elements in the oracle (the curved mesh of Section 4.2).
 
 The element map is the degree-p interpolant of warp(multilinear(xi)) at the GLL points.
 Pins: with an affine warp it is the (warped) multilinear map exactly; on one quarter of

@@ -134,7 +134,7 @@ def test_spd_threshold_and_eta_robust_iterations(form):
 
 
 def test_dg_counts_bounded_under_h_refinement_table7():
-    """Section 5.3, Table 7: BR2 counts do not grow under h-refinement (25, 24, 23, 22 on
+    """Section 4.3, Table 7: BR2 counts do not grow under h-refinement (25, 24, 23, 22 on
     mesh (a), golden file).  B_DG with B(1) inside on perturbed 3^2 and 6^2 meshes of
     [-1,1]^2 (Q4, eta = 10): measured 19 and 19 (12^2: 18); with vertex patches 36, 38, 39."""
     import os

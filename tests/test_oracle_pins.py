@@ -363,7 +363,7 @@ def _paper_table3():
 
 @pytest.mark.parametrize("p,nx", [(2, 2), (2, 4), (4, 2), (4, 4), (4, 8), (6, 4)])
 def test_iteration_counts_vs_table3(p, nx):
-    """Table 3 (Section 5.1): vertex-patch counts on the Cartesian grid.  Ordering and R_0
+    """Table 3 (Section 4.1): vertex-patch counts on the Cartesian grid.  Ordering and R_0
     differ (lexicographic ILU, own coarse V-cycle) and the paper does not state its
     right-hand side (the manufactured sin(pi x) sin(pi y) one is used), so only the
     magnitude is pinned."""

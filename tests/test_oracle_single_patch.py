@@ -1,4 +1,4 @@
-"""Pins of the oracle's single-patch preconditioner B(1) (Section 5.1): the whole
+"""Pins of the oracle's single-patch preconditioner B(1) (Section 4.1): the whole
 domain as one patch, i.e. one element-structured V(1,1) cycle on K_h with ILU(0)
 smoothing and R_0 at the vertex level."""
 import os
@@ -36,7 +36,7 @@ def _cartesian(nx, p):
 
 @pytest.mark.parametrize("p,nx", [(4, 2), (4, 4), (4, 8), (6, 2), (6, 4), (6, 8), (8, 2), (8, 4), (8, 8)])
 def test_single_patch_counts_match_table2(p, nx):
-    """Table 2 (Section 5.1): within one iteration of the paper's counts, although the
+    """Table 2 (Section 4.1): within one iteration of the paper's counts, although the
     ordering (lexicographic vs MDF) and R_0 (own V-cycle vs BoomerAMG) differ."""
     paper = _paper_table2()[(p, nx)]
     m, N, K, b = _cartesian(nx, p)
@@ -54,7 +54,7 @@ def test_single_patch_p2_magnitude(nx):
 
 
 def test_vertex_patches_need_more_iterations_than_one_patch():
-    """Section 5.1: with vertex patches the counts grow (about twice those of one
+    """Section 4.1: with vertex patches the counts grow (about twice those of one
     patch per domain in the paper's tables)."""
     for p, nx in ((4, 4), (6, 4), (8, 4)):
         m, N, K, b = _cartesian(nx, p)
@@ -274,7 +274,7 @@ def test_pou_weights_are_square_roots_of_the_coarse_basis(dim, n, p):
 
 
 def test_pou_weighted_vertex_patches_close_the_gap_to_one_patch():
-    """Section 5.1 reports vertex patches needing about twice the iterations of one patch
+    """Section 4.1 reports vertex patches needing about twice the iterations of one patch
     B(1).  Measured (Cartesian 4 x 4, Q4): B(1) 15, vertex patches with unit weights 25,
     with partition-of-unity weights 16: the gap is the unit-weight overlap sum."""
     v, k = make_mesh(2, 4, seed=0, perturb=0.0, kappa_const=1.0)

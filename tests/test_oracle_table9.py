@@ -1,4 +1,4 @@
-"""Magnitudes of Table 9 (Section 5.4): one patch B(1) against one patch per vertex B(V),
+"""Magnitudes of Table 9 (Section 4.4): one patch B(1) against one patch per vertex B(V),
 for CG and for the BR2 DG method (eta = 10, B_DG of Eq. (dg-as) with R_p = B(1) or B(V)).
 The paper's mesh has 80 curved unstructured quadrilaterals; the stand-in is a perturbed
 9 x 9 mesh of [-1,1]^2, so this is a magnitude check (ours / paper in [0.75, 1.25]), not

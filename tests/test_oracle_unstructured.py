@@ -1,4 +1,4 @@
-"""Pins of the unstructured-mesh oracle (`oracle.unstructured`, Section 5.2 meshes).
+"""Pins of the unstructured-mesh oracle (`oracle.unstructured`, Section 4.2 meshes).
 
 * A structured grid given as an unstructured mesh reproduces the structured oracle's
   K_p, K_h, P_0 and (with exact patch and coarse solves) B exactly, after matching
@@ -8,7 +8,7 @@
   opposite directions by their two elements) the numbering is conforming, linear
   functions pass the patch test, the patch hierarchy is Galerkin and the V(1,1) cycle
   has the textbook error propagation, the additive Schwarz sum with exact solves obeys
-  the colouring bound, and the CG counts stay bounded in h (Section 5.2: iteration
+  the colouring bound, and the CG counts stay bounded in h (Section 4.2: iteration
   counts remain bounded on unstructured meshes).
 """
 import numpy as np

@@ -1,0 +1,75 @@
+"""The ILU(0) orderings of the library's host code (lor_box_ordering: reverse
+Cuthill-McKee and minimum discarded fill, Section 3.4) against the oracle's, node for
+node, on the patch matrices of small meshes (no GPU: host code of the C ABI)."""
+import numpy as np
+import pytest
+
+from oracle import lor as olor
+from oracle import ordering as ordo
+from oracle.mesh import Mesh
+from paper_1908_07071_gb300.synthetic import make_mesh
+
+
+@pytest.fixture(scope="module")
+def lor():
+    from paper_1908_07071_gb300.build import build_library
+    build_library()
+    from paper_1908_07071_gb300 import lor as mod
+    return mod
+
+
+def _a27(Aj, dims, dim):
+    """Stencil layout of a box matrix: per node its 3^d values in stencil-offset order."""
+    A, B = dims[0], dims[1]
+    C = dims[2] if dim == 3 else 1
+    n = A * B * C
+    NS = 27 if dim == 3 else 9
+    out = np.zeros((n, NS))
+    for i in range(n):
+        x, y, z = i % A, (i // A) % B, i // (A * B)
+        for o in range(NS):
+            dx, dy, dz = o % 3 - 1, (o // 3) % 3 - 1, (o // 9 - 1 if dim == 3 else 0)
+            X, Y, Z = x + dx, y + dy, z + dz
+            if 0 <= X < A and 0 <= Y < B and 0 <= Z < C:
+                out[i, o] = Aj[i, (Z * B + Y) * A + X]
+    return out
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, 3, 4), (3, 2, 3), (3, 3, 2), (2, 4, 6)])
+@pytest.mark.parametrize("kind,code", [("rcm", 1), ("mdf", 2)])
+def test_box_orderings_equal_the_oracle(lor, dim, n, p, kind, code):
+    v, k = make_mesh(dim, n, seed=1, perturb=0.15)
+    B = olor.LORPreconditioner(Mesh(v, k), p, ordering=kind, coarse=False)
+    checked = 0
+    for P in B.patches:
+        for lev in P["levels"][:-1]:
+            if "perm" not in lev:
+                continue
+            dims = [len(r) for r in lev["ranges"]]
+            a27 = _a27(lev["A"], dims, dim) if code == 2 else None
+            perm = lor.box_ordering(dims, code, a27)
+            np.testing.assert_array_equal(perm, lev["perm"])
+            checked += 1
+    assert checked > 0
+
+
+def test_box_ordering_rejects_bad_input_and_reports_breakdown(lor):
+    with pytest.raises(lor.LorError) as err:
+        lor.box_ordering((3, 3, 3), 3)
+    assert err.value.status == lor.LOR_EINVAL
+    with pytest.raises(lor.LorError):
+        lor.box_ordering((3, 3, 3), 2)                  # MDF needs the matrix
+    a27 = np.zeros((8, 9))
+    a27[:, 4] = -1.0                                    # non-positive pivots
+    with pytest.raises(lor.LorError) as err:
+        lor.box_ordering((4, 2), 2, a27)
+    assert err.value.status == lor.LOR_EBREAKDOWN
+    np.testing.assert_array_equal(lor.box_ordering((4, 2), 0), np.arange(8))
+    # RCM of a box is a permutation with the bandwidth scipy's routine reaches
+    pat = np.ones((1, 1), dtype=bool)
+    for dims in [(5, 4, 3), (6, 1, 1), (4, 4)]:
+        perm = lor.box_ordering(dims, 1)
+        assert sorted(perm.tolist()) == list(range(int(np.prod(dims))))
+        ranges = [np.arange(d) for d in dims]
+        pat = olor.box_pattern(ranges)
+        assert ordo.bandwidth(pat, perm) == ordo.bandwidth(pat, ordo.rcm_order(pat))
