@@ -73,6 +73,10 @@ def parse():
     ap.add_argument("--weighting", type=int, default=0, choices=[0, 1, 2],
                     help="patch-sum weighting of the timed form: 0 unit (the paper's method), 1 counting matrix, "
                          "2 partition of unity")
+    ap.add_argument("--leg", choices=["learned", "schwarz", "batch"],
+                    help="run only this leg at --p/--n (learned: trained on an n/2 mesh for --learned-steps "
+                         "steps) and print its JSON; a profiling entry point, not the bench line")
+    ap.add_argument("--learned-steps", type=int, default=300)
     ap.add_argument("--summarize-ncu", metavar="CSV",
                     help="print per-kernel launches, total time and share of an ncu launch list "
                          "(--metrics gpu__time_duration.sum --csv) and exit")
@@ -123,6 +127,7 @@ def cpu_sample_worker(p: int, n: int, seed: int, budget_s: float, iters: int) ->
     from oracle.mesh import Mesh
     from paper_1908_07071_gb300.synthetic import make_mesh
 
+    t_start = time.perf_counter()
     verts, kappa = make_mesh(3, n, seed=seed, perturb=0.15)
     m = Mesh(verts, kappa)
     rng = np.random.default_rng(0)
@@ -154,7 +159,7 @@ def cpu_sample_worker(p: int, n: int, seed: int, budget_s: float, iters: int) ->
     J = (n + 1) ** 3
     per_it = nel * t_el / n_el + J * t_pa / n_pa
     solve_s = iters * per_it
-    return {"solve_s": solve_s, "sample": f"{n_el} element applies (Q{p}, dense element matrix) and {n_pa} "
+    return {"solve_s": solve_s, "wall_s": time.perf_counter() - t_start, "sample": f"{n_el} element applies (Q{p}, dense element matrix) and {n_pa} "
             f"interior patch V-cycles timed, extrapolated to {nel} elements + {J} patches per iteration "
             f"x {iters} iterations", "cores": 1}
 
@@ -244,16 +249,20 @@ class Clocks:
 def reference_arm(args, rank):
     if rank != 0:
         return
-    steps = []
+    steps, walls = [], []
     res = None
     for k in range(args.warmup + args.steps):
         res = run_cpu_leg(args.p, args.n, 0, args.cpu_sample_s, REF_ITERS)
         if k >= args.warmup:
             steps.append(res["solve_s"])
+            walls.append(res["wall_s"])
+    # a step is one bounded sample of the workload (its wall time is ms_per_step); the
+    # solves/s value extrapolates the sample to whole solves
     solve_s = statistics.mean(steps)
     value = 1.0 / solve_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(walls) * 1e3,
+            "extrapolated_solve_s": solve_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "p": args.p, "n": args.n},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": res["cores"], "kind": "oracle",
@@ -487,8 +496,7 @@ def leg_learned(n: int = 32, p: int = 6, train_n: int = 16, steps: int = 300):
            "ndof": s.info.ndof, "train": {"mesh": f"{train_n}^3, seed 100", "steps": steps, "batch": 256,
                                           "ms": train_ms, "loss_first5": float(np.mean(hist[:5])),
                                           "loss_last20": float(np.mean(hist[-20:]))}}
-    for on, key in ((False, "plain"), (True, "learned")):
-        s.learned_enable(on)
+    def timed(key):
         x = torch.zeros_like(b)
         s.solve(b, x)
         x.zero_()
@@ -497,7 +505,27 @@ def leg_learned(n: int = 32, p: int = 6, train_n: int = 16, steps: int = 300):
         e1.record()
         torch.cuda.synchronize()
         out[key] = {"time_to_tol_ms": e0.elapsed_time(e1), "iterations": it, "rel_res_fp64": rel}
+
+    for on, key in ((False, "plain"), (True, "learned")):
+        s.learned_enable(on)
+        timed(key)
     out["speedup_learned_vs_plain"] = out["plain"]["time_to_tol_ms"] / out["learned"]["time_to_tol_ms"]
+    # replace variant: the correction takes the place of the level-0 post-smoothing;
+    # trained on the same family with that cycle's pairs
+    tr = lor.Solver(vt, kt, p, prec=lor.LOR_MIXED, rtol=1e-8, factor_bf16=True)
+    tr.learned_variant(1)
+    tr.learned_params(learned_init_params(seed=1))
+    hist_r = tr.learned_train(steps, batch=256, lr=2e-3, seed=5)
+    params_r = tr.learned_params()
+    tr.close()
+    s.learned_variant(1)
+    s.learned_params(learned_init_params(seed=1))     # zero output layer: the cut cycle alone
+    s.learned_enable(True)
+    timed("cycle_without_level0_post_smoothing")
+    s.learned_params(params_r)
+    timed("replace_variant")
+    out["replace_variant"]["loss_first5"] = float(np.mean(hist_r[:5]))
+    out["replace_variant"]["loss_last20"] = float(np.mean(hist_r[-20:]))
     s.close()
     return out
 
@@ -514,6 +542,15 @@ def main():
     args = parse()
     if args.summarize_ncu:
         print(summarize_ncu_launches(args.summarize_ncu))
+        return
+    if args.leg:
+        if args.leg == "learned":
+            out = leg_learned(n=args.n, p=args.p, train_n=max(2, args.n // 2), steps=args.learned_steps)
+        elif args.leg == "schwarz":
+            out = leg_schwarz(n=args.n, degrees=(args.p,))
+        else:
+            out = leg_batch(args.batch_n, 0)
+        print(json.dumps(out), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -321,6 +321,12 @@ void lor_batch_destroy(lor_batch* batch);
  * W3[1][16][27] b3[1], taps ordered (dz+1)*9+(dy+1)*3+(dx+1).
  * lor_learned_params: copy host parameters in (h_in) and/or out (h_out).
  * lor_learned_enable: switch the correction on (1) or off (0).
+ * lor_learned_variant: 0 (default) = the correction is added after the whole
+ *   V(1,1) cycle; 1 = it replaces the level-0 post-smoothing: the patch cycle
+ *   returns after the coarse correction and the network sees the residual that
+ *   leaves.  The variant applies to training (the pairs come from the cycle of
+ *   the variant) and to inference, so parameters trained for one variant are
+ *   not meant for the other.  LOR_EINVAL for other values.
  * lor_learned_train: `steps` Adam steps (learning rate lr) on batches of
  *   `batch` interior patches of this context; each step draws random errors e,
  *   runs the plain V-cycle x = V(A e) and minimises
@@ -334,6 +340,7 @@ void lor_batch_destroy(lor_batch* batch);
 #define LOR_LEARNED_NPARAM 8241
 lor_status lor_learned_params(lor_ctx* ctx, const float* h_in, float* h_out, int count);
 lor_status lor_learned_enable(lor_ctx* ctx, int on);
+lor_status lor_learned_variant(lor_ctx* ctx, int variant);
 lor_status lor_learned_train(lor_ctx* ctx, int steps, int batch, float lr, unsigned long long seed, float* h_loss);
 lor_status lor_learned_eval(lor_ctx* ctx, int npatch, const int* d_ids, const float* d_t, const float* d_delta,
                             float* d_c, float* d_loss, float* h_grad);

@@ -261,7 +261,7 @@ class LORPreconditioner:
     def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0,
                  exact_local: bool = False, exact_coarse: bool = False, K_h=None,
                  patch_subset=None, coarse=True, ordering: str = "lex", weighting: str = "none",
-                 patch_spans=None):
+                 patch_spans=None, post_smooth0: bool = True):
         """patch_subset: vertex multi-indices whose patches are built (default all);
         patch_spans: {vertex: [(lo_k, hi_k) per axis]} element spans of enlarged patches
         (`isotropic_overlap_spans`, Section 4.5); vertices not listed keep the vertex patch;
@@ -272,7 +272,10 @@ class LORPreconditioner:
         both sides by D^{-1/2}, D = number of patches containing each node (the counting
         matrix Section 4.1 names as future work), or "pou": each patch scaled on both
         sides by W_j = sqrt(theta_j), theta_j the Q1 vertex function of its vertex in
-        the element reference coordinates at the level-0 nodes (`pou_weights`)."""
+        the element reference coordinates at the level-0 nodes (`pou_weights`);
+        post_smooth0=False leaves out the post-smoothing of the patch level 0 (the cycle
+        the learned correction's replace variant completes)."""
+        self.post_smooth0 = post_smooth0
         self.ordering = ordering
         self.patch_spans = patch_spans or {}
         if weighting not in ("none", "count", "pou"):
@@ -347,6 +350,8 @@ class LORPreconditioner:
         P = lev["P"]
         if P.shape[1] > 0:
             x = x + P @ self.vcycle(levels, l + 1, P.T @ t)
+        if l == 0 and not self.post_smooth0:
+            return x
         t = r - A @ x
         return x + self.smooth(lev, t)
 

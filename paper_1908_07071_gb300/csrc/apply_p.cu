@@ -89,6 +89,10 @@ struct PatchArgs {
   // residual capture (learned-correction inference): the level-0 residual left by
   // the cycle on every interior patch is written to tout + visiting position * vstride
   void* tout;
+  // the learned correction's replace variant: the level-0 post-smoothing is left out
+  // (the cycle returns x0 after the coarse correction; the residual r - A x0 it
+  // leaves is what the correction sees)
+  int skip_post0;
 };
 
 
@@ -858,7 +862,8 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, nullptr, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
         }
       }
-      if (ok) ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
+      if (ok && !a.skip_post0)
+        ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
     }
     if (!ok) {
       // a bulk copy did not arrive in time: report, drain what is still in flight, leave
@@ -872,7 +877,7 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
     // ---- x_j = x0 + t0: patch-local output, or scatter-add R_j^T x_j
     if (a.plist) {
       T* dst = (T*)a.xloc + jo * a.vstride;
-      for (int lex = lane; lex < b0.rows; lex += 32) dst[lex] = xslot[lex] + t0[lex];
+      for (int lex = lane; lex < b0.rows; lex += 32) dst[lex] = xslot[lex] + (a.skip_post0 ? T(0) : t0[lex]);
       continue;
     }
     // the weighted R_j^T x_j goes to the patch's own output slice (lexicographic
@@ -899,9 +904,9 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
         for (int u = 0; u < U; ++u) {
           const int lex = l0 + 32 * u;
           if (lex < b0.rows) {
-            const T xj = xv[u] + t0[lex];
+            const T xj = a.skip_post0 ? xv[u] : xv[u] + t0[lex];
             zj[lex] = w[u] * xj;
-            if (a.tout && sh == 0) t0[lex] = xj;
+            if (a.tout && sh == 0 && !a.skip_post0) t0[lex] = xj;
           }
         }
       }
@@ -910,7 +915,9 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
     if (a.tout && sh == 0) {   // residual left on an interior patch, for the learned correction
       T* prev = vec + (b0.A + 1);
       T* tmp = prev + AB0 + (b0.A + 1);
-      resid0_inplace<DIM, T>(b0, lv0, rg0, nullptr, t0, prev, tmp, nullptr, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
+      // (without the post-smoothing t0 already holds r - A x0)
+      if (!a.skip_post0)
+        resid0_inplace<DIM, T>(b0, lv0, rg0, nullptr, t0, prev, tmp, nullptr, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
       T* dst = (T*)a.tout + jo * a.vstride;
       for (int lex = lane; lex < b0.rows; lex += 32) dst[lex] = t0[lex];
       __syncwarp();
@@ -1314,6 +1321,7 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
   a.porder = c->d_porder;
   a.conv = c->conv_flag;
   a.plist = nullptr; a.nlist = 0; a.rloc = nullptr; a.xloc = nullptr; a.vstride = 0; a.tout = nullptr;
+  a.skip_post0 = 0;
   a.wp = c->opt.weighting ? c->p : 0;
   a.wmode = c->opt.weighting;
   a.hat = Sel<T>::p0w(c);
@@ -1385,6 +1393,7 @@ lor_status patch_part(lor_ctx* c, const T* r, T* z, const FT* F) {
   if (c->learned_on && sizeof(T) == 4) {
     a.tout = c->learned_tout;
     a.vstride = c->shapes[0].rows;
+    a.skip_post0 = c->learned_replace ? 1 : 0;
   }
   const int pk = sizeof(T) == 8 ? 0 : 1;
   lor_prof_begin(c, pk);
@@ -1521,11 +1530,13 @@ lor_status lor_patch_local32(lor_ctx* c, const int* plist, int nlist, const floa
     fill_patch_args<float, __nv_bfloat16>(c, a, c->d_F16);
     a.plist = plist; a.nlist = nlist; a.rloc = rloc; a.xloc = xloc; a.vstride = vstride;
     a.wp = 0;   // patch-local problems: unit weights
+    a.skip_post0 = c->learned_replace ? 1 : 0;
     return launch_patch_kernel<float, __nv_bfloat16>(c, a);
   }
   fill_patch_args<float, float>(c, a, c->d_F32);
   a.plist = plist; a.nlist = nlist; a.rloc = rloc; a.xloc = xloc; a.vstride = vstride;
   a.wp = 0;   // patch-local problems: unit weights
+  a.skip_post0 = c->learned_replace ? 1 : 0;
   return launch_patch_kernel<float, float>(c, a);
 }
 

@@ -667,6 +667,13 @@ lor_status lor_learned_enable(lor_ctx* c, int on) {
   return LOR_OK;
 }
 
+lor_status lor_learned_variant(lor_ctx* c, int variant) {
+  if (!c || !c->setup_done) return LOR_EINVAL;
+  if (variant < 0 || variant > 1) return lor_fail(c, LOR_EINVAL, "learned variant: 0 (add) or 1 (replace)");
+  c->learned_replace = variant == 1;
+  return LOR_OK;
+}
+
 lor_status lor_learned_eval(lor_ctx* c, int npatch, const int* d_ids, const float* d_t, const float* d_delta,
                             float* d_c, float* d_loss, float* h_grad) {
   if (!c || !c->learned || npatch < 1 || npatch > LS(c)->S || !d_ids || !d_t) return LOR_EINVAL;

@@ -254,6 +254,7 @@ struct lor_ctx {
   void* single = nullptr;
   void* learned = nullptr;
   bool learned_on = false;
+  bool learned_replace = false;        // variant: the correction replaces the level-0 post-smoothing
   float* learned_tout = nullptr;       // level-0 residuals of interior patches after the cycle
   size_t bytes = 0;
   long long launches = 0;      // kernels launched by this context

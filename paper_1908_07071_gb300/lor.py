@@ -114,9 +114,11 @@ def load():
         getattr(lib, name).restype = ctypes.c_int
     lib.lor_learned_params.argtypes = [vp, vp, vp, i]
     lib.lor_learned_enable.argtypes = [vp, i]
+    lib.lor_learned_variant.argtypes = [vp, i]
     lib.lor_learned_train.argtypes = [vp, i, i, ctypes.c_float, ctypes.c_ulonglong, vp]
     lib.lor_learned_eval.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
-    for name in ("lor_learned_params", "lor_learned_enable", "lor_learned_train", "lor_learned_eval"):
+    for name in ("lor_learned_params", "lor_learned_enable", "lor_learned_variant", "lor_learned_train",
+                 "lor_learned_eval"):
         getattr(lib, name).restype = ctypes.c_int
     lib.lor_rhs_static.argtypes = [i, i, i, i, i, vp, i, vp, vp]
     lib.lor_rhs_static.restype = ctypes.c_int
@@ -397,6 +399,10 @@ class Solver:
     def learned_enable(self, on=True):
         """Switches the learned per-patch correction (flexible CG) on or off."""
         self._check(self.lib.lor_learned_enable(self.ctx, int(bool(on))))
+
+    def learned_variant(self, variant):
+        """0: correction added after the V(1,1) cycle; 1: it replaces the level-0 post-smoothing."""
+        self._check(self.lib.lor_learned_variant(self.ctx, int(variant)))
 
     def learned_train(self, steps, batch=64, lr=1e-3, seed=0):
         """Trains the network on the GPU (Adam); returns the loss of every step."""

@@ -102,3 +102,32 @@ def test_dg_mixed_precision(form):
     bo = b.cpu().numpy()
     assert np.linalg.norm(bo - A @ x.cpu().numpy()) / np.linalg.norm(bo) <= 1.01e-8
     s.close()
+
+
+class _Hybrid:
+    """The hybrid Schwarz form as the conforming-part preconditioner of B_DG."""
+
+    def __init__(self, B):
+        self.B = B
+
+    def apply(self, r):
+        return self.B.apply_hybrid(r)
+
+
+@pytest.mark.parametrize("mode", [1, 2], ids=["hybrid", "single_patch"])
+def test_dg_apply_P_with_hybrid_and_single_patch_conforming_part(mode):
+    """B_DG = R_B Q_B + E B E^T with B the hybrid form or B(1) (Table 9's DG columns use
+    B(1) and B(V)): the GPU's DG preconditioner after lor_set_schwarz against the
+    oracle's DGPreconditioner built on the same conforming-part preconditioner."""
+    from oracle.single_patch import SinglePatchPreconditioner
+    n, p, form, eta = (2, 3, 2), 4, "br2", 10.0
+    s, m, A = _setup(n, p, form, eta)
+    s.set_schwarz(mode)
+    Bc = _Hybrid(olor.LORPreconditioner(m, p)) if mode == 1 else SinglePatchPreconditioner(m, p)
+    P = odg.DGPreconditioner(m, p, A, Bc)
+    r = random_vector(s.nvec, 33)
+    ref = P.apply(r)
+    z = torch.full((s.nvec,), np.nan, dtype=torch.float64, device="cuda")
+    s.apply_P(torch.from_numpy(r).cuda(), z)
+    assert _rel(z.cpu().numpy(), ref) < 1e-10
+    s.close()

@@ -108,3 +108,43 @@ def test_training_lowers_loss_and_correction_in_fcg():
     # test_exact_patch_solves_bound_the_learned_gain)
     assert it_l <= it_plain
     s.close()
+
+
+def test_replace_variant_cycle_and_training():
+    """Variant 1: the correction replaces the level-0 post-smoothing.  With a zero output
+    layer the FP32 preconditioner equals the oracle's cycle without that post-smoothing
+    (bf16 factors: within 8 u_bf16); training on the variant's own pairs lowers the loss,
+    and the trained correction may not cost iterations against the cycle it completes."""
+    from paper_1908_07071_gb300 import lor
+    from paper_1908_07071_gb300.synthetic import random_vector
+    v, k = make_mesh(3, 4, seed=11, perturb=0.15)
+    p = 4
+    s = lor.Solver(v, k, p, prec=lor.LOR_MIXED, rtol=1e-8, factor_bf16=True)
+    s.learned_variant(1)
+    s.learned_params(_flat(L.init_params(seed=1)).astype(np.float32))   # W3 = 0: no correction
+    s.learned_enable(True)
+    B = olor.LORPreconditioner(Mesh(v, k), p, post_smooth0=False)
+    r = random_vector(s.nvec, 37)
+    z = torch.empty(s.nvec, dtype=torch.float32, device="cuda")
+    s.apply_P(torch.from_numpy(r).float().cuda(), z, prec=lor.LOR_FP32)
+    ref = B.apply(r)
+    err = np.abs(z.double().cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < 8 * 2.0 ** -8, err
+    b = torch.empty(s.nvec, dtype=torch.float64, device="cuda")
+    s.rhs(b, 0)
+    x = torch.zeros_like(b)
+    it_cut, rel_cut = s.solve(b, x)
+    hist = s.learned_train(300, batch=64, lr=2e-3, seed=5)
+    assert hist[-20:].mean() < 0.9 * hist[:5].mean(), hist[::30]
+    x.zero_()
+    it_net, rel_net = s.solve(b, x)
+    s.learned_variant(0)
+    s.learned_enable(False)
+    x.zero_()
+    it_full, _ = s.solve(b, x)
+    print(f"replace variant FCG iterations: cycle without level-0 post-smoothing {it_cut}, "
+          f"with the trained correction {it_net}, full cycle {it_full}; "
+          f"loss {hist[:5].mean():.3f} -> {hist[-20:].mean():.3f}")
+    assert rel_cut <= 1e-8 and rel_net <= 1e-8
+    assert it_net <= it_cut
+    s.close()

@@ -95,6 +95,25 @@ def test_vcycle_error_propagation_is_the_textbook_product(dim, n, p, mg):
         assert A_last.shape == ((1, 1) if pt["v"] == interior else (0, 0))
 
 
+def test_vcycle_without_level0_post_smoothing_drops_the_last_factor():
+    """post_smooth0=False (the cycle the learned correction's replace variant
+    completes): the level-0 error propagation is (I - P V_1 P^T A)(I - M^{-1} A), the
+    textbook product without its last factor, and the coarser levels are unchanged."""
+    v, k = make_mesh(3, 2, seed=5, perturb=0.15)
+    full = lor.LORPreconditioner(Mesh(v, k), 4, coarse=False)
+    cut = lor.LORPreconditioner(Mesh(v, k), 4, coarse=False, post_smooth0=False)
+    lv = [pt for pt in cut.patches if pt["v"] == (1, 1, 1)][0]["levels"]
+    A, P = lv[0]["A"], lv[0]["P"]
+    m = A.shape[0]
+    Lf, Uf = lv[0]["LU"]
+    S = np.eye(m) - np.linalg.solve(Lf @ Uf, A)
+    V1 = _vcycle_matrix(full, lv, 1)
+    np.testing.assert_allclose(_vcycle_matrix(cut, lv, 1), V1, atol=1e-12)
+    E = (np.eye(m) - P @ V1 @ P.T @ A) @ S
+    np.testing.assert_allclose(np.eye(m) - _vcycle_matrix(cut, lv, 0) @ A, E, atol=1e-10)
+    assert np.abs(_vcycle_matrix(full, lv, 0) - _vcycle_matrix(cut, lv, 0)).max() > 1e-3
+
+
 @pytest.mark.parametrize("dim,n,p", [(2, 3, 5), (3, 2, 4)])
 def test_coarse_basis_maps_vertex_coordinates_to_node_coordinates(dim, n, p):
     v, k = make_mesh(dim, n, seed=7, perturb=0.2)
