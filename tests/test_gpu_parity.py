@@ -189,7 +189,10 @@ def test_mixed_precision_reaches_fp64_accuracy(bf16):
     bo = b.cpu().numpy()
     res = np.linalg.norm(bo - cg.apply_A(K, N, xmx.cpu().numpy())) / np.linalg.norm(bo)
     assert res <= rtol * 1.01      # FP64 residual recomputed by the oracle
-    assert itmx <= 3 * it64
+    print(f"mixed precision (bf16 factors {bf16}): {itmx} inner iterations, FP64 PCG {it64}")
+    # the FP32 preconditioner (fp32 or bf16 factors) perturbs B by 1e-7..1e-2 relative and the
+    # refinement restarts the inner flexible CG; measured 80 vs 74 here, 161 vs 152 at Q8 32^3
+    assert itmx <= 1.15 * it64 + 2
     s64.close()
     smx.close()
 
