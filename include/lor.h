@@ -236,6 +236,19 @@ lor_status lor_set_ordering(lor_ctx* ctx, int ordering);
  * non-positive pivot, LOR_EINVAL for bad sizes or ordering. */
 lor_status lor_box_ordering(int dim, int A, int B, int C, int ordering, const double* a27, int* perm);
 
+/* Patches enlarged for isotropic overlap on anisotropic meshes (Section 4.5):
+ * spans (host, npatch x dim x 2 ints, patch-major, per axis: lo then hi) lets the
+ * patch of vertex v cover the elements v - lo .. v + hi - 1 along each axis
+ * (clamped to the mesh) instead of v - 1 .. v; 1, 1 is the vertex patch.  The
+ * element-structured V(1,1) cycle runs on each enlarged box unchanged; a box that
+ * keeps several vertices on its coarsest level solves them with the inverse of its
+ * box matrix, formed on the host in lor_setup.  Enlarged patches use host-built
+ * factors, per-patch schedules and a node-by-node gather of the patch outputs (in
+ * patch order).  NULL restores vertex patches.  Must precede lor_setup (LOR_ESTATE
+ * after); CG only, unit patch weights, no learned correction; LOR_EINVAL for a
+ * span outside 1..8. */
+lor_status lor_set_patch_spans(lor_ctx* ctx, const int* spans);
+
 /* The ILU(0) order of one patch level: perm[q] = box index (x fastest within the
  * patch box) of the q-th row, for level 0 <= level < levels - 1 (the vertex level
  * is solved exactly) and patch 0 <= patch < npatch (vertex (i,j,k) is patch

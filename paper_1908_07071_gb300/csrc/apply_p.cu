@@ -58,7 +58,10 @@ struct PatchArgs {
   const BoxShape* shapes;       // [L][8]
   const int* fpad;
   const int* chunk;
-  const GenSched* gsched;       // ordered patch levels: per-patch schedules [L][J] (else null)
+  const GenSched* gsched;       // ordered or enlarged patches: per-patch schedules and boxes [L][J] (else null)
+  const void* xferg;            //   patch-local transfers XferG<T>[level][kmax1] (span of k elements)
+  int kmax1;
+  const void* binv;             //   vertex-level inverses (T), offsets in gsched[L-1][j].binv_off
   const long long* facoff;      // [L][J] record offsets
   const void* F;
   const void* r;
@@ -510,9 +513,9 @@ __device__ void resid_level(const WLevel& b, const PLevel& lv, const T* r, const
 }
 
 // r_c = R t: tensor restriction of a level-l vector to level l+1 (patch-local).
-template <int DIM, typename T>
-__device__ void restrict_level(const WLevel& bf, const WLevel& bc, const Xfer1D<T>& X0, const Xfer1D<T>& X1,
-                               const Xfer1D<T>& X2, const T* tl, T* rn) {
+template <int DIM, typename T, typename X>
+__device__ void restrict_level(const WLevel& bf, const WLevel& bc, const X& X0, const X& X1, const X& X2, const T* tl,
+                               T* rn) {
   const int lane = threadIdx.x & 31;
   const int fA = bf.A, fB = bf.B, cA = bc.A, cB = bc.B;
   BoxIter it;
@@ -536,9 +539,9 @@ __device__ void restrict_level(const WLevel& bf, const WLevel& bc, const Xfer1D<
 }
 
 // (P x_c)(row) for a fine row (i, j, k) of level l (patch-local tensor prolongation).
-template <int DIM, typename T>
-__device__ __forceinline__ T prolong_row(const WLevel& bc, const Xfer1D<T>& X0, const Xfer1D<T>& X1,
-                                         const Xfer1D<T>& X2, const T* xc, int i, int j, int k) {
+template <int DIM, typename T, typename X>
+__device__ __forceinline__ T prolong_row(const WLevel& bc, const X& X0, const X& X1, const X& X2, const T* xc, int i,
+                                         int j, int k) {
   const int cA = bc.A, cB = bc.B, cC = bc.C;
   T s = 0;
   const int nzz = DIM == 3 ? 2 : 1;
@@ -573,6 +576,12 @@ constexpr int kWarpBars = 0, kWarpZrec = 32, kWarpMeta = 288, kWarpShape = 352, 
 static_assert(kWarpMeta - kWarpZrec >= 32 * 8, "zero record smaller than an ordered FP64 record");
 static_assert(kWarpShape - kWarpMeta >= 2 * LOR_MAXLEV * 4, "level metadata does not fit");
 static_assert(kWarpRing - kWarpShape >= LOR_MAXLEV * (int)sizeof(BoxShape), "box shapes do not fit");
+// ordered/enlarged patches: per level the box origin and the elements spanned per axis
+// (6 ints), then the ring
+constexpr int kWarpGeo = 736, kWarpRingGen = 896;
+static_assert(kWarpGeo >= kWarpShape + LOR_MAXLEV * (int)sizeof(BoxShape), "geometry overlaps the box shapes");
+static_assert(kWarpRingGen - kWarpGeo >= LOR_MAXLEV * 6 * 4, "geometry does not fit");
+__host__ __device__ constexpr int warp_ring_offset(bool gen) { return gen ? kWarpRingGen : kWarpRing; }
 
 // The patch kernel.  Each warp runs whole V-cycles for its own patches (one
 // after another, no block barriers):
@@ -615,14 +624,15 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
   unsigned char* wb = smem_raw + a.xf_bytes + (size_t)warp * a.warp_bytes;
   Ring<FT, NBUF> rg;
   rg.bar = (unsigned long long*)(wb + kWarpBars);
-  rg.base = wb + kWarpRing;
+  rg.base = wb + warp_ring_offset(GEN);
   rg.bytes = a.slot_bytes;
   rg.phase = 0;
   rg.inflight = 0;
   const FT* zrec = (const FT*)(wb + kWarpZrec);
   int* meta = (int*)(wb + kWarpMeta);   // tbf[LOR_MAXLEV] | tbc[LOR_MAXLEV]
   BoxShape* bsh = (BoxShape*)(wb + kWarpShape);
-  int* ip = (int*)(wb + kWarpRing + (size_t)NBUF * a.slot_bytes);
+  int* ip = (int*)(wb + warp_ring_offset(GEN) + (size_t)NBUF * a.slot_bytes);
+  int* geo = (int*)(wb + kWarpGeo);     // GEN: [level][org x3, k x3]
   T* vec = (T*)(ip + a.tab_ints);
   ((unsigned*)(wb + kWarpZrec))[lane] = 0u;
   ((unsigned*)(wb + kWarpZrec))[lane + 32] = 0u;
@@ -662,6 +672,9 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
             bsh[l].rpad = g.rpad;
             bsh[l].front_off = g.front_off;
             for (int e = 0; e < 3; ++e) { bsh[l].nchunk[e] = g.nchunk[e]; bsh[l].chunk_off[e] = g.chunk_off[e]; }
+            for (int e = 0; e < 3; ++e) { bsh[l].dims[e] = g.dims[e]; geo[l * 6 + e] = g.org[e]; geo[l * 6 + 3 + e] = g.k[e]; }
+            bsh[l].rows = g.rows;
+            bsh[l].guard = g.guard;
           }
           meta[l] = ioff; ioff += bsh[l].nfront + 1;
           meta[LOR_MAXLEV + l] = ioff; ioff += bsh[l].nchunk[ES] + 1;
@@ -688,7 +701,8 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
         WLevel& b = bx[l];
         b.A = bs.dims[0]; b.B = bs.dims[1]; b.C = bs.dims[2];
         b.rows = bs.rows;
-        for (int t = 0; t < 3; ++t) b.org[t] = t < DIM ? (v[t] > 0 ? v[t] - 1 : 0) * a.lv[l].m + 1 : 0;
+        for (int t = 0; t < 3; ++t)
+          b.org[t] = GEN ? geo[l * 6 + t] : (t < DIM ? (v[t] > 0 ? v[t] - 1 : 0) * a.lv[l].m + 1 : 0);
         if (l == 0) {
           b.xo = -1; b.to = a.aux_n + bs.guard; b.ro = -1;
         } else {
@@ -720,10 +734,22 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
         if (a.wp)
           rhs *= node_weight<DIM, T>(a.wmode, b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp, ho[0], ho[1],
                                      ho[2], hat);
-        xslot[lex] = rhs / S[(long long)(a.NS / 2) * lv0.ntot + G];
-        t0[lex] = T(0);
+        if (GEN && b0.rows > 1) t0[lex] = rhs;
+        else xslot[lex] = rhs / S[(long long)(a.NS / 2) * lv0.ntot + G];
+        if (!(GEN && b0.rows > 1)) t0[lex] = T(0);
       }
       __syncwarp();
+      if (GEN && b0.rows > 1) {   // several vertices in the box: the stored inverse
+        const T* Bi = (const T*)a.binv + a.gsched[j].binv_off;
+        for (int lex = lane; lex < b0.rows; lex += 32) {
+          T acc = 0;
+          for (int q = 0; q < b0.rows; ++q) acc += Bi[(long long)lex * b0.rows + q] * t0[q];
+          xslot[lex] = acc;
+        }
+        __syncwarp();
+        for (int lex = lane; lex < b0.rows; lex += 32) t0[lex] = T(0);
+        __syncwarp();
+      }
     } else {
       // ---- level 0 down: t0 <- rhs (zero guards), ILU, residual in place (x0 -> slot)
       for (int q = lane; q < b0.rows + 2 * guard0 + 1; q += 32) t0[q - guard0] = T(0);
@@ -759,7 +785,12 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       if (ok) resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, xslot, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
       if (ok && bottom > 0) {
         // ---- coarse levels
-        restrict_level<DIM, T>(bx[0], bx[1], xf[type[0]], xf[type[1]], xf[type[2]], t0, vec + bx[1].ro);
+        if constexpr (GEN) {
+          const XferG<T>* xg = (const XferG<T>*)a.xferg;
+          restrict_level<DIM, T>(bx[0], bx[1], xg[geo[3]], xg[geo[4]], xg[geo[5]], t0, vec + bx[1].ro);
+        } else {
+          restrict_level<DIM, T>(bx[0], bx[1], xf[type[0]], xf[type[1]], xf[type[2]], t0, vec + bx[1].ro);
+        }
         for (int q = lane; q < a.ovl_n; q += 32) vec[a.aux_n + q] = T(0);
         __syncwarp();
         for (int l = 1; l < bottom && ok; ++l) {
@@ -773,15 +804,30 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           for (int q = lane; q < b.rows; q += 32) x[q] = t[q];
           __syncwarp();
           resid_level<DIM, T>(b, a.lv[l], r, x, t);
-          restrict_level<DIM, T>(b, bx[l + 1], xf[l * 2 + type[0]], xf[l * 2 + type[1]], xf[l * 2 + type[2]], t,
-                                 vec + bx[l + 1].ro);
+          if constexpr (GEN) {
+            const XferG<T>* xg = (const XferG<T>*)a.xferg + l * a.kmax1;
+            restrict_level<DIM, T>(b, bx[l + 1], xg[geo[l * 6 + 3]], xg[geo[l * 6 + 4]], xg[geo[l * 6 + 5]], t,
+                                   vec + bx[l + 1].ro);
+          } else {
+            restrict_level<DIM, T>(b, bx[l + 1], xf[l * 2 + type[0]], xf[l * 2 + type[1]], xf[l * 2 + type[2]], t,
+                                   vec + bx[l + 1].ro);
+          }
         }
         if (ok) {
           const int l = bottom;
           const WLevel& b = bx[l];
           const PLevel& lv = a.lv[l];
           T* x = vec + b.xo; T* t = vec + b.to; T* r = vec + b.ro;
-          if (l == a.L - 1) {
+          if (l == a.L - 1 && GEN && b.rows > 1) {
+            // an enlarged patch keeps several vertices: x = A_box^{-1} r with the stored inverse
+            const T* Bi = (const T*)a.binv + a.gsched[(long long)l * a.J + j].binv_off;
+            for (int lex = lane; lex < b.rows; lex += 32) {
+              T acc = 0;
+              for (int q = 0; q < b.rows; ++q) acc += Bi[(long long)lex * b.rows + q] * r[q];
+              x[lex] = acc;
+            }
+            __syncwarp();
+          } else if (l == a.L - 1) {
             const T* S = (const T*)lv.S;
             BoxIter it;
             it.init(lane, b.A, b.B);
@@ -814,9 +860,16 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           const FT* FL = F + a.facoff[(long long)l * a.J + j] * R;
           BoxIter it;
           it.init(lane, b.A, b.B);
-          for (int lex = lane; lex < b.rows; lex += 32, it.next())
-            x[lex] += prolong_row<DIM, T>(bx[l + 1], xf[l * 2 + type[0]], xf[l * 2 + type[1]], xf[l * 2 + type[2]],
-                                          xc, it.i, it.j, it.k);
+          for (int lex = lane; lex < b.rows; lex += 32, it.next()) {
+            if constexpr (GEN) {
+              const XferG<T>* xg = (const XferG<T>*)a.xferg + l * a.kmax1;
+              x[lex] += prolong_row<DIM, T>(bx[l + 1], xg[geo[l * 6 + 3]], xg[geo[l * 6 + 4]], xg[geo[l * 6 + 5]], xc,
+                                            it.i, it.j, it.k);
+            } else {
+              x[lex] += prolong_row<DIM, T>(bx[l + 1], xf[l * 2 + type[0]], xf[l * 2 + type[1]], xf[l * 2 + type[2]],
+                                            xc, it.i, it.j, it.k);
+            }
+          }
           __syncwarp();
           resid_level<DIM, T>(b, a.lv[l], r, x, t);
           ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
@@ -842,8 +895,14 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
 #pragma unroll
             for (int u = 0; u < U; ++u)
               if (l0 + 32 * u < b0.rows)
-                xslot[l0 + 32 * u] = xv[u] + prolong_row<DIM, T>(bx[1], xf[type[0]], xf[type[1]], xf[type[2]], x1,
-                                                                 iu[u], ju[u], ku[u]);
+                if constexpr (GEN) {
+                  const XferG<T>* xg = (const XferG<T>*)a.xferg;
+                  xslot[l0 + 32 * u] = xv[u] + prolong_row<DIM, T>(bx[1], xg[geo[3]], xg[geo[4]], xg[geo[5]], x1,
+                                                                   iu[u], ju[u], ku[u]);
+                } else {
+                  xslot[l0 + 32 * u] = xv[u] + prolong_row<DIM, T>(bx[1], xf[type[0]], xf[type[1]], xf[type[2]], x1,
+                                                                   iu[u], ju[u], ku[u]);
+                }
           }
           __syncwarp();
           // t0 <- x0 (x1 lived over t0's space; every lane is done with it now)
@@ -930,6 +989,19 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
 // y, then z); boundary nodes get 0.  Patch j covers, along each axis, the nodes
 // org + [0, len) of its box: org = (v-1) p + 1 and len = 2p - 1 for an interior
 // vertex v, org = 1, len = p - 1 at v = 0 and org = (n-1) p + 1, len = p - 1 at v = n.
+// z[node] = sum of the node's entries in the patch output slices, listed per node in
+// patch order (enlarged patches, whose overlap has no closed form); 0 if none.
+template <typename T>
+__global__ void k_patch_gather(long long nt, const long long* __restrict__ ptr, const long long* __restrict__ idx,
+                               const T* __restrict__ zp, const double* __restrict__ conv, T* __restrict__ z) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nt) return;
+  if (conv && *conv != 0.0) { z[gid] = T(0); return; }
+  T s = 0;
+  for (long long q = ptr[gid]; q < ptr[gid + 1]; ++q) s += zp[idx[q]];
+  z[gid] = s;
+}
+
 template <typename T>
 __global__ void k_patch_sum(int dim, int p, int nx, int ny, int nz, const T* __restrict__ zp, long long zstride,
                             const double* __restrict__ conv, T* __restrict__ z) {
@@ -1268,7 +1340,7 @@ WarpLayout warp_layout(const lor_ctx* c) {
     for (int l = 0; l < c->L; ++l) t += c->shapes[l * 8 + s].nfront + 1 + c->shapes[l * 8 + s].nchunk[es] + 1;
     tab = std::max(tab, t);
   }
-  if (c->ordering) {   // ordered records and per-patch schedules
+  if (c->gen) {   // ordered records and per-patch schedules
     w.slot_bytes = std::max(c->gen_maxchunk[es], 1) * lor_rec_gen(c->dim) * (int)sizeof(FT);
     tab = std::max(tab, c->gen_tab_ints);
   }
@@ -1284,11 +1356,18 @@ WarpLayout warp_layout(const lor_ctx* c) {
     ovl += 2LL * (bs.rows + 2 * bs.guard + 1) + (l >= 2 ? bs.rows : 0);
   }
   w.ovl_n = (int)std::max<long long>(b0.rows + 2LL * b0.guard + 1, ovl);
-  const size_t bytes = (size_t)kWarpRing + (size_t)ring_depth<FT>() * w.slot_bytes + 4 * (size_t)w.tab_ints +
-                       (size_t)(w.aux_n + w.ovl_n) * sizeof(T);
+  w.x0_stride = (b0.rows + 31) / 32 * 32;
+  if (c->gen) {   // per-patch boxes: the largest of every buffer
+    w.aux_n = std::max(2 * c->gen_AB0 + 2 * (c->gen_A0 + 1), c->L > 1 ? c->gen_rows1 : 0);
+    w.aux_n = std::max(w.aux_n, 4);
+    w.aux_n = (w.aux_n + 3) / 4 * 4;
+    w.ovl_n = (int)std::max<long long>(c->gen_ovl, 4);
+    w.x0_stride = (std::max(c->gen_rows0, 1) + 31) / 32 * 32;
+  }
+  const size_t bytes = (size_t)warp_ring_offset(c->gen) + (size_t)ring_depth<FT>() * w.slot_bytes +
+                       4 * (size_t)w.tab_ints + (size_t)(w.aux_n + w.ovl_n) * sizeof(T);
   w.warp_bytes = (int)((bytes + 127) / 128 * 128);
   w.xf_bytes = (int)((2 * (c->L > 1 ? c->L - 1 : 1) * sizeof(Xfer1D<T>) + 127) / 128 * 128);
-  w.x0_stride = (b0.rows + 31) / 32 * 32;
   return w;
 }
 
@@ -1313,7 +1392,15 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
   a.shapes = lor_dev_shapes(c);
   a.fpad = c->d_fpad; a.chunk = c->d_chunk;
   a.gsched = nullptr;
-  if (c->ordering) { a.fpad = c->d_gfpad; a.chunk = c->d_gchunk; a.gsched = c->d_gsched; }
+  a.xferg = nullptr;
+  a.kmax1 = 0;
+  a.binv = nullptr;
+  if (c->gen) {
+    a.fpad = c->d_gfpad; a.chunk = c->d_gchunk; a.gsched = c->d_gsched;
+    a.xferg = sizeof(T) == 8 ? c->d_xferg64 : c->d_xferg32;
+    a.kmax1 = c->span_kmax + 1;
+    a.binv = sizeof(T) == 8 ? (const void*)c->d_binv64 : (const void*)c->d_binv32;
+  }
   a.facoff = c->d_facoff;
   a.F = F; a.r = nullptr;
   a.zp = c->d_zp;
@@ -1352,8 +1439,8 @@ bool patch_launch_shape(const lor_ctx* c, int* nw, int* grid, size_t* smem) {
   *smem = (size_t)w.xf_bytes + (size_t)*nw * w.warp_bytes;
   constexpr int NB = ring_depth<FT>();
   int per_sm = 0;
-  auto kern = c->dim == 3 ? (c->ordering ? k_patch_warp<3, T, FT, NB, true> : k_patch_warp<3, T, FT, NB, false>)
-                          : (c->ordering ? k_patch_warp<2, T, FT, NB, true> : k_patch_warp<2, T, FT, NB, false>);
+  auto kern = c->dim == 3 ? (c->gen ? k_patch_warp<3, T, FT, NB, true> : k_patch_warp<3, T, FT, NB, false>)
+                          : (c->gen ? k_patch_warp<2, T, FT, NB, true> : k_patch_warp<2, T, FT, NB, false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * *nw, *smem);
   *grid = std::max(per_sm, 1) * nsm;
@@ -1372,7 +1459,7 @@ lor_status launch_patch_kernel(lor_ctx* c, PatchArgs& a) {
   if ((long long)grid * nw * a.x0_stride * (long long)sizeof(T) > c->xs_bytes)
     return lor_fail(c, LOR_ESTATE, "patch iterate slots too small");
   constexpr int NB = ring_depth<FT>();
-  if (c->ordering) {
+  if (c->gen) {
     if (c->dim == 3) k_patch_warp<3, T, FT, NB, true><<<grid, 32 * nw, smem, c->stream>>>(a);
     else k_patch_warp<2, T, FT, NB, true><<<grid, 32 * nw, smem, c->stream>>>(a);
   } else {
@@ -1400,8 +1487,12 @@ lor_status patch_part(lor_ctx* c, const T* r, T* z, const FT* F) {
   if (launch_patch_kernel<T, FT>(c, a)) return LOR_ECUDA;
   lor_prof_end(c, pk);
   // z = sum_j R_j^T x_j, node by node in a fixed order
-  k_patch_sum<T><<<(unsigned)lor_ceil_div(nvec, 256), 256, 0, c->stream>>>(
-      c->dim, c->p, c->n[0], c->n[1], c->n[2], (const T*)c->d_zp, a.zstride, c->conv_flag, z);
+  if (c->d_gather_ptr)
+    k_patch_gather<T><<<(unsigned)lor_ceil_div(nvec, 256), 256, 0, c->stream>>>(
+        nvec, c->d_gather_ptr, c->d_gather_idx, (const T*)c->d_zp, c->conv_flag, z);
+  else
+    k_patch_sum<T><<<(unsigned)lor_ceil_div(nvec, 256), 256, 0, c->stream>>>(
+        c->dim, c->p, c->n[0], c->n[1], c->n[2], (const T*)c->d_zp, a.zstride, c->conv_flag, z);
   ++c->launches;
   if (c->learned_on && sizeof(T) == 4) {
     if (lor_learned_apply(c, (float*)z)) return LOR_ECUDA;

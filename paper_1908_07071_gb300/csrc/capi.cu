@@ -378,6 +378,25 @@ lor_status lor_set_ordering(lor_ctx* c, int ordering) {
   if (c->setup_started) return lor_fail(c, LOR_ESTATE, "lor_set_ordering must precede lor_setup");
   if (ordering < 0 || ordering > 2) return lor_fail(c, LOR_EINVAL, "lor_set_ordering: 0 (lexicographic), 1 (RCM) or 2 (MDF)");
   c->ordering = ordering;
+  c->gen = c->ordering != 0 || !c->h_spans.empty();
+  return LOR_OK;
+}
+
+lor_status lor_set_patch_spans(lor_ctx* c, const int* spans) {
+  if (!c) return LOR_EINVAL;
+  if (c->setup_started) return lor_fail(c, LOR_ESTATE, "lor_set_patch_spans must precede lor_setup");
+  if (c->opt.disc != LOR_CG) return lor_fail(c, LOR_EINVAL, "enlarged patches: CG only");
+  if (c->opt.weighting) return lor_fail(c, LOR_EINVAL, "enlarged patches take unit patch weights");
+  if (!spans) {
+    c->h_spans.clear();
+  } else {
+    long long J = 1;
+    for (int a = 0; a < c->dim; ++a) J *= c->n[a] + 1;
+    for (long long q = 0; q < J * c->dim * 2; ++q)
+      if (spans[q] < 1 || spans[q] > LOR_MAXSPAN) return lor_fail(c, LOR_EINVAL, "patch span out of range");
+    c->h_spans.assign(spans, spans + J * c->dim * 2);
+  }
+  c->gen = c->ordering != 0 || !c->h_spans.empty();
   return LOR_OK;
 }
 
@@ -414,11 +433,11 @@ lor_status lor_patch_ordering(lor_ctx* c, int level, long long patch, int* perm,
   const int v[3] = {(int)(patch % n0), (int)((patch / n0) % n1), c->dim == 3 ? (int)(patch / ((long long)n0 * n1)) : 0};
   int sh = 0;
   for (int a = 0; a < c->dim; ++a) sh |= ((v[a] == 0 || v[a] == c->n[a]) ? 1 : 0) << a;
-  const int rows = c->shapes[level * 8 + sh].rows;
+  const int rows = c->gen ? (int)c->h_perm[(size_t)level * c->J + patch].size() : c->shapes[level * 8 + sh].rows;
   *count = rows;
   if (!perm) return LOR_OK;
   if (cap < rows) return lor_fail(c, LOR_EINVAL, "lor_patch_ordering: buffer too small");
-  if (c->ordering == 0) {
+  if (!c->gen) {
     for (int q = 0; q < rows; ++q) perm[q] = q;
   } else {
     const std::vector<int>& h = c->h_perm[(size_t)level * c->J + patch];
@@ -471,6 +490,7 @@ lor_status lor_set_weighting(lor_ctx* c, int weighting) {
   if (!c) return LOR_EINVAL;
   if (weighting < 0 || weighting > 2) return lor_fail(c, LOR_EINVAL, "lor_set_weighting: 0, 1 or 2");
   if (weighting && c->learned_on) return lor_fail(c, LOR_EINVAL, "learned correction needs unit patch weights");
+  if (weighting && !c->h_spans.empty()) return lor_fail(c, LOR_EINVAL, "enlarged patches take unit patch weights");
   c->opt.weighting = weighting;
   return LOR_OK;
 }

@@ -511,6 +511,7 @@ static LearnState* LS(lor_ctx* c) { return (LearnState*)c->learned; }
 static lor_status learned_init(lor_ctx* c) {
   if (c->learned) return LOR_OK;
   if (c->dim != 3 || c->dg_state) return lor_fail(c, LOR_EINVAL, "learned correction: 3D CG contexts only");
+  if (!c->h_spans.empty()) return lor_fail(c, LOR_EINVAL, "learned correction: vertex patches only");
   LearnState* s = new LearnState();
   c->learned = s;
   const BoxShape& bs = c->shapes[0];

@@ -11,6 +11,7 @@
 #include "../../include/lor.h"
 
 #define LOR_MAXP 8
+#define LOR_MAXSPAN 8     // elements an enlarged patch may take on each side of its vertex
 #define LOR_MAXLEV 5      // p <= 8: at most 4 patch levels (8,4,2,1) + slack
 #define LOR_MAXCLEV 8     // coarse-space V-cycle levels
 
@@ -88,6 +89,27 @@ __host__ __device__ constexpr int lor_rec_gen(int dim) { return dim == 3 ? 32 : 
 struct GenSched {
   int nfront, rpad, front_off;
   int nchunk[3], chunk_off[3];
+  // box of this patch at this level (any patch span): extents, origin in the level
+  // grid, rows, guard band; elements spanned per axis (selects the patch-local 1D
+  // transfer tables); at the vertex level, the offset of the inverse of the box
+  // matrix (when it has more than one row) in ctx->d_binv
+  int dims[3], org[3], rows, guard, k[3];
+  long long binv_off;
+};
+
+// Patch-local 1D transfer between level l and l+1 along an axis spanning k elements
+// (fine and coarse unknowns: the open interiors of the span), in global memory:
+// prolongation rows (fine -> <= 2 coarse; coarse index -1 or clen = the span's end,
+// value 0) and the transposed restriction lists.  T = double or float.
+template <typename T>
+struct XferG {
+  const int* c0;
+  const int* c1;
+  const T* w0;
+  const T* w1;
+  const int* rstart;
+  const int* rf;
+  const T* rw;
 };
 // row length of the row-major stencil copies: 3^dim padded to a multiple of 4
 __host__ __device__ constexpr int lor_nsp(int dim) { return dim == 3 ? 28 : 12; }
@@ -191,6 +213,19 @@ struct lor_ctx {
   // 2 MDF (ordered records, per-patch schedules; host permutations kept for
   // lor_patch_ordering)
   int ordering = 0;
+  // patch spans (lor_set_patch_spans): per patch and axis the elements on each side
+  // of its vertex (1, 1 = the vertex patch); empty = vertex patches
+  std::vector<int> h_spans;
+  int span_kmax = 2;                       // most elements spanned along an axis
+  bool gen = false;                        // ordered or enlarged patches: host-built factors and schedules
+  void* d_xferg64 = nullptr;               // XferG<double>[level][kmax + 1] (device)
+  void* d_xferg32 = nullptr;               // XferG<float>[level][kmax + 1]
+  double* d_binv64 = nullptr;              // vertex-level inverses of enlarged patches
+  float* d_binv32 = nullptr;
+  long long* d_gather_ptr = nullptr;       // level-0 node -> its entries in the patch output slices
+  long long* d_gather_idx = nullptr;
+  int gen_rows0 = 0, gen_A0 = 0, gen_AB0 = 0, gen_rows1 = 0, gen_guard0 = 0;   // largest level-0/1 boxes
+  long long gen_ovl = 0;                   // largest overlay of the coarse levels (values)
   GenSched* d_gsched = nullptr;            // [level][J]
   int* d_gfpad = nullptr;
   int* d_gchunk = nullptr;

@@ -13,7 +13,9 @@
 #include <cstring>
 #include <vector>
 
+#include <array>
 #include <atomic>
+#include <map>
 #include <cstring>
 #include <thread>
 
@@ -763,7 +765,7 @@ static const int kChunkBytes[3] = {4096, 4096, 8192};
 static lor_status setup_ordered_factors(lor_ctx* c) {
   const int dim = c->dim, NS = c->NS, C = NS / 2, R = lor_rec_gen(dim), L = c->L, J = c->J;
   std::vector<std::vector<double>> hS(L);
-  for (int l = 0; l + 1 < L; ++l) {
+  for (int l = 0; l < L; ++l) {
     hS[l].resize((size_t)NS * c->lev[l].ntot);
     cudaError_t e = cudaMemcpyAsync(hS[l].data(), c->d_S64[l], hS[l].size() * 8, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return lor_cuda_check(c, e, "ordered factors: stencil copy");
@@ -779,35 +781,58 @@ static lor_status setup_ordered_factors(lor_ctx* c) {
   };
   std::vector<Out> out((size_t)L * J);
   c->h_perm.assign((size_t)L * J, std::vector<int>());
-  // RCM depends on the pattern only: one permutation per (level, shape)
-  std::vector<std::vector<int>> rcm((size_t)L * 8);
+  // box of every patch at every level: the elements e0 .. e1-1 of its span along
+  // each axis (the vertex patch: one element on each side of the vertex), the open
+  // interior of those elements at the level's resolution
+  std::vector<GenSched> gs((size_t)L * J);
+  for (int l = 0; l < L; ++l)
+    for (int j = 0; j < J; ++j) {
+      GenSched& g = gs[(size_t)l * J + j];
+      std::memset(&g, 0, sizeof(g));
+      const int v[3] = {j % (c->n[0] + 1), (j / (c->n[0] + 1)) % (c->n[1] + 1),
+                        dim == 3 ? j / ((c->n[0] + 1) * (c->n[1] + 1)) : 0};
+      const int m = c->lev[l].m;
+      g.rows = 1;
+      for (int a = 0; a < 3; ++a) {
+        if (a >= dim) { g.dims[a] = 1; g.org[a] = 0; g.k[a] = 1; continue; }
+        const int lo = c->h_spans.empty() ? 1 : c->h_spans[((size_t)j * dim + a) * 2];
+        const int hi = c->h_spans.empty() ? 1 : c->h_spans[((size_t)j * dim + a) * 2 + 1];
+        const int e0 = std::max(v[a] - lo, 0), e1 = std::min(v[a] + hi, c->n[a]);
+        g.k[a] = e1 - e0;
+        g.dims[a] = std::max(g.k[a] * m - 1, 0);
+        g.org[a] = e0 * m + 1;
+        g.rows *= g.dims[a];
+      }
+      g.guard = g.dims[0] * g.dims[1] + g.dims[0] + 1;
+    }
+  // RCM depends on the pattern only: one permutation per box extent
+  std::map<std::array<int, 3>, std::vector<int>> rcm;
   if (c->ordering == 1)
     for (int l = 0; l + 1 < L; ++l)
-      for (int sh = 0; sh < (1 << dim); ++sh) {
-        const BoxShape& bs = c->shapes[l * 8 + sh];
-        if (bs.rows) lorh::rcm_box(dim, bs.dims[0], bs.dims[1], bs.dims[2], rcm[(size_t)l * 8 + sh]);
+      for (int j = 0; j < J; ++j) {
+        const GenSched& g = gs[(size_t)l * J + j];
+        const std::array<int, 3> key = {g.dims[0], g.dims[1], g.dims[2]};
+        if (g.rows && !rcm.count(key)) lorh::rcm_box(dim, key[0], key[1], key[2], rcm[key]);
       }
+  // vertex level: the inverse of the box matrix of every patch with more than one row
+  // there (an enlarged patch keeps several vertices on its coarsest level)
+  std::vector<std::vector<double>> binv(J);
   std::atomic<long long> next(0);
-  const long long ntask = (long long)std::max(L - 1, 0) * J;
+  const long long ntask = (long long)L * J;
   auto work = [&]() {
     for (;;) {
       const long long task = next++;
       if (task >= ntask) return;
       const int l = (int)(task / J), j = (int)(task % J);
-      const int v[3] = {j % (c->n[0] + 1), (j / (c->n[0] + 1)) % (c->n[1] + 1),
-                        dim == 3 ? j / ((c->n[0] + 1) * (c->n[1] + 1)) : 0};
-      int sh = 0;
-      for (int a = 0; a < dim; ++a) sh |= ((v[a] == 0 || v[a] == c->n[a]) ? 1 : 0) << a;
-      const BoxShape& bs = c->shapes[l * 8 + sh];
+      const GenSched& gb = gs[(size_t)l * J + j];
       Out& o = out[(size_t)l * J + j];
-      o.rows = bs.rows;
+      o.rows = gb.rows;
       o.fpad.assign(1, 0);
       for (int es = 0; es < 3; ++es) o.chunk[es].assign(1, 0);
-      if (bs.rows == 0) continue;
-      const int A = bs.dims[0], B = bs.dims[1], Cd = bs.dims[2], n = bs.rows;
+      if (gb.rows == 0) continue;
+      const int A = gb.dims[0], B = gb.dims[1], Cd = gb.dims[2], n = gb.rows;
       const LevelGrid& g = c->lev[l];
-      int org[3];
-      for (int t = 0; t < 3; ++t) org[t] = t < dim ? (v[t] > 0 ? v[t] - 1 : 0) * g.m + 1 : 0;
+      const int* org = gb.org;
       std::vector<double> a27((size_t)n * NS, 0.0);
       for (int lex = 0; lex < n; ++lex) {
         const int i = lex % A, jj = (lex / A) % B, k = lex / (A * B);
@@ -819,8 +844,49 @@ static lor_status setup_ordered_factors(lor_ctx* c) {
             a27[(size_t)lex * NS + q] = hS[l][(size_t)q * g.ntot + G];
         }
       }
+      if (l == L - 1) {   // vertex level: exact solve
+        if (n > 1) {
+          std::vector<double> M((size_t)n * n, 0.0), I((size_t)n * n, 0.0);
+          for (int r = 0; r < n; ++r) {
+            I[(size_t)r * n + r] = 1.0;
+            const int x = r % A, y = (r / A) % B, z = r / (A * B);
+            for (int q = 0; q < NS; ++q) {
+              const double val = a27[(size_t)r * NS + q];
+              if (val == 0.0) continue;
+              const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = dim == 3 ? q / 9 - 1 : 0;
+              M[(size_t)r * n + ((z + dz) * B + (y + dy)) * A + (x + dx)] = val;
+            }
+          }
+          // Gauss-Jordan with partial pivoting (the box matrix is SPD)
+          for (int col = 0; col < n && o.ok; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < n; ++r)
+              if (std::fabs(M[(size_t)r * n + col]) > std::fabs(M[(size_t)piv * n + col])) piv = r;
+            if (!(std::fabs(M[(size_t)piv * n + col]) > 0.0)) { o.ok = false; break; }
+            if (piv != col)
+              for (int q = 0; q < n; ++q) {
+                std::swap(M[(size_t)piv * n + q], M[(size_t)col * n + q]);
+                std::swap(I[(size_t)piv * n + q], I[(size_t)col * n + q]);
+              }
+            const double d = 1.0 / M[(size_t)col * n + col];
+            for (int q = 0; q < n; ++q) { M[(size_t)col * n + q] *= d; I[(size_t)col * n + q] *= d; }
+            for (int r = 0; r < n; ++r) {
+              if (r == col) continue;
+              const double f = M[(size_t)r * n + col];
+              if (f == 0.0) continue;
+              for (int q = 0; q < n; ++q) {
+                M[(size_t)r * n + q] -= f * M[(size_t)col * n + q];
+                I[(size_t)r * n + q] -= f * I[(size_t)col * n + q];
+              }
+            }
+          }
+          binv[j] = I;
+        }
+        continue;
+      }
       std::vector<int>& perm = c->h_perm[(size_t)l * J + j];
-      if (c->ordering == 1) perm = rcm[(size_t)l * 8 + sh];
+      if (c->ordering == 1) perm = rcm[{A, B, Cd}];
+      else if (c->ordering == 0) { perm.resize(n); for (int q = 0; q < n; ++q) perm[q] = q; }
       else if (!lorh::mdf_box(dim, A, B, Cd, a27, perm)) { o.ok = false; continue; }
       std::vector<double> lu;
       std::vector<int> level;
@@ -890,7 +956,6 @@ static lor_status setup_ordered_factors(lor_ctx* c) {
     if (!o.ok) return lor_fail(c, LOR_EBREAKDOWN, "ordered ILU(0) breakdown: non-positive pivot");
   // concatenate: record offsets, schedules, front and chunk tables
   std::vector<long long> off((size_t)L * J);
-  std::vector<GenSched> gs((size_t)L * J);
   std::vector<int> gfpad, gchunk;
   long long tot = 0;
   c->gen_tab_ints = 0;
@@ -922,6 +987,124 @@ static lor_status setup_ordered_factors(lor_ctx* c) {
       if (l + 1 < L) c->fac_rows += o.rows;
     }
   for (int j = 0; j < J; ++j) c->gen_tab_ints = std::max(c->gen_tab_ints, tab[j]);
+  // vertex-level inverses
+  std::vector<double> hb;
+  for (int j = 0; j < J; ++j) {
+    GenSched& g = gs[(size_t)(L - 1) * J + j];
+    g.binv_off = (long long)hb.size();
+    hb.insert(hb.end(), binv[j].begin(), binv[j].end());
+  }
+  if (hb.empty()) hb.push_back(0.0);
+  {
+    std::vector<float> hb32(hb.begin(), hb.end());
+    if (upload(c, (void**)&c->d_binv64, hb.data(), hb.size() * 8)) return LOR_ENOMEM;
+    if (upload(c, (void**)&c->d_binv32, hb32.data(), hb32.size() * 4)) return LOR_ENOMEM;
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return lor_cuda_check(c, e, "vertex-level inverses");
+  }
+  // largest boxes (shared-memory layout of the patch kernel)
+  c->gen_rows0 = c->gen_A0 = c->gen_AB0 = c->gen_rows1 = c->gen_guard0 = 0;
+  c->gen_ovl = 0;
+  c->span_kmax = 2;
+  for (int j = 0; j < J; ++j) {
+    const GenSched& g0 = gs[j];
+    c->gen_rows0 = std::max(c->gen_rows0, g0.rows);
+    c->gen_A0 = std::max(c->gen_A0, g0.dims[0]);
+    c->gen_AB0 = std::max(c->gen_AB0, g0.dims[0] * g0.dims[1]);
+    c->gen_guard0 = std::max(c->gen_guard0, g0.guard);
+    if (L > 1) c->gen_rows1 = std::max(c->gen_rows1, gs[(size_t)J + j].rows);
+    long long ovl = 0;
+    for (int l = 1; l < L; ++l) {
+      const GenSched& g = gs[(size_t)l * J + j];
+      ovl += 2LL * (g.rows + 2 * g.guard + 1) + (l >= 2 ? g.rows : 0);
+    }
+    c->gen_ovl = std::max(c->gen_ovl, std::max<long long>(ovl, g0.rows + 2LL * g0.guard + 1));
+    for (int a = 0; a < dim; ++a) c->span_kmax = std::max(c->span_kmax, g0.k[a]);
+  }
+  // patch-local 1D transfers for every level and span length k (1 .. kmax elements)
+  {
+    const int K1 = c->span_kmax + 1;
+    std::vector<int> ib;              // int pool: c0 | c1 | rstart | rf per (l, k)
+    std::vector<double> wb;           // weight pool: w0 | w1 | rw per (l, k)
+    struct Off { size_t c0, c1, rs, rf, w0, w1, rw; };
+    std::vector<Off> offs((size_t)L * K1, Off{0, 0, 0, 0, 0, 0, 0});
+    for (int l = 0; l + 1 < L; ++l)
+      for (int k = 1; k <= c->span_kmax; ++k) {
+        const int m = c->lev[l].m, mc = c->lev[l + 1].m;
+        std::vector<Prolong1D> P = prolong_axis(k, c->gll_x, c->sel[l], c->sel[l + 1]);
+        const int len = std::max(k * m - 1, 0), clen = std::max(k * mc - 1, 0);
+        Off& o = offs[(size_t)l * K1 + k];
+        o.c0 = ib.size(); for (int f = 0; f < len; ++f) ib.push_back(P[f + 1].c0 >= 0 ? P[f + 1].c0 - 1 : -2);
+        o.c1 = ib.size(); for (int f = 0; f < len; ++f) ib.push_back(P[f + 1].c1 >= 0 ? P[f + 1].c1 - 1 : -2);
+        o.w0 = wb.size(); for (int f = 0; f < len; ++f) wb.push_back(P[f + 1].w0);
+        o.w1 = wb.size(); for (int f = 0; f < len; ++f) wb.push_back(P[f + 1].w1);
+        // transpose: coarse local index -> the fine local indices feeding it
+        std::vector<std::vector<std::pair<int, double>>> rows(std::max(clen, 1));
+        for (int f = 0; f < len; ++f) {
+          const int cs[2] = {ib[o.c0 + f], ib[o.c1 + f]};
+          const double ws[2] = {wb[o.w0 + f], wb[o.w1 + f]};
+          for (int s2 = 0; s2 < 2; ++s2)
+            if (cs[s2] >= 0 && cs[s2] < clen && ws[s2] != 0.0) rows[cs[s2]].push_back({f, ws[s2]});
+        }
+        o.rs = ib.size();
+        int q = 0;
+        std::vector<int> rf;
+        std::vector<double> rw;
+        for (int cc = 0; cc < clen; ++cc) {
+          ib.push_back(q);
+          for (auto& pr : rows[cc]) { rf.push_back(pr.first); rw.push_back(pr.second); ++q; }
+        }
+        ib.push_back(q);
+        o.rf = ib.size(); ib.insert(ib.end(), rf.begin(), rf.end());
+        o.rw = wb.size(); wb.insert(wb.end(), rw.begin(), rw.end());
+      }
+    if (ib.empty()) ib.push_back(0);
+    if (wb.empty()) wb.push_back(0.0);
+    std::vector<float> wb32(wb.begin(), wb.end());
+    int* d_ib = nullptr;
+    double* d_wb64 = nullptr;
+    float* d_wb32 = nullptr;
+    if (upload(c, (void**)&d_ib, ib.data(), ib.size() * 4)) return LOR_ENOMEM;
+    if (upload(c, (void**)&d_wb64, wb.data(), wb.size() * 8)) return LOR_ENOMEM;
+    if (upload(c, (void**)&d_wb32, wb32.data(), wb32.size() * 4)) return LOR_ENOMEM;
+    std::vector<XferG<double>> x64((size_t)L * K1);
+    std::vector<XferG<float>> x32((size_t)L * K1);
+    for (size_t t = 0; t < offs.size(); ++t) {
+      const Off& o = offs[t];
+      x64[t] = {d_ib + o.c0, d_ib + o.c1, d_wb64 + o.w0, d_wb64 + o.w1, d_ib + o.rs, d_ib + o.rf, d_wb64 + o.rw};
+      x32[t] = {d_ib + o.c0, d_ib + o.c1, d_wb32 + o.w0, d_wb32 + o.w1, d_ib + o.rs, d_ib + o.rf, d_wb32 + o.rw};
+    }
+    if (upload(c, &c->d_xferg64, x64.data(), x64.size() * sizeof(XferG<double>))) return LOR_ENOMEM;
+    if (upload(c, &c->d_xferg32, x32.data(), x32.size() * sizeof(XferG<float>))) return LOR_ENOMEM;
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return lor_cuda_check(c, e, "patch transfer tables");
+  }
+  // enlarged patches: every level-0 node's entries in the patch output slices (patches in
+  // index order), summed by k_patch_gather in place of the closed-form vertex-patch sum
+  if (!c->h_spans.empty()) {
+    const long long nt = c->lev[0].ntot;
+    const long long zstride = (c->gen_rows0 + 31) / 32 * 32;
+    std::vector<long long> cnt(nt + 1, 0);
+    const LevelGrid& g0l = c->lev[0];
+    auto each = [&](auto&& fn) {
+      for (int j = 0; j < J; ++j) {
+        const GenSched& g = gs[j];
+        for (int lex = 0; lex < g.rows; ++lex) {
+          const int i = lex % g.dims[0], jj = (lex / g.dims[0]) % g.dims[1], k = lex / (g.dims[0] * g.dims[1]);
+          const long long G = ((long long)(g.org[2] + k) * g0l.N[1] + (g.org[1] + jj)) * g0l.N[0] + (g.org[0] + i);
+          fn(G, (long long)j * zstride + lex);
+        }
+      }
+    };
+    each([&](long long G, long long) { ++cnt[G + 1]; });
+    for (long long q = 0; q < nt; ++q) cnt[q + 1] += cnt[q];
+    std::vector<long long> idx(std::max<long long>(cnt[nt], 1)), pos(cnt.begin(), cnt.end() - 1);
+    each([&](long long G, long long z) { idx[pos[G]++] = z; });
+    if (upload(c, (void**)&c->d_gather_ptr, cnt.data(), cnt.size() * 8)) return LOR_ENOMEM;
+    if (upload(c, (void**)&c->d_gather_idx, idx.data(), idx.size() * 8)) return LOR_ENOMEM;
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return lor_cuda_check(c, e, "patch gather list");
+  }
   const long long nval = tot * R;
   std::vector<double> all((size_t)std::max<long long>(nval, 1), 0.0);
   for (size_t t = 0; t < out.size(); ++t)
@@ -1093,7 +1276,7 @@ lor_status lor_setup_patches(lor_ctx* c) {
     if ((long long)order.size() != c->J) return lor_fail(c, LOR_EINVAL, "patch order incomplete");
     if (upload(c, (void**)&c->d_porder, order.data(), order.size() * 4)) return LOR_ENOMEM;
   }
-  if (c->ordering) return setup_ordered_factors(c);
+  if (c->gen) return setup_ordered_factors(c);
   // factor storage offsets (records; a patch level holds 2*rpad records)
   std::vector<long long> off((size_t)c->L * c->J);
   long long tot = 0;

@@ -128,6 +128,7 @@ def load():
     lib.lor_set_weighting.argtypes = [vp, i]
     lib.lor_set_schwarz.argtypes = [vp, i]
     lib.lor_set_ordering.argtypes = [vp, i]
+    lib.lor_set_patch_spans.argtypes = [vp, vp]
     lib.lor_box_ordering.argtypes = [i, i, i, i, i, vp, vp]
     lib.lor_patch_ordering.argtypes = [vp, i, ctypes.c_longlong, vp, i, ctypes.POINTER(i)]
     lib.lor_coefficient_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -142,7 +143,7 @@ def load():
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
     for name in ("lor_coefficient_sizes", "lor_coefficient_points", "lor_set_coefficient", "lor_set_node_coordinates",
                  "lor_pcg_state_size", "lor_pcg_state_save", "lor_pcg_resume",
-                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_set_schwarz", "lor_set_ordering", "lor_box_ordering", "lor_patch_ordering", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_measure_fp64_peak", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
+                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_set_schwarz", "lor_set_ordering", "lor_set_patch_spans", "lor_box_ordering", "lor_patch_ordering", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_measure_fp64_peak", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -189,13 +190,15 @@ class Solver:
 
     def __init__(self, vertices, kappa, p, *, mg_levels=0, prec=LOR_FP64, rtol=1e-8, max_it=1000,
                  inner_rtol=1e-3, factor_bf16=False, disc=LOR_CG, eta=1.0, weighting=0, coefficient=None,
-                 node_coordinates=None, ordering=0, stream=None):
+                 node_coordinates=None, ordering=0, patch_spans=None, stream=None):
         """coefficient: optional callable b(X) of physical points X (n, dim) -> (n,) replacing the
         per-element kappa (CG only); it is evaluated at the points lor_coefficient_points lists.
         node_coordinates: optional (ntot, dim) physical coordinates of the level-0 GLL nodes in
         L-vector order, for curved (isoparametric) elements (CG only).
         ordering: ILU(0) ordering of the patch levels, 0 lexicographic, 1 RCM, 2 MDF
-        (ORDER_LEX / ORDER_RCM / ORDER_MDF)."""
+        (ORDER_LEX / ORDER_RCM / ORDER_MDF).
+        patch_spans: optional int array (npatch, dim, 2): elements (lo, hi) each patch takes on
+        either side of its vertex along each axis (1, 1 = the vertex patch); CG only."""
         import torch
         self.lib = load()
         vertices = np.ascontiguousarray(vertices, dtype=np.float64)
@@ -224,6 +227,11 @@ class Solver:
         self.ctx = ctx
         if ordering:
             self._check(self.lib.lor_set_ordering(ctx, int(ordering)))
+        if patch_spans is not None:
+            sp = np.ascontiguousarray(patch_spans, dtype=np.int32)
+            if sp.shape != (int(np.prod([v + 1 for v in n])), dim, 2):
+                raise ValueError("patch_spans must have shape (npatch, dim, 2)")
+            self._check(self.lib.lor_set_patch_spans(ctx, sp.ctypes.data_as(ctypes.c_void_p)))
         if node_coordinates is not None:
             Xn = np.ascontiguousarray(np.asarray(node_coordinates, dtype=np.float64).T)
             ntot = int(np.prod([v * p + 1 for v in n]))
