@@ -248,6 +248,18 @@ struct SingleState {
   float* F32[LOR_MAXLEV] = {};
   // per level: r, x, t, w (float64-sized) and two transfer buffers
   double* vec[LOR_MAXLEV][6] = {};
+  // the apply as a CUDA graph per precision (index 0 FP64, 1 FP32), for one (r, z) pair:
+  // its thousands of hyperplane launches replay as one graph launch
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec[2] = {};
+  const void* gr[2] = {};
+  void* gz[2] = {};
+  long long glaunches[2] = {};
+  ~SingleState() {
+    for (int q = 0; q < 2; ++q)
+      if (exec[q]) cudaGraphExecDestroy(exec[q]);
+    if (cap) cudaStreamDestroy(cap);
+  }
 };
 
 static SingleState* SS(lor_ctx* c) { return (SingleState*)c->single; }
@@ -419,10 +431,11 @@ lor_status vcycle(lor_ctx* c, int l, const T* r, T* x) {
 
 }  // namespace
 
+namespace {
+
 template <typename T>
-lor_status lor_single_apply(lor_ctx* c, const T* r, T* z) {
+lor_status single_apply_launches(lor_ctx* c, const T* r, T* z) {
   SingleState* s = SS(c);
-  if (!s) return lor_fail(c, LOR_ESTATE, "single-patch preconditioner not prepared");
   const GridArg g0 = grid_of(c, 0);
   if (s->levels == 0) {          // p = 1: the level grid is the vertex grid, B(1) = R_0
     if (interior_count(c, 0) == 0)
@@ -439,6 +452,57 @@ lor_status lor_single_apply(lor_ctx* c, const T* r, T* z) {
   k_s_copy_masked<T><<<nblk(g0.ntot), 256, 0, c->stream>>>(g0, r, r0);
   ++c->launches;
   return vcycle<T>(c, 0, r0, z);
+}
+
+}  // namespace
+
+// The apply is captured once per (r, z, precision) into a CUDA graph on a private
+// stream and replayed on the context's stream; inside an enclosing capture (a batch)
+// its kernels are launched directly.
+template <typename T>
+lor_status lor_single_apply(lor_ctx* c, const T* r, T* z) {
+  SingleState* s = SS(c);
+  if (!s) return lor_fail(c, LOR_ESTATE, "single-patch preconditioner not prepared");
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c->stream, &cst) != cudaSuccess || cst != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return single_apply_launches<T>(c, r, z);
+  }
+  const int q = sizeof(T) == 8 ? 0 : 1;
+  if (!(s->exec[q] && s->gr[q] == (const void*)r && s->gz[q] == (void*)z)) {
+    if (s->exec[q]) { cudaGraphExecDestroy(s->exec[q]); s->exec[q] = nullptr; }
+    if (!s->cap && cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess)
+      return lor_fail(c, LOR_ECUDA, "B(1): capture stream");
+    const cudaStream_t keep = c->stream;
+    const long long l0 = c->launches;
+    c->stream = s->cap;
+    if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      c->stream = keep;
+      return lor_fail(c, LOR_ECUDA, "B(1): begin capture");
+    }
+    const lor_status st = single_apply_launches<T>(c, r, z);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+    c->stream = keep;
+    if (st || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return st ? st : lor_fail(c, LOR_ECUDA, "B(1): capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&s->exec[q], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      s->exec[q] = nullptr;
+      cudaGetLastError();
+      return lor_fail(c, LOR_ECUDA, "B(1): graph instantiate");
+    }
+    s->gr[q] = r;
+    s->gz[q] = z;
+    s->glaunches[q] = c->launches - l0;
+    c->launches = l0;
+  }
+  c->launches += s->glaunches[q];
+  return lor_cuda_check(c, cudaGraphLaunch(s->exec[q], c->stream), "B(1) graph launch");
 }
 
 template lor_status lor_single_apply<double>(lor_ctx*, const double*, double*);

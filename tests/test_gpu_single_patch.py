@@ -96,6 +96,14 @@ def test_single_patch_mode_switches_back_to_additive():
     s.set_schwarz(2)
     s.apply_P(r, z1)
     assert float(torch.linalg.norm(z1 - z0)) > 1e-3 * float(torch.linalg.norm(z0))
+    # the apply is replayed from its captured graph: same pointers give the same bits,
+    # new pointers capture again and give the same values
+    z2 = torch.empty_like(r)
+    s.apply_P(r, z2)
+    z3 = torch.full_like(r, float("nan"))
+    s.apply_P(r.clone(), z3)
+    s.apply_P(r, z1)
+    assert torch.equal(z1, z2) and torch.equal(z1, z3)
     s.set_schwarz(0)
     s.apply_P(r, z1)
     assert torch.equal(z0, z1)          # deterministic additive apply, bit for bit
