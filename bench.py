@@ -390,10 +390,12 @@ def leg_dg():
                     ms = e0.elapsed_time(e1) / 5
                     per[name] = {"ms": ms, "MDOF/s": s.nvec / (ms * 1e-3) / 1e6}
                 # DG apply_A FP64 against the FP64 peak: volume sum factorization plus the
-                # face terms, ((p+1)^3 + 3 (p+1)^2) multiply-adds per face point and side
+                # sum-factorized face terms, 17 contractions of (p+1)^3 multiply-adds per face
+                # side (normal derivative, interpolation to and from the face points, node
+                # updates) and ~10 operations per face point
                 Qd, nel_dg = 5, 24 ** 3
                 nface = 3 * 25 * 24 * 24
-                fl = nel_dg * (24 * Qd ** 4 + 18 * Qd ** 3) + nface * 2 * Qd ** 2 * 2 * (Qd ** 3 + 3 * Qd ** 2)
+                fl = nel_dg * (24 * Qd ** 4 + 18 * Qd ** 3) + nface * (2 * 2 * 17 * Qd ** 3 + 10 * Qd ** 2)
                 ach = fl / (per["apply_A_fp64"]["ms"] * 1e-3) / 1e12
                 pk64 = lor.measure_fp64_peak()
                 per["apply_A_fp64"]["roofline"] = {"bound": "alu", "achieved": ach, "peak": pk64, "unit": "TFLOP/s",

@@ -254,118 +254,148 @@ struct Tab {     // 1D tables (precision T): B/D at Gauss points, GLL nodal deri
   const void* Dn;   // [Q][Q]  l_j'(gll_i) (nodal differentiation matrix)
 };
 
-// per (face, Gauss point): averaged flux, jump, value-test coefficients
+// All face terms of the faces of class k, one CTA per face, sum-factorized in shared
+// memory (O(Q^3) work per face and side):
+//  1. per side, the trace x(end, j, k) and the nodal normal derivative
+//     sum_i Dn[end][i] x(i, j, k) at the face's GLL nodes;
+//  2. both interpolated to the Gauss points (contractions along j, then k): u,
+//     the tangential derivatives and the normal derivative, combined with the
+//     side's geometric coefficients into c . grad u;
+//  3. per point the averaged flux, the jump and the penalty (IP; BR2 adds its
+//     nodal penalty in step 5): value-test weights of each side and the
+//     gradient-test weight;
+//  4. per side the transposed interpolation of those weights back to the face
+//     nodes (contractions along q2, then q1): G1 (times the normal derivative of
+//     the test function) and G2 (value and tangential-derivative tests);
+//  5. every element node (i, j, k) of each side: y += Dn[end][i] G1(j, k), plus
+//     G2(j, k) and the BR2 penalty at i = end.
+// No two faces of a class share an element, so the adds need no atomics.
 template <typename T>
-__global__ void k_face_flux(int p, int nface, int br2, FaceData<T> fd, Tab tb, const T* __restrict__ x,
-                            T* __restrict__ buf) {
+__global__ void __launch_bounds__(128) k_face_sf(int p, FaceClass fk, int n0, int n1, int n2, int br2,
+                                                 FaceData<T> fd, Tab tb, const T* __restrict__ x, T* y) {
+  constexpr int MQ2 = (LOR_MAXP + 1) * (LOR_MAXP + 1);
   const int Q = p + 1, Q2 = Q * Q, Q3 = Q2 * Q;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)nface * Q2) return;
-  const int f = (int)(gid / Q2), q = (int)(gid - (long long)f * Q2);
-  const int q1 = q % Q, q2 = q / Q;
+  __shared__ T sB[MQ2], sD[MQ2], sDn[MQ2];
+  __shared__ T tr[2][MQ2], nd[2][MQ2];            // [side][j + Q k]
+  __shared__ T c1[2][MQ2], c2[2][MQ2], c3[2][MQ2];  // [side][q1 + Q k] partial contractions
+  __shared__ T uv[2][MQ2], fl[2][MQ2];            // [side][q]: u and c . grad u at the Gauss points
+  __shared__ T wv[3][MQ2];                        // [q]: value test of side 0, of side 1, gradient test
+  __shared__ T m1[2][MQ2], m2[2][MQ2], m3[2][MQ2], m4[2][MQ2];
+  __shared__ T g1[2][MQ2], g2[2][MQ2];            // [side][j + Q k]
+  const int n[3] = {n0, n1, n2};
+  const int f = class_face(fk, n, blockIdx.x);
   const FaceTopo t = fd.topo[f];
-  const T* B = (const T*)tb.B;
-  const T* D = (const T*)tb.D;
-  const T* Dn = (const T*)tb.Dn;
-  T uval[2], flux[2];
   const int ns = t.eS >= 0 ? 2 : 1;
-  for (int s = 0; s < ns; ++s) {
-    const int e = s ? t.eS : t.eF;
-    const int end = s ? t.endS : t.endF;
-    const T* xe = x + (long long)e * Q3;
-    const T* cv = (s ? fd.cS : fd.cF) + (long long)f * 3 * Q2;
-    T u = 0, db = 0, dc = 0, da = 0;
-    for (int k = 0; k < Q; ++k)
-      for (int j = 0; j < Q; ++j) {
-        const T bb = B[q1 * Q + j], bc = B[q2 * Q + k];
-        const T ue = xe[loc3(Q, t.a, end, j, k)];
-        u += bb * bc * ue;
-        db += D[q1 * Q + j] * bc * ue;
-        dc += bb * D[q2 * Q + k] * ue;
-        T ln = 0;
-        for (int i = 0; i < Q; ++i) ln += Dn[end * Q + i] * xe[loc3(Q, t.a, i, j, k)];
-        da += bb * bc * ln;
-      }
-    T g[3];
-    const int b = t.a == 0 ? 1 : 0, c = t.a == 2 ? 1 : 2;
-    g[t.a] = da; g[b] = db; g[c] = dc;
-    uval[s] = u;
-    flux[s] = cv[q] * g[0] + cv[Q2 + q] * g[1] + cv[2 * Q2 + q] * g[2];
-  }
-  const T half = ns == 2 ? T(0.5) : T(1);
-  const T jump = ns == 2 ? uval[0] - uval[1] : uval[0];
-  const T avg = half * (ns == 2 ? flux[0] + flux[1] : flux[0]);
-  const T pen = br2 ? T(0) : fd.sigma[f] * fd.W[(long long)f * Q2 + q] * jump;
-  T* bq = buf + (long long)f * 3 * Q2;
-  bq[q] = -avg + pen;              // value test, first side (sign +)
-  bq[Q2 + q] = avg - pen;          // value test, second side (sign -)
-  bq[2 * Q2 + q] = -half * jump;   // gradient test coefficient (times c_k . grad phi)
-}
-
-// per (face of class k, side, element node): apply the transposed trace / normal
-// derivative, added into the element node (no other face of the class touches it)
-template <typename T>
-__global__ void k_face_scatter(int p, FaceClass fk, int n0, int n1, int n2, FaceData<T> fd, Tab tb,
-                               const T* __restrict__ buf, T* y) {
-  const int Q = p + 1, Q2 = Q * Q, Q3 = Q2 * Q;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= fk.count * 2 * Q3) return;
-  const int n[3] = {n0, n1, n2};
-  const long long fi = gid / (2 * Q3);
-  const int f = class_face(fk, n, fi);
-  const int r = (int)(gid - fi * 2 * Q3);
-  const int s = r / Q3, node = r % Q3;
-  const FaceTopo t = fd.topo[f];
-  if (s == 1 && t.eS < 0) return;
-  const int i = node % Q, j = (node / Q) % Q, k = node / Q2;   // i along a, (j, k) along (b, c)
-  const int e = s ? t.eS : t.eF;
-  const int end = s ? t.endS : t.endF;
-  const T* B = (const T*)tb.B;
-  const T* D = (const T*)tb.D;
-  const T* Dn = (const T*)tb.Dn;
-  const T* cv = (s ? fd.cS : fd.cF) + (long long)f * 3 * Q2;
-  const T* bq = buf + (long long)f * 3 * Q2;
-  const T* sv = bq + s * Q2;
-  const T* sg = bq + 2 * Q2;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int b = t.a == 0 ? 1 : 0, c = t.a == 2 ? 1 : 2;
-  const T* ca = cv + t.a * Q2;
-  const T* cb = cv + b * Q2;
-  const T* cc = cv + c * Q2;
-  const T dn = Dn[end * Q + i];
-  T acc = 0;
-  for (int q2 = 0; q2 < Q; ++q2)
-    for (int q1 = 0; q1 < Q; ++q1) {
-      const int q = q2 * Q + q1;
-      const T bb = B[q1 * Q + j], bc = B[q2 * Q + k];
-      T v = sg[q] * ca[q] * dn * bb * bc;
-      if (i == end) v += sv[q] * bb * bc + sg[q] * (cb[q] * D[q1 * Q + j] * bc + cc[q] * bb * D[q2 * Q + k]);
-      acc += v;
-    }
-  y[(long long)e * Q3 + loc3(Q, t.a, i, j, k)] += acc;
-}
-
-// BR2 nodal penalty at the GLL face nodes of the faces of class k
-template <typename T>
-__global__ void k_face_br2(int p, FaceClass fk, int n0, int n1, int n2, FaceData<T> fd, const T* __restrict__ x,
-                           T* y) {
-  const int Q = p + 1, Q2 = Q * Q, Q3 = Q2 * Q;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= fk.count * Q2) return;
-  const int n[3] = {n0, n1, n2};
-  const long long fi = gid / Q2;
-  const int f = class_face(fk, n, fi), q = (int)(gid - fi * Q2);
-  const int j = q % Q, k = q / Q;
-  const FaceTopo t = fd.topo[f];
-  const long long iF = (long long)t.eF * Q3 + loc3(Q, t.a, t.endF, j, k);
-  T jump = x[iF];
-  long long iS = -1;
-  if (t.eS >= 0) {
-    iS = (long long)t.eS * Q3 + loc3(Q, t.a, t.endS, j, k);
-    jump -= x[iS];
+  for (int i = tid; i < Q2; i += nt) {
+    sB[i] = ((const T*)tb.B)[i];
+    sD[i] = ((const T*)tb.D)[i];
+    sDn[i] = ((const T*)tb.Dn)[i];
   }
-  const T v = fd.beta[(long long)f * Q2 + q] * jump;
-  y[iF] += v;
-  if (iS >= 0) y[iS] -= v;
+  __syncthreads();
+  // 1. traces and nodal normal derivatives
+  for (int idx = tid; idx < ns * Q2; idx += nt) {
+    const int s = idx / Q2, jk = idx - s * Q2, j = jk % Q, k = jk / Q;
+    const int e = s ? t.eS : t.eF, end = s ? t.endS : t.endF;
+    const T* xe = x + (long long)e * Q3;
+    tr[s][jk] = xe[loc3(Q, t.a, end, j, k)];
+    T ln = 0;
+    for (int i = 0; i < Q; ++i) ln += sDn[end * Q + i] * xe[loc3(Q, t.a, i, j, k)];
+    nd[s][jk] = ln;
+  }
+  __syncthreads();
+  // 2a. along j
+  for (int idx = tid; idx < ns * Q2; idx += nt) {
+    const int s = idx / Q2, r = idx - s * Q2, q1 = r % Q, k = r / Q;
+    T a1 = 0, a2 = 0, a3 = 0;
+    for (int j = 0; j < Q; ++j) {
+      const T v = tr[s][j + Q * k];
+      a1 += sB[q1 * Q + j] * v;
+      a2 += sD[q1 * Q + j] * v;
+      a3 += sB[q1 * Q + j] * nd[s][j + Q * k];
+    }
+    c1[s][r] = a1; c2[s][r] = a2; c3[s][r] = a3;
+  }
+  __syncthreads();
+  // 2b. along k: u and c . grad u at every Gauss point
+  for (int idx = tid; idx < ns * Q2; idx += nt) {
+    const int s = idx / Q2, q = idx - s * Q2, q1 = q % Q, q2 = q / Q;
+    T u = 0, db = 0, dc = 0, da = 0;
+    for (int k = 0; k < Q; ++k) {
+      const T bk = sB[q2 * Q + k];
+      u += bk * c1[s][q1 + Q * k];
+      db += bk * c2[s][q1 + Q * k];
+      dc += sD[q2 * Q + k] * c1[s][q1 + Q * k];
+      da += bk * c3[s][q1 + Q * k];
+    }
+    T g[3];
+    g[t.a] = da; g[b] = db; g[c] = dc;
+    const T* cv = (s ? fd.cS : fd.cF) + (long long)f * 3 * Q2;
+    uv[s][q] = u;
+    fl[s][q] = cv[q] * g[0] + cv[Q2 + q] * g[1] + cv[2 * Q2 + q] * g[2];
+  }
+  __syncthreads();
+  // 3. flux, jump and penalty per point
+  for (int q = tid; q < Q2; q += nt) {
+    const T half = ns == 2 ? T(0.5) : T(1);
+    const T jump = ns == 2 ? uv[0][q] - uv[1][q] : uv[0][q];
+    const T avg = half * (ns == 2 ? fl[0][q] + fl[1][q] : fl[0][q]);
+    const T pen = br2 ? T(0) : fd.sigma[f] * fd.W[(long long)f * Q2 + q] * jump;
+    wv[0][q] = -avg + pen;
+    wv[1][q] = avg - pen;
+    wv[2][q] = -half * jump;
+  }
+  __syncthreads();
+  // 4a. per side and point the four weight fields, contracted along q2
+  for (int idx = tid; idx < ns * Q2; idx += nt) {
+    const int s = idx / Q2, r = idx - s * Q2, q1 = r % Q, k = r / Q;
+    const T* cv = (s ? fd.cS : fd.cF) + (long long)f * 3 * Q2;
+    const T* ca = cv + t.a * Q2;
+    const T* cb = cv + b * Q2;
+    const T* cc = cv + c * Q2;
+    T h1 = 0, h2 = 0, h3 = 0, h4 = 0;
+    for (int q2 = 0; q2 < Q; ++q2) {
+      const int q = q2 * Q + q1;
+      const T bk = sB[q2 * Q + k];
+      const T sg = wv[2][q];
+      h1 += bk * sg * ca[q];
+      h2 += bk * wv[s][q];
+      h3 += bk * sg * cb[q];
+      h4 += sD[q2 * Q + k] * sg * cc[q];
+    }
+    m1[s][r] = h1; m2[s][r] = h2; m3[s][r] = h3; m4[s][r] = h4;
+  }
+  __syncthreads();
+  // 4b. along q1: G1 and G2 at the face nodes (j, k)
+  for (int idx = tid; idx < ns * Q2; idx += nt) {
+    const int s = idx / Q2, jk = idx - s * Q2, j = jk % Q, k = jk / Q;
+    T a1 = 0, a2 = 0;
+    for (int q1 = 0; q1 < Q; ++q1) {
+      const T bj = sB[q1 * Q + j];
+      a1 += bj * m1[s][q1 + Q * k];
+      a2 += bj * (m2[s][q1 + Q * k] + m4[s][q1 + Q * k]) + sD[q1 * Q + j] * m3[s][q1 + Q * k];
+    }
+    g1[s][jk] = a1;
+    g2[s][jk] = a2;
+  }
+  __syncthreads();
+  // 5. element nodes of both sides
+  for (int idx = tid; idx < ns * Q3; idx += nt) {
+    const int s = idx / Q3, node = idx - s * Q3;
+    const int i = node % Q, jk = node / Q, j = jk % Q, k = jk / Q;
+    const int e = s ? t.eS : t.eF, end = s ? t.endS : t.endF;
+    T v = sDn[end * Q + i] * g1[s][jk];
+    if (i == end) {
+      v += g2[s][jk];
+      if (br2) {
+        const T jump = ns == 2 ? tr[0][jk] - tr[1][jk] : tr[0][jk];
+        const T pb = fd.beta[(long long)f * Q2 + jk] * jump;
+        v += s ? -pb : pb;
+      }
+    }
+    y[(long long)e * Q3 + loc3(Q, t.a, i, j, k)] += v;
+  }
 }
 
 // diagonal of A_DG: volume part per node, face part per (face, side, face node)
@@ -513,8 +543,6 @@ struct DGState {
   FaceTopo* topo = nullptr;
   double *cF64, *cS64, *W64, *sig64, *beta64;
   float *cF32, *cS32, *W32, *sig32, *beta32;
-  double* buf64;
-  float* buf32;
   double* dinv64;
   float* dinv32;
   double *tab64;   // B | D | Dn  (Q*Q each)
@@ -559,7 +587,7 @@ lor_status lor_setup_dg(lor_ctx* c) {
   s->sig64 = A64(nf); s->beta64 = A64(nf * Q2);
   s->cF32 = A32(nf * 3 * Q2); s->cS32 = A32(nf * 3 * Q2); s->W32 = A32(nf * Q2);
   s->sig32 = A32(nf); s->beta32 = A32(nf * Q2);
-  s->buf64 = A64(nf * 3 * Q2); s->buf32 = A32(nf * 3 * Q2);
+
   s->dinv64 = A64(ndg); s->dinv32 = A32(ndg);
   s->tab64 = A64(3 * Q2); s->tab32 = A32(3 * Q2);
   s->cgin64 = A64(c->lev[0].ntot); s->cgout64 = A64(c->lev[0].ntot);
@@ -567,7 +595,7 @@ lor_status lor_setup_dg(lor_ctx* c) {
   double* vol = A64(nel);
   double* diag = A64(ndg);
   if (!s->topo || !s->cF64 || !s->cS64 || !s->W64 || !s->sig64 || !s->beta64 || !s->cF32 || !s->cS32 || !s->W32 ||
-      !s->sig32 || !s->beta32 || !s->buf64 || !s->buf32 || !s->dinv64 || !s->dinv32 || !s->tab64 || !s->tab32 ||
+      !s->sig32 || !s->beta32 || !s->dinv64 || !s->dinv32 || !s->tab64 || !s->tab32 ||
       !s->cgin64 || !s->cgout64 || !s->cgin32 || !s->cgout32 || !vol || !diag)
     return lor_fail(c, LOR_ENOMEM, "alloc DG data");
   // 1D tables: B, D at Gauss points (as in the volume kernel) and the nodal GLL derivative
@@ -623,9 +651,6 @@ lor_status lor_setup_dg(lor_ctx* c) {
   return lor_cuda_check(c, cudaGetLastError(), "DG setup");
 }
 
-template <typename T> static T* dgbuf(lor_ctx* c);
-template <> double* dgbuf<double>(lor_ctx* c) { return dgs(c)->buf64; }
-template <> float* dgbuf<float>(lor_ctx* c) { return dgs(c)->buf32; }
 
 template <typename T>
 static lor_status apply_A_dg(lor_ctx* c, const T* x, T* y) {
@@ -634,26 +659,16 @@ static lor_status apply_A_dg(lor_ctx* c, const T* x, T* y) {
   lor_status st = sizeof(T) == 8 ? lor_launch_dgvol64(c, (const double*)x, (double*)y)
                                  : lor_launch_dgvol32(c, (const float*)x, (float*)y);
   if (st) return st;
-  const int p = c->p, Q = p + 1, Q2 = Q * Q, Q3 = Q2 * Q;
-  const long long nf = dgs(c)->nface;
+  const int p = c->p, Q = p + 1;
   const bool br2 = c->opt.disc == LOR_DG_BR2;
-  T* buf = dgbuf<T>(c);
-  k_face_flux<T><<<(unsigned)lor_ceil_div(nf * Q2, 128), 128, 0, c->stream>>>(p, (int)nf, br2, face_data<T>(c),
-                                                                                tabs<T>(c, Q), x, buf);
-  ++c->launches;
   // face classes one after another (no two faces of a class share an element)
   for (int a = 0; a < 3; ++a)
     for (int par = 0; par < 2; ++par) {
       const FaceClass fk = face_class(c->n, a, par);
       if (fk.count == 0) continue;
-      k_face_scatter<T><<<(unsigned)lor_ceil_div(fk.count * 2 * Q3, 128), 128, 0, c->stream>>>(
-          p, fk, c->n[0], c->n[1], c->n[2], face_data<T>(c), tabs<T>(c, Q), buf, y);
+      k_face_sf<T><<<(unsigned)fk.count, 128, 0, c->stream>>>(p, fk, c->n[0], c->n[1], c->n[2], br2 ? 1 : 0,
+                                                              face_data<T>(c), tabs<T>(c, Q), x, y);
       ++c->launches;
-      if (br2) {
-        k_face_br2<T><<<(unsigned)lor_ceil_div(fk.count * Q2, 128), 128, 0, c->stream>>>(
-            p, fk, c->n[0], c->n[1], c->n[2], face_data<T>(c), x, y);
-        ++c->launches;
-      }
     }
   return lor_cuda_check(c, cudaGetLastError(), "DG apply");
 }
