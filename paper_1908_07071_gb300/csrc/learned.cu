@@ -154,6 +154,10 @@ __device__ __forceinline__ void ldsm4(unsigned addr, unsigned* r) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
 }
 
+__device__ __forceinline__ void ldsm2(unsigned addr, unsigned* r) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(addr));
+}
+
 __device__ __forceinline__ void ldsm4t(unsigned addr, unsigned* r) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
@@ -249,9 +253,14 @@ __global__ void __launch_bounds__(256) k_tc_conv(PBox b, int nin, const void* __
       const int r = prow + (dz * P1 + dy) * P0 + dx;
       unsigned a[4], bq[4];
       ldsm4(swz(bbase, r, hl), a);
-      ldsm4(swz(wbase, tap * 16 + on, wh), bq);
-      mma16816(acc[0], a, bq[0], bq[1]);
-      mma16816(acc[1], a, bq[2], bq[3]);
+      if constexpr (OUT == 2) {   // one output channel: the n 0-7 half only
+        ldsm2(swz(wbase, tap * 16 + on, wh), bq);
+        mma16816(acc[0], a, bq[0], bq[1]);
+      } else {
+        ldsm4(swz(wbase, tap * 16 + on, wh), bq);
+        mma16816(acc[0], a, bq[0], bq[1]);
+        mma16816(acc[1], a, bq[2], bq[3]);
+      }
     }
     const long long v0 = (long long)tile * 16 + g, v1 = v0 + 8;
 #pragma unroll
