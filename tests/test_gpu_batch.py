@@ -39,7 +39,8 @@ def test_batch_members_match_the_oracle():
         m = Mesh(v, k)
         K = cg.assemble_stiffness(m, p)
         N = cg.node_shape(m.n, p)
-        B = olor.LORPreconditioner(m, p)
+        order = "rcm" if s_i == 2 else "lex"            # one member with RCM-ordered patches
+        B = olor.LORPreconditioner(m, p, ordering=order)
         b = cg.load_vector(m, p, lambda X: np.ones(len(X)))
         _, it_or, _, _ = krylov.pcg(lambda u: cg.apply_A(K, N, u), B.apply, b, rtol=rtol, flexible=True)
         mask = ~cg.boundary_mask(N)
@@ -49,7 +50,8 @@ def test_batch_members_match_the_oracle():
         lmax = spl.eigsh(Ai, k=1, which="LA", return_eigenvectors=False)[0]
         lmin = spl.eigsh(Ai, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
         bf16 = s_i % 2 == 1
-        solvers.append(lor.Solver(v, k, p, rtol=rtol, factor_bf16=bf16))
+        solvers.append(lor.Solver(v, k, p, rtol=rtol, factor_bf16=bf16,
+                                  ordering=lor.ORDER_RCM if order == "rcm" else lor.ORDER_LEX))
         bs.append(torch.from_numpy(b).cuda())
         refs.append((it_or, xd, lmax / lmin, bf16))
     batch = lor.Batch(solvers)

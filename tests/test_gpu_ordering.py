@@ -103,3 +103,46 @@ def test_ordering_is_set_before_setup_only():
     assert s.lib.lor_set_ordering(s.ctx, 1) == lor.LOR_ESTATE
     np.testing.assert_array_equal(s.patch_ordering(0, 13), np.arange(125))   # lexicographic: identity
     s.close()
+
+
+def test_orderings_combine_with_enlarged_patches_hybrid_and_dg():
+    """The ordered path under the other options: MDF on patches enlarged across an
+    anisotropic strip, RCM inside the hybrid Schwarz form, and RCM inside the DG
+    preconditioner's conforming part, each against the oracle built the same way."""
+    from oracle import dg as odg
+    from paper_1908_07071_gb300 import lor
+    from paper_1908_07071_gb300.synthetic import make_strip_mesh
+    # MDF on enlarged patches
+    v, k = make_strip_mesh(6, 150.0, layers=4, seed=0)
+    m = Mesh(v, k)
+    spans = olor.isotropic_overlap_spans(m)
+    B = olor.LORPreconditioner(m, 3, ordering="mdf", patch_spans=spans)
+    arr = np.ones((len(spans), 2, 2), dtype=np.int32)
+    for vv, per in spans.items():
+        arr[vv[0] + (m.n[0] + 1) * vv[1]] = np.array(per, dtype=np.int32)
+    s = lor.Solver(v, k, 3, ordering=lor.ORDER_MDF, patch_spans=arr)
+    r = random_vector(s.nvec, 43)
+    z = torch.full((s.nvec,), np.nan, dtype=torch.float64, device="cuda")
+    s.apply_P(torch.from_numpy(r).cuda(), z)
+    assert _rel(z.cpu().numpy(), B.apply(r)) < 1e-10
+    s.close()
+    # RCM inside the hybrid form
+    v, k = make_mesh(3, 3, seed=5, perturb=0.15)
+    m = Mesh(v, k)
+    B = olor.LORPreconditioner(m, 3, ordering="rcm")
+    s = lor.Solver(v, k, 3, ordering=lor.ORDER_RCM)
+    s.set_schwarz(1)
+    r = random_vector(s.nvec, 44)
+    z = torch.full((s.nvec,), np.nan, dtype=torch.float64, device="cuda")
+    s.apply_P(torch.from_numpy(r).cuda(), z)
+    assert _rel(z.cpu().numpy(), B.apply_hybrid(r)) < 1e-10
+    s.close()
+    # RCM inside B_DG
+    A = odg.assemble_dg(m, 3, 10.0, form="br2")
+    P = odg.DGPreconditioner(m, 3, A, olor.LORPreconditioner(m, 3, ordering="rcm"))
+    s = lor.Solver(v, k, 3, disc=lor.LOR_DG_BR2, eta=10.0, ordering=lor.ORDER_RCM)
+    r = random_vector(s.nvec, 45)
+    z = torch.full((s.nvec,), np.nan, dtype=torch.float64, device="cuda")
+    s.apply_P(torch.from_numpy(r).cuda(), z)
+    assert _rel(z.cpu().numpy(), P.apply(r)) < 1e-10
+    s.close()
