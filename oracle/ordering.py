@@ -40,7 +40,8 @@ def discarded_fill(a, pattern, alive, nbrs, i):
     for x, j in enumerate(nb):
         for y, k in enumerate(nb):
             if j != k and not pattern[j, k]:
-                s += (col[x] * row[y]) ** 2
+                v = col[x] * row[y]
+                s += v * v          # the square as a product (a power call may round differently)
     return float(np.sqrt(s))
 
 
