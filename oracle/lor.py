@@ -261,7 +261,7 @@ class LORPreconditioner:
     def __init__(self, mesh: Mesh, p: int, mg_levels: int = 0,
                  exact_local: bool = False, exact_coarse: bool = False, K_h=None,
                  patch_subset=None, coarse=True, ordering: str = "lex", weighting: str = "none",
-                 patch_spans=None, post_smooth0: bool = True):
+                 patch_spans=None, post_smooth0: bool = True, patch_orders=None):
         """patch_subset: vertex multi-indices whose patches are built (default all);
         patch_spans: {vertex: [(lo_k, hi_k) per axis]} element spans of enlarged patches
         (`isotropic_overlap_spans`, Section 4.5); vertices not listed keep the vertex patch;
@@ -274,7 +274,12 @@ class LORPreconditioner:
         sides by W_j = sqrt(theta_j), theta_j the Q1 vertex function of its vertex in
         the element reference coordinates at the level-0 nodes (`pou_weights`);
         post_smooth0=False leaves out the post-smoothing of the patch level 0 (the cycle
-        the learned correction's replace variant completes)."""
+        the learned correction's replace variant completes);
+        patch_orders: {(vertex, level): permutation} taken in place of the computed
+        ordering for those patch levels (an order is not unique when the ordering's
+        greedy choices tie, e.g. MDF on meshes with exact symmetries, so a check of
+        another implementation's ILU(0) in its own order needs that order)."""
+        self.patch_orders = patch_orders or {}
         self.post_smooth0 = post_smooth0
         self.ordering = ordering
         self.patch_spans = patch_spans or {}
@@ -325,7 +330,10 @@ class LORPreconditioner:
                     if self.ordering == "lex":
                         lev["LU"] = ilu0(Aj, pat)
                     else:
-                        perm = ordering.order_for(self.ordering, Aj, pat)
+                        perm = self.patch_orders.get((tuple(v), l))
+                        if perm is None:
+                            perm = ordering.order_for(self.ordering, Aj, pat)
+                        perm = np.asarray(perm, dtype=np.int64)
                         lev["LU"] = ilu0(Aj[np.ix_(perm, perm)], pat[np.ix_(perm, perm)])
                         lev["perm"] = perm
                 if l < L - 1:

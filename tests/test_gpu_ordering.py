@@ -112,15 +112,26 @@ def test_orderings_combine_with_enlarged_patches_hybrid_and_dg():
     from oracle import dg as odg
     from paper_1908_07071_gb300 import lor
     from paper_1908_07071_gb300.synthetic import make_strip_mesh
-    # MDF on enlarged patches
+    # MDF on enlarged patches.  The strip mesh is made of congruent rectangles with kappa = 1,
+    # so MDF's greedy choices tie exactly in exact arithmetic and the last bits of the patch
+    # matrices (assembled in another order by the oracle) decide them: the order is not
+    # unique.  The oracle factors and sweeps in the library's own orders, which must be
+    # permutations; what is unique, B r in those orders, is compared.
     v, k = make_strip_mesh(6, 150.0, layers=4, seed=0)
     m = Mesh(v, k)
     spans = olor.isotropic_overlap_spans(m)
-    B = olor.LORPreconditioner(m, 3, ordering="mdf", patch_spans=spans)
     arr = np.ones((len(spans), 2, 2), dtype=np.int32)
     for vv, per in spans.items():
         arr[vv[0] + (m.n[0] + 1) * vv[1]] = np.array(per, dtype=np.int32)
     s = lor.Solver(v, k, 3, ordering=lor.ORDER_MDF, patch_spans=arr)
+    orders = {}
+    for vv in spans:
+        j = vv[0] + (m.n[0] + 1) * vv[1]
+        for lev in range(2):                          # Q3: levels [3, 2, 1], two smoothed levels
+            perm = s.patch_ordering(lev, j)
+            assert sorted(perm.tolist()) == list(range(len(perm)))
+            orders[(tuple(vv), lev)] = perm
+    B = olor.LORPreconditioner(m, 3, ordering="mdf", patch_spans=spans, patch_orders=orders)
     r = random_vector(s.nvec, 43)
     z = torch.full((s.nvec,), np.nan, dtype=torch.float64, device="cuda")
     s.apply_P(torch.from_numpy(r).cuda(), z)
