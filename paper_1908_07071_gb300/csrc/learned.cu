@@ -190,7 +190,10 @@ __device__ __forceinline__ void sts128(unsigned addr, uint4 v) {
 
 // Padded input box of patch k in shared memory (rows of 16 bf16 channels, zero
 // halo).  IN 0: bf16 rows with ReLU applied (a = max(z, 0)); IN 1: bf16 rows as
-// they are; IN 2: fp32 channel-planar [nin][V] (nin <= 2), rounded to bf16.
+// they are; IN 2: fp32 channel-planar [nin][V] (nin <= 2), rounded to bf16 and
+// packed along x: the row of voxel (i, j, k) holds the nin channels of voxels
+// i-1, i, i+1 (columns 2 dxi + c, zero outside the box), so that a convolution
+// takes the three x-taps in one K = 16 step and loops over 9 (dy, dz) groups.
 template <int IN>
 __device__ __forceinline__ void load_box(const PBox& b, int k, int nin, const void* __restrict__ in, unsigned char* box) {
   const int P0 = b.A + 2, P1 = b.B + 2, P2 = b.C + 2;
@@ -205,7 +208,13 @@ __device__ __forceinline__ void load_box(const PBox& b, int k, int nin, const vo
       if constexpr (IN == 2) {
         if (h == 0) {
           const float* f = (const float*)in + (long long)k * nin * b.V;
-          val.x = pack_bf16(f[v], nin > 1 ? f[b.V + v] : 0.0f);
+          unsigned w3[3];
+          for (int dxi = 0; dxi < 3; ++dxi) {
+            const int ii = pi - 1 + dxi - 1;
+            w3[dxi] = 0u;
+            if (ii >= 0 && ii < b.A) w3[dxi] = pack_bf16(f[v + dxi - 1], nin > 1 ? f[b.V + v + dxi - 1] : 0.0f);
+          }
+          val.x = w3[0]; val.y = w3[1]; val.z = w3[2];
         }
       } else {
         val = ((const uint4*)in)[((long long)k * b.V + v) * 2 + h];
@@ -220,7 +229,7 @@ __device__ __forceinline__ void load_box(const PBox& b, int k, int nin, const vo
 }
 
 // Implicit-GEMM convolution of one patch per CTA (256 threads, 8 warps, tiles of
-// 16 voxels).  Wt: [27][16 n][16 k] bf16.  OUT 0: bf16 rows out[v][n] = acc + bias[n]
+// 16 voxels).  Wt: [27][16 n][16 k] bf16 (IN 2: [9 (dy, dz) groups][16 n][16 packed k]).  OUT 0: bf16 rows out[v][n] = acc + bias[n]
 // (pre-activation); OUT 1: bf16 rows masked, out[v][n] = zmask[v][n] > 0 ? acc : 0
 // (a backward-data step through a ReLU); OUT 2: fp32 out[v] = acc[v][0] + bias[0].
 template <int IN, int OUT>
@@ -247,9 +256,11 @@ __global__ void __launch_bounds__(256) k_tc_conv(PBox b, int nin, const void* __
     const int i = v % b.A, j = (v / b.A) % b.B, kk = v / (b.A * b.B);
     const int prow = ((kk + 1) * P1 + (j + 1)) * P0 + (i + 1);
     float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    constexpr int NT = IN == 2 ? 9 : 27;   // x-packed input: one step per (dy, dz)
 #pragma unroll 3
-    for (int tap = 0; tap < 27; ++tap) {
-      const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+    for (int tap = 0; tap < NT; ++tap) {
+      const int dx = IN == 2 ? 0 : tap % 3 - 1;
+      const int dy = IN == 2 ? tap % 3 - 1 : (tap / 3) % 3 - 1, dz = IN == 2 ? tap / 3 - 1 : tap / 9 - 1;
       const int r = prow + (dz * P1 + dy) * P0 + dx;
       unsigned a[4], bq[4];
       ldsm4(swz(bbase, r, hl), a);
@@ -299,8 +310,9 @@ __global__ void __launch_bounds__(256) k_tc_conv(PBox b, int nin, const void* __
 // Weight gradient of one patch per CTA: dWp[k][tap][o][ci] = sum_v g[v][o] act[v + tap][ci]
 // and dbp[k][o] = sum_v g[v][o].  GIN 0: g as bf16 rows; GIN 1: g fp32 [V] (one
 // channel), rounded to bf16.  AIN: the activation box as in load_box (0: bf16 rows
-// + ReLU, 2: fp32 planar x0).  The voxels stream through shared memory 64 at a
-// time; warp w accumulates the taps w, w+8, w+16, w+24.
+// + ReLU, 2: fp32 planar x0, packed along x: the tap slots are then the 9 (dy, dz)
+// groups and the columns 2 dxi + ci).  The voxels stream through shared memory 64
+// at a time; warp w accumulates the tap slots w, w+8, w+16, w+24.
 template <int GIN, int AIN>
 __global__ void __launch_bounds__(256) k_tc_wgrad(PBox b, int nin, const void* __restrict__ gin,
                                                   const void* __restrict__ act, float* __restrict__ dWp,
@@ -356,8 +368,9 @@ __global__ void __launch_bounds__(256) k_tc_wgrad(PBox b, int nin, const void* _
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int tap = warp + 8 * m;
-        if (tap < 27) {
-          const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+        if (tap < (AIN == 2 ? 9 : 27)) {
+          const int dx = AIN == 2 ? 0 : tap % 3 - 1;
+          const int dy = AIN == 2 ? tap % 3 - 1 : (tap / 3) % 3 - 1, dz = AIN == 2 ? tap / 3 - 1 : tap / 9 - 1;
           unsigned bq[4];
           ldsm4t(swz(bbase, prow + (dz * P1 + dy) * P0 + dx, bh), bq);
           mma16816(acc[m][0], a, bq[0], bq[1]);
@@ -370,7 +383,7 @@ __global__ void __launch_bounds__(256) k_tc_wgrad(PBox b, int nin, const void* _
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     const int tap = warp + 8 * m;
-    if (tap >= 27) continue;
+    if (tap >= (AIN == 2 ? 9 : 27)) continue;
     float* d = dWp + ((long long)k * 27 + tap) * 256;
 #pragma unroll
     for (int nh = 0; nh < 2; ++nh) {
@@ -385,15 +398,17 @@ __global__ void __launch_bounds__(256) k_tc_wgrad(PBox b, int nin, const void* _
 }
 
 // G[W][o][ci][tap] = sum over the S patches (in order) of dWp[k][tap][o][ci], for
-// o < cout, ci < cin; G[b][o] likewise from dbp.
-__global__ void k_tc_wreduce(int S, int cin, int cout, const float* __restrict__ dWp, const float* __restrict__ dbp,
-                             float* __restrict__ GW, float* __restrict__ Gb) {
+// o < cout, ci < cin (packed: dWp[k][tap / 3][o][2 (tap % 3) + ci], the x-packed
+// layout); G[b][o] likewise from dbp.
+__global__ void k_tc_wreduce(int S, int cin, int cout, int packed, const float* __restrict__ dWp,
+                             const float* __restrict__ dbp, float* __restrict__ GW, float* __restrict__ Gb) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int nw = cout * cin * 27;
   if (idx < nw) {
     const int tap = idx % 27, ci = (idx / 27) % cin, o = idx / (27 * cin);
+    const int slot = packed ? tap / 3 : tap, col = packed ? 2 * (tap % 3) + ci : ci;
     float s = 0.f;
-    for (int k = 0; k < S; ++k) s += dWp[((long long)k * 27 + tap) * 256 + o * 16 + ci];
+    for (int k = 0; k < S; ++k) s += dWp[((long long)k * 27 + slot) * 256 + o * 16 + col];
     GW[idx] = s;
   } else if (idx < nw + cout) {
     const int o = idx - nw;
@@ -406,17 +421,29 @@ __global__ void k_tc_wreduce(int S, int cin, int cout, const float* __restrict__
 // Tensor-core weight sets from the bf16 parameters W[o][ci][tap] (cout x cin):
 // forward Wt[tap][n = o][k = ci]; backward data (the transposed convolution, taps
 // mirrored) Wt[tap][n = ci][k = o] = W[o][ci][26 - tap]; zero outside the layer's
-// channels.  Padded biases: bias16[n] = b[n] for n < cout, else 0.
+// channels.  packed (for an x-packed input, at most 2 input channels): slot g =
+// (dz+1) 3 + (dy+1) and column 2 dxi + c hold the entry of tap 3 g + dxi, channel c.
+// Padded biases: bias16[n] = b[n] for n < cout, else 0.
 __global__ void k_tc_prep(const __nv_bfloat16* __restrict__ Wb, const float* __restrict__ bias, int cin, int cout,
-                          int transpose, __nv_bfloat16* __restrict__ Wt, float* __restrict__ bias16) {
+                          int transpose, int packed, __nv_bfloat16* __restrict__ Wt, float* __restrict__ bias16) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < 27 * 256) {
-    const int tap = idx / 256, n = (idx / 16) % 16, kk = idx % 16;
+    const int slot = idx / 256, n = (idx / 16) % 16, col = idx % 16;
+    // the tap and the input channel (k) of this entry
+    int tap = slot, kk = col;
+    bool live = true;
+    if (packed) {
+      tap = 3 * slot + col / 2;
+      kk = col % 2;
+      live = slot < 9 && col < 6;
+    }
     __nv_bfloat16 w = __float2bfloat16(0.0f);
-    if (!transpose) {
-      if (n < cout && kk < cin) w = Wb[(n * cin + kk) * 27 + tap];
-    } else {
-      if (kk < cout && n < cin) w = Wb[(kk * cin + n) * 27 + (26 - tap)];
+    if (live) {
+      if (!transpose) {
+        if (n < cout && kk < cin) w = Wb[(n * cin + kk) * 27 + tap];
+      } else {
+        if (kk < cout && n < cin) w = Wb[(kk * cin + n) * 27 + (26 - tap)];
+      }
     }
     Wt[idx] = w;
   }
@@ -580,11 +607,12 @@ static lor_status learned_init(lor_ctx* c) {
 static void prep_weights(lor_ctx* c) {
   LearnState* s = LS(c);
   const unsigned g = (27 * 256 + 255) / 256;
-  k_tc_prep<<<g, 256, 0, c->stream>>>(s->Pb + OFF_W1, s->P + OFF_B1, 2, CH, 0, s->Wt[0], s->bias16[0]);
-  k_tc_prep<<<g, 256, 0, c->stream>>>(s->Pb + OFF_W2, s->P + OFF_B2, CH, CH, 0, s->Wt[1], s->bias16[1]);
-  k_tc_prep<<<g, 256, 0, c->stream>>>(s->Pb + OFF_W3, s->P + OFF_B3, CH, 1, 0, s->Wt[2], s->bias16[2]);
-  k_tc_prep<<<g, 256, 0, c->stream>>>(s->Pb + OFF_W3, nullptr, CH, 1, 1, s->Wt[3], nullptr);
-  k_tc_prep<<<g, 256, 0, c->stream>>>(s->Pb + OFF_W2, nullptr, CH, CH, 1, s->Wt[4], nullptr);
+  // layer 1 reads the x-packed features, the layer-3 backward-data step the x-packed gy
+  k_tc_prep<<<g, 256, 0, c->stream>>>(s->Pb + OFF_W1, s->P + OFF_B1, 2, CH, 0, 1, s->Wt[0], s->bias16[0]);
+  k_tc_prep<<<g, 256, 0, c->stream>>>(s->Pb + OFF_W2, s->P + OFF_B2, CH, CH, 0, 0, s->Wt[1], s->bias16[1]);
+  k_tc_prep<<<g, 256, 0, c->stream>>>(s->Pb + OFF_W3, s->P + OFF_B3, CH, 1, 0, 0, s->Wt[2], s->bias16[2]);
+  k_tc_prep<<<g, 256, 0, c->stream>>>(s->Pb + OFF_W3, nullptr, CH, 1, 1, 1, s->Wt[3], nullptr);
+  k_tc_prep<<<g, 256, 0, c->stream>>>(s->Pb + OFF_W2, nullptr, CH, CH, 1, 0, s->Wt[4], nullptr);
   c->launches += 5;
 }
 
@@ -612,17 +640,17 @@ static void backward(lor_ctx* c, int S, const int* ids, const float* t, const fl
                  gw1 = (unsigned)lor_ceil_div(CH * 2 * 27 + CH, 256);
   // layer 3: weight gradient from gy and a2 = relu(z2); data gradient g2 = (W3^T gy) relu'(z2)
   k_tc_wgrad<1, 0><<<S, 256, s->smem_wgrad, c->stream>>>(b, 0, s->gy, s->z2, s->dWp, s->dbp);
-  k_tc_wreduce<<<gw3, 256, 0, c->stream>>>(S, CH, 1, s->dWp, s->dbp, s->G + OFF_W3, s->G + OFF_B3);
+  k_tc_wreduce<<<gw3, 256, 0, c->stream>>>(S, CH, 1, 0, s->dWp, s->dbp, s->G + OFF_W3, s->G + OFF_B3);
   k_tc_conv<2, 1><<<S, 256, s->smem_conv, c->stream>>>(b, 1, s->gy, s->Wt[3], nullptr, (const __nv_bfloat16*)s->z2,
                                                         s->g2);
   // layer 2: weight gradient from g2 and a1 = relu(z1); g1 = (W2^T g2) relu'(z1)
   k_tc_wgrad<0, 0><<<S, 256, s->smem_wgrad, c->stream>>>(b, 0, s->g2, s->z1, s->dWp, s->dbp);
-  k_tc_wreduce<<<gw2, 256, 0, c->stream>>>(S, CH, CH, s->dWp, s->dbp, s->G + OFF_W2, s->G + OFF_B2);
+  k_tc_wreduce<<<gw2, 256, 0, c->stream>>>(S, CH, CH, 0, s->dWp, s->dbp, s->G + OFF_W2, s->G + OFF_B2);
   k_tc_conv<1, 1><<<S, 256, s->smem_conv, c->stream>>>(b, 0, s->g2, s->Wt[4], nullptr, (const __nv_bfloat16*)s->z1,
                                                         s->g1);
   // layer 1: weight gradient from g1 and the features x0
   k_tc_wgrad<0, 2><<<S, 256, s->smem_wgrad, c->stream>>>(b, 2, s->g1, s->x0, s->dWp, s->dbp);
-  k_tc_wreduce<<<gw1, 256, 0, c->stream>>>(S, 2, CH, s->dWp, s->dbp, s->G + OFF_W1, s->G + OFF_B1);
+  k_tc_wreduce<<<gw1, 256, 0, c->stream>>>(S, 2, CH, 1, s->dWp, s->dbp, s->G + OFF_W1, s->G + OFF_B1);
   c->launches += 10;
 }
 
