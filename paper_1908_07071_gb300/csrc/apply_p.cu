@@ -4,7 +4,8 @@
 // of the element-structured hierarchy (Section 3.3) smoothed by lexicographic
 // ILU(0) (Section 3.4).
 //
-// Patch kernel: each warp runs the whole V-cycle of one patch at a time:
+// Patch kernel: each patch group (one warp, or two warps when shared memory
+// holds at most 8 patches per SM) runs the whole V-cycle of one patch at a time:
 // gather R_j r, per level ILU(0) pre-smoothing (wavefront-scheduled forward and
 // backward sweeps over factor records streamed by bulk copies), 3^d-point
 // residual with the level's Galerkin LOR stencil, tensor restriction, exact
@@ -13,10 +14,11 @@
 // per-patch buffer, and a gather kernel sums the slices of the (at most 2^d)
 // patches containing each node in a fixed order, so z is reproducible bit for
 // bit.  Many patches
-// are in flight per SM (one per warp), so the latency-bound sweeps of one patch
-// overlap those of the others.  Vectors live in zero-padded boxes so that
-// factor reads need no bounds checks (factors of out-of-box couplings are
-// stored as 0); the level-0 iterate is kept in a per-warp global slot (L2) and
+// are in flight per SM (one per group), so the latency-bound sweeps of one patch
+// overlap those of the others; a two-warp group splits the rows of every loop
+// and of every wavefront between its warps.  Vectors live in zero-padded boxes
+// so that factor reads need no bounds checks (factors of out-of-box couplings
+// are stored as 0); the level-0 iterate is kept in a per-group global slot (L2) and
 // the level-0 residual is formed in place, which keeps a patch's shared-memory
 // footprint to the level-0 work vector, the coarse levels and the copy ring.
 //
@@ -69,12 +71,12 @@ struct PatchArgs {
   long long zstride;
   int* status;
   int slot_bytes;               // ring slot size (bytes, multiple of 16)
-  int tab_ints;                 // per-warp shared-memory ints reserved for wavefront tables
+  int tab_ints;                 // per-group shared-memory ints reserved for wavefront tables
   int xf_bytes;                 // shared transfer tables at the start of dynamic shared memory
-  int warp_bytes;               // per-warp block size (bytes, multiple of 128)
-  int aux_n;                    // per-warp vector layout: auxiliary buffers (plane buffers / r1)
+  int warp_bytes;               // per-group block size (bytes, multiple of 128)
+  int aux_n;                    // per-group vector layout: auxiliary buffers (plane buffers / r1)
   int ovl_n;                    //   then level-0 t with guards, overlaid by the coarse levels
-  void* xs;                     // per-warp level-0 iterate slots (T), x0_stride values each
+  void* xs;                     // per-group level-0 iterate slots (T), x0_stride values each
   long long x0_stride;
   const int* porder;            // patch visiting order (grouped by box shape)
   const double* conv;           // optional: skip all work when *conv != 0 (converged batched solve)
@@ -149,6 +151,20 @@ struct Ring {
   unsigned inflight;  // producer view: bit s set while a copy into slot s is pending
 };
 
+
+// The threads that run one patch: one warp (WG = 1) or two warps (WG = 2, named
+// barrier 1 + group index over their 64 threads).  Every branch that a group
+// takes around a sync() depends only on values the whole group holds alike.
+template <int WG>
+struct Grp {
+  static constexpr int NT = 32 * WG;
+  int gl;   // thread index in the group
+  int id;   // group index in the CTA
+  __device__ __forceinline__ void sync() const {
+    if constexpr (WG == 1) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + id), "r"(NT) : "memory");
+  }
+};
 
 // One factor record held in registers: R values of type FT as 32-bit words.
 template <int R, typename FT>
@@ -242,50 +258,60 @@ __device__ __forceinline__ void sweep_front(const FT* const* rec, int* li, const
   for (int u = 0; u < NR; ++u) li[u] = ln[u];
 }
 
-// One triangular sweep over a level, run by ONE warp.  Factor blocks stream
-// through the ring in chunks of whole fronts: lane 0 issues the bulk copies and
-// observes their completion, __syncwarp publishes them to the other lanes.
-// Inside a chunk, lane q takes records q and q+32 of a front (fronts hold at
-// most 64 records; the second row only when the front is wider than 32).  A
-// lane without a row reads the all-zero record zrec, whose row index `dummy`
-// is the first guard cell after the box, and writes 0 there, like a padding
-// record.  The row indices of the next front are read ahead so that a front's
-// critical path is one round of shared-memory loads of t.  __syncwarp
-// separates fronts.  t has a zero guard band, so neighbour reads need no
-// clamping (multipliers of out-of-box neighbours are stored as 0).  BACK
-// selects the backward sweep (U part, fronts in reverse, scaled by 1/u_ii).
-template <int DIM, bool BACK, typename T, typename FT, int NBUF, bool GEN>
+// One triangular sweep over a level, run by one patch group.  Factor blocks
+// stream through the ring in chunks of whole fronts: thread 0 of the group issues
+// the bulk copies and observes their completion, then publishes it (and whether
+// the copy arrived in time) to the group.  Inside a chunk, a one-warp group takes
+// records q and q+32 of a front in lane q (fronts hold at most 64 records; the
+// second row only when the front is wider than 32); a two-warp group takes record
+// q in thread q, and its second warp sits out fronts of at most 32 rows.  A thread
+// without a row reads the all-zero record zrec, whose row index `dummy` is the
+// first guard cell after the box, and writes 0 there, like a padding record.  The
+// row indices of the next front are read ahead so that a front's critical path is
+// one round of shared-memory loads of t.  The group synchronizes between fronts.
+// t has a zero guard band, so neighbour reads need no clamping (multipliers of
+// out-of-box neighbours are stored as 0).  BACK selects the backward sweep (U
+// part, fronts in reverse, scaled by 1/u_ii).  okf: a shared word of the group.
+template <int DIM, bool BACK, typename T, typename FT, int NBUF, bool GEN, int WG>
 __device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __restrict__ fp,
                                       const int* __restrict__ ch, int nc, int A, int AB, int dummy,
-                                      const FT* zrec, T* t, Ring<FT, NBUF>& rg) {
+                                      const FT* zrec, T* t, Ring<FT, NBUF>& rg, const Grp<WG>& g, int* okf) {
   constexpr int R = GEN ? lor_rec_gen(DIM) : lor_rec(DIM);
-  const int lane = threadIdx.x & 31;
-  if (lane == 0) {
+  const int gl = g.gl;
+  // chunk c of the sweep (fronts in reverse order when BACK): its records
+  auto chunk_src = [&](int c) { return part + (long long)fp[ch[BACK ? nc - 1 - c : c]] * R; };
+  auto chunk_bytes = [&](int c) {
+    const int k = BACK ? nc - 1 - c : c;
+    return (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * R * sizeof(FT));
+  };
+  if (gl == 0) {
     for (int c = 0; c < NBUF - 1 && c < nc; ++c) {
-      const int k = BACK ? nc - 1 - c : c;
-      bulk_load(rg.slot(c % NBUF), part + (long long)fp[ch[k]] * R,
-                (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * R * sizeof(FT)), rg.bar + (c % NBUF));
+      bulk_load(rg.slot(c % NBUF), chunk_src(c), chunk_bytes(c), rg.bar + (c % NBUF));
       rg.inflight |= 1u << (c % NBUF);
     }
   }
   for (int c = 0; c < nc; ++c) {
     const int sl = c % NBUF;
     int ok = 1;
-    if (lane == 0) ok = mbar_wait(rg.bar + sl, (rg.phase >> sl) & 1u) ? 1 : 0;
+    if (gl == 0) ok = mbar_wait(rg.bar + sl, (rg.phase >> sl) & 1u) ? 1 : 0;
     rg.phase ^= 1u << sl;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if constexpr (WG == 1) {
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+    } else {
+      if (gl == 0) *okf = ok;
+      g.sync();
+      ok = *okf;
+    }
     if (!ok) return false;
-    if (lane == 0) {
+    if (gl == 0) {
       rg.inflight &= ~(1u << sl);
       const int cn = c + NBUF - 1;
       if (cn < nc) {
-        const int k = BACK ? nc - 1 - cn : cn;
-        bulk_load(rg.slot(cn % NBUF), part + (long long)fp[ch[k]] * R,
-                  (unsigned)((fp[ch[k + 1]] - fp[ch[k]]) * R * sizeof(FT)), rg.bar + (cn % NBUF));
+        bulk_load(rg.slot(cn % NBUF), chunk_src(cn), chunk_bytes(cn), rg.bar + (cn % NBUF));
         rg.inflight |= 1u << (cn % NBUF);
       }
     }
-    __syncwarp();
+    if constexpr (WG == 1) __syncwarp();
     const FT* blk = rg.slot(sl);
     const int k = BACK ? nc - 1 - c : c;
     const int fa = ch[k], fb = ch[k + 1], nf = fb - fa;
@@ -293,68 +319,93 @@ __device__ __forceinline__ bool sweep(const FT* __restrict__ part, const int* __
     // records [b, e) of the block for the current front, and their row indices
     int f = BACK ? fb - 1 : fa;
     int b = fp[f] - r0, e = fp[f + 1] - r0;
-    int li[2];
-    li[0] = lane < e - b ? rec_index<R, FT>(blk + (b + lane) * R) : dummy;
-    li[1] = lane + 32 < e - b ? rec_index<R, FT>(blk + (b + lane + 32) * R) : dummy;
-    for (int q = 0; q < nf; ++q) {
-      const int n = e - b;
-      const bool more = q + 1 < nf;
-      // the next front shares one bound with this one
-      int bn = b, en = e;
-      if (more) {
-        if (BACK) { en = b; bn = fp[f - 1] - r0; }
-        else { bn = e; en = fp[f + 2] - r0; }
+    if constexpr (WG == 1) {
+      const int lane = gl;
+      int li[2];
+      li[0] = lane < e - b ? rec_index<R, FT>(blk + (b + lane) * R) : dummy;
+      li[1] = lane + 32 < e - b ? rec_index<R, FT>(blk + (b + lane + 32) * R) : dummy;
+      for (int q = 0; q < nf; ++q) {
+        const int n = e - b;
+        const bool more = q + 1 < nf;
+        // the next front shares one bound with this one
+        int bn = b, en = e;
+        if (more) {
+          if (BACK) { en = b; bn = fp[f - 1] - r0; }
+          else { bn = e; en = fp[f + 2] - r0; }
+        }
+        const FT* rec[2] = {lane < n ? blk + (b + lane) * R : zrec, lane + 32 < n ? blk + (b + lane + 32) * R : zrec};
+        const FT* nrec[2] = {lane < en - bn ? blk + (bn + lane) * R : zrec,
+                             lane + 32 < en - bn ? blk + (bn + lane + 32) * R : zrec};
+        if (n > 32) {   // warp-uniform
+          sweep_front<DIM, BACK, T, FT, 2, GEN>(rec, li, nrec, more, A, AB, t);
+        } else {
+          sweep_front<DIM, BACK, T, FT, 1, GEN>(rec, li, nrec, more, A, AB, t);
+          li[1] = more ? rec_index<R, FT>(nrec[1]) : dummy;
+        }
+        if (more) {
+          // lanes past the next front's rows take the zero record (index dummy)
+          if (!(lane < en - bn)) li[0] = dummy;
+          if (!(lane + 32 < en - bn)) li[1] = dummy;
+        }
+        f = BACK ? f - 1 : f + 1; b = bn; e = en;
+        __syncwarp();
       }
-      const FT* rec[2] = {lane < n ? blk + (b + lane) * R : zrec, lane + 32 < n ? blk + (b + lane + 32) * R : zrec};
-      const FT* nrec[2] = {lane < en - bn ? blk + (bn + lane) * R : zrec,
-                           lane + 32 < en - bn ? blk + (bn + lane + 32) * R : zrec};
-      if (n > 32) {   // warp-uniform
-        sweep_front<DIM, BACK, T, FT, 2, GEN>(rec, li, nrec, more, A, AB, t);
-      } else {
-        sweep_front<DIM, BACK, T, FT, 1, GEN>(rec, li, nrec, more, A, AB, t);
-        li[1] = more ? rec_index<R, FT>(nrec[1]) : dummy;
+    } else {
+      const int w32 = gl & ~31;   // first record of this warp
+      int li[1];
+      li[0] = gl < e - b ? rec_index<R, FT>(blk + (b + gl) * R) : dummy;
+      for (int q = 0; q < nf; ++q) {
+        const int n = e - b;
+        const bool more = q + 1 < nf;
+        int bn = b, en = e;
+        if (more) {
+          if (BACK) { en = b; bn = fp[f - 1] - r0; }
+          else { bn = e; en = fp[f + 2] - r0; }
+        }
+        const FT* rec[1] = {gl < n ? blk + (b + gl) * R : zrec};
+        const FT* nrec[1] = {gl < en - bn ? blk + (bn + gl) * R : zrec};
+        if (n > w32) sweep_front<DIM, BACK, T, FT, 1, GEN>(rec, li, nrec, more, A, AB, t);   // warp-uniform
+        else li[0] = more ? rec_index<R, FT>(nrec[0]) : dummy;
+        if (more && !(gl < en - bn)) li[0] = dummy;
+        f = BACK ? f - 1 : f + 1; b = bn; e = en;
+        g.sync();
       }
-      if (more) {
-        // lanes past the next front's rows take the zero record (index dummy)
-        if (!(lane < en - bn)) li[0] = dummy;
-        if (!(lane + 32 < en - bn)) li[1] = dummy;
-      }
-      f = BACK ? f - 1 : f + 1; b = bn; e = en;
-      __syncwarp();
     }
   }
   return true;
 }
 
-// in-place (L U)^{-1} t on one level, run by the calling warp (forward then
-// backward sweep).  Returns false if a bulk copy timed out.
+// in-place (L U)^{-1} t on one level, run by the calling group (forward then
+// backward sweep).  Returns false if a bulk copy timed out (the whole group
+// returns false).
 template <typename FT>
 constexpr int elem_class() { return sizeof(FT) == 2 ? 0 : (sizeof(FT) == 4 ? 1 : 2); }
 
-template <int DIM, typename T, typename FT, int NBUF, bool GEN>
+template <int DIM, typename T, typename FT, int NBUF, bool GEN, int WG>
 __device__ __forceinline__ bool ilu_solve(const BoxShape& bs, const int* fp, const int* ch, const FT* FL, T* t,
-                                          Ring<FT, NBUF>& rg, const FT* zrec) {
+                                          Ring<FT, NBUF>& rg, const FT* zrec, const Grp<WG>& g, int* okf) {
   constexpr int ES = elem_class<FT>();
   constexpr int R = GEN ? lor_rec_gen(DIM) : lor_rec(DIM);
   const int A = bs.dims[0], AB = bs.dims[0] * bs.dims[1];
-  bool ok = sweep<DIM, false, T, FT, NBUF, GEN>(FL, fp, ch, bs.nchunk[ES], A, AB, bs.rows, zrec, t, rg);
+  bool ok = sweep<DIM, false, T, FT, NBUF, GEN, WG>(FL, fp, ch, bs.nchunk[ES], A, AB, bs.rows, zrec, t, rg, g, okf);
   if (ok)
-    ok = sweep<DIM, true, T, FT, NBUF, GEN>(FL + (long long)bs.rpad * R, fp, ch, bs.nchunk[ES], A, AB, bs.rows, zrec,
-                                             t, rg);
-  __syncwarp();
+    ok = sweep<DIM, true, T, FT, NBUF, GEN, WG>(FL + (long long)bs.rpad * R, fp, ch, bs.nchunk[ES], A, AB, bs.rows,
+                                                 zrec, t, rg, g, okf);
+  g.sync();
   return ok;
 }
 
-// Lane-strided walk over the rows of a box in lexicographic order: the lane
-// starts at row lex0 and advances by 32 rows per step, tracking (i, j, k).
+// Strided walk over the rows of a box in lexicographic order: the thread starts
+// at row lex0 and advances by `stride` rows per step (the threads of its patch
+// group), tracking (i, j, k).
 struct BoxIter {
   int i, j, k;
-  int si, sj, sk;   // 32 = sk*A*B + sj*A + si
+  int si, sj, sk;   // stride = sk*A*B + sj*A + si
   int A, B;
-  __device__ __forceinline__ void init(int lex0, int A_, int B_) {
+  __device__ __forceinline__ void init(int lex0, int A_, int B_, int stride) {
     A = A_; B = B_;
     i = lex0 % A; j = (lex0 / A) % B; k = lex0 / (A * B);
-    si = 32 % A; sj = (32 / A) % B; sk = 32 / (A * B);
+    si = stride % A; sj = (stride / A) % B; sk = stride / (A * B);
   }
   __device__ __forceinline__ void next() {
     i += si;
@@ -454,12 +505,13 @@ __device__ __forceinline__ void hat_offsets(int j, int n0, int n1, int p, int* h
 // into tmp from prev (x of plane k-1, guarded) and t (planes k, k+1 still x),
 // then plane k's x moves to prev (and to xout, when given) and tmp into t.
 // wp > 0: the global right-hand side is weighted (node_weight with mode wmode).
-template <int DIM, typename T>
+template <int DIM, typename T, int WG>
 __device__ void resid0_inplace(const WLevel& b, const PLevel& lv, const T* __restrict__ rg0,
                                const T* __restrict__ rloc, T* t, T* prev, T* tmp, T* xout, int wp, int wmode,
-                               int jp, int n0, int n1, const T* __restrict__ hat) {
+                               int jp, int n0, int n1, const T* __restrict__ hat, const Grp<WG>& g) {
   constexpr int NSP = lor_nsp(DIM);
-  const int lane = threadIdx.x & 31;
+  constexpr int NT = Grp<WG>::NT;
+  const int gl = g.gl;
   const int A = b.A, B = b.B, C = b.C, AB = A * B;
   const T* Sa = (const T*)lv.Sa;
   const int N0 = lv.N[0], N1 = lv.N[1];
@@ -467,8 +519,8 @@ __device__ void resid0_inplace(const WLevel& b, const PLevel& lv, const T* __res
   if (wmode == 2) hat_offsets<DIM>(jp, n0, n1, wp, ho);
   for (int k = 0; k < C; ++k) {
     BoxIter it;
-    it.init(lane, A, B);   // walks plane-local rows (k component unused)
-    for (int p = lane; p < AB; p += 32, it.next()) {
+    it.init(gl, A, B, NT);   // walks plane-local rows (k component unused)
+    for (int p = gl; p < AB; p += NT, it.next()) {
       const int i = it.i, j = it.j;
       const int lex = k * AB + p;
       const int G = ((b.org[2] + k) * N1 + (b.org[1] + j)) * N0 + (b.org[0] + i);
@@ -480,28 +532,28 @@ __device__ void resid0_inplace(const WLevel& b, const PLevel& lv, const T* __res
         return dz < 0 ? prev[p + dy * A + dx] : t[lex + dz * AB + dy * A + dx];
       });
     }
-    __syncwarp();
-    for (int p = lane; p < AB; p += 32) {
+    g.sync();
+    for (int p = gl; p < AB; p += NT) {
       const T xv = t[k * AB + p];
       prev[p] = xv;
       if (xout) xout[k * AB + p] = xv;
       t[k * AB + p] = tmp[p];
     }
-    __syncwarp();
+    g.sync();
   }
 }
 
 // t = r - A x on a level l >= 1 (separate guarded arrays).
-template <int DIM, typename T>
-__device__ void resid_level(const WLevel& b, const PLevel& lv, const T* r, const T* x, T* t) {
+template <int DIM, typename T, int WG>
+__device__ void resid_level(const WLevel& b, const PLevel& lv, const T* r, const T* x, T* t, const Grp<WG>& g) {
   constexpr int NSP = lor_nsp(DIM);
-  const int lane = threadIdx.x & 31;
+  constexpr int NT = Grp<WG>::NT;
   const int A = b.A, B = b.B, C = b.C, AB = A * B;
   const T* Sa = (const T*)lv.Sa;
   const int N0 = lv.N[0], N1 = lv.N[1];
   BoxIter it;
-  it.init(lane, A, B);
-  for (int lex = lane; lex < b.rows; lex += 32, it.next()) {
+  it.init(g.gl, A, B, NT);
+  for (int lex = g.gl; lex < b.rows; lex += NT, it.next()) {
     const int G = ((b.org[2] + it.k) * N1 + (b.org[1] + it.j)) * N0 + (b.org[0] + it.i);
     T s[NSP];
     load_row<DIM, T>(Sa, G, s);
@@ -509,18 +561,18 @@ __device__ void resid_level(const WLevel& b, const PLevel& lv, const T* r, const
       return x[lex + dz * AB + dy * A + dx];
     });
   }
-  __syncwarp();
+  g.sync();
 }
 
 // r_c = R t: tensor restriction of a level-l vector to level l+1 (patch-local).
-template <int DIM, typename T, typename X>
+template <int DIM, typename T, typename X, int WG>
 __device__ void restrict_level(const WLevel& bf, const WLevel& bc, const X& X0, const X& X1, const X& X2, const T* tl,
-                               T* rn) {
-  const int lane = threadIdx.x & 31;
+                               T* rn, const Grp<WG>& g) {
+  constexpr int NT = Grp<WG>::NT;
   const int fA = bf.A, fB = bf.B, cA = bc.A, cB = bc.B;
   BoxIter it;
-  it.init(lane, cA, cB);
-  for (int lex = lane; lex < bc.rows; lex += 32, it.next()) {
+  it.init(g.gl, cA, cB, NT);
+  for (int lex = g.gl; lex < bc.rows; lex += NT, it.next()) {
     const int ci = it.i, cj = it.j, ck = it.k;
     T s = 0;
     const int z0 = DIM == 3 ? X2.rstart[ck] : 0, z1 = DIM == 3 ? X2.rstart[ck + 1] : 1;
@@ -535,7 +587,7 @@ __device__ void restrict_level(const WLevel& bf, const WLevel& bc, const X& X0, 
     }
     rn[lex] = s;
   }
-  __syncwarp();
+  g.sync();
 }
 
 // (P x_c)(row) for a fine row (i, j, k) of level l (patch-local tensor prolongation).
@@ -568,11 +620,13 @@ __device__ __forceinline__ T prolong_row(const WLevel& bc, const X& X0, const X&
 // latency covers all of them.
 constexpr int kRowsInFlight = 4;
 
-// Per-warp shared-memory block (byte offsets): mbarriers, a zero factor record,
-// level metadata of the current box shape, the bulk-copy ring, the wavefront
-// tables of the shape, and the vectors.
+// Per-group shared-memory block (byte offsets): mbarriers, the group's
+// copy-arrival flag, a zero factor record, level metadata of the current box
+// shape, the bulk-copy ring, the wavefront tables of the shape, and the vectors.
 // The zero record spans the widest record (32 doubles of an ordered FP64 level).
 constexpr int kWarpBars = 0, kWarpZrec = 32, kWarpMeta = 288, kWarpShape = 352, kWarpRing = 768;
+constexpr int kWarpOk = 24;   // after the ring mbarriers
+static_assert(kWarpBars + 2 * 8 <= kWarpOk && kWarpOk + 4 <= kWarpZrec, "group flag overlaps the mbarriers");
 static_assert(kWarpMeta - kWarpZrec >= 32 * 8, "zero record smaller than an ordered FP64 record");
 static_assert(kWarpShape - kWarpMeta >= 2 * LOR_MAXLEV * 4, "level metadata does not fit");
 static_assert(kWarpRing - kWarpShape >= LOR_MAXLEV * (int)sizeof(BoxShape), "box shapes do not fit");
@@ -583,8 +637,8 @@ static_assert(kWarpGeo >= kWarpShape + LOR_MAXLEV * (int)sizeof(BoxShape), "geom
 static_assert(kWarpRingGen - kWarpGeo >= LOR_MAXLEV * 6 * 4, "geometry does not fit");
 __host__ __device__ constexpr int warp_ring_offset(bool gen) { return gen ? kWarpRingGen : kWarpRing; }
 
-// The patch kernel.  Each warp runs whole V-cycles for its own patches (one
-// after another, no block barriers):
+// The patch kernel.  Each group of WG warps runs whole V-cycles for its own
+// patches (one after another; no block barriers, only the group's own):
 //   t0 <- R_j r; t0 <- ILU(t0) (= x0); x0 -> its global slot, t0 <- r - A x0
 //   (in place); r1 <- R t0; levels 1..bottom as below; x0 += P x1 (global
 //   slot); t0 <- x0; t0 <- r - A x0; t0 <- ILU(t0); z += R_j^T (x0 + t0).
@@ -592,13 +646,16 @@ __host__ __device__ constexpr int warp_ring_offset(bool gen) { return gen ? kWar
 // ILU, x <- t, t <- r - A x, r_{l+1} <- R t; the vertex level is solved exactly
 // (<= 1 unknown), a truncated box (boundary patch whose vertex level is empty)
 // is smoothed by ILU twice instead; up: x += P x_{l+1}, t <- r - A x, ILU, x += t.
-template <int DIM, typename T, typename FT, int NBUF, bool GEN>
-__global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
+template <int DIM, typename T, typename FT, int NBUF, bool GEN, int WG>
+__global__ void __launch_bounds__(WG == 2 ? 512 : 384, 1) k_patch_warp(PatchArgs a) {
   constexpr int ES = elem_class<FT>();
   constexpr int R = GEN ? lor_rec_gen(DIM) : lor_rec(DIM);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (a.conv && *a.conv != 0.0) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  static_assert(NBUF * 8 <= kWarpOk, "ring mbarriers overlap the group flag");
+  constexpr int NT = Grp<WG>::NT;
+  const Grp<WG> g{(int)(threadIdx.x % NT), (int)(threadIdx.x / NT)};
+  const int gl = g.gl, ng = blockDim.x / NT;
   // CTA-wide: 1D transfer tables of every level (independent of the patch)
   Xfer1D<T>* xf = (Xfer1D<T>*)smem_raw;   // [level][axis type]
   for (int l = 0; l + 1 < a.L; ++l)
@@ -620,8 +677,8 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       }
     }
   __syncthreads();
-  // per-warp block
-  unsigned char* wb = smem_raw + a.xf_bytes + (size_t)warp * a.warp_bytes;
+  // per-group block
+  unsigned char* wb = smem_raw + a.xf_bytes + (size_t)g.id * a.warp_bytes;
   Ring<FT, NBUF> rg;
   rg.bar = (unsigned long long*)(wb + kWarpBars);
   rg.base = wb + warp_ring_offset(GEN);
@@ -629,22 +686,22 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
   rg.phase = 0;
   rg.inflight = 0;
   const FT* zrec = (const FT*)(wb + kWarpZrec);
+  int* okf = (int*)(wb + kWarpOk);   // copy-arrival flag published to the group
   int* meta = (int*)(wb + kWarpMeta);   // tbf[LOR_MAXLEV] | tbc[LOR_MAXLEV]
   BoxShape* bsh = (BoxShape*)(wb + kWarpShape);
   int* ip = (int*)(wb + warp_ring_offset(GEN) + (size_t)NBUF * a.slot_bytes);
   int* geo = (int*)(wb + kWarpGeo);     // GEN: [level][org x3, k x3]
   T* vec = (T*)(ip + a.tab_ints);
-  ((unsigned*)(wb + kWarpZrec))[lane] = 0u;
-  ((unsigned*)(wb + kWarpZrec))[lane + 32] = 0u;
-  if (lane == 0) {
+  for (int q = gl; q < 64; q += NT) ((unsigned*)(wb + kWarpZrec))[q] = 0u;
+  if (gl == 0) {
     for (int s = 0; s < NBUF; ++s) mbar_init(rg.bar + s, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncwarp();
-  const long long gw = (long long)blockIdx.x * nw + warp;
-  T* xslot = (T*)a.xs + gw * a.x0_stride;       // this warp's level-0 iterate
+  g.sync();
+  const long long gw = (long long)blockIdx.x * ng + g.id;
+  T* xslot = (T*)a.xs + gw * a.x0_stride;       // this group's level-0 iterate
   const int nwork = a.plist ? a.nlist : a.J;
-  const long long step = (long long)gridDim.x * nw;
+  const long long step = (long long)gridDim.x * ng;
   int cur_sh = -1;
   const FT* F = (const FT*)a.F;
   const T* hat = (const T*)a.hat;
@@ -661,32 +718,32 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
     }
     if (GEN || sh != cur_sh) {
       // wavefront tables of every level of this shape (ordered levels: of this patch)
-      __syncwarp();
-      if (lane == 0) {
+      g.sync();
+      if (gl == 0) {
         int ioff = 0;
         for (int l = 0; l < a.L; ++l) {
           bsh[l] = a.shapes[l * 8 + sh];
           if (GEN) {
-            const GenSched g = a.gsched[(long long)l * a.J + j];
-            bsh[l].nfront = g.nfront;
-            bsh[l].rpad = g.rpad;
-            bsh[l].front_off = g.front_off;
-            for (int e = 0; e < 3; ++e) { bsh[l].nchunk[e] = g.nchunk[e]; bsh[l].chunk_off[e] = g.chunk_off[e]; }
-            for (int e = 0; e < 3; ++e) { bsh[l].dims[e] = g.dims[e]; geo[l * 6 + e] = g.org[e]; geo[l * 6 + 3 + e] = g.k[e]; }
-            bsh[l].rows = g.rows;
-            bsh[l].guard = g.guard;
+            const GenSched gs = a.gsched[(long long)l * a.J + j];
+            bsh[l].nfront = gs.nfront;
+            bsh[l].rpad = gs.rpad;
+            bsh[l].front_off = gs.front_off;
+            for (int e = 0; e < 3; ++e) { bsh[l].nchunk[e] = gs.nchunk[e]; bsh[l].chunk_off[e] = gs.chunk_off[e]; }
+            for (int e = 0; e < 3; ++e) { bsh[l].dims[e] = gs.dims[e]; geo[l * 6 + e] = gs.org[e]; geo[l * 6 + 3 + e] = gs.k[e]; }
+            bsh[l].rows = gs.rows;
+            bsh[l].guard = gs.guard;
           }
           meta[l] = ioff; ioff += bsh[l].nfront + 1;
           meta[LOR_MAXLEV + l] = ioff; ioff += bsh[l].nchunk[ES] + 1;
         }
       }
-      __syncwarp();
+      g.sync();
       for (int l = 0; l < a.L; ++l) {
         const int nf1 = bsh[l].nfront + 1;
-        for (int i = lane; i < nf1; i += 32) ip[meta[l] + i] = a.fpad[bsh[l].front_off + i];
-        for (int i = lane; i <= bsh[l].nchunk[ES]; i += 32) ip[meta[LOR_MAXLEV + l] + i] = a.chunk[bsh[l].chunk_off[ES] + i];
+        for (int i = gl; i < nf1; i += NT) ip[meta[l] + i] = a.fpad[bsh[l].front_off + i];
+        for (int i = gl; i <= bsh[l].nchunk[ES]; i += NT) ip[meta[LOR_MAXLEV + l] + i] = a.chunk[bsh[l].chunk_off[ES] + i];
       }
-      __syncwarp();
+      g.sync();
       cur_sh = sh;
     }
     if (bsh[0].rows == 0) continue;
@@ -725,10 +782,10 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
       // the level-0 box is the vertex level: exact solve
       const T* S = (const T*)lv0.S;
       BoxIter it;
-      it.init(lane, b0.A, b0.B);
+      it.init(gl, b0.A, b0.B, NT);
       int ho[3] = {0, 0, 0};
       if (a.wmode == 2) hat_offsets<DIM>(j, a.n[0], a.n[1], a.wp, ho);
-      for (int lex = lane; lex < b0.rows; lex += 32, it.next()) {
+      for (int lex = gl; lex < b0.rows; lex += NT, it.next()) {
         const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
         T rhs = rloc ? rloc[lex] : rg0[G];
         if (a.wp)
@@ -738,33 +795,33 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
         else xslot[lex] = rhs / S[(long long)(a.NS / 2) * lv0.ntot + G];
         if (!(GEN && b0.rows > 1)) t0[lex] = T(0);
       }
-      __syncwarp();
+      g.sync();
       if (GEN && b0.rows > 1) {   // several vertices in the box: the stored inverse
         const T* Bi = (const T*)a.binv + a.gsched[j].binv_off;
-        for (int lex = lane; lex < b0.rows; lex += 32) {
+        for (int lex = gl; lex < b0.rows; lex += NT) {
           T acc = 0;
           for (int q = 0; q < b0.rows; ++q) acc += Bi[(long long)lex * b0.rows + q] * t0[q];
           xslot[lex] = acc;
         }
-        __syncwarp();
-        for (int lex = lane; lex < b0.rows; lex += 32) t0[lex] = T(0);
-        __syncwarp();
+        g.sync();
+        for (int lex = gl; lex < b0.rows; lex += NT) t0[lex] = T(0);
+        g.sync();
       }
     } else {
       // ---- level 0 down: t0 <- rhs (zero guards), ILU, residual in place (x0 -> slot)
-      for (int q = lane; q < b0.rows + 2 * guard0 + 1; q += 32) t0[q - guard0] = T(0);
-      __syncwarp();
+      for (int q = gl; q < b0.rows + 2 * guard0 + 1; q += NT) t0[q - guard0] = T(0);
+      g.sync();
       {
         constexpr int U = kRowsInFlight;
         BoxIter it;
-        it.init(lane, b0.A, b0.B);
+        it.init(gl, b0.A, b0.B, NT);
         int ho[3] = {0, 0, 0};
         if (a.wmode == 2) hat_offsets<DIM>(j, a.n[0], a.n[1], a.wp, ho);
-        for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
+        for (int l0 = gl; l0 < b0.rows; l0 += NT * U) {
           T v[U];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            const int lex = l0 + 32 * u;
+            const int lex = l0 + NT * u;
             const int G = ((b0.org[2] + it.k) * lv0.N[1] + (b0.org[1] + it.j)) * lv0.N[0] + (b0.org[0] + it.i);
             const T w = a.wp ? node_weight<DIM, T>(a.wmode, b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp,
                                                    ho[0], ho[1], ho[2], hat)
@@ -774,43 +831,46 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           }
 #pragma unroll
           for (int u = 0; u < U; ++u)
-            if (l0 + 32 * u < b0.rows) t0[l0 + 32 * u] = v[u];
+            if (l0 + NT * u < b0.rows) t0[l0 + NT * u] = v[u];
         }
       }
-      __syncwarp();
+      g.sync();
       const FT* FL0 = F + a.facoff[j] * R;
-      ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
+      ok = ilu_solve<DIM, T, FT, NBUF, GEN, WG>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV],
+                                                FL0, t0, rg, zrec, g, okf);
       T* prev = vec + (b0.A + 1);                 // guarded plane buffers
       T* tmp = prev + AB0 + (b0.A + 1);
-      if (ok) resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, xslot, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
+      if (ok) resid0_inplace<DIM, T, WG>(b0, lv0, rg0, rloc, t0, prev, tmp, xslot,
+                                         a.wp, a.wmode, j, a.n[0], a.n[1], hat, g);
       if (ok && bottom > 0) {
         // ---- coarse levels
         if constexpr (GEN) {
           const XferG<T>* xg = (const XferG<T>*)a.xferg;
-          restrict_level<DIM, T>(bx[0], bx[1], xg[geo[3]], xg[geo[4]], xg[geo[5]], t0, vec + bx[1].ro);
+          restrict_level<DIM, T>(bx[0], bx[1], xg[geo[3]], xg[geo[4]], xg[geo[5]], t0, vec + bx[1].ro, g);
         } else {
-          restrict_level<DIM, T>(bx[0], bx[1], xf[type[0]], xf[type[1]], xf[type[2]], t0, vec + bx[1].ro);
+          restrict_level<DIM, T>(bx[0], bx[1], xf[type[0]], xf[type[1]], xf[type[2]], t0, vec + bx[1].ro, g);
         }
-        for (int q = lane; q < a.ovl_n; q += 32) vec[a.aux_n + q] = T(0);
-        __syncwarp();
+        for (int q = gl; q < a.ovl_n; q += NT) vec[a.aux_n + q] = T(0);
+        g.sync();
         for (int l = 1; l < bottom && ok; ++l) {
           const WLevel& b = bx[l];
           T* x = vec + b.xo; T* t = vec + b.to; T* r = vec + b.ro;
           const FT* FL = F + a.facoff[(long long)l * a.J + j] * R;
-          for (int q = lane; q < b.rows; q += 32) t[q] = r[q];
-          __syncwarp();
-          ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+          for (int q = gl; q < b.rows; q += NT) t[q] = r[q];
+          g.sync();
+          ok = ilu_solve<DIM, T, FT, NBUF, GEN, WG>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l],
+                                                    FL, t, rg, zrec, g, okf);
           if (!ok) break;
-          for (int q = lane; q < b.rows; q += 32) x[q] = t[q];
-          __syncwarp();
-          resid_level<DIM, T>(b, a.lv[l], r, x, t);
+          for (int q = gl; q < b.rows; q += NT) x[q] = t[q];
+          g.sync();
+          resid_level<DIM, T, WG>(b, a.lv[l], r, x, t, g);
           if constexpr (GEN) {
             const XferG<T>* xg = (const XferG<T>*)a.xferg + l * a.kmax1;
             restrict_level<DIM, T>(b, bx[l + 1], xg[geo[l * 6 + 3]], xg[geo[l * 6 + 4]], xg[geo[l * 6 + 5]], t,
-                                   vec + bx[l + 1].ro);
+                                   vec + bx[l + 1].ro, g);
           } else {
             restrict_level<DIM, T>(b, bx[l + 1], xf[l * 2 + type[0]], xf[l * 2 + type[1]], xf[l * 2 + type[2]], t,
-                                   vec + bx[l + 1].ro);
+                                   vec + bx[l + 1].ro, g);
           }
         }
         if (ok) {
@@ -821,35 +881,37 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           if (l == a.L - 1 && GEN && b.rows > 1) {
             // an enlarged patch keeps several vertices: x = A_box^{-1} r with the stored inverse
             const T* Bi = (const T*)a.binv + a.gsched[(long long)l * a.J + j].binv_off;
-            for (int lex = lane; lex < b.rows; lex += 32) {
+            for (int lex = gl; lex < b.rows; lex += NT) {
               T acc = 0;
               for (int q = 0; q < b.rows; ++q) acc += Bi[(long long)lex * b.rows + q] * r[q];
               x[lex] = acc;
             }
-            __syncwarp();
+            g.sync();
           } else if (l == a.L - 1) {
             const T* S = (const T*)lv.S;
             BoxIter it;
-            it.init(lane, b.A, b.B);
-            for (int lex = lane; lex < b.rows; lex += 32, it.next()) {
+            it.init(gl, b.A, b.B, NT);
+            for (int lex = gl; lex < b.rows; lex += NT, it.next()) {
               const int G = ((b.org[2] + it.k) * lv.N[1] + (b.org[1] + it.j)) * lv.N[0] + (b.org[0] + it.i);
               x[lex] = r[lex] / S[(long long)(a.NS / 2) * lv.ntot + G];
             }
-            __syncwarp();
+            g.sync();
           } else {
             const FT* FL = F + a.facoff[(long long)l * a.J + j] * R;
-            for (int q = lane; q < b.rows; q += 32) t[q] = r[q];
-            __syncwarp();
-            ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+            for (int q = gl; q < b.rows; q += NT) t[q] = r[q];
+            g.sync();
+            ok = ilu_solve<DIM, T, FT, NBUF, GEN, WG>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l],
+                                                      FL, t, rg, zrec, g, okf);
             if (ok) {
-              for (int q = lane; q < b.rows; q += 32) x[q] = t[q];
-              __syncwarp();
-              resid_level<DIM, T>(b, lv, r, x, t);
-              ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+              for (int q = gl; q < b.rows; q += NT) x[q] = t[q];
+              g.sync();
+              resid_level<DIM, T, WG>(b, lv, r, x, t, g);
+              ok = ilu_solve<DIM, T, FT, NBUF, GEN, WG>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l],
+                                                        FL, t, rg, zrec, g, okf);
             }
             if (ok) {
-              for (int q = lane; q < b.rows; q += 32) x[q] += t[q];
-              __syncwarp();
+              for (int q = gl; q < b.rows; q += NT) x[q] += t[q];
+              g.sync();
             }
           }
         }
@@ -859,8 +921,8 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
           const T* xc = vec + bx[l + 1].xo;
           const FT* FL = F + a.facoff[(long long)l * a.J + j] * R;
           BoxIter it;
-          it.init(lane, b.A, b.B);
-          for (int lex = lane; lex < b.rows; lex += 32, it.next()) {
+          it.init(gl, b.A, b.B, NT);
+          for (int lex = gl; lex < b.rows; lex += NT, it.next()) {
             if constexpr (GEN) {
               const XferG<T>* xg = (const XferG<T>*)a.xferg + l * a.kmax1;
               x[lex] += prolong_row<DIM, T>(bx[l + 1], xg[geo[l * 6 + 3]], xg[geo[l * 6 + 4]], xg[geo[l * 6 + 5]], xc,
@@ -870,63 +932,66 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
                                             xc, it.i, it.j, it.k);
             }
           }
-          __syncwarp();
-          resid_level<DIM, T>(b, a.lv[l], r, x, t);
-          ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l], FL, t, rg, zrec);
+          g.sync();
+          resid_level<DIM, T, WG>(b, a.lv[l], r, x, t, g);
+          ok = ilu_solve<DIM, T, FT, NBUF, GEN, WG>(bsh[l], ip + meta[l], ip + meta[LOR_MAXLEV + l],
+                                                    FL, t, rg, zrec, g, okf);
           if (!ok) break;
-          for (int q = lane; q < b.rows; q += 32) x[q] += t[q];
-          __syncwarp();
+          for (int q = gl; q < b.rows; q += NT) x[q] += t[q];
+          g.sync();
         }
         if (ok) {
           // ---- level 0 up: x0 += P x1 in the slot, t0 <- x0, residual in place
           const T* x1 = vec + bx[1].xo;
           constexpr int U = kRowsInFlight;
           BoxIter it;
-          it.init(lane, b0.A, b0.B);
-          for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
+          it.init(gl, b0.A, b0.B, NT);
+          for (int l0 = gl; l0 < b0.rows; l0 += NT * U) {
             T xv[U];
             int iu[U], ju[U], ku[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
               iu[u] = it.i; ju[u] = it.j; ku[u] = it.k;
               it.next();
-              if (l0 + 32 * u < b0.rows) xv[u] = xslot[l0 + 32 * u];
+              if (l0 + NT * u < b0.rows) xv[u] = xslot[l0 + NT * u];
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-              if (l0 + 32 * u < b0.rows)
+              if (l0 + NT * u < b0.rows)
                 if constexpr (GEN) {
                   const XferG<T>* xg = (const XferG<T>*)a.xferg;
-                  xslot[l0 + 32 * u] = xv[u] + prolong_row<DIM, T>(bx[1], xg[geo[3]], xg[geo[4]], xg[geo[5]], x1,
+                  xslot[l0 + NT * u] = xv[u] + prolong_row<DIM, T>(bx[1], xg[geo[3]], xg[geo[4]], xg[geo[5]], x1,
                                                                    iu[u], ju[u], ku[u]);
                 } else {
-                  xslot[l0 + 32 * u] = xv[u] + prolong_row<DIM, T>(bx[1], xf[type[0]], xf[type[1]], xf[type[2]], x1,
+                  xslot[l0 + NT * u] = xv[u] + prolong_row<DIM, T>(bx[1], xf[type[0]], xf[type[1]], xf[type[2]], x1,
                                                                    iu[u], ju[u], ku[u]);
                 }
           }
-          __syncwarp();
-          // t0 <- x0 (x1 lived over t0's space; every lane is done with it now)
-          for (int q = lane; q < guard0; q += 32) { t0[q - guard0] = T(0); t0[b0.rows + q] = T(0); }
-          if (lane == 0) t0[b0.rows + guard0] = T(0);
-          for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
+          g.sync();
+          // t0 <- x0 (x1 lived over t0's space; every thread is done with it now)
+          for (int q = gl; q < guard0; q += NT) { t0[q - guard0] = T(0); t0[b0.rows + q] = T(0); }
+          if (gl == 0) t0[b0.rows + guard0] = T(0);
+          for (int l0 = gl; l0 < b0.rows; l0 += NT * U) {
             T xv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u)
-              if (l0 + 32 * u < b0.rows) xv[u] = xslot[l0 + 32 * u];
+              if (l0 + NT * u < b0.rows) xv[u] = xslot[l0 + NT * u];
 #pragma unroll
             for (int u = 0; u < U; ++u)
-              if (l0 + 32 * u < b0.rows) t0[l0 + 32 * u] = xv[u];
+              if (l0 + NT * u < b0.rows) t0[l0 + NT * u] = xv[u];
           }
-          __syncwarp();
-          resid0_inplace<DIM, T>(b0, lv0, rg0, rloc, t0, prev, tmp, nullptr, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
+          g.sync();
+          resid0_inplace<DIM, T, WG>(b0, lv0, rg0, rloc, t0, prev, tmp, nullptr,
+                                     a.wp, a.wmode, j, a.n[0], a.n[1], hat, g);
         }
       }
       if (ok && !a.skip_post0)
-        ok = ilu_solve<DIM, T, FT, NBUF, GEN>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV], FL0, t0, rg, zrec);
+        ok = ilu_solve<DIM, T, FT, NBUF, GEN, WG>(bsh[0], ip + meta[0], ip + meta[LOR_MAXLEV],
+                                                  FL0, t0, rg, zrec, g, okf);
     }
     if (!ok) {
       // a bulk copy did not arrive in time: report, drain what is still in flight, leave
-      if (lane == 0) {
+      if (gl == 0) {
         atomicOr(a.status, 4);
         for (int s = 0; s < NBUF; ++s)
           if (rg.inflight & (1u << s)) mbar_wait(rg.bar + s, (rg.phase >> s) & 1u);
@@ -936,7 +1001,8 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
     // ---- x_j = x0 + t0: patch-local output, or scatter-add R_j^T x_j
     if (a.plist) {
       T* dst = (T*)a.xloc + jo * a.vstride;
-      for (int lex = lane; lex < b0.rows; lex += 32) dst[lex] = xslot[lex] + (a.skip_post0 ? T(0) : t0[lex]);
+      for (int lex = gl; lex < b0.rows; lex += NT) dst[lex] = xslot[lex] + (a.skip_post0 ? T(0) : t0[lex]);
+      g.sync();   // the next patch overwrites t0 and the slot
       continue;
     }
     // the weighted R_j^T x_j goes to the patch's own output slice (lexicographic
@@ -945,23 +1011,23 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
     {
       constexpr int U = kRowsInFlight;
       BoxIter it;
-      it.init(lane, b0.A, b0.B);
+      it.init(gl, b0.A, b0.B, NT);
       int ho[3] = {0, 0, 0};
       if (a.wmode == 2) hat_offsets<DIM>(j, a.n[0], a.n[1], a.wp, ho);
-      for (int l0 = lane; l0 < b0.rows; l0 += 32 * U) {
+      for (int l0 = gl; l0 < b0.rows; l0 += NT * U) {
         T xv[U], w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          w[u] = a.wp && l0 + 32 * u < b0.rows
+          w[u] = a.wp && l0 + NT * u < b0.rows
                      ? node_weight<DIM, T>(a.wmode, b0.org[0] + it.i, b0.org[1] + it.j, b0.org[2] + it.k, a.wp, ho[0],
                                            ho[1], ho[2], hat)
                      : T(1);
           it.next();
-          if (l0 + 32 * u < b0.rows) xv[u] = xslot[l0 + 32 * u];
+          if (l0 + NT * u < b0.rows) xv[u] = xslot[l0 + NT * u];
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const int lex = l0 + 32 * u;
+          const int lex = l0 + NT * u;
           if (lex < b0.rows) {
             const T xj = a.skip_post0 ? xv[u] : xv[u] + t0[lex];
             zj[lex] = w[u] * xj;
@@ -970,16 +1036,17 @@ __global__ void __launch_bounds__(384, 1) k_patch_warp(PatchArgs a) {
         }
       }
     }
-    __syncwarp();
+    g.sync();
     if (a.tout && sh == 0) {   // residual left on an interior patch, for the learned correction
       T* prev = vec + (b0.A + 1);
       T* tmp = prev + AB0 + (b0.A + 1);
       // (without the post-smoothing t0 already holds r - A x0)
       if (!a.skip_post0)
-        resid0_inplace<DIM, T>(b0, lv0, rg0, nullptr, t0, prev, tmp, nullptr, a.wp, a.wmode, j, a.n[0], a.n[1], hat);
+        resid0_inplace<DIM, T, WG>(b0, lv0, rg0, nullptr, t0, prev, tmp, nullptr,
+                                   a.wp, a.wmode, j, a.n[0], a.n[1], hat, g);
       T* dst = (T*)a.tout + jo * a.vstride;
-      for (int lex = lane; lex < b0.rows; lex += 32) dst[lex] = t0[lex];
-      __syncwarp();
+      for (int lex = gl; lex < b0.rows; lex += NT) dst[lex] = t0[lex];
+      g.sync();
     }
   }
 }
@@ -1317,12 +1384,19 @@ T* coarse_vcycle(lor_ctx* c, int l) {
   return cur;
 }
 
-const int kMaxPatchWarps = 12;   // warps per CTA (one CTA per SM when shared memory allows)
+// Patch groups per CTA (one CTA per SM when shared memory allows): up to 12
+// one-warp groups, or up to 8 two-warp groups (512 threads, at most 128 registers
+// each).  Two warps per patch are used in FP32 when shared memory holds at most 8
+// patches per SM anyway (large boxes, wide wavefronts), so the second warp costs
+// no patch in flight; FP64 (more registers) and smaller boxes run one warp per
+// patch.  Each group owns a named barrier 1 + index (ids 1..15).
+const int kMaxGroups1 = 12, kMaxGroups2 = 8;
+static_assert(kMaxGroups1 <= 15 && kMaxGroups2 <= 15, "named barrier ids 1..15");
 
 template <typename FT>
 constexpr int ring_depth() { return 2; }
 
-// Per-warp shared-memory layout of the patch kernel (sizes for the largest,
+// Per-group shared-memory layout of the patch kernel (sizes for the largest,
 // interior, box shape; other shapes fit inside).
 struct WarpLayout {
   int slot_bytes, tab_ints, aux_n, ovl_n, warp_bytes, xf_bytes;
@@ -1426,8 +1500,15 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
 
 // Launch shape of the patch kernel: warps per CTA (shared memory) and resident
 // CTAs per SM; returns false if not even one warp fits.
+template <typename T, typename FT, int WG>
+auto patch_kernel(const lor_ctx* c) {
+  constexpr int NB = ring_depth<FT>();
+  return c->dim == 3 ? (c->gen ? k_patch_warp<3, T, FT, NB, true, WG> : k_patch_warp<3, T, FT, NB, false, WG>)
+                     : (c->gen ? k_patch_warp<2, T, FT, NB, true, WG> : k_patch_warp<2, T, FT, NB, false, WG>);
+}
+
 template <typename T, typename FT>
-bool patch_launch_shape(const lor_ctx* c, int* nw, int* grid, size_t* smem) {
+bool patch_launch_shape(const lor_ctx* c, int* ng, int* wg, int* grid, size_t* smem) {
   const WarpLayout w = warp_layout<T, FT>(c);
   int dev = 0, nsm = 0, maxsm = 0;
   cudaGetDevice(&dev);
@@ -1435,14 +1516,22 @@ bool patch_launch_shape(const lor_ctx* c, int* nw, int* grid, size_t* smem) {
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int fit = (maxsm - w.xf_bytes) / w.warp_bytes;
   if (fit < 1) return false;
-  *nw = std::min(kMaxPatchWarps, fit);
-  *smem = (size_t)w.xf_bytes + (size_t)*nw * w.warp_bytes;
-  constexpr int NB = ring_depth<FT>();
+  *wg = sizeof(T) == 4 && fit <= kMaxGroups2 ? 2 : 1;
+  *ng = std::min(*wg == 2 ? kMaxGroups2 : kMaxGroups1, fit);
+  *smem = (size_t)w.xf_bytes + (size_t)*ng * w.warp_bytes;
   int per_sm = 0;
-  auto kern = c->dim == 3 ? (c->gen ? k_patch_warp<3, T, FT, NB, true> : k_patch_warp<3, T, FT, NB, false>)
-                          : (c->gen ? k_patch_warp<2, T, FT, NB, true> : k_patch_warp<2, T, FT, NB, false>);
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * *nw, *smem);
+  if constexpr (sizeof(T) == 4) {
+    if (*wg == 2) {
+      auto kern = patch_kernel<T, FT, 2>(c);
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64 * *ng, *smem);
+    }
+  }
+  if (*wg == 1) {
+    auto kern = patch_kernel<T, FT, 1>(c);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * *ng, *smem);
+  }
   *grid = std::max(per_sm, 1) * nsm;
   return true;
 }
@@ -1451,21 +1540,17 @@ template <typename T, typename FT>
 lor_status launch_patch_kernel(lor_ctx* c, PatchArgs& a) {
   const long long work = a.plist ? a.nlist : c->J;
   if (work <= 0) return LOR_OK;
-  int nw = 0, grid = 0;
+  int ng = 0, wg = 1, grid = 0;
   size_t smem = 0;
-  if (!patch_launch_shape<T, FT>(c, &nw, &grid, &smem)) return lor_fail(c, LOR_EINVAL, "patch does not fit");
-  // persistent warps: as many as fit, each walking patches w, w + (all warps), ...
-  grid = (int)std::min<long long>(grid, (work + nw - 1) / nw);
-  if ((long long)grid * nw * a.x0_stride * (long long)sizeof(T) > c->xs_bytes)
+  if (!patch_launch_shape<T, FT>(c, &ng, &wg, &grid, &smem)) return lor_fail(c, LOR_EINVAL, "patch does not fit");
+  // persistent groups: as many as fit, each walking patches g, g + (all groups), ...
+  grid = (int)std::min<long long>(grid, (work + ng - 1) / ng);
+  if ((long long)grid * ng * a.x0_stride * (long long)sizeof(T) > c->xs_bytes)
     return lor_fail(c, LOR_ESTATE, "patch iterate slots too small");
-  constexpr int NB = ring_depth<FT>();
-  if (c->gen) {
-    if (c->dim == 3) k_patch_warp<3, T, FT, NB, true><<<grid, 32 * nw, smem, c->stream>>>(a);
-    else k_patch_warp<2, T, FT, NB, true><<<grid, 32 * nw, smem, c->stream>>>(a);
-  } else {
-    if (c->dim == 3) k_patch_warp<3, T, FT, NB, false><<<grid, 32 * nw, smem, c->stream>>>(a);
-    else k_patch_warp<2, T, FT, NB, false><<<grid, 32 * nw, smem, c->stream>>>(a);
+  if constexpr (sizeof(T) == 4) {
+    if (wg == 2) patch_kernel<T, FT, 2>(c)<<<grid, 64 * ng, smem, c->stream>>>(a);
   }
+  if (wg == 1) patch_kernel<T, FT, 1>(c)<<<grid, 32 * ng, smem, c->stream>>>(a);
   ++c->launches;
   return lor_cuda_check(c, cudaGetLastError(), "patch vcycle");
 }
@@ -1632,21 +1717,21 @@ lor_status lor_patch_local32(lor_ctx* c, const int* plist, int nlist, const floa
 }
 
 // Checks that the patch kernel fits (every precision this context can run) and
-// allocates the per-warp level-0 iterate slots for the largest launch and the
+// allocates the per-group level-0 iterate slots for the largest launch and the
 // per-patch output slices (J slices of x0_stride values, float64-sized).
 lor_status lor_patch_prepare(lor_ctx* c) {
   long long need = 0;
-  int nw = 0, grid = 0;
+  int ng = 0, wg = 1, grid = 0;
   size_t smem = 0;
-  if (!patch_launch_shape<double, double>(c, &nw, &grid, &smem))
+  if (!patch_launch_shape<double, double>(c, &ng, &wg, &grid, &smem))
     return lor_fail(c, LOR_EINVAL, "patch does not fit in shared memory");
-  need = std::max(need, (long long)grid * nw * warp_layout<double, double>(c).x0_stride * 8);
+  need = std::max(need, (long long)grid * ng * warp_layout<double, double>(c).x0_stride * 8);
   c->smem_patch64 = (int)smem;
   const bool bf = c->d_F16 != nullptr;
-  const bool ok32 = bf ? patch_launch_shape<float, __nv_bfloat16>(c, &nw, &grid, &smem)
-                       : patch_launch_shape<float, float>(c, &nw, &grid, &smem);
+  const bool ok32 = bf ? patch_launch_shape<float, __nv_bfloat16>(c, &ng, &wg, &grid, &smem)
+                       : patch_launch_shape<float, float>(c, &ng, &wg, &grid, &smem);
   if (!ok32) return lor_fail(c, LOR_EINVAL, "patch does not fit in shared memory");
-  need = std::max(need, (long long)grid * nw * warp_layout<float, float>(c).x0_stride * 4);
+  need = std::max(need, (long long)grid * ng * warp_layout<float, float>(c).x0_stride * 4);
   c->smem_patch32 = (int)smem;
   c->xs_bytes = need;
   c->d_xs = lor_alloc(c, (size_t)std::max<long long>(need, 8));
