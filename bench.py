@@ -32,8 +32,8 @@ METRIC = "3D Q_p PCG time-to-1e-8 and MDOF/s per apply: plain FP64 vs chosen for
 REF_ITERS = 152   # FP64 PCG iterations to 1e-8 on the Q8 32^3 workload (measured on GB300)
 # DRAM bytes (read + written) of one patch-kernel launch on Q8 32^3, mixed bf16: the ncu
 # capture of one launch on Q8 12^3 scaled by the factor rows (profiles/patch_warp_q8_dram.md);
-# measured on the kernel as built
-PATCH_TRAFFIC_Q8N32 = 22.7e9
+# measured on the kernel as built (two warps per patch)
+PATCH_TRAFFIC_Q8N32 = 23.3e9
 WORKLOAD = "3D CG Q8, 32^3 perturbed hex mesh (+-0.15h), log-normal kappa (sigma 1), f=1, rtol 1e-8"
 
 
