@@ -14,7 +14,7 @@
  *    vertices[c*NV + (k*(ny+1)+j)*(nx+1)+i], NV = (nx+1)(ny+1)(nz+1).
  *    kappa[(ez*ny+ey)*nx+ex] > 0 is the piecewise-constant coefficient b of
  *    Eq. (poisson) (lor_set_coefficient replaces it by a pointwise b(x)).
- *    Both are HOST pointers, copied by lor_create.
+ *    Both are host or device pointers, copied by lor_create.
  *  - CG vectors ("L-vectors"): float64 (or float32 where a call says so) on
  *    the full Q_p node grid Nx*Ny(*Nz), N = p*n+1 per direction, x fastest:
  *    node (I,J,K) at (K*Ny+J)*Nx+I.  Boundary (Dirichlet) entries of inputs are
@@ -80,10 +80,14 @@ typedef struct {
 void lor_default_options(lor_options* opt);
 
 /* Creates a context for the mesh (Section 2).  Validates the options and sizes
- * (element count and vertex count x dim at most INT_MAX), copies the host mesh
+ * (element count and vertex count x dim at most INT_MAX), copies the mesh
  * arrays into the context and rejects non-finite vertices and kappa <= 0
- * (LOR_EINVAL); LOR_ENOMEM if the host copy cannot be allocated.  No CUDA call
- * is made here.  stream: a cudaStream_t or NULL. */
+ * (LOR_EINVAL); LOR_ENOMEM if the host copy cannot be allocated.  vertices and
+ * kappa may be HOST or DEVICE pointers: an array the CUDA runtime reports as
+ * device or managed memory is copied to the host on `stream` (the call waits
+ * for it; LOR_ECUDA if the copy fails); any other pointer, and every pointer
+ * when no CUDA device is present, is read as host memory.  Nothing else of
+ * CUDA is touched here.  stream: a cudaStream_t or NULL. */
 lor_status lor_create(lor_ctx** ctx, const lor_options* opt,
                       const double* vertices, const double* kappa, void* stream);
 

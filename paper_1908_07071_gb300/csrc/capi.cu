@@ -1,4 +1,5 @@
 // C ABI of the LOR solver (declared in include/lor.h).
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -125,6 +126,26 @@ void lor_default_options(lor_options* o) {
   o->weighting = 0;
 }
 
+// Copies n doubles at src into dst: through the copy engine when the CUDA runtime
+// reports src as device or managed memory, else (host memory, or no device at
+// all) directly.  False if a device copy fails.
+static bool read_mesh_array(const double* src, size_t n, std::vector<double>& dst, cudaStream_t st) {
+  dst.resize(n);
+  cudaPointerAttributes at;
+  const cudaError_t e = cudaPointerGetAttributes(&at, src);
+  if (e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+    if (cudaMemcpyAsync(dst.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  }
+  if (e != cudaSuccess) cudaGetLastError();   // no device, or memory the runtime does not track
+  std::copy(src, src + n, dst.begin());
+  return true;
+}
+
 lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* vertices, const double* kappa,
                       void* stream) {
   if (!out || !opt || !vertices || !kappa) return LOR_EINVAL;
@@ -151,8 +172,11 @@ lor_status lor_create(lor_ctx** out, const lor_options* opt, const double* verti
   c->nel = c->n[0] * c->n[1] * c->n[2];
   c->stream = (cudaStream_t)stream;
   try {
-    c->h_vert.assign(vertices, vertices + nv_ll * c->dim);
-    c->h_kappa.assign(kappa, kappa + c->nel);
+    if (!read_mesh_array(vertices, (size_t)nv_ll * c->dim, c->h_vert, c->stream) ||
+        !read_mesh_array(kappa, (size_t)c->nel, c->h_kappa, c->stream)) {
+      delete c;
+      return LOR_ECUDA;
+    }
   } catch (const std::bad_alloc&) {
     delete c;
     return LOR_ENOMEM;

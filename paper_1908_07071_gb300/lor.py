@@ -191,7 +191,9 @@ class Solver:
     def __init__(self, vertices, kappa, p, *, mg_levels=0, prec=LOR_FP64, rtol=1e-8, max_it=1000,
                  inner_rtol=1e-3, factor_bf16=False, disc=LOR_CG, eta=1.0, weighting=0, coefficient=None,
                  node_coordinates=None, ordering=0, patch_spans=None, stream=None):
-        """coefficient: optional callable b(X) of physical points X (n, dim) -> (n,) replacing the
+        """vertices (dim, nz+1, ny+1, nx+1) and kappa (nz, ny, nx): numpy arrays or torch tensors, on the
+        host or on the device (lor_create copies them either way).
+        coefficient: optional callable b(X) of physical points X (n, dim) -> (n,) replacing the
         per-element kappa (CG only); it is evaluated at the points lor_coefficient_points lists.
         node_coordinates: optional (ntot, dim) physical coordinates of the level-0 GLL nodes in
         L-vector order, for curved (isoparametric) elements (CG only).
@@ -201,8 +203,17 @@ class Solver:
         either side of its vertex along each axis (1, 1 = the vertex patch); CG only."""
         import torch
         self.lib = load()
-        vertices = np.ascontiguousarray(vertices, dtype=np.float64)
-        kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+
+        def mesh_array(a):
+            # torch CUDA tensors go to lor_create as device pointers, anything else as host arrays
+            if isinstance(a, torch.Tensor) and a.is_cuda:
+                a = a.detach().to(torch.float64).contiguous()
+                return a, ctypes.c_void_p(a.data_ptr())
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            return a, a.ctypes.data_as(ctypes.c_void_p)
+
+        vertices, vptr = mesh_array(vertices)
+        kappa, kptr = mesh_array(kappa)
         dim = vertices.shape[0]
         n = list(reversed(kappa.shape))
         opt = Options()
@@ -220,8 +231,7 @@ class Solver:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
         ctx = ctypes.c_void_p()
-        st = self.lib.lor_create(ctypes.byref(ctx), ctypes.byref(opt), vertices.ctypes.data_as(ctypes.c_void_p),
-                                 kappa.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(stream))
+        st = self.lib.lor_create(ctypes.byref(ctx), ctypes.byref(opt), vptr, kptr, ctypes.c_void_p(stream))
         if st != LOR_OK:
             raise LorError(st, "lor_create rejected the input")
         self.ctx = ctx

@@ -112,6 +112,28 @@ def test_apply_P_fp32(case, bf16):
     s.close()
 
 
+def test_mesh_from_device_arrays():
+    """lor_create reads vertices and kappa from device memory as well as from host memory: a
+    context built from torch CUDA tensors applies A and B like the oracle (1e-10) and bit for bit
+    like the context built from the same arrays on the host."""
+    verts, kappa, m = _problem(3, (3, 2, 2), 4, 0.15, None, 0)
+    s_dev = _solver(torch.from_numpy(verts).cuda(), torch.from_numpy(kappa).cuda(), 4)
+    s_host = _solver(verts, kappa, 4)
+    x = torch.from_numpy(random_vector(s_dev.nvec, 14)).cuda()
+    y_dev, y_host = torch.empty_like(x), torch.empty_like(x)
+    s_dev.apply_A(x, y_dev)
+    s_host.apply_A(x, y_host)
+    assert torch.equal(y_dev, y_host)
+    N = cg.node_shape(m.n, 4)
+    assert _rel(y_dev.cpu().numpy(), cg.apply_A(cg.assemble_stiffness(m, 4), N, x.cpu().numpy())) < 1e-10
+    s_dev.apply_P(x, y_dev)
+    s_host.apply_P(x, y_host)
+    assert torch.equal(y_dev, y_host)
+    assert _rel(y_dev.cpu().numpy(), olor.LORPreconditioner(m, 4).apply(x.cpu().numpy())) < 1e-10
+    s_dev.close()
+    s_host.close()
+
+
 def test_rhs_matches_oracle_load_vector():
     for dim, n, p in ((2, 4, 3), (3, 2, 4)):
         verts, kappa = make_mesh(dim, n, seed=5, perturb=0.15)
