@@ -1386,10 +1386,11 @@ T* coarse_vcycle(lor_ctx* c, int l) {
 
 // Patch groups per CTA (one CTA per SM when shared memory allows): up to 12
 // one-warp groups, or up to 8 two-warp groups (512 threads, at most 128 registers
-// each).  Two warps per patch are used in FP32 when shared memory holds at most 8
-// patches per SM anyway (large boxes, wide wavefronts), so the second warp costs
-// no patch in flight; FP64 (more registers) and smaller boxes run one warp per
-// patch.  Each group owns a named barrier 1 + index (ids 1..15).
+// each).  Two warps per patch are used for 3D boxes in FP32 when shared memory
+// holds at most 8 patches per SM anyway (large boxes, wide wavefronts), so the
+// second warp costs no patch in flight; FP64 (more registers), 2D and smaller
+// boxes run one warp per patch.  Each group owns a named barrier 1 + index
+// (ids 1..15).
 const int kMaxGroups1 = 12, kMaxGroups2 = 8;
 static_assert(kMaxGroups1 <= 15 && kMaxGroups2 <= 15, "named barrier ids 1..15");
 
@@ -1500,11 +1501,15 @@ void fill_patch_args(lor_ctx* c, PatchArgs& a, const FT* F) {
 
 // Launch shape of the patch kernel: warps per CTA (shared memory) and resident
 // CTAs per SM; returns false if not even one warp fits.
+// The kernel instantiation for a context; two-warp groups exist in 3D only.
 template <typename T, typename FT, int WG>
 auto patch_kernel(const lor_ctx* c) {
   constexpr int NB = ring_depth<FT>();
-  return c->dim == 3 ? (c->gen ? k_patch_warp<3, T, FT, NB, true, WG> : k_patch_warp<3, T, FT, NB, false, WG>)
-                     : (c->gen ? k_patch_warp<2, T, FT, NB, true, WG> : k_patch_warp<2, T, FT, NB, false, WG>);
+  if constexpr (WG == 2)
+    return c->gen ? k_patch_warp<3, T, FT, NB, true, 2> : k_patch_warp<3, T, FT, NB, false, 2>;
+  else
+    return c->dim == 3 ? (c->gen ? k_patch_warp<3, T, FT, NB, true, 1> : k_patch_warp<3, T, FT, NB, false, 1>)
+                       : (c->gen ? k_patch_warp<2, T, FT, NB, true, 1> : k_patch_warp<2, T, FT, NB, false, 1>);
 }
 
 template <typename T, typename FT>
@@ -1516,7 +1521,7 @@ bool patch_launch_shape(const lor_ctx* c, int* ng, int* wg, int* grid, size_t* s
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int fit = (maxsm - w.xf_bytes) / w.warp_bytes;
   if (fit < 1) return false;
-  *wg = sizeof(T) == 4 && fit <= kMaxGroups2 ? 2 : 1;
+  *wg = sizeof(T) == 4 && c->dim == 3 && fit <= kMaxGroups2 ? 2 : 1;
   *ng = std::min(*wg == 2 ? kMaxGroups2 : kMaxGroups1, fit);
   *smem = (size_t)w.xf_bytes + (size_t)*ng * w.warp_bytes;
   int per_sm = 0;
