@@ -21,6 +21,7 @@
 // compiled without floating-point contraction, so every product and sum rounds
 // on its own, as in a plain evaluation of the definition.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <set>
 #include <utility>
@@ -33,16 +34,6 @@ namespace {
 struct Box {
   int dim, A, B, C, n;
   int coord(int i, int a) const { return a == 0 ? i % A : a == 1 ? (i / A) % B : i / (A * B); }
-  // stencil-offset index of node k seen from node i (both in the box, adjacent)
-  int off(int i, int k) const {
-    const int dx = coord(k, 0) - coord(i, 0), dy = coord(k, 1) - coord(i, 1), dz = coord(k, 2) - coord(i, 2);
-    return dim == 3 ? (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1) : (dy + 1) * 3 + (dx + 1);
-  }
-  bool adjacent(int i, int k) const {
-    for (int a = 0; a < 3; ++a)
-      if (std::abs(coord(k, a) - coord(i, a)) > 1) return false;
-    return true;
-  }
   // neighbours (other than i) in increasing index order
   std::vector<int> nbrs(int i) const {
     std::vector<int> out;
@@ -106,58 +97,116 @@ void rcm_box(int dim, int A, int B, int C, std::vector<int>& perm) {
 bool mdf_box(int dim, int A, int B, int C, const std::vector<double>& a27, std::vector<int>& perm) {
   const Box b = make_box(dim, A, B, C);
   const int NS = dim == 3 ? 27 : 9, D = NS / 2;
+  // Stencil offsets o (o = (dz+1)*9 + (dy+1)*3 + (dx+1), 2D without dz) relative
+  // to the node being eliminated.  Two neighbours at offsets o1, o2 are adjacent
+  // (or equal) when their coordinates differ by at most one along every axis;
+  // rel[o1][o2] is then the offset of the second seen from the first, and bit o2
+  // of far[o1] is set when they are not.  A node's in-box neighbours by increasing
+  // offset are its neighbours by increasing index (the box is numbered x fastest),
+  // so walking set bits upwards visits nodes in index order.
+  int rel[27][27];
+  unsigned far[27];
+  for (int o1 = 0; o1 < NS; ++o1) {
+    far[o1] = 0;
+    for (int o2 = 0; o2 < NS; ++o2) {
+      const int dx = o2 % 3 - o1 % 3, dy = (o2 / 3) % 3 - (o1 / 3) % 3, dz = dim == 3 ? o2 / 9 - o1 / 9 : 0;
+      const bool adj = std::abs(dx) <= 1 && std::abs(dy) <= 1 && std::abs(dz) <= 1;
+      rel[o1][o2] = adj ? (dim == 3 ? (dz + 1) * 9 : 0) + (dy + 1) * 3 + (dx + 1) : -1;
+      if (!adj) far[o1] |= 1u << o2;
+    }
+  }
+  int step[27];   // index step of offset o
+  for (int o = 0; o < NS; ++o)
+    step[o] = (o % 3 - 1) + ((o / 3) % 3 - 1) * A + (dim == 3 ? (o / 9 - 1) * A * B : 0);
+  std::vector<unsigned> inbox(b.n);   // bit o: the neighbour at offset o lies in the box
+  for (int i = 0; i < b.n; ++i) {
+    const int x = b.coord(i, 0), y = b.coord(i, 1), z = b.coord(i, 2);
+    unsigned m = 0;
+    for (int o = 0; o < NS; ++o) {
+      const int X = x + o % 3 - 1, Y = y + (o / 3) % 3 - 1, Z = z + (dim == 3 ? o / 9 - 1 : 0);
+      if (o != D && X >= 0 && X < A && Y >= 0 && Y < B && Z >= 0 && Z < C) m |= 1u << o;
+    }
+    inbox[i] = m;
+  }
   std::vector<double> a(a27);
-  std::vector<std::vector<int>> nb(b.n);
-  for (int i = 0; i < b.n; ++i) nb[i] = b.nbrs(i);
   std::vector<char> alive(b.n, 1);
-  auto at = [&](int i, int k) -> double& { return a[(size_t)i * NS + (i == k ? D : b.off(i, k))]; };
+  auto live_mask = [&](int i) {   // offsets of the remaining neighbours of i
+    unsigned m = 0;
+    for (unsigned r = inbox[i]; r; r &= r - 1) {
+      const int o = __builtin_ctz(r);
+      if (alive[i + step[o]]) m |= 1u << o;
+    }
+    return m;
+  };
+  // 2-norm of the fill that eliminating i would discard: the products
+  // (a_ji / a_ii) a_ik over ordered pairs (j, k) of distinct, non-adjacent
+  // remaining neighbours, summed j-major in index order
   auto fill = [&](int i) {
-    std::vector<int> live;
-    for (int j : nb[i])
-      if (alive[j]) live.push_back(j);
-    if (live.size() < 2) return 0.0;
-    const double piv = at(i, i);
-    std::vector<double> col(live.size()), row(live.size());
-    for (size_t x = 0; x < live.size(); ++x) {
-      col[x] = at(live[x], i) / piv;
-      row[x] = at(i, live[x]);
+    const unsigned lm = live_mask(i);
+    if (__builtin_popcount(lm) < 2) return 0.0;
+    const double* ai = &a[(size_t)i * NS];
+    const double piv = ai[D];
+    double col[27];
+    for (unsigned r = lm; r; r &= r - 1) {
+      const int o = __builtin_ctz(r);
+      col[o] = a[(size_t)(i + step[o]) * NS + (NS - 1 - o)] / piv;   // a_{j i} / a_ii, j at offset o
     }
     double s = 0.0;
-    for (size_t x = 0; x < live.size(); ++x)
-      for (size_t y = 0; y < live.size(); ++y) {
-        if (live[x] == live[y] || b.adjacent(live[x], live[y])) continue;
-        const double v = col[x] * row[y];
+    for (unsigned r = lm; r; r &= r - 1) {
+      const int ox = __builtin_ctz(r);
+      const double cx = col[ox];
+      for (unsigned q = lm & far[ox]; q; q &= q - 1) {
+        const double v = cx * ai[__builtin_ctz(q)];
         s += v * v;
       }
+    }
     return std::sqrt(s);
   };
-  std::vector<double> df(b.n);
-  std::set<std::pair<double, int>> queue;
-  for (int i = 0; i < b.n; ++i) {
-    df[i] = fill(i);
-    queue.insert({df[i], i});
-  }
+  // next node: smallest (discarded fill, index) among the remaining ones; heap
+  // entries whose stamp is out of date are skipped
+  struct Entry {
+    double df;
+    int i;
+    unsigned stamp;
+    bool operator>(const Entry& o) const { return df != o.df ? df > o.df : i > o.i; }
+  };
+  std::vector<Entry> heap;
+  heap.reserve((size_t)b.n * 4);
+  std::vector<unsigned> stamp(b.n, 0);
+  auto push = [&](double df, int i) {
+    heap.push_back({df, i, stamp[i]});
+    std::push_heap(heap.begin(), heap.end(), std::greater<Entry>());
+  };
+  for (int i = 0; i < b.n; ++i) push(fill(i), i);
   perm.clear();
   perm.reserve(b.n);
-  while (!queue.empty()) {
-    const int i = queue.begin()->second;
-    queue.erase(queue.begin());
+  while (!heap.empty()) {
+    std::pop_heap(heap.begin(), heap.end(), std::greater<Entry>());
+    const Entry e = heap.back();
+    heap.pop_back();
+    if (!alive[e.i] || e.stamp != stamp[e.i]) continue;
+    const int i = e.i;
     perm.push_back(i);
     alive[i] = 0;
-    const double piv = at(i, i);
+    const double* ai = &a[(size_t)i * NS];
+    const double piv = ai[D];
     if (!(piv > 0.0)) return false;
-    std::vector<int> live;
-    for (int j : nb[i])
-      if (alive[j]) live.push_back(j);
-    for (int j : live) {
-      const double lj = at(j, i) / piv;
-      for (int k : live)
-        if (j == k || b.adjacent(j, k)) at(j, k) = at(j, k) - lj * at(i, k);
+    const unsigned lm = live_mask(i);
+    // kept part of the elimination: a_jk -= (a_ji / a_ii) a_ik for adjacent or equal j, k
+    for (unsigned r = lm; r; r &= r - 1) {
+      const int ox = __builtin_ctz(r);
+      double* aj = &a[(size_t)(i + step[ox]) * NS];
+      const double lj = aj[NS - 1 - ox] / piv;
+      for (unsigned q = lm & ~far[ox]; q; q &= q - 1) {
+        const int oy = __builtin_ctz(q);
+        const int t = rel[ox][oy];
+        aj[t] = aj[t] - lj * ai[oy];
+      }
     }
-    for (int u : live) {
-      queue.erase({df[u], u});
-      df[u] = fill(u);
-      queue.insert({df[u], u});
+    for (unsigned r = lm; r; r &= r - 1) {
+      const int u = i + step[__builtin_ctz(r)];
+      ++stamp[u];
+      push(fill(u), u);
     }
   }
   return true;
@@ -169,31 +218,55 @@ bool ilu0_ordered(int dim, int A, int B, int C, const std::vector<double>& a27, 
   const int NS = dim == 3 ? 27 : 9, D = NS / 2;
   std::vector<int> pos(b.n);
   for (int q = 0; q < b.n; ++q) pos[perm[q]] = q;
+  // offset tables as in mdf_box: rel[o1][o2] is the offset of the neighbour at o2
+  // seen from the neighbour at o1 when the two are adjacent, else -1
+  int rel[27][27], step[27];
+  for (int o1 = 0; o1 < NS; ++o1)
+    for (int o2 = 0; o2 < NS; ++o2) {
+      const int dx = o2 % 3 - o1 % 3, dy = (o2 / 3) % 3 - (o1 / 3) % 3, dz = dim == 3 ? o2 / 9 - o1 / 9 : 0;
+      rel[o1][o2] = (std::abs(dx) <= 1 && std::abs(dy) <= 1 && std::abs(dz) <= 1)
+                        ? (dim == 3 ? (dz + 1) * 9 : 0) + (dy + 1) * 3 + (dx + 1)
+                        : -1;
+    }
+  for (int o = 0; o < NS; ++o)
+    step[o] = (o % 3 - 1) + ((o / 3) % 3 - 1) * A + (dim == 3 ? (o / 9 - 1) * A * B : 0);
   lu = a27;
   level.assign(b.n, 0);
-  auto at = [&](int i, int k) -> double& { return lu[(size_t)i * NS + (i == k ? D : b.off(i, k))]; };
   for (int q = 0; q < b.n; ++q) {
     const int i = perm[q];
-    std::vector<int> nb = b.nbrs(i);
-    std::vector<int> lower;
-    for (int k : nb)
-      if (pos[k] < q) lower.push_back(k);
-    std::sort(lower.begin(), lower.end(), [&](int u, int v) { return pos[u] < pos[v]; });
+    const int x = b.coord(i, 0), y = b.coord(i, 1), z = b.coord(i, 2);
+    // the in-box neighbours of i (offsets, increasing = increasing index), and
+    // those ordered before i, sorted by their position in the order
+    int nbo[26], low[26];
+    int nn = 0, nl = 0;
+    for (int o = 0; o < NS; ++o) {
+      const int X = x + o % 3 - 1, Y = y + (o / 3) % 3 - 1, Z = z + (dim == 3 ? o / 9 - 1 : 0);
+      if (o == D || X < 0 || X >= A || Y < 0 || Y >= B || Z < 0 || Z >= C) continue;
+      nbo[nn++] = o;
+      if (pos[i + step[o]] < q) low[nl++] = o;
+    }
+    for (int u = 1; u < nl; ++u)   // insertion sort by position (positions are distinct)
+      for (int v = u; v > 0 && pos[i + step[low[v - 1]]] > pos[i + step[low[v]]]; --v) std::swap(low[v - 1], low[v]);
+    double* li = &lu[(size_t)i * NS];
     int lev = 0;
-    for (int k : lower) {
-      double& aik = at(i, k);
-      aik = aik / at(k, k);
-      const double l = aik;
+    for (int u = 0; u < nl; ++u) {
+      const int ok = low[u];
+      const int k = i + step[ok];
+      const double* lk = &lu[(size_t)k * NS];
+      li[ok] = li[ok] / lk[D];
+      const double l = li[ok];
       // entries j of row i's pattern that come after k in the order: a_ij -= l a_kj
-      for (int j : nb) {
-        if (pos[j] <= pos[k] || !b.adjacent(k, j)) continue;
-        at(i, j) = at(i, j) - l * at(k, j);
+      for (int w = 0; w < nn; ++w) {
+        const int oj = nbo[w];
+        const int t = rel[ok][oj];
+        if (t < 0 || pos[i + step[oj]] <= pos[k]) continue;
+        li[oj] = li[oj] - l * lk[t];
       }
-      if (pos[i] > pos[k] && b.adjacent(k, i)) at(i, i) = at(i, i) - l * at(k, i);
+      li[D] = li[D] - l * lk[NS - 1 - ok];
       lev = std::max(lev, level[k] + 1);
     }
     level[i] = lev;
-    if (!(at(i, i) > 0.0)) return false;
+    if (!(li[D] > 0.0)) return false;
   }
   return true;
 }
