@@ -53,6 +53,32 @@ def test_box_orderings_equal_the_oracle(lor, dim, n, p, kind, code):
     assert checked > 0
 
 
+def _box_matrix(dims, dim, kind, seed):
+    """Dense symmetric matrix on the 3^d-point pattern of a box: equal couplings (every
+    MDF step is decided by exact ties, broken by the smallest index) or random ones."""
+    pat = olor.box_pattern([np.arange(d) for d in dims])
+    m = pat.shape[0]
+    rng = np.random.default_rng(seed)
+    A = np.zeros((m, m))
+    for r in range(m):
+        for c in range(r + 1, m):
+            if pat[r, c]:
+                A[r, c] = A[c, r] = -1.0 if kind == "ties" else -rng.uniform(0.2, 1.0)
+    A[np.arange(m), np.arange(m)] = np.abs(A).sum(axis=1) + 0.5
+    return A, pat
+
+
+@pytest.mark.parametrize("dims", [(3, 3, 3), (4, 3, 2), (2, 2, 2), (1, 4, 3), (6, 5), (7, 1), (4, 4, 4)])
+@pytest.mark.parametrize("kind", ["ties", "random"])
+def test_mdf_of_box_matrices_equals_the_oracle(lor, dims, kind):
+    """MDF through lor_box_ordering against the oracle's greedy elimination on whole
+    box matrices, node for node, including matrices whose every step is a tie."""
+    dim = len(dims)
+    A, pat = _box_matrix(dims, dim, kind, seed=len(dims) * 100 + dims[0])
+    perm = lor.box_ordering(dims, 2, _a27(A, dims, dim))
+    np.testing.assert_array_equal(perm, ordo.mdf_order(A, pat))
+
+
 def test_box_ordering_rejects_bad_input_and_reports_breakdown(lor):
     with pytest.raises(lor.LorError) as err:
         lor.box_ordering((3, 3, 3), 3)
