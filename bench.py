@@ -103,8 +103,8 @@ def summarize_ncu_launches(path: str) -> str:
     for r in rows:
         if len(r) <= k_val or r[k_metric] != "gpu__time_duration.sum":
             continue
-        name = re.sub(r"\(.*", "", r[k_name]).replace("void ", "").strip()
-        name = re.sub(r"<unnamed>::|\(anonymous namespace\)::", "", name)
+        name = re.sub(r"<unnamed>::|\(anonymous namespace\)::", "", r[k_name])   # before the argument list goes
+        name = re.sub(r"\(.*", "", name).replace("void ", "").strip()
         tot[name] += float(r[k_val].replace(",", "")) * to_ms.get(r[k_unit], 1.0)
         cnt[name] += 1
     all_ms = sum(tot.values())
