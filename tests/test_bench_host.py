@@ -1,4 +1,5 @@
-"""The launch-list summary bench.py prints from an ncu CSV (`--summarize-ncu`), which
+"""Host logic of bench.py (no GPU needed). The launch-list summary printed from an ncu
+CSV (`--summarize-ncu`), which
 the committed profile summaries quote: kernel names stripped of their argument lists
 and anonymous namespaces, launches counted, device time summed across units, shares
 of the total, and every other metric and every log line ignored (no GPU needed)."""
@@ -31,3 +32,30 @@ def test_summary_rejects_a_file_without_the_csv_header(tmp_path):
     path.write_text("==PROF== nothing here\n")
     with pytest.raises(ValueError):
         bench.summarize_ncu_launches(str(path))
+
+
+class _DoneProcess:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_samples_median_and_throttle_reasons(tmp_path):
+    """The clock record of the timed region: median SM clock of the benchmarked device,
+    its maximum, and the throttle reasons seen Active (other devices and malformed lines
+    are skipped), from nvidia-smi's csv,noheader,nounits sampling."""
+    path = tmp_path / "clocks.csv"
+    path.write_text(
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "1, 1200, 2070, 300.0, 0x0000000000000004, Not Active, Active, Not Active, Not Active\n"
+        "0, 1965, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "0, [N/A], 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 2070, 2070, 1100.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "garbage line\n")
+    c = bench.Clocks()
+    c.proc, c.path = _DoneProcess(), str(path)
+    rec = c.stop(dev_index=0)
+    assert rec == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not path.exists()
