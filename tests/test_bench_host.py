@@ -1,8 +1,10 @@
-"""Host logic of bench.py (no GPU needed). The launch-list summary printed from an ncu
-CSV (`--summarize-ncu`), which
-the committed profile summaries quote: kernel names stripped of their argument lists
-and anonymous namespaces, launches counted, device time summed across units, shares
-of the total, and every other metric and every log line ignored (no GPU needed)."""
+"""Host logic of bench.py (no GPU needed).
+
+- The launch-list summary printed from an ncu CSV (`--summarize-ncu`), which the
+  committed profile summaries quote: kernel names stripped of their argument lists and
+  anonymous namespaces, launches counted, device time summed across units, shares of
+  the total, every other metric and every log line ignored.
+- The clock record of the timed region, parsed from nvidia-smi's sampling."""
 import bench
 
 CSV = '''==PROF== Connected to process 1 (/usr/bin/python3)
