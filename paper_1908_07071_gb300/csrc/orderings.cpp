@@ -162,8 +162,9 @@ bool mdf_box(int dim, int A, int B, int C, const std::vector<double>& a27, std::
     }
     return std::sqrt(s);
   };
-  // next node: smallest (discarded fill, index) among the remaining ones; heap
-  // entries whose stamp is out of date are skipped
+  // next node: smallest (discarded fill, index) among the remaining ones, from a
+  // binary min-heap (Section 3.6: O(n log n) per patch); entries whose stamp is out
+  // of date are skipped
   struct Entry {
     double df;
     int i;
