@@ -240,6 +240,22 @@ lor_status lor_set_ordering(lor_ctx* ctx, int ordering);
  * non-positive pivot, LOR_EINVAL for bad sizes or ordering. */
 lor_status lor_box_ordering(int dim, int A, int B, int C, int ordering, const double* a27, int* perm);
 
+/* Host-only utility (no context, no CUDA call): the ILU(0) factorization in a
+ * given order (Section 3.4) that lor_setup applies to every RCM- or MDF-ordered
+ * patch level, for one box laid out as in lor_box_ordering.  perm (A*B*C ints):
+ * the elimination order, perm[q] = box index of the q-th node; it must be a
+ * permutation.  lu (A*B*C x 3^d doubles, host, written): per node its factor
+ * entries in stencil-offset order: at the offsets of neighbours eliminated
+ * before it the multipliers of the unit lower factor, at the centre the pivot
+ * u_ii, at the other in-box offsets the entries of the upper factor, 0 outside
+ * the box.  level (A*B*C ints, host, written; may be NULL): the dependency level
+ * of each node (0 without earlier neighbours, else one more than the largest
+ * level among them), i.e. the wavefronts of the ordered sweeps.  LOR_EBREAKDOWN
+ * on a non-positive pivot, LOR_EINVAL for bad sizes or a perm that is not a
+ * permutation. */
+lor_status lor_box_ilu0(int dim, int A, int B, int C, const double* a27, const int* perm, double* lu,
+                        int* level);
+
 /* Patches enlarged for isotropic overlap on anisotropic meshes (Section 4.5):
  * spans (host, npatch x dim x 2 ints, patch-major, per axis: lo then hi) lets the
  * patch of vertex v cover the elements v - lo .. v + hi - 1 along each axis

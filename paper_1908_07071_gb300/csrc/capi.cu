@@ -448,6 +448,29 @@ lor_status lor_box_ordering(int dim, int A, int B, int C, int ordering, const do
   return LOR_OK;
 }
 
+lor_status lor_box_ilu0(int dim, int A, int B, int C, const double* a27, const int* perm, double* lu, int* level) {
+  if ((dim != 2 && dim != 3) || A < 1 || B < 1 || C < 1 || (dim == 2 && C != 1) || !a27 || !perm || !lu)
+    return LOR_EINVAL;
+  const long long n = (long long)A * B * C;
+  if (n > (1 << 20)) return LOR_EINVAL;
+  const int NS = dim == 3 ? 27 : 9;
+  try {
+    std::vector<char> seen(n, 0);
+    for (long long q = 0; q < n; ++q) {
+      if (perm[q] < 0 || perm[q] >= n || seen[perm[q]]) return LOR_EINVAL;
+      seen[perm[q]] = 1;
+    }
+    std::vector<double> a(a27, a27 + n * NS), out;
+    std::vector<int> p(perm, perm + n), lev;
+    if (!lorh::ilu0_ordered(dim, A, B, C, a, p, out, lev)) return LOR_EBREAKDOWN;
+    std::copy(out.begin(), out.end(), lu);
+    if (level) std::copy(lev.begin(), lev.end(), level);
+  } catch (const std::bad_alloc&) {
+    return LOR_ENOMEM;
+  }
+  return LOR_OK;
+}
+
 lor_status lor_patch_ordering(lor_ctx* c, int level, long long patch, int* perm, int cap, int* count) {
   if (!c || !count) return LOR_EINVAL;
   if (!c->setup_done) return lor_fail(c, LOR_ESTATE, "lor_patch_ordering: call lor_setup first");

@@ -60,6 +60,30 @@ def box_ordering(dims, ordering, a27=None):
     return perm.astype(np.int64)
 
 
+def box_ilu0(dims, a27, perm):
+    """ILU(0) of a box matrix in the order perm (lor_box_ilu0, host only): the factors in
+    the stencil layout of a27 (lower multipliers at earlier neighbours, u_ii at the centre,
+    upper entries at later ones) and the dependency level of every node."""
+    dim = len(dims)
+    A, B = int(dims[0]), int(dims[1])
+    C = int(dims[2]) if dim == 3 else 1
+    n = A * B * C
+    buf = np.ascontiguousarray(a27, dtype=np.float64)
+    if buf.shape != (n, 27 if dim == 3 else 9):
+        raise ValueError("a27 must have shape (nodes, 3^d)")
+    pm = np.ascontiguousarray(perm, dtype=np.int32)
+    if pm.shape != (n,):
+        raise ValueError("perm must have one entry per node")
+    lu = np.zeros_like(buf)
+    level = np.zeros(n, dtype=np.int32)
+    vp = ctypes.c_void_p
+    st = load().lor_box_ilu0(dim, A, B, C, buf.ctypes.data_as(vp), pm.ctypes.data_as(vp), lu.ctypes.data_as(vp),
+                             level.ctypes.data_as(vp))
+    if st != LOR_OK:
+        raise LorError(st, "lor_box_ilu0 failed")
+    return lu, level
+
+
 class Options(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("p", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("disc", ctypes.c_int), ("eta", ctypes.c_double),
@@ -130,6 +154,7 @@ def load():
     lib.lor_set_ordering.argtypes = [vp, i]
     lib.lor_set_patch_spans.argtypes = [vp, vp]
     lib.lor_box_ordering.argtypes = [i, i, i, i, i, vp, vp]
+    lib.lor_box_ilu0.argtypes = [i, i, i, i, vp, vp, vp, vp]
     lib.lor_patch_ordering.argtypes = [vp, i, ctypes.c_longlong, vp, i, ctypes.POINTER(i)]
     lib.lor_coefficient_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.lor_coefficient_points.argtypes = [vp, vp, vp]
@@ -143,7 +168,7 @@ def load():
     lib.lor_profile_read.argtypes = [vp, i, pd, ctypes.POINTER(ctypes.c_longlong)]
     for name in ("lor_coefficient_sizes", "lor_coefficient_points", "lor_set_coefficient", "lor_set_node_coordinates",
                  "lor_pcg_state_size", "lor_pcg_state_save", "lor_pcg_resume",
-                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_set_schwarz", "lor_set_ordering", "lor_set_patch_spans", "lor_box_ordering", "lor_patch_ordering", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_measure_fp64_peak", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
+                 "lor_device_status", "lor_selftest_wait", "lor_set_prec", "lor_set_weighting", "lor_set_schwarz", "lor_set_ordering", "lor_set_patch_spans", "lor_box_ordering", "lor_box_ilu0", "lor_patch_ordering", "lor_launch_count", "lor_profile", "lor_profile_read", "lor_create", "lor_setup", "lor_get_info", "lor_rhs", "lor_rhs_f", "lor_measure_fp64_peak", "lor_quadrature_points", "lor_apply_A", "lor_apply_P",
                  "lor_pcg_solve", "lor_pcg_solve_host", "lor_residual_history"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib

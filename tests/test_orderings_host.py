@@ -79,6 +79,71 @@ def test_mdf_of_box_matrices_equals_the_oracle(lor, dims, kind):
     np.testing.assert_array_equal(perm, ordo.mdf_order(A, pat))
 
 
+def _stencil_dense(lu, dims, dim, perm):
+    """Dense factors, in elimination order, from the stencil layout of lor_box_ilu0."""
+    A, B = dims[0], dims[1]
+    C = dims[2] if dim == 3 else 1
+    n = A * B * C
+    NS = 27 if dim == 3 else 9
+    pos = np.empty(n, dtype=np.int64)
+    pos[perm] = np.arange(n)
+    L, U = np.eye(n), np.zeros((n, n))
+    for i in range(n):
+        x, y, z = i % A, (i // A) % B, i // (A * B)
+        for o in range(NS):
+            dx, dy, dz = o % 3 - 1, (o // 3) % 3 - 1, (o // 9 - 1 if dim == 3 else 0)
+            X, Y, Z = x + dx, y + dy, z + dz
+            if not (0 <= X < A and 0 <= Y < B and 0 <= Z < C):
+                assert lu[i, o] == 0.0
+                continue
+            k = (Z * B + Y) * A + X
+            if pos[k] < pos[i]:
+                L[pos[i], pos[k]] = lu[i, o]
+            else:
+                U[pos[i], pos[k]] = lu[i, o]
+    return L, U, pos
+
+
+@pytest.mark.parametrize("dims", [(3, 3, 3), (4, 3, 2), (1, 4, 3), (6, 5), (2, 7)])
+@pytest.mark.parametrize("order", ["lex", "rcm", "mdf", "random"])
+def test_ordered_ilu0_of_box_matrices_equals_the_oracle(lor, dims, order):
+    """lor_box_ilu0 (the factorization lor_setup runs for RCM/MDF-ordered patches)
+    against the oracle's IKJ ILU(0) of the permuted matrix: factors bit for bit (both
+    sides round every product and difference alone, in the same order), and dependency
+    levels equal to their definition (0 without earlier neighbours, else one more than
+    the largest earlier neighbour's)."""
+    dim = len(dims)
+    A, pat = _box_matrix(dims, dim, "random", seed=sum(dims))
+    a27 = _a27(A, dims, dim)
+    n = A.shape[0]
+    perm = {"lex": np.arange(n), "rcm": lor.box_ordering(dims, 1), "mdf": lor.box_ordering(dims, 2, a27),
+            "random": np.random.default_rng(n).permutation(n)}[order]
+    lu, level = lor.box_ilu0(dims, a27, perm)
+    L, U, pos = _stencil_dense(lu, dims, dim, perm)
+    Lo, Uo = olor.ilu0(A[np.ix_(perm, perm)], pat[np.ix_(perm, perm)])
+    np.testing.assert_array_equal(L, Lo)
+    np.testing.assert_array_equal(U, Uo)
+    want = np.zeros(n, dtype=np.int64)
+    for q in range(n):
+        i = perm[q]
+        earlier = [k for k in np.nonzero(pat[i])[0] if pos[k] < q]
+        want[i] = 1 + max(want[k] for k in earlier) if earlier else 0
+    np.testing.assert_array_equal(level, want)
+
+
+def test_box_ilu0_rejects_bad_orders_and_reports_breakdown(lor):
+    A, pat = _box_matrix((3, 2), 2, "random", seed=1)
+    a27 = _a27(A, (3, 2), 2)
+    with pytest.raises(lor.LorError) as err:
+        lor.box_ilu0((3, 2), a27, [0, 1, 2, 3, 4, 4])      # not a permutation
+    assert err.value.status == lor.LOR_EINVAL
+    bad = a27.copy()
+    bad[:, 4] = 0.05                                       # pivots too small: breakdown
+    with pytest.raises(lor.LorError) as err:
+        lor.box_ilu0((3, 2), bad, np.arange(6))
+    assert err.value.status == lor.LOR_EBREAKDOWN
+
+
 def test_box_ordering_rejects_bad_input_and_reports_breakdown(lor):
     with pytest.raises(lor.LorError) as err:
         lor.box_ordering((3, 3, 3), 3)
