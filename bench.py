@@ -119,8 +119,9 @@ def summarize_ncu_launches(path: str) -> str:
 def cpu_sample_worker(p: int, n: int, seed: int, budget_s: float, iters: int) -> dict:
     """Times the CPU oracle as it stands on a bounded sample of the workload and
     extrapolates one solve: per iteration nel element applies (dense element
-    matrix times element vector, the oracle's assembled-operator cost) and J
-    patch V-cycles (ILU(0) V(1,1) on a 2x2x2-element patch), times `iters`."""
+    matrix times element vector, the oracle's assembled-operator cost), J patch
+    V-cycles (ILU(0) V(1,1) on a 2x2x2-element patch), the coarse-space
+    correction and the PCG vector updates, times `iters`."""
     import numpy as np
     from oracle import cg as ocg
     from oracle import lor as olor
@@ -157,11 +158,35 @@ def cpu_sample_worker(p: int, n: int, seed: int, budget_s: float, iters: int) ->
         n_pa += 1
     nel = n ** 3
     J = (n + 1) ** 3
-    per_it = nel * t_el / n_el + J * t_pa / n_pa
+    ndof = (n * p + 1) ** 3
+    # the coarse-space correction (P_0^T r, the vertex-grid solve, P_0 e) on a Q_p mesh
+    # of 4^3 elements, and two inner products plus three vector updates of 2^22
+    # entries, each scaled to the workload by its unknowns (both are linear in them,
+    # Section 3.6 Table 1)
+    vc, kc = make_mesh(3, 4, seed=seed, perturb=0.15)
+    Bc = olor.LORPreconditioner(Mesh(vc, kc), p, patch_subset=[], coarse=True)
+    rc0 = rng.standard_normal(Bc.P0.shape[0])
+    ts = time.perf_counter()
+    for _ in range(3):
+        ec = np.zeros(Bc.P0.shape[1])
+        ec[Bc.vmask] = Bc.coarse_solve((Bc.P0.T @ rc0)[Bc.vmask])
+        Bc.P0 @ ec
+    t_co = (time.perf_counter() - ts) / 3 * ndof / Bc.P0.shape[0]
+    mv = 1 << 22
+    xv, yv = rng.standard_normal(mv), rng.standard_normal(mv)
+    ts = time.perf_counter()
+    for _ in range(3):
+        xv @ yv
+        xv @ yv
+        for _ in range(3):
+            yv += 0.5 * xv
+    t_vec = (time.perf_counter() - ts) / 3 * ndof / mv
+    per_it = nel * t_el / n_el + J * t_pa / n_pa + t_co + t_vec
     solve_s = iters * per_it
     return {"solve_s": solve_s, "wall_s": time.perf_counter() - t_start, "sample": f"{n_el} element applies (Q{p}, dense element matrix) and {n_pa} "
-            f"interior patch V-cycles timed, extrapolated to {nel} elements + {J} patches per iteration "
-            f"x {iters} iterations", "cores": 1}
+            f"interior patch V-cycles timed, extrapolated to {nel} elements + {J} patches per iteration; "
+            f"the coarse-space correction (timed on Q{p} 4^3) and 2 inner products + 3 vector updates "
+            f"(timed at 2^22 entries) scaled to {ndof} unknowns; x {iters} iterations", "cores": 1}
 
 
 def run_cpu_leg(p, n, seed, budget_s, iters):

@@ -36,28 +36,6 @@ def test_reference_arm_other_ranks_print_nothing():
     assert not [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
 
 
-def test_ncu_launch_list_summary(tmp_path):
-    """bench.py --summarize-ncu: launches, total time and share per kernel from an ncu
-    --csv launch list (units converted to ms, template and argument lists trimmed)."""
-    csv = tmp_path / "launches.csv"
-    csv.write_text(
-        '==PROF== Connected to process\n'
-        '"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
-        '"0","void k_patch_warp<3, float, __nv_bfloat16, 2>(PatchArgs)","gpu__time_duration.sum","msecond","3.000"\n'
-        '"1","k_dot<float, float>(const float*, int)","gpu__time_duration.sum","usecond","500"\n'
-        '"2","void k_patch_warp<3, float, __nv_bfloat16, 2>(PatchArgs)","gpu__time_duration.sum","nsecond","1,000,000"\n'
-        '"3","k_dot<float, float>(const float*, int)","dram__bytes_read.sum","byte","123"\n')
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--summarize-ncu", str(csv)],
-                       capture_output=True, text=True, timeout=120, cwd=ROOT)
-    assert r.returncode == 0, r.stderr[-2000:]
-    rows = {ln.split()[0]: ln.split() for ln in r.stdout.splitlines()[1:]}
-    patch = [v for k, v in rows.items() if k.startswith("k_patch_warp")][0]
-    assert patch[-3:] == ["2", "4.000", "88.89%"]
-    dot = rows["k_dot<float,"]
-    assert dot[-3:] == ["1", "0.500", "11.11%"]
-    assert rows["all"][-2:] == ["3", "4.500"]
-
-
 def test_all_cores_cpu_baseline_sums_concurrent_samples():
     """run_cpu_leg_all_cores: one single-threaded oracle sample per process, run together;
     the reported throughput is the sum of the per-process rates (replica semantics)."""
